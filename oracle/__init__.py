@@ -1,0 +1,331 @@
+"""FP64 CPU oracle for preconditioned CG on kernel matrices.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline import this package; the library itself never does.  It shares no
+code with the CUDA path.  The heavy loops live in ``kpcg_oracle.c`` (plain C,
+FP64, OpenMP over rows); this module loads it with ctypes and assembles the
+gradient of the log marginal likelihood (Eq. 2 with the stochastic trace of
+Sec. 2.1) from its products.
+
+Every function cites the passage of the paper it restates.  Parameters are
+taken in log space: ``log_theta = [log l_1..log l_d, log s^2]`` (ARD) or
+``[log l, log s^2]`` (isotropic), noise sigma^2 separate.  Gradients are
+d log p / d(log l_r), d/d(log s^2), d/d(log sigma^2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kpcg_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def build(force: bool = False) -> str:
+    """Compile ``kpcg_oracle.c`` into ``_liboracle.so`` (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.or_num_threads.restype = _int
+            lib.or_gram.argtypes = [_d, _i64, _d, _i64, _int, _d, ctypes.c_double, _d]
+            lib.or_kyv.argtypes = [_d, _i64, _int, _d, ctypes.c_double, ctypes.c_double,
+                                   _d, _i64, _int, _d, _i64]
+            lib.or_dkv.argtypes = [_d, _i64, _int, _d, ctypes.c_double, _d, _i64, _int, _d]
+            lib.or_chol.argtypes = [_d, _i64]
+            lib.or_chol.restype = _int
+            lib.or_chol_solve.argtypes = [_d, _i64, _d, _i64, _int]
+            lib.or_nys_setup.argtypes = [_d, _i64, _int, _d, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int64), _i64, _d, _d, _d]
+            lib.or_nys_setup.restype = _int
+            lib.or_nys_apply.argtypes = [_i64, _i64, ctypes.c_double, _d, _d, _d, _i64, _int,
+                                         _d, _i64]
+            lib.or_bj_setup.argtypes = [_d, _i64, _int, _d, ctypes.c_double, ctypes.c_double,
+                                        _i64, _d]
+            lib.or_bj_setup.restype = _int
+            lib.or_bj_apply.argtypes = [_i64, _i64, _d, _d, _i64, _int, _d, _i64]
+            lib.or_pcg.argtypes = [_d, _i64, _int, _d, ctypes.c_double, ctypes.c_double, _int,
+                                   _d, _d, _i64, _d, _i64, _d, _i64, _int, ctypes.c_double, _int,
+                                   _int, _d, _d, _i64, ctypes.POINTER(ctypes.c_int), _d]
+            lib.or_pcg.restype = _int
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_d)
+
+
+def _f64c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f64f(a) -> np.ndarray:
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return np.asfortranarray(a)
+
+
+def split_theta(log_theta, d: int, ard: bool):
+    """(lengthscales[d], s2) from log parameters (Eq. 1)."""
+    lt = np.asarray(log_theta, dtype=np.float64)
+    ell = np.exp(lt[:-1]) if ard else np.full(d, np.exp(lt[0]))
+    if ard and ell.shape[0] != d:
+        raise ValueError("ARD log_theta needs d lengthscales")
+    return np.ascontiguousarray(ell), float(np.exp(lt[-1]))
+
+
+# ---------------------------------------------------------------------------
+# Kernel entries and products (Eq. 1; Sec. 2.1)
+# ---------------------------------------------------------------------------
+def gram(X, Z, ell, s2) -> np.ndarray:
+    """K(X, Z) with entries s2 * exp(-1/2 sum_r (x_r - z_r)^2 / l_r^2)  (Eq. 1)."""
+    X = _f64c(X)
+    Z = _f64c(Z)
+    n, d = X.shape
+    m = Z.shape[0]
+    G = np.empty((n, m), dtype=np.float64)
+    _load().or_gram(_p(X), n, _p(Z), m, d, _p(_f64c(ell)), float(s2), _p(G))
+    return G
+
+
+def kyv(X, ell, s2, noise, V) -> np.ndarray:
+    """(K + noise I) V, matrix-free, entries recomputed from X (Sec. 2.1)."""
+    X = _f64c(X)
+    n, d = X.shape
+    Vf = _f64f(V)
+    c = Vf.shape[1]
+    O = np.zeros((n, c), dtype=np.float64, order="F")
+    if n and c:
+        _load().or_kyv(_p(X), n, d, _p(_f64c(ell)), float(s2), float(noise), _p(Vf), n, c,
+                       _p(O), n)
+    return O[:, 0] if np.ndim(V) == 1 else O
+
+
+def dkv(X, ell, s2, W) -> np.ndarray:
+    """[dK/dlog l_1 W, ..., dK/dlog l_d W, dK/dlog s2 W] as a (d+1, n, c) array.
+
+    dK_ij/dlog l_r = K_ij (x_ir - x_jr)^2 / l_r^2 and dK/dlog s2 = K, the
+    derivatives of Eq. 1 that enter Eq. 2.
+    """
+    X = _f64c(X)
+    n, d = X.shape
+    Wf = _f64f(W)
+    c = Wf.shape[1]
+    G = np.zeros((d + 1) * n * c, dtype=np.float64)
+    if n and c:
+        _load().or_dkv(_p(X), n, d, _p(_f64c(ell)), float(s2), _p(Wf), n, c, _p(G))
+    return G.reshape(d + 1, c, n).transpose(0, 2, 1)
+
+
+def cholesky(A) -> np.ndarray:
+    """Textbook lower Cholesky factor; raises ValueError if A is not SPD."""
+    L = np.array(A, dtype=np.float64, order="C", copy=True)
+    n = L.shape[0]
+    st = _load().or_chol(_p(L), n)
+    if st:
+        raise ValueError(f"not positive definite at pivot {st - 1}")
+    return L
+
+
+def chol_solve(L, B) -> np.ndarray:
+    """Solve (L L^T) X = B by forward and back substitution."""
+    L = _f64c(L)
+    Bf = np.array(_f64f(B), order="F", copy=True)
+    n, c = Bf.shape
+    _load().or_chol_solve(_p(L), n, _p(Bf), n, c)
+    return Bf[:, 0] if np.ndim(B) == 1 else Bf
+
+
+def dense_ky(X, ell, s2, noise) -> np.ndarray:
+    K = gram(X, X, ell, s2)
+    K[np.diag_indices_from(K)] += noise
+    return K
+
+
+def dense_solve(X, ell, s2, noise, B) -> np.ndarray:
+    """alpha = K_y^{-1} B by Cholesky: the exact solution PCG converges to."""
+    return chol_solve(cholesky(dense_ky(X, ell, s2, noise)), B)
+
+
+def logml(X, ell, s2, noise, y) -> float:
+    """log p(y|theta,X) = -1/2 log|K_y| - 1/2 y^T K_y^{-1} y - n/2 log 2pi (Sec. 2.1)."""
+    L = cholesky(dense_ky(X, ell, s2, noise))
+    a = chol_solve(L, y)
+    n = L.shape[0]
+    return float(-np.sum(np.log(np.diag(L))) - 0.5 * np.dot(y, a) - 0.5 * n * np.log(2 * np.pi))
+
+
+# ---------------------------------------------------------------------------
+# Preconditioners (Sec. 3)
+# ---------------------------------------------------------------------------
+class Nystrom:
+    """P = K_XU K_UU^{-1} K_UX + noise I (Sec. 3.1), applied by the inversion lemma
+    P^{-1} = noise^{-1} [I - K_XU (noise K_UU + K_UX K_XU)^{-1} K_UX]."""
+
+    kind = 1
+
+    def __init__(self, X, ell, s2, noise, idx):
+        X = _f64c(X)
+        self.n, d = X.shape
+        self.idx = np.ascontiguousarray(idx, dtype=np.int64)
+        self.m = int(self.idx.shape[0])
+        self.noise = float(noise)
+        self.KXU = np.empty((self.n, self.m), dtype=np.float64)
+        self.LM = np.empty((self.m, self.m), dtype=np.float64)
+        jit = ctypes.c_double(0.0)
+        st = _load().or_nys_setup(_p(X), self.n, d, _p(_f64c(ell)), float(s2), self.noise,
+                                  self.idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  self.m, _p(self.KXU), _p(self.LM), ctypes.byref(jit))
+        if st:
+            raise ValueError("Nystrom inner matrix not positive definite after jitter")
+        self.jitter = jit.value
+
+    def apply(self, R) -> np.ndarray:
+        Rf = _f64f(R)
+        Z = np.zeros_like(Rf, order="F")
+        _load().or_nys_apply(self.n, self.m, self.noise, _p(self.KXU), _p(self.LM), _p(Rf),
+                             self.n, Rf.shape[1], _p(Z), self.n)
+        return Z[:, 0] if np.ndim(R) == 1 else Z
+
+
+class BlockJacobi:
+    """P = bldiag(K_y) over contiguous blocks of b rows (Sec. 3.3.1)."""
+
+    kind = 2
+
+    def __init__(self, X, ell, s2, noise, b):
+        X = _f64c(X)
+        self.n, d = X.shape
+        self.b = int(b)
+        nb = (self.n + self.b - 1) // self.b
+        self.L = np.zeros(nb * self.b * self.b, dtype=np.float64)
+        st = _load().or_bj_setup(_p(X), self.n, d, _p(_f64c(ell)), float(s2), float(noise),
+                                 self.b, _p(self.L))
+        if st:
+            raise ValueError(f"block of K_y not positive definite near row {st - 1}")
+
+    def apply(self, R) -> np.ndarray:
+        Rf = _f64f(R)
+        Z = np.zeros_like(Rf, order="F")
+        _load().or_bj_apply(self.n, self.b, _p(self.L), _p(Rf), self.n, Rf.shape[1], _p(Z),
+                            self.n)
+        return Z[:, 0] if np.ndim(R) == 1 else Z
+
+
+def pcg(X, ell, s2, noise, B, *, precond=None, tol=1e-8, tol_mode=0, max_iter=100000, X0=None):
+    """Algorithm 1 (textbook form) on each column of B.
+
+    Returns (Xsol, iters, relres, rc): iters per column (-1 = breakdown),
+    relres = recomputed ||b - K_y x|| / ||b||, rc 0 ok / 1 max_iter / 2 breakdown.
+    """
+    Xd = _f64c(X)
+    n, d = Xd.shape
+    Bf = _f64f(B)
+    c = Bf.shape[1]
+    out = np.zeros((n, c), dtype=np.float64, order="F")
+    iters = (ctypes.c_int * c)()
+    rel = np.zeros(c, dtype=np.float64)
+    X0f = _f64f(X0) if X0 is not None else None
+    kind = 0 if precond is None else precond.kind
+    KXU = precond.KXU if kind == 1 else None
+    LM = precond.LM if kind == 1 else None
+    Lbj = precond.L if kind == 2 else None
+    m = precond.m if kind == 1 else 0
+    b = precond.b if kind == 2 else 0
+    nul = ctypes.cast(None, _d)
+    rc = _load().or_pcg(_p(Xd), n, d, _p(_f64c(ell)), float(s2), float(noise), kind,
+                        _p(KXU) if KXU is not None else nul, _p(LM) if LM is not None else nul, m,
+                        _p(Lbj) if Lbj is not None else nul, b, _p(Bf), n, c, float(tol),
+                        int(tol_mode), int(max_iter), _p(X0f) if X0f is not None else nul,
+                        _p(out), n, iters, _p(rel))
+    it = np.array(list(iters), dtype=np.int64)
+    sol = out[:, 0] if np.ndim(B) == 1 else out
+    return sol, it, rel, int(rc)
+
+
+# ---------------------------------------------------------------------------
+# Gradient of the log marginal likelihood (Eq. 2) and its stochastic form
+# ---------------------------------------------------------------------------
+def _chain_iso(g_ard: np.ndarray, d: int, ard: bool) -> np.ndarray:
+    """Isotropic kernel: d/dlog l = sum_r d/dlog l_r (all l_r tied)."""
+    if ard:
+        return g_ard
+    return np.concatenate([[g_ard[:d].sum()], g_ard[d:]])
+
+
+def grad_exact(X, log_theta, noise, y, ard=True) -> np.ndarray:
+    """Eq. 2 with the exact trace: g_i = -1/2 tr(K_y^{-1} dK_y) + 1/2 a^T dK_y a.
+
+    Dense, O(n^3): small n only.  Returns [d/dlog l_r..., d/dlog s2, d/dlog noise].
+    """
+    Xd = _f64c(X)
+    n, d = Xd.shape
+    ell, s2 = split_theta(log_theta, d, ard)
+    L = cholesky(dense_ky(Xd, ell, s2, noise))
+    Kinv = chol_solve(L, np.eye(n))
+    a = chol_solve(L, y)
+    K = gram(Xd, Xd, ell, s2)
+    g = np.empty(d + 2)
+    for r in range(d):
+        diff2 = ((Xd[:, None, r] - Xd[None, :, r]) / ell[r]) ** 2
+        dK = K * diff2
+        g[r] = -0.5 * np.sum(Kinv * dK) + 0.5 * a @ dK @ a
+    g[d] = -0.5 * np.sum(Kinv * K) + 0.5 * a @ K @ a
+    g[d + 1] = -0.5 * noise * np.trace(Kinv) + 0.5 * noise * (a @ a)
+    return _chain_iso(g, d, ard)
+
+
+def grad_stochastic(X, log_theta, noise, y, probes, ard=True, solve=None) -> np.ndarray:
+    """Eq. 2 with the trace replaced by the Rademacher estimate of Sec. 2.1:
+
+    tr(K_y^{-1} dK_y) ~ (1/t) sum_k r_k^T K_y^{-1} dK_y r_k = (1/t) sum_k w_k^T (dK_y r_k),
+    w_k = K_y^{-1} r_k (K_y^{-1} is symmetric).  ``solve(B)`` returns K_y^{-1} B;
+    by default a dense Cholesky solve.
+    """
+    Xd = _f64c(X)
+    n, d = Xd.shape
+    ell, s2 = split_theta(log_theta, d, ard)
+    R = _f64f(probes)
+    t = R.shape[1]
+    Bblk = np.asfortranarray(np.column_stack([np.asarray(y, dtype=np.float64), R]))
+    if solve is None:
+        S = dense_solve(Xd, ell, s2, noise, Bblk)
+    else:
+        S = solve(Bblk)
+    a = S[:, 0]
+    Wt = S[:, 1:]
+    G = dkv(Xd, ell, s2, np.column_stack([a, R]))  # (d+1, n, 1+t)
+    g = np.empty(d + 2)
+    for q in range(d + 1):
+        quad = a @ G[q][:, 0]
+        tr = np.mean(np.sum(Wt * G[q][:, 1:], axis=0)) if t else 0.0
+        g[q] = -0.5 * tr + 0.5 * quad
+    trn = np.mean(np.sum(Wt * R, axis=0)) if t else 0.0
+    g[d + 1] = -0.5 * noise * trn + 0.5 * noise * (a @ a)
+    return _chain_iso(g, d, ard)

@@ -1,0 +1,323 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these tests retypes the oracle's formula and compares it with itself:
+each pin is a closed form, an invariant the paper states, a special case that
+reduces to a library routine (SciPy / LAPACK), a finite-difference check, or
+brute force on tiny inputs.  Each is chosen so that a plausible slip in the
+oracle (a dropped term, a sign, a wrong index) fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.spatial.distance import cdist
+
+import oracle
+import synthetic
+
+
+def _lib_gram(X, Z, ell, s2):
+    """RBF Gram matrix from SciPy's squared-Euclidean distance (Eq. 1)."""
+    Xs = np.asarray(X, np.float64) / ell
+    Zs = np.asarray(Z, np.float64) / ell
+    return s2 * np.exp(-0.5 * cdist(Xs, Zs, "sqeuclidean"))
+
+
+def _small(n=40, d=3, seed=0, ell=0.8, s2=1.3, noise=0.05):
+    g = synthetic.rng(seed)
+    X = g.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    ls = np.full(d, ell) * np.exp(0.2 * g.standard_normal(d))
+    y = g.standard_normal(n)
+    return X, ls, s2, noise, y
+
+
+# --------------------------------------------------------------------- Eq. 1
+def test_entry_closed_forms():
+    # d = 1: |x - x'| = 1, l = 1 -> exp(-1/2); l = 2 and |x - x'| = 2 -> exp(-1/2)
+    K = oracle.gram(np.array([[0.0]]), np.array([[1.0]]), np.array([1.0]), 1.0)
+    assert K[0, 0] == pytest.approx(math.exp(-0.5), rel=1e-15)
+    K = oracle.gram(np.array([[0.0]]), np.array([[2.0]]), np.array([2.0]), 3.0)
+    assert K[0, 0] == pytest.approx(3.0 * math.exp(-0.5), rel=1e-15)
+    # d = 2 with different lengthscales: exponent -1/2 (1/0.5^2 + 4/4) = -2.5
+    K = oracle.gram(np.array([[0.0, 0.0]]), np.array([[1.0, 2.0]]), np.array([0.5, 2.0]), 1.0)
+    assert K[0, 0] == pytest.approx(math.exp(-2.5), rel=1e-15)
+
+
+def test_entries_match_library_and_invariants():
+    X, ell, s2, _, _ = _small(n=30, d=4)
+    K = oracle.gram(X, X, ell, s2)
+    np.testing.assert_allclose(K, _lib_gram(X, X, ell, s2), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(np.diag(K), s2, rtol=1e-15)
+    np.testing.assert_array_equal(K, K.T)
+    assert np.all(K > 0) and np.all(K <= s2 * (1 + 1e-15))
+    # ARD with tied lengthscales equals the isotropic kernel
+    iso = np.full(4, 0.7)
+    np.testing.assert_allclose(oracle.gram(X, X, iso, s2), _lib_gram(X, X, 0.7, s2), rtol=1e-13)
+
+
+def test_matvec_matches_dense_product():
+    X, ell, s2, noise, _ = _small(n=57, d=5)
+    V = synthetic.rng(3).standard_normal((57, 3))
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(57)
+    np.testing.assert_allclose(oracle.kyv(X, ell, s2, noise, V), Ky @ V, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.kyv(X, ell, s2, noise, V[:, 0]), Ky @ V[:, 0], rtol=1e-12,
+                               atol=1e-12)
+
+
+# --------------------------------------------------------- Cholesky / solve
+def test_cholesky_and_solve_match_lapack():
+    X, ell, s2, noise, y = _small(n=80, d=3)
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(80)
+    L = oracle.cholesky(Ky)
+    np.testing.assert_allclose(L, np.linalg.cholesky(Ky), rtol=1e-10, atol=1e-12)
+    B = np.column_stack([y, synthetic.rng(5).standard_normal(80)])
+    np.testing.assert_allclose(oracle.chol_solve(L, B), sla.solve(Ky, B, assume_a="pos"),
+                               rtol=1e-8, atol=1e-10)
+    with pytest.raises(ValueError):
+        oracle.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+def test_logml_matches_library():
+    X, ell, s2, noise, y = _small(n=50, d=2)
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(50)
+    sign, ld = np.linalg.slogdet(Ky)
+    ref = -0.5 * ld - 0.5 * y @ np.linalg.solve(Ky, y) - 25 * np.log(2 * np.pi)
+    assert sign > 0
+    assert oracle.logml(X, ell, s2, noise, y) == pytest.approx(ref, rel=1e-11)
+
+
+# ------------------------------------------------------------- Algorithm 1
+def test_cg_converges_within_n_and_matches_solve():
+    # P = I, small well-conditioned system: exact arithmetic needs at most n
+    # steps; in FP64 the n-th iterate is already at rounding level.
+    g = synthetic.rng(11)
+    X = g.standard_normal((16, 2))
+    ell = np.full(2, 0.4)
+    y = g.standard_normal(16)
+    x, it, rel, rc = oracle.pcg(X, ell, 1.0, 0.1, y, tol=1e-8)
+    assert rc == 0 and 0 < it[0] <= 16 and rel[0] <= 1e-8
+    Ky = _lib_gram(X, X, ell, 1.0) + 0.1 * np.eye(16)
+    np.testing.assert_allclose(x, sla.solve(Ky, y, assume_a="pos"), rtol=1e-8, atol=1e-10)
+
+
+def _krylov_minimizer(A, Pinv, b, k):
+    """argmin over K_k(Pinv A, Pinv b) of the A-norm error: the k-th (P)CG iterate."""
+    v = Pinv @ b
+    Q = np.zeros((len(b), 0))
+    for _ in range(k):
+        for _ in range(2):  # Gram-Schmidt with re-orthogonalisation
+            v = v - Q @ (Q.T @ v)
+        Q = np.column_stack([Q, v / np.linalg.norm(v)])
+        v = Pinv @ (A @ Q[:, -1])
+    c = np.linalg.solve(Q.T @ A @ Q, Q.T @ b)
+    return Q @ c
+
+
+@pytest.mark.parametrize("precond", ["none", "nystrom", "bj"])
+def test_pcg_iterates_are_krylov_minimizers(precond):
+    # The k-th PCG iterate minimizes ||x - x*||_A over the preconditioned
+    # Krylov space; a wrong alpha, beta, sign or z/r mix-up breaks this.
+    X, ell, s2, noise, y = _small(n=48, d=3, noise=0.05)
+    A = _lib_gram(X, X, ell, s2) + noise * np.eye(48)
+    if precond == "nystrom":
+        P = oracle.Nystrom(X, ell, s2, noise, synthetic.inducing_subset(48, 6, 1))
+        Pinv = P.apply(np.eye(48))
+    elif precond == "bj":
+        P = oracle.BlockJacobi(X, ell, s2, noise, 10)
+        Pinv = P.apply(np.eye(48))
+    else:
+        P, Pinv = None, np.eye(48)
+    for k in range(1, 6):
+        xk, it, _, rc = oracle.pcg(X, ell, s2, noise, y, precond=P, tol=1e-15, max_iter=k)
+        assert it[0] == k and rc == 1
+        ref = _krylov_minimizer(A, Pinv, y, k)
+        np.testing.assert_allclose(xk, ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+
+
+def test_cg_terminates_by_distinct_eigenvalue_count():
+    # Three distinct points repeated: K has rank <= 3, so K_y has at most 4
+    # distinct eigenvalues and CG (exact arithmetic) stops within 4 steps.
+    # A wrong beta, sign or denominator in the recurrence breaks this.
+    base = np.array([[0.0, 0.0], [0.7, -0.2], [-0.4, 1.1]])
+    X = np.repeat(base, 20, axis=0)
+    y = synthetic.rng(2).standard_normal(60)
+    x, it, rel, rc = oracle.pcg(X, np.ones(2), 1.0, 0.3, y, tol=1e-11)
+    assert rc == 0 and it[0] <= 4, it
+    assert rel[0] <= 1e-11
+
+
+def test_pcg_paper_absolute_stop_rule():
+    X, ell, s2, noise, y = _small(n=60, d=3, noise=0.01)
+    # ||r||^2 < n * 1e-10, the rule of Sec. 4
+    x, it, rel, rc = oracle.pcg(X, ell, s2, noise, y, tol=1e-10, tol_mode=1)
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(60)
+    r = y - Ky @ x
+    assert rc == 0 and r @ r < 60 * 1e-10
+
+
+def test_pcg_zero_rhs_and_warm_start():
+    X, ell, s2, noise, y = _small(n=40, d=3)
+    B = np.column_stack([np.zeros(40), y])
+    x, it, rel, rc = oracle.pcg(X, ell, s2, noise, B, tol=1e-10)
+    assert it[0] == 0 and np.all(x[:, 0] == 0) and rel[0] == 0
+    # starting from the solution needs no iteration
+    x2, it2, _, _ = oracle.pcg(X, ell, s2, noise, y, tol=1e-8, X0=x[:, 1])
+    assert it2[0] == 0
+
+
+# ------------------------------------------------------- preconditioners
+def test_nystrom_with_all_points_is_exact_one_step():
+    # m = n: M = K (noise I + K), so P = K_y and PCG converges in one step.
+    g = synthetic.rng(7)
+    X = g.standard_normal((64, 8))
+    ell = np.ones(8)
+    y = g.standard_normal(64)
+    P = oracle.Nystrom(X, ell, 1.0, 0.1, np.arange(64))
+    x, it, rel, rc = oracle.pcg(X, ell, 1.0, 0.1, y, precond=P, tol=1e-10)
+    assert rc == 0 and it[0] == 1, it
+    assert rel[0] <= 1e-10
+
+
+def test_nystrom_inverse_against_dense_P():
+    X, ell, s2, noise, _ = _small(n=128, d=3, noise=0.02)
+    idx = synthetic.inducing_subset(128, 16, seed=4)
+    P = oracle.Nystrom(X, ell, s2, noise, idx)
+    KXU = _lib_gram(X, X[idx], ell, s2)
+    KUU = _lib_gram(X[idx], X[idx], ell, s2)
+    Pd = KXU @ np.linalg.solve(KUU, KXU.T) + noise * np.eye(128)
+    v = synthetic.rng(9).standard_normal((128, 2))
+    np.testing.assert_allclose(P.apply(Pd @ v), v, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(P.apply(v), np.linalg.solve(Pd, v), rtol=1e-8, atol=1e-8)
+
+
+def test_block_jacobi_inverse_and_full_block():
+    X, ell, s2, noise, y = _small(n=100, d=3)
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(100)
+    b = 32  # blocks 32, 32, 32, 4 (ragged tail)
+    Pd = np.zeros_like(Ky)
+    for r0 in range(0, 100, b):
+        sl = slice(r0, min(r0 + b, 100))
+        Pd[sl, sl] = Ky[sl, sl]
+    P = oracle.BlockJacobi(X, ell, s2, noise, b)
+    v = synthetic.rng(1).standard_normal((100, 2))
+    np.testing.assert_allclose(P.apply(v), np.linalg.solve(Pd, v), rtol=1e-9, atol=1e-9)
+    # one block covering everything is P = K_y: one step
+    Pfull = oracle.BlockJacobi(X, ell, s2, noise, 100)
+    x, it, rel, rc = oracle.pcg(X, ell, s2, noise, y, precond=Pfull, tol=1e-10)
+    assert rc == 0 and it[0] == 1
+
+
+def test_preconditioned_system_is_spd():
+    X, ell, s2, noise, _ = _small(n=96, d=3, noise=0.01)
+    Ky = _lib_gram(X, X, ell, s2) + noise * np.eye(96)
+    assert np.linalg.eigvalsh(Ky).min() >= noise * (1 - 1e-10)
+    I = np.eye(96)
+    for P in (oracle.Nystrom(X, ell, s2, noise, synthetic.inducing_subset(96, 10, 0)),
+              oracle.BlockJacobi(X, ell, s2, noise, 24)):
+        Pinv = P.apply(I)
+        np.testing.assert_allclose(Pinv, Pinv.T, atol=1e-8 * np.abs(Pinv).max())
+        ev = np.linalg.eigvals(Pinv @ Ky)
+        assert np.abs(ev.imag).max() < 1e-6 * np.abs(ev.real).max()
+        assert ev.real.min() > 0
+
+
+# -------------------------------------------- Eq. 2 and the stochastic trace
+def test_exact_gradient_matches_finite_differences():
+    X, ell, s2, noise, y = _small(n=45, d=3, noise=0.07)
+    lt = np.concatenate([np.log(ell), [np.log(s2)]])
+    g = oracle.grad_exact(X, lt, noise, y, ard=True)
+    h = 1e-5
+
+    def lp(theta, lnoise):
+        e, s = oracle.split_theta(theta, 3, True)
+        return oracle.logml(X, e, s, math.exp(lnoise), y)
+
+    fd = np.empty(5)
+    for q in range(4):
+        tp, tm = lt.copy(), lt.copy()
+        tp[q] += h
+        tm[q] -= h
+        fd[q] = (lp(tp, math.log(noise)) - lp(tm, math.log(noise))) / (2 * h)
+    fd[4] = (lp(lt, math.log(noise) + h) - lp(lt, math.log(noise) - h)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_isotropic_gradient_matches_finite_differences():
+    X, _, s2, noise, y = _small(n=30, d=2, noise=0.05)
+    lt = np.array([math.log(0.9), math.log(s2)])
+    g = oracle.grad_exact(X, lt, noise, y, ard=False)
+    h = 1e-5
+
+    def lp(theta):
+        e, s = oracle.split_theta(theta, 2, False)
+        return oracle.logml(X, e, s, noise, y)
+
+    fd = [(lp(lt + h * np.eye(2)[q]) - lp(lt - h * np.eye(2)[q])) / (2 * h) for q in range(2)]
+    np.testing.assert_allclose(g[:2], fd, rtol=1e-6, atol=1e-7)
+
+
+def test_dkv_matches_finite_differences_of_matvec():
+    X, ell, s2, _, _ = _small(n=33, d=3)
+    W = synthetic.rng(4).standard_normal((33, 2))
+    G = oracle.dkv(X, ell, s2, W)
+    h = 1e-6
+    for r in range(3):
+        ep, em = ell.copy(), ell.copy()
+        ep[r] *= math.exp(h)
+        em[r] *= math.exp(-h)
+        fd = (oracle.kyv(X, ep, s2, 0.0, W) - oracle.kyv(X, em, s2, 0.0, W)) / (2 * h)
+        np.testing.assert_allclose(G[r], fd, rtol=1e-7, atol=1e-9)
+    fd = (oracle.kyv(X, ell, s2 * math.exp(h), 0.0, W)
+          - oracle.kyv(X, ell, s2 * math.exp(-h), 0.0, W)) / (2 * h)
+    np.testing.assert_allclose(G[3], fd, rtol=1e-7, atol=1e-9)
+
+
+def test_hutchinson_over_all_sign_vectors_equals_exact_gradient():
+    # E[r r^T] = I over Rademacher r: averaging over all 2^n sign vectors is
+    # exactly the trace, so the stochastic gradient equals Eq. 2.
+    n = 10
+    X, ell, s2, noise, y = _small(n=n, d=2, noise=0.2)
+    lt = np.concatenate([np.log(ell), [np.log(s2)]])
+    R = np.array(list(itertools.product([-1.0, 1.0], repeat=n))).T
+    gs = oracle.grad_stochastic(X, lt, noise, y, R, ard=True)
+    ge = oracle.grad_exact(X, lt, noise, y, ard=True)
+    np.testing.assert_allclose(gs, ge, rtol=1e-10, atol=1e-12)
+
+
+def test_hutchinson_variance_closed_form():
+    # Var(r^T A r) = sum_{i != j} A_ij (A_ij + A_ji) for Rademacher r.
+    n = 8
+    A = synthetic.rng(6).standard_normal((n, n))
+    R = np.array(list(itertools.product([-1.0, 1.0], repeat=n)))
+    q = np.einsum("ki,ij,kj->k", R, A, R)
+    assert q.mean() == pytest.approx(np.trace(A), abs=1e-12)
+    off = A * (A + A.T)
+    np.fill_diagonal(off, 0.0)
+    assert q.var() == pytest.approx(off.sum(), rel=1e-12)
+
+
+def test_stochastic_gradient_with_pcg_solves_matches_dense():
+    X, ell, s2, noise, y = _small(n=70, d=3, noise=0.03)
+    lt = np.concatenate([np.log(ell), [np.log(s2)]])
+    R = synthetic.rademacher(70, 5, seed=1)
+    P = oracle.Nystrom(X, ell, s2, noise, synthetic.inducing_subset(70, 9, 2))
+
+    def solve(B):
+        return oracle.pcg(X, ell, s2, noise, B, precond=P, tol=1e-13)[0]
+
+    np.testing.assert_allclose(oracle.grad_stochastic(X, lt, noise, y, R, solve=solve),
+                               oracle.grad_stochastic(X, lt, noise, y, R), rtol=1e-8, atol=1e-9)
+
+
+def test_synthetic_inputs_are_seeded():
+    a = synthetic.config1(seed=0, n=256)
+    b = synthetic.config1(seed=0, n=256)
+    assert a.X.dtype == np.float32 and a.X.flags.c_contiguous
+    np.testing.assert_array_equal(a.X, b.X)
+    np.testing.assert_array_equal(a.y, b.y)
+    R = synthetic.rademacher(100, 4, 3)
+    assert set(np.unique(R)) == {-1.0, 1.0} and R.flags.f_contiguous
+    idx = synthetic.inducing_subset(100, 10, 0)
+    assert np.all(np.diff(idx) > 0) and idx.max() < 100
