@@ -1,0 +1,181 @@
+/*
+ * kpcg.h -- C ABI of the GB300 library for preconditioned conjugate gradients
+ * on kernel matrices, after Cutajar, Osborne, Cunningham and Filippone,
+ * "Preconditioning Kernel Matrices" (ICML 2016).
+ *
+ * The library solves (K(X,X|theta) + sigma^2 I) alpha = B for a block of
+ * right-hand sides (Sec. 2.1, Algorithm 1) with the RBF/ARD kernel of Eq. 1,
+ * preconditioned by the Nystrom (Sec. 3.1) or block-Jacobi (Sec. 3.3.1)
+ * approximation, and estimates the gradient of the log marginal likelihood
+ * (Eq. 2) with Rademacher probes (Sec. 2.1).  K is never stored: its entries
+ * are rebuilt from X inside every product.
+ *
+ * Notation: amplitude s^2 (the paper's sigma^2 in Eq. 1), noise sigma^2 (the
+ * paper's lambda), lengthscales l_r.  Parameters are passed in log space:
+ *   ARD:       log_theta = [log l_1, ..., log l_d, log s^2]   (d+1 values)
+ *   isotropic: log_theta = [log l, log s^2]                    (2 values)
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a kpcg_status; KPCG_OK is 0.  On error the
+ *     message is available from kpcg_last_error(h) until the next call on h.
+ *   - Pointers are DEVICE pointers unless the argument says "host".
+ *   - Block vectors are column-major: column k of B starts at B + k*ldb,
+ *     ldb >= n.  Device pointers of doubles must be 8-byte aligned.
+ *   - The caller owns every buffer it passes; the library copies X at
+ *     kpcg_create and owns its own workspaces, released by kpcg_destroy.
+ *   - A handle is bound to the CUDA device current at kpcg_create and to the
+ *     stream given there; all work is enqueued on that stream and every call
+ *     returns after the stream has finished the call's work.  Handles are not
+ *     thread-safe; distinct handles may be used from distinct threads.
+ *   - No call falls back to the CPU: a missing or failing GPU is an error.
+ */
+#ifndef KPCG_H
+#define KPCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kpcg_ctx* kpcg_t;
+
+typedef enum {
+    KPCG_OK = 0,
+    KPCG_ERR_ARG = 1,            /* invalid argument (sizes, NULL, alignment)   */
+    KPCG_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+    KPCG_ERR_OOM = 3,            /* device allocation failed                    */
+    KPCG_ERR_NOT_SPD = 4,        /* a factorization met a non-positive pivot    */
+    KPCG_ERR_BREAKDOWN = 5,      /* p^T K_y p <= 0 or NaN inside CG             */
+    KPCG_ERR_NO_CONVERGENCE = 6, /* tolerance not met within the limits         */
+    KPCG_ERR_TIMEOUT = 7,        /* a bounded device wait expired               */
+    KPCG_ERR_STATE = 8           /* call out of order (e.g. no preconditioner)  */
+} kpcg_status;
+
+typedef enum {
+    KPCG_PREC_NONE = 0,          /* P = I: plain CG                              */
+    KPCG_PREC_NYSTROM = 1,       /* P = K_XU K_UU^-1 K_UX + sigma^2 I (Sec. 3.1)  */
+    KPCG_PREC_BLOCK_JACOBI = 2   /* P = bldiag(K_y) (Sec. 3.3.1)                  */
+} kpcg_precond_kind;
+
+typedef enum {
+    KPCG_FP64 = 0,     /* FP64 entries, vectors and scalars throughout           */
+    KPCG_FP32 = 1,     /* plain FP32 PCG: FP32 entries (direct differences),
+                          FP32 vectors; no refinement                            */
+    KPCG_FP32_IR = 2,  /* inner FP32 PCG refined by FP64 outer residuals         */
+    KPCG_TF32_IR = 3   /* inner PCG on the tensor-core K.V (tcgen05, TF32 split
+                          distances, FP32 accumulate) refined by FP64 residuals  */
+} kpcg_precision;
+
+typedef struct {
+    int32_t max_iter;     /* CG iterations per solve (all inner ones in IR
+                             modes); default 100000 (the paper's cap, Sec. 4)  */
+    int32_t precision;    /* kpcg_precision; default KPCG_TF32_IR              */
+    int32_t tol_mode;     /* 0: ||b - K_y x|| <= tol ||b|| per column (default);
+                             1: the paper's absolute ||r||^2 < n*tol (Sec. 4)  */
+    int32_t max_outer;    /* refinement steps in IR modes; default 40          */
+    double inner_tol;     /* relative reduction asked of each inner solve in
+                             IR modes; default 1e-4                            */
+    int32_t check_every;  /* host polls convergence every k iterations; def. 4 */
+    int32_t max_restarts; /* residual-replacement restarts in non-IR modes;
+                             default 5                                         */
+} kpcg_options;
+
+typedef struct {
+    int32_t iters_total;  /* CG iterations run (sum over inner solves)          */
+    int32_t outer_steps;  /* FP64 residual evaluations (IR modes), else restarts */
+    double max_rel_res;   /* max over columns of ||b - K_y x|| / ||b||,
+                             recomputed in FP64 on the device at return        */
+    double time_ms;       /* wall time of the call on the host                  */
+    double setup_ms;      /* part of time_ms spent in preconditioner set-up     */
+} kpcg_info;
+
+/* Fill *opt with the defaults documented in kpcg_options. */
+void kpcg_default_options(kpcg_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* kpcg_status_string(kpcg_status s);
+
+/* Create a handle for the n x d inputs X (device, float32, row-major,
+ * borrowed for the duration of the call and copied).  log_theta (host) holds
+ * d+1 (ard != 0) or 2 (ard == 0) log parameters as described above;
+ * noise_var is sigma^2 > 0.  opt may be NULL (defaults).  stream is a
+ * cudaStream_t (NULL = the legacy default stream).  Supports 1 <= d <= 32.
+ * Eq. 1 defines the kernel; Sec. 2.1 defines K_y = K + sigma^2 I. */
+kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_theta,
+                        int32_t ard, double noise_var, const kpcg_options* opt,
+                        void* stream, kpcg_t* out);
+
+/* Replace the hyperparameters (host log_theta, same length as at create).
+ * Drops the preconditioner, which must be rebuilt with kpcg_precond. */
+kpcg_status kpcg_set_theta(kpcg_t h, const double* log_theta, double noise_var);
+
+/* Replace the options (host struct). */
+kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt);
+
+/* Build the preconditioner for the current theta.
+ *   KPCG_PREC_NYSTROM: size = m, idx (host, m distinct sorted row indices of X)
+ *     names the inducing points U (Sec. 3.1; the paper draws them at random
+ *     from X, Sec. 5).  P^-1 = sigma^-2 [I - K_XU (sigma^2 K_UU + K_UX K_XU)^-1
+ *     K_UX], the inversion lemma applied to P (the printed form drops the
+ *     sigma^2 on K_UU).  If the inner matrix is not positive definite, jitter
+ *     1e-12*tr/m*10^k (k = 0..6) is added to its diagonal.
+ *   KPCG_PREC_BLOCK_JACOBI: size = b, idx ignored; contiguous blocks of b rows,
+ *     the last one shorter, P = bldiag(K_y) (Sec. 3.3.1).
+ *   KPCG_PREC_NONE: removes the preconditioner.
+ * Returns KPCG_ERR_NOT_SPD if a factorization fails. */
+kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx);
+
+/* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
+ * matrix-free product of Sec. 2.1, entries built in FP64 from X. */
+kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
+                            int64_t ldo);
+
+/* O = (K + sigma^2 I) V in reduced precision (device float32).
+ * impl 0: FP32 entries by direct differences on the CUDA cores;
+ * impl 1: tensor-core distances (tcgen05, TF32 hi/lo split), FP32 exp and
+ *         accumulation -- the kernel KPCG_TF32_IR iterates with. */
+kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
+                            int64_t ldo, int32_t impl);
+
+/* Z = P^{-1} R with the current preconditioner (device float64). */
+kpcg_status kpcg_precond_apply_f64(kpcg_t h, const double* R, int64_t ldr, int32_t c, double* Z,
+                                   int64_t ldz);
+
+/* Solve (K + sigma^2 I) Xout = B for c columns (device float64), Algorithm 1
+ * with the textbook recurrence, each column with its own scalars.  X0 is the
+ * initial guess (device, ldx) or NULL for zero.  tol follows opt.tol_mode.
+ * iters (host, nullable, c entries) receives per-column CG iterations.
+ * Xout holds the best iterate also on KPCG_ERR_NO_CONVERGENCE.  A zero
+ * column of B yields a zero solution in 0 iterations. */
+kpcg_status kpcg_solve(kpcg_t h, const double* B, int64_t ldb, int32_t c, double tol,
+                       const double* X0, double* Xout, int64_t ldx, int32_t* iters,
+                       kpcg_info* info);
+
+/* G_q = dK/dtheta_q W for q = log l_1..log l_d (ARD) or log l (isotropic),
+ * then log s^2: the derivative products of Eq. 2 (device float64).  G holds
+ * n_theta = (ard ? d : 1) + 1 blocks of n x c, block q at G + q*ldg*c,
+ * column k at + k*ldg.  The noise derivative sigma^2 W is left to the caller. */
+kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* G, int64_t ldg);
+
+/* Stochastic gradient of log p(y|theta) (Eq. 2, trace by Rademacher probes as
+ * in Sec. 2.1):  g_q = -1/2 (1/t) sum_k w_k^T dK_q r_k + 1/2 a^T dK_q a, with
+ * [a, w_1..w_t] = K_y^{-1} [y, r_1..r_t] solved as one block to tol.
+ * y (device, n doubles), probes (device, n x t column-major, ld = n, entries
+ * +-1, t >= 1).  grad (host) receives n_theta + 1 values:
+ * d/dlog l_r (or d/dlog l), d/dlog s^2, d/dlog sigma^2.  alpha (device,
+ * nullable) receives a = K_y^{-1} y. */
+kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
+                      double* grad, double* alpha, kpcg_info* info);
+
+/* Release the handle and every device buffer it owns.  NULL is ignored. */
+void kpcg_destroy(kpcg_t h);
+
+/* Message of the last failing call on h (or of the last failed create when
+ * h is NULL).  Valid until the next call on h. */
+const char* kpcg_last_error(kpcg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPCG_H */

@@ -1,0 +1,25 @@
+"""kpcg: preconditioned conjugate gradients on kernel matrices for GB300.
+
+A thin ctypes binding over ``libkpcg.so`` (the C ABI in ``include/kpcg.h``).
+It only marshals arguments: every step of the solve runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback: if the library or a GPU is missing, the binding raises.
+"""
+from .binding import (  # noqa: F401
+    KPCG_FP32,
+    KPCG_FP32_IR,
+    KPCG_FP64,
+    KPCG_PREC_BLOCK_JACOBI,
+    KPCG_PREC_NONE,
+    KPCG_PREC_NYSTROM,
+    KPCG_TF32_IR,
+    KpcgError,
+    Options,
+    Solver,
+    Info,
+    default_options,
+    exported_symbols,
+    fortran_empty,
+    lib,
+    library_path,
+)

@@ -1,0 +1,303 @@
+"""ctypes binding of the kpcg C ABI (``include/kpcg.h``), same names and arguments.
+
+``lib()`` loads ``libkpcg.so`` (built in-tree by ``build.py``) and raises if
+it is missing.  ``Solver`` wraps one handle and takes torch CUDA tensors,
+passing their device pointers and the current CUDA stream to the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libkpcg.so")
+
+KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI = 0, 1, 2
+KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TF32_IR = 0, 1, 2, 3
+
+_STATUS = {
+    0: "KPCG_OK", 1: "KPCG_ERR_ARG", 2: "KPCG_ERR_CUDA", 3: "KPCG_ERR_OOM",
+    4: "KPCG_ERR_NOT_SPD", 5: "KPCG_ERR_BREAKDOWN", 6: "KPCG_ERR_NO_CONVERGENCE",
+    7: "KPCG_ERR_TIMEOUT", 8: "KPCG_ERR_STATE",
+}
+
+SYMBOLS = (
+    "kpcg_default_options", "kpcg_status_string", "kpcg_create", "kpcg_set_theta",
+    "kpcg_set_options", "kpcg_precond", "kpcg_matvec_f64", "kpcg_matvec_f32",
+    "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
+    "kpcg_last_error",
+)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("max_iter", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("tol_mode", ctypes.c_int32),
+        ("max_outer", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double),
+        ("check_every", ctypes.c_int32),
+        ("max_restarts", ctypes.c_int32),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("iters_total", ctypes.c_int32),
+        ("outer_steps", ctypes.c_int32),
+        ("max_rel_res", ctypes.c_double),
+        ("time_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KpcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libkpcg.so; raise if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build it with `python -m paper_1602_06693_gb300.build` "
+                "(the library has no CPU fallback)")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        pdbl = ctypes.POINTER(ctypes.c_double)
+        L.kpcg_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.kpcg_default_options.restype = None
+        L.kpcg_status_string.argtypes = [ctypes.c_int]
+        L.kpcg_status_string.restype = ctypes.c_char_p
+        L.kpcg_create.argtypes = [vp, i64, i32, pdbl, i32, dbl, ctypes.POINTER(Options), vp,
+                                  ctypes.POINTER(vp)]
+        L.kpcg_set_theta.argtypes = [vp, pdbl, dbl]
+        L.kpcg_set_options.argtypes = [vp, ctypes.POINTER(Options)]
+        L.kpcg_precond.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.kpcg_matvec_f64.argtypes = [vp, vp, i64, i32, vp, i64]
+        L.kpcg_matvec_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32]
+        L.kpcg_precond_apply_f64.argtypes = [vp, vp, i64, i32, vp, i64]
+        L.kpcg_solve.argtypes = [vp, vp, i64, i32, dbl, vp, vp, i64,
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
+        L.kpcg_dkv.argtypes = [vp, vp, i64, i32, vp, i64]
+        L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, pdbl, vp, ctypes.POINTER(Info)]
+        L.kpcg_destroy.argtypes = [vp]
+        L.kpcg_destroy.restype = None
+        L.kpcg_last_error.argtypes = [vp]
+        L.kpcg_last_error.restype = ctypes.c_char_p
+        for name in SYMBOLS[2:]:
+            if name not in ("kpcg_destroy", "kpcg_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def exported_symbols():
+    """Names from include/kpcg.h that the loaded library exports."""
+    L = lib()
+    return [s for s in SYMBOLS if hasattr(L, s)]
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().kpcg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dptr(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _colmajor(t, name):
+    """(ptr-able tensor, ld, c) for a 1-D or column-major 2-D tensor."""
+    if t.dim() == 1:
+        return t, t.shape[0], 1
+    if t.dim() == 2 and t.stride(0) == 1:
+        return t, t.stride(1) if t.shape[1] > 1 else t.shape[0], t.shape[1]
+    raise ValueError(f"{name} must be 1-D or column-major 2-D (use .t().contiguous().t())")
+
+
+def fortran_empty(n, c, dtype, device):
+    """n x c column-major CUDA tensor."""
+    torch = _torch()
+    return torch.empty((c, n), dtype=dtype, device=device).t()
+
+
+class Solver:
+    """One kpcg handle (kpcg_create ... kpcg_destroy) bound to the current stream."""
+
+    def __init__(self, X, log_theta, noise, ard=True, options: Options | None = None,
+                 stream=None):
+        torch = _torch()
+        L = lib()
+        if X.dtype != torch.float32 or not X.is_cuda or not X.is_contiguous():
+            raise TypeError("X must be a contiguous float32 CUDA tensor (n x d row-major)")
+        self.n, self.d = int(X.shape[0]), int(X.shape[1])
+        self.ard = bool(ard)
+        self.device = X.device
+        lt = np.ascontiguousarray(log_theta, dtype=np.float64)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        opt = options if options is not None else default_options()
+        self.options = opt
+        st = L.kpcg_create(ctypes.c_void_p(X.data_ptr()), self.n, self.d,
+                           lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(self.ard),
+                           float(noise), ctypes.byref(opt),
+                           ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise KpcgError(st, L.kpcg_last_error(None).decode())
+        self._h = h
+
+    # -- plumbing
+    def _check(self, st):
+        if st != 0:
+            raise KpcgError(st, lib().kpcg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kpcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def n_theta(self):
+        return (self.d if self.ard else 1) + 1
+
+    # -- API
+    def set_theta(self, log_theta, noise):
+        lt = np.ascontiguousarray(log_theta, dtype=np.float64)
+        self._check(lib().kpcg_set_theta(self._h, lt.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_double)), float(noise)))
+
+    def set_options(self, options: Options):
+        self.options = options
+        self._check(lib().kpcg_set_options(self._h, ctypes.byref(options)))
+
+    def precond(self, kind, size=0, idx=None):
+        p = None
+        if idx is not None:
+            idx = np.ascontiguousarray(idx, dtype=np.int64)
+            p = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        self._check(lib().kpcg_precond(self._h, int(kind), int(size), p))
+
+    def matvec_f64(self, V, out=None):
+        torch = _torch()
+        V, ldv, c = _colmajor(V, "V")
+        O = out if out is not None else (torch.empty_like(V) if V.dim() == 1 else
+                                         fortran_empty(self.n, c, torch.float64, V.device))
+        O_, ldo, _ = _colmajor(O, "out")
+        self._check(lib().kpcg_matvec_f64(self._h, _dptr(V, torch.float64, "V"), ldv, c,
+                                          _dptr(O_, torch.float64, "out"), ldo))
+        return O
+
+    def matvec_f32(self, V, impl=0, out=None):
+        torch = _torch()
+        V, ldv, c = _colmajor(V, "V")
+        O = out if out is not None else (torch.empty_like(V) if V.dim() == 1 else
+                                         fortran_empty(self.n, c, torch.float32, V.device))
+        O_, ldo, _ = _colmajor(O, "out")
+        self._check(lib().kpcg_matvec_f32(self._h, _dptr(V, torch.float32, "V"), ldv, c,
+                                          _dptr(O_, torch.float32, "out"), ldo, int(impl)))
+        return O
+
+    def precond_apply(self, R):
+        torch = _torch()
+        R, ldr, c = _colmajor(R, "R")
+        Z = torch.empty_like(R) if R.dim() == 1 else fortran_empty(self.n, c, torch.float64,
+                                                                  R.device)
+        Z_, ldz, _ = _colmajor(Z, "Z")
+        self._check(lib().kpcg_precond_apply_f64(self._h, _dptr(R, torch.float64, "R"), ldr, c,
+                                                 _dptr(Z_, torch.float64, "Z"), ldz))
+        return Z
+
+    def solve(self, B, tol=1e-8, X0=None, raise_on_error=True):
+        """Solve K_y X = B; returns (X, iters per column, Info, status)."""
+        torch = _torch()
+        B, ldb, c = _colmajor(B, "B")
+        X = torch.empty_like(B) if B.dim() == 1 else fortran_empty(self.n, c, torch.float64,
+                                                                  B.device)
+        X_, ldx, _ = _colmajor(X, "X")
+        x0p = None
+        if X0 is not None:
+            X0_, ldx0, _ = _colmajor(X0, "X0")
+            if ldx0 != ldx:
+                X0_ = X0_.clone() if X0_.dim() == 1 else X0_.t().contiguous().t()
+            x0p = _dptr(X0_, torch.float64, "X0")
+        iters = (ctypes.c_int32 * c)()
+        info = Info()
+        st = lib().kpcg_solve(self._h, _dptr(B, torch.float64, "B"), ldb, c, float(tol), x0p,
+                              _dptr(X_, torch.float64, "X"), ldx, iters, ctypes.byref(info))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return X, np.array(list(iters), dtype=np.int64), info, st
+
+    def dkv(self, W):
+        torch = _torch()
+        W, ldw, c = _colmajor(W, "W")
+        G = torch.empty((self.n_theta, c, self.n), dtype=torch.float64, device=W.device)
+        self._check(lib().kpcg_dkv(self._h, _dptr(W, torch.float64, "W"), ldw, c,
+                                   ctypes.c_void_p(G.data_ptr()), self.n))
+        return G.transpose(1, 2)  # (n_theta, n, c)
+
+    def grad(self, y, probes, tol=1e-8, want_alpha=False):
+        """Stochastic gradient of log p (Eq. 2): returns (grad[n_theta+1], alpha|None, Info)."""
+        torch = _torch()
+        if y.dim() != 1 or not y.is_contiguous():
+            raise ValueError("y must be a contiguous 1-D tensor")
+        P, ldp, t = _colmajor(probes, "probes")
+        if ldp != self.n:
+            raise ValueError("probes must have leading dimension n")
+        g = np.zeros(self.n_theta + 1, dtype=np.float64)
+        alpha = torch.empty(self.n, dtype=torch.float64, device=y.device) if want_alpha else None
+        info = Info()
+        self._check(lib().kpcg_grad(self._h, _dptr(y, torch.float64, "y"),
+                                    _dptr(P, torch.float64, "probes"), t, float(tol),
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    _dptr(alpha, torch.float64, "alpha") if want_alpha else None,
+                                    ctypes.byref(info)))
+        return g, alpha, info

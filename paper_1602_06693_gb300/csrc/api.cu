@@ -1,0 +1,730 @@
+// C ABI of libkpcg: handle life cycle, the batched PCG driver (Algorithm 1),
+// mixed-precision refinement, and the stochastic gradient of Eq. 2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kpcg_internal.cuh"
+#include "ctx.cuh"
+#include "precond.cuh"
+
+namespace kpcg {
+
+[[noreturn]] void fail(kpcg_status s, const std::string& msg) { throw Error{s, msg}; }
+
+void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
+    if (e == cudaSuccess) return;
+    const char* f = strrchr(file, '/');
+    fail(e == cudaErrorMemoryAllocation ? KPCG_ERR_OOM : KPCG_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e) + " (" + (f ? f + 1 : file) + ":" +
+             std::to_string(line) + ")");
+}
+
+int padded_dim(int d) {
+    if (d <= 4) return 4;
+    if (d <= 8) return 8;
+    if (d <= 12) return 12;
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    return -1;
+}
+
+namespace {
+
+// Column means of X (FP64), one CTA per feature.
+__global__ void colmean_kernel(const float* __restrict__ X, int64_t n, int d,
+                               double* __restrict__ mu) {
+    __shared__ double sh[256];
+    const int q = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)X[i * d + q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mu[q] = sh[0] / (double)n;
+}
+
+// x' = (x - mu) / l * g, zero-padded to dp columns; FP64 (g = sqrt(1/2)) and
+// FP32 (g = sqrt(log2(e)/2)) copies.
+__global__ void prescale_kernel(const float* __restrict__ X, int64_t n, int d, int dp,
+                                const double* __restrict__ mu, const double* __restrict__ inv_ell,
+                                double g64, double g32, double* __restrict__ xs64,
+                                float* __restrict__ xs32) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * dp) return;
+    const int64_t i = e / dp;
+    const int q = (int)(e - i * dp);
+    double v = 0.0;
+    if (q < d) v = ((double)X[i * d + q] - mu[q]) * inv_ell[q];
+    xs64[e] = v * g64;
+    xs32[e] = (float)(v * g32);
+}
+
+template <typename T>
+__global__ void sub_cols_t_kernel(T* __restrict__ R, int64_t ldr, const T* __restrict__ B,
+                                  int64_t ldb, const T* __restrict__ Q, int64_t ldq, int64_t n) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        R[i + k * ldr] = B[i + k * ldb] - Q[i + k * ldq];
+}
+
+unsigned gx(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4096));
+}
+
+}  // namespace
+
+static thread_local std::string g_create_err;
+
+static void ctx_rescale(Ctx& h) {
+    std::vector<double> inv(h.d);
+    for (int q = 0; q < h.d; ++q) {
+        const double lt = h.ard ? h.log_theta[q] : h.log_theta[0];
+        inv[q] = std::exp(-lt);
+    }
+    h.s2 = std::exp(h.log_theta.back());
+    KPCG_CUDA(cudaMemcpyAsync(h.inv_ell.p, inv.data(), sizeof(double) * h.d,
+                              cudaMemcpyHostToDevice, h.stream));
+    const int64_t tot = h.n * h.dp;
+    prescale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h.stream>>>(
+        h.X.p, h.n, h.d, h.dp, h.mu.p, h.inv_ell.p, std::sqrt(0.5), std::sqrt(0.5 * kLog2e),
+        h.xs64.p, h.xs32.p);
+    KPCG_LAUNCHED("prescale_kernel");
+    KPCG_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+static void check_theta(const double* log_theta, int n_theta, double noise) {
+    if (!log_theta) fail(KPCG_ERR_ARG, "log_theta is NULL");
+    for (int i = 0; i < n_theta; ++i)
+        if (!std::isfinite(log_theta[i])) fail(KPCG_ERR_ARG, "log_theta has a non-finite entry");
+    if (!(noise > 0.0) || !std::isfinite(noise)) fail(KPCG_ERR_ARG, "noise_var must be > 0");
+}
+
+static void check_dev_ptr(const void* p, const char* name) {
+    if (!p) fail(KPCG_ERR_ARG, std::string(name) + " is NULL");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(KPCG_ERR_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        fail(KPCG_ERR_ARG, std::string(name) + " is not a device pointer");
+}
+
+// ------------------------------------------------------------------ PCG
+// Per-column batched PCG (Algorithm 1, textbook recurrence) in vector type T.
+// X holds x0 on entry (zero if x0_zero) and the iterate on return.
+// Returns the number of iterations run (max over columns).
+template <typename T, typename MV, typename PC>
+static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, bool x0_zero,
+                    double tol, int tol_mode, int max_iter, MV&& matvec, PC&& precond,
+                    CgBufs<T>& bufs, std::vector<int>& iters_out, int& broken) {
+    const int64_t n = h.n, ld = h.ld;
+    cudaStream_t st = h.stream;
+    T* r = bufs.r.need((size_t)ld * c);
+    T* z = bufs.z.need((size_t)ld * c);
+    T* p = bufs.p.need((size_t)ld * c);
+    T* q = bufs.q.need((size_t)ld * c);
+    const int nblk = dot_blocks(n);
+    double* partial = h.partial.need((size_t)nblk * c);
+    double* sc = h.scal.need((size_t)6 * c);
+    int* isc = h.iscal.need((size_t)2 * c + 2);
+    CgScalars S{sc, sc + c, sc + 2 * c, sc + 3 * c, sc + 4 * c, sc + 5 * c, isc, isc + c,
+                isc + 2 * c};
+    KPCG_CUDA(cudaMemsetAsync(S.flags, 0, 2 * sizeof(int), st));
+
+    dot_cols<T>(B, ldb, B, ldb, n, c, partial, nblk, st);
+    finalize(partial, nblk, c, FIN_NORM_B, S, tol, tol_mode, n, nullptr, st);
+    if (x0_zero) {
+        fill_zero_cols(X, sizeof(T), ldx, n, c, st);
+        copy_cols<T>(r, ld, B, ldb, n, c, st);
+    } else {
+        matvec(X, ldx, c, q, ld);
+        sub_cols_t_kernel<T><<<dim3(gx(n), c), 256, 0, st>>>(r, ld, B, ldb, q, ld, n);
+        KPCG_LAUNCHED("sub_cols_t_kernel");
+    }
+    // initial stop test (no iteration counted)
+    dot_cols<T>(r, ld, r, ld, n, c, partial, nblk, st);
+    finalize(partial, nblk, c, FIN_RR, S, tol, tol_mode, n, nullptr, st);
+    // FIN_RR counted one iteration for active columns: undo by resetting.
+    KPCG_CUDA(cudaMemsetAsync(S.iters, 0, sizeof(int) * c, st));
+    precond(r, ld, c, z, ld);
+    copy_cols<T>(p, ld, z, ld, n, c, st);
+    dot_cols<T>(r, ld, z, ld, n, c, partial, nblk, st);
+    finalize(partial, nblk, c, FIN_RHO0, S, tol, tol_mode, n, nullptr, st);
+
+    int it = 0;
+    const int every = std::max(1, h.opt.check_every);
+    int* hf = h.hflags;
+    KPCG_CUDA(cudaMemcpyAsync(hf, S.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    int active = hf[0];
+    while (active > 0 && it < max_iter) {
+        matvec(p, ld, c, q, ld);
+        dot_cols<T>(p, ld, q, ld, n, c, partial, nblk, st);
+        finalize(partial, nblk, c, FIN_ALPHA, S, tol, tol_mode, n, nullptr, st);
+        update_xr<T>(X, ldx, r, ld, p, ld, q, ld, n, c, S.alpha, partial, nblk, st);
+        finalize(partial, nblk, c, FIN_RR, S, tol, tol_mode, n, nullptr, st);
+        ++it;
+        if (it % every == 0 || it >= max_iter) {
+            KPCG_CUDA(cudaMemcpyAsync(hf, S.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            KPCG_CUDA(cudaStreamSynchronize(st));
+            active = hf[0];
+            if (active == 0) break;
+        }
+        precond(r, ld, c, z, ld);
+        dot_cols<T>(r, ld, z, ld, n, c, partial, nblk, st);
+        finalize(partial, nblk, c, FIN_BETA, S, tol, tol_mode, n, nullptr, st);
+        update_p<T>(p, ld, z, ld, n, c, S.beta, S.active, st);
+    }
+    std::vector<int> its((size_t)c);
+    KPCG_CUDA(cudaMemcpyAsync(its.data(), S.iters, sizeof(int) * c, cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaMemcpyAsync(hf, S.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    broken = hf[1];
+    iters_out.assign(its.begin(), its.end());
+    return it;
+}
+
+// Per-column ||B - K_y X||^2 and ||B||^2 in FP64 (host vectors).
+static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const double* X, int64_t ldx,
+                         double* R, std::vector<double>& rr, std::vector<double>& bb) {
+    cudaStream_t st = h.stream;
+    kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, X, ldx, c, B, ldb, R, h.ld, h.kvws, st);
+    const int nblk = dot_blocks(h.n);
+    double* partial = h.partial.need((size_t)nblk * c * 2);
+    dot_cols<double>(R, h.ld, R, h.ld, h.n, c, partial, nblk, st);
+    dot_cols<double>(B, ldb, B, ldb, h.n, c, partial + (size_t)nblk * c, nblk, st);
+    std::vector<double> hp((size_t)nblk * c * 2);
+    KPCG_CUDA(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(),
+                              cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    rr.assign(c, 0.0);
+    bb.assign(c, 0.0);
+    for (int k = 0; k < c; ++k)
+        for (int b = 0; b < nblk; ++b) {
+            rr[k] += hp[(size_t)k * nblk + b];
+            bb[k] += hp[(size_t)(c + k) * nblk + b];
+        }
+}
+
+static bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
+    if (bb == 0.0) return true;
+    return tol_mode == 1 ? rr < (double)n * tol : rr <= tol * tol * bb;
+}
+
+static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
+                              const double* X0, double* Xout, int64_t ldx, int32_t* iters_host,
+                              kpcg_info* info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n, ld = h.ld;
+    const int prec = h.opt.precision;
+    if (prec == KPCG_TF32_IR && !kv_tc_supported(h.dp))
+        fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+    std::vector<int> iters_col((size_t)c, 0);
+    int iters_total = 0, steps = 0, broken = 0;
+    kpcg_status status = KPCG_OK;
+    std::vector<double> rr, bb;
+    double* R = h.R64.need((size_t)ld * c);
+
+    if (prec == KPCG_FP64 || prec == KPCG_FP32) {
+        // Plain PCG in one precision with residual replacement restarts.
+        const bool f64 = (prec == KPCG_FP64);
+        if (f64) {
+            if (X0)
+                copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
+        }
+        float* x32 = nullptr;
+        float* b32 = nullptr;
+        if (!f64) {
+            x32 = h.c32.x.need((size_t)ld * c);
+            b32 = h.c32.b.need((size_t)ld * c);
+            convert_scale_cols<float, double>(b32, ld, B, ldb, n, c, nullptr, 0, st);
+            if (X0) convert_scale_cols<float, double>(x32, ld, X0, ldx, n, c, nullptr, 0, st);
+        }
+        bool x0_zero = (X0 == nullptr);
+        for (int pass = 0; pass <= std::max(0, h.opt.max_restarts); ++pass) {
+            std::vector<int> its;
+            int br = 0;
+            const int budget = h.opt.max_iter - iters_total;
+            if (budget <= 0) break;
+            int ran;
+            if (f64) {
+                ran = pcg_core<double>(
+                    h, c, B, ldb, Xout, ldx, x0_zero, tol, h.opt.tol_mode, budget,
+                    [&](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
+                        kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, V, ldv, cc, nullptr, 0, O,
+                               ldo, h.kvws, st);
+                    },
+                    [&](const double* Rr, int64_t ldr, int cc, double* Z, int64_t ldz) {
+                        precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, st);
+                    },
+                    h.c64, its, br);
+            } else {
+                ran = pcg_core<float>(
+                    h, c, b32, ld, x32, ld, x0_zero, tol, h.opt.tol_mode, budget,
+                    [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O, ldo,
+                               h.kvws, st);
+                    },
+                    [&](const float* Rr, int64_t ldr, int cc, float* Z, int64_t ldz) {
+                        precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
+                    },
+                    h.c32, its, br);
+            }
+            iters_total += ran;
+            for (int k = 0; k < c; ++k) iters_col[k] += std::abs(its[k] < 0 ? -1 - its[k] : its[k]);
+            broken += br;
+            x0_zero = false;
+            if (br) break;
+            // true residual in the working precision decides a restart
+            bool all = true;
+            if (f64) {
+                residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+            } else {
+                float* q32 = h.c32.q.need((size_t)ld * c);
+                float* r32 = h.c32.r.need((size_t)ld * c);
+                kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, x32, ld, c, q32, ld, h.kvws,
+                       st);
+                sub_cols_t_kernel<float><<<dim3(gx(n), c), 256, 0, st>>>(r32, ld, b32, ld, q32,
+                                                                         ld, n);
+                KPCG_LAUNCHED("sub_cols_t_kernel");
+                const int nblk = dot_blocks(n);
+                double* partial = h.partial.need((size_t)nblk * c * 2);
+                dot_cols<float>(r32, ld, r32, ld, n, c, partial, nblk, st);
+                dot_cols<float>(b32, ld, b32, ld, n, c, partial + (size_t)nblk * c, nblk, st);
+                std::vector<double> hp((size_t)nblk * c * 2);
+                KPCG_CUDA(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(),
+                                          cudaMemcpyDeviceToHost, st));
+                KPCG_CUDA(cudaStreamSynchronize(st));
+                rr.assign(c, 0.0);
+                bb.assign(c, 0.0);
+                for (int k = 0; k < c; ++k)
+                    for (int b = 0; b < nblk; ++b) {
+                        rr[k] += hp[(size_t)k * nblk + b];
+                        bb[k] += hp[(size_t)(c + k) * nblk + b];
+                    }
+            }
+            for (int k = 0; k < c; ++k)
+                all = all && col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
+            steps = pass;
+            if (all || ran == 0) break;
+        }
+        if (!f64) convert_scale_cols<double, float>(Xout, ldx, x32, ld, n, c, nullptr, 0, st);
+    } else {
+        // Mixed precision: FP64 outer residuals, reduced-precision inner PCG
+        // on the normalised residual, x += ||r|| d (iterative refinement).
+        if (X0)
+            copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
+        else
+            fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
+        float* b32 = h.c32.b.need((size_t)ld * c);
+        float* d32 = h.c32.x.need((size_t)ld * c);
+        double* cs = h.colscale.need((size_t)c);
+        std::vector<double> hcs((size_t)c);
+        double best = INFINITY;
+        int stall = 0;
+        const bool tc = (prec == KPCG_TF32_IR);
+        for (int outer = 0;; ++outer) {
+            residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+            bool all = true;
+            double worst = 0.0;
+            for (int k = 0; k < c; ++k) {
+                const bool ok = col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
+                all = all && ok;
+                hcs[k] = ok ? 0.0 : std::sqrt(rr[k]);
+                if (bb[k] > 0) worst = std::max(worst, std::sqrt(rr[k] / bb[k]));
+            }
+            steps = outer;
+            if (all) break;
+            if (outer >= h.opt.max_outer || iters_total >= h.opt.max_iter) {
+                status = KPCG_ERR_NO_CONVERGENCE;
+                break;
+            }
+            if (worst < best * 0.9) {
+                best = worst;
+                stall = 0;
+            } else if (++stall >= 3) {
+                status = KPCG_ERR_NO_CONVERGENCE;
+                break;
+            }
+            KPCG_CUDA(cudaMemcpyAsync(cs, hcs.data(), sizeof(double) * c, cudaMemcpyHostToDevice,
+                                      st));
+            convert_scale_cols<float, double>(b32, ld, R, ld, n, c, cs, 1, st);
+            std::vector<int> its;
+            int br = 0;
+            const int budget = h.opt.max_iter - iters_total;
+            const int ran = pcg_core<float>(
+                h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, budget,
+                [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+                    if (tc)
+                        kv_tc_apply(h, V, ldv, cc, O, ldo);
+                    else
+                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O, ldo,
+                               h.kvws, st);
+                },
+                [&](const float* Rr, int64_t ldr, int cc, float* Z, int64_t ldz) {
+                    precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
+                },
+                h.c32, its, br);
+            iters_total += ran;
+            for (int k = 0; k < c; ++k) iters_col[k] += (its[k] < 0 ? -1 - its[k] : its[k]);
+            // a breakdown in the inner solve still leaves a usable correction
+            axpy_scaled_f64(Xout, ldx, d32, ld, n, c, cs, st);
+        }
+    }
+    // FP64 residual of what is returned
+    double maxrel = 0.0;
+    if (prec == KPCG_FP64 || prec == KPCG_FP32 || status != KPCG_OK || rr.empty())
+        residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+    bool all = true;
+    for (int k = 0; k < c; ++k) {
+        if (bb[k] > 0) maxrel = std::max(maxrel, std::sqrt(rr[k] / bb[k]));
+        all = all && col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
+    }
+    if (status == KPCG_OK && !all) status = broken ? KPCG_ERR_BREAKDOWN : KPCG_ERR_NO_CONVERGENCE;
+    if (iters_host)
+        for (int k = 0; k < c; ++k) iters_host[k] = iters_col[k];
+    if (info) {
+        info->iters_total = iters_total;
+        info->outer_steps = steps;
+        info->max_rel_res = maxrel;
+        info->time_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                .count();
+        info->setup_ms = 0.0;
+    }
+    if (status != KPCG_OK)
+        h.err = std::string(kpcg_status_string(status)) +
+                ": max relative residual " + std::to_string(maxrel);
+    return status;
+}
+
+}  // namespace kpcg
+
+using kpcg::Ctx;
+using kpcg::fail;
+
+struct kpcg_ctx : kpcg::Ctx {};
+
+#define KPCG_GUARD(hptr, ...)                                               \
+    try {                                                                   \
+        __VA_ARGS__;                                                        \
+    } catch (const kpcg::Error& e) {                                        \
+        if (hptr) (hptr)->err = e.msg;                                      \
+        else kpcg::g_create_err = e.msg;                                    \
+        return e.status;                                                    \
+    } catch (const std::exception& e) {                                     \
+        if (hptr) (hptr)->err = e.what();                                   \
+        else kpcg::g_create_err = e.what();                                 \
+        return KPCG_ERR_ARG;                                                \
+    }
+
+extern "C" {
+
+void kpcg_default_options(kpcg_options* opt) {
+    if (!opt) return;
+    opt->max_iter = 100000;
+    opt->precision = KPCG_FP32_IR;
+    opt->tol_mode = 0;
+    opt->max_outer = 40;
+    opt->inner_tol = 1e-4;
+    opt->check_every = 4;
+    opt->max_restarts = 5;
+}
+
+const char* kpcg_status_string(kpcg_status s) {
+    switch (s) {
+        case KPCG_OK: return "KPCG_OK";
+        case KPCG_ERR_ARG: return "KPCG_ERR_ARG";
+        case KPCG_ERR_CUDA: return "KPCG_ERR_CUDA";
+        case KPCG_ERR_OOM: return "KPCG_ERR_OOM";
+        case KPCG_ERR_NOT_SPD: return "KPCG_ERR_NOT_SPD";
+        case KPCG_ERR_BREAKDOWN: return "KPCG_ERR_BREAKDOWN";
+        case KPCG_ERR_NO_CONVERGENCE: return "KPCG_ERR_NO_CONVERGENCE";
+        case KPCG_ERR_TIMEOUT: return "KPCG_ERR_TIMEOUT";
+        case KPCG_ERR_STATE: return "KPCG_ERR_STATE";
+    }
+    return "KPCG_UNKNOWN";
+}
+
+static void check_opts(const kpcg_options* o) {
+    if (o->max_iter < 0 || o->max_outer < 0 || o->check_every < 1 || o->max_restarts < 0)
+        fail(KPCG_ERR_ARG, "invalid options");
+    if (o->precision < KPCG_FP64 || o->precision > KPCG_TF32_IR)
+        fail(KPCG_ERR_ARG, "invalid precision");
+    if (o->tol_mode != 0 && o->tol_mode != 1) fail(KPCG_ERR_ARG, "invalid tol_mode");
+    if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) fail(KPCG_ERR_ARG, "inner_tol not in (0,1)");
+}
+
+kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_theta, int32_t ard,
+                        double noise_var, const kpcg_options* opt, void* stream, kpcg_t* out) {
+    kpcg_ctx* h = nullptr;
+    try {
+        if (!out) fail(KPCG_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (n < 1) fail(KPCG_ERR_ARG, "n must be >= 1");
+        if (n > (int64_t)1 << 31) fail(KPCG_ERR_ARG, "n too large");
+        if (d < 1 || kpcg::padded_dim(d) < 0) fail(KPCG_ERR_ARG, "d must be in [1, 32]");
+        kpcg::check_theta(log_theta, ard ? d + 1 : 2, noise_var);
+        kpcg::check_dev_ptr(X, "X");
+        if (((uintptr_t)X) % 4) fail(KPCG_ERR_ARG, "X must be 4-byte aligned");
+        h = new kpcg_ctx();
+        KPCG_CUDA(cudaGetDevice(&h->device));
+        h->stream = (cudaStream_t)stream;
+        h->n = n;
+        h->ld = ((n + 31) / 32) * 32;
+        h->d = d;
+        h->dp = kpcg::padded_dim(d);
+        h->ard = ard ? 1 : 0;
+        h->log_theta.assign(log_theta, log_theta + (ard ? d + 1 : 2));
+        h->noise = noise_var;
+        kpcg_default_options(&h->opt);
+        if (opt) {
+            check_opts(opt);
+            h->opt = *opt;
+        }
+        KPCG_CUDA(cudaHostAlloc((void**)&h->hflags, 4 * sizeof(int), cudaHostAllocDefault));
+        h->X.need((size_t)n * d);
+        KPCG_CUDA(cudaMemcpyAsync(h->X.p, X, sizeof(float) * n * d, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        h->mu.need(d);
+        h->inv_ell.need(d);
+        h->xs64.need((size_t)n * h->dp);
+        h->xs32.need((size_t)n * h->dp);
+        kpcg::colmean_kernel<<<d, 256, 0, h->stream>>>(h->X.p, n, d, h->mu.p);
+        KPCG_LAUNCHED("colmean_kernel");
+        kpcg::ctx_rescale(*h);
+        *out = h;
+        return KPCG_OK;
+    } catch (const kpcg::Error& e) {
+        kpcg::g_create_err = e.msg;
+        if (h) {
+            if (h->hflags) cudaFreeHost(h->hflags);
+            delete h;
+        }
+        return e.status;
+    }
+}
+
+kpcg_status kpcg_set_theta(kpcg_t h, const double* log_theta, double noise_var) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        kpcg::check_theta(log_theta, h->ard ? h->d + 1 : 2, noise_var);
+        h->log_theta.assign(log_theta, log_theta + (h->ard ? h->d + 1 : 2));
+        h->noise = noise_var;
+        h->P.reset();
+        kpcg::ctx_rescale(*h);
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (!opt) fail(KPCG_ERR_ARG, "opt is NULL");
+        check_opts(opt);
+        h->opt = *opt;
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        h->P.reset();
+        if (kind == KPCG_PREC_NONE) return KPCG_OK;
+        if (kind == KPCG_PREC_NYSTROM) {
+            if (size < 1 || size > h->n || size > 4096)
+                fail(KPCG_ERR_ARG, "Nystrom m must be in [1, min(n, 4096)]");
+            if (!idx) fail(KPCG_ERR_ARG, "Nystrom needs the inducing indices");
+            for (int64_t a = 0; a < size; ++a) {
+                if (idx[a] < 0 || idx[a] >= h->n) fail(KPCG_ERR_ARG, "inducing index out of range");
+                if (a && idx[a] <= idx[a - 1])
+                    fail(KPCG_ERR_ARG, "inducing indices must be sorted and distinct");
+            }
+            kpcg::nystrom_setup(h->P, h->xs32.p, h->xs64.p, h->n, h->dp, h->c0_32(), h->c0_64(),
+                                h->noise, idx, size, h->stream);
+        } else if (kind == KPCG_PREC_BLOCK_JACOBI) {
+            if (size < 1 || size > 4096) fail(KPCG_ERR_ARG, "block size must be in [1, 4096]");
+            kpcg::block_jacobi_setup(h->P, h->xs64.p, h->n, h->dp, h->c0_64(), h->noise,
+                                     std::min<int64_t>(size, h->n), h->stream);
+        } else {
+            fail(KPCG_ERR_ARG, "unknown preconditioner kind");
+        }
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
+                            int64_t ldo) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (c < 0 || ldv < h->n || ldo < h->n) fail(KPCG_ERR_ARG, "bad sizes");
+        if (c == 0) return KPCG_OK;
+        kpcg::check_dev_ptr(V, "V");
+        kpcg::check_dev_ptr(O, "O");
+        kpcg::kv_f64(h->xs64.p, h->n, h->dp, h->c0_64(), h->noise, V, ldv, c, nullptr, 0, O, ldo,
+                     h->kvws, h->stream);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
+                            int64_t ldo, int32_t impl) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (c < 0 || ldv < h->n || ldo < h->n) fail(KPCG_ERR_ARG, "bad sizes");
+        if (c == 0) return KPCG_OK;
+        kpcg::check_dev_ptr(V, "V");
+        kpcg::check_dev_ptr(O, "O");
+        if (impl == 0) {
+            kpcg::kv_f32(h->xs32.p, h->n, h->dp, h->c0_32(), (float)h->noise, V, ldv, c, O, ldo,
+                         h->kvws, h->stream);
+        } else if (impl == 1) {
+            if (!kpcg::kv_tc_supported(h->dp))
+                fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+            kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo);
+        } else {
+            fail(KPCG_ERR_ARG, "unknown impl");
+        }
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_precond_apply_f64(kpcg_t h, const double* R, int64_t ldr, int32_t c, double* Z,
+                                   int64_t ldz) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (c < 0 || ldr < h->n || ldz < h->n) fail(KPCG_ERR_ARG, "bad sizes");
+        if (c == 0) return KPCG_OK;
+        kpcg::check_dev_ptr(R, "R");
+        kpcg::check_dev_ptr(Z, "Z");
+        h->P.n = h->n;
+        kpcg::precond_apply_f64(h->P, R, ldr, c, Z, ldz, h->stream);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_solve(kpcg_t h, const double* B, int64_t ldb, int32_t c, double tol,
+                       const double* X0, double* Xout, int64_t ldx, int32_t* iters,
+                       kpcg_info* info) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (c < 0 || ldb < h->n || ldx < h->n) fail(KPCG_ERR_ARG, "bad sizes");
+        if (!(tol > 0.0)) fail(KPCG_ERR_ARG, "tol must be > 0");
+        if (c == 0) return KPCG_OK;
+        kpcg::check_dev_ptr(B, "B");
+        kpcg::check_dev_ptr(Xout, "Xout");
+        if (X0) kpcg::check_dev_ptr(X0, "X0");
+        h->P.n = h->n;
+        return kpcg::solve_impl(*h, B, ldb, c, tol, X0, Xout, ldx, iters, info);
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* G, int64_t ldg) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (c < 0 || ldw < h->n || ldg < h->n) fail(KPCG_ERR_ARG, "bad sizes");
+        if (c == 0) return KPCG_OK;
+        kpcg::check_dev_ptr(W, "W");
+        kpcg::check_dev_ptr(G, "G");
+        float* w32 = h->W32.need((size_t)h->ld * c);
+        kpcg::convert_scale_cols<float, double>(w32, h->ld, W, ldw, h->n, c, nullptr, 0,
+                                                h->stream);
+        kpcg::dkv_f32(h->xs32.p, h->n, h->dp, h->d, h->ard, h->c0_32(), w32, h->ld, c, G, ldg,
+                      h->kvws, h->stream);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
+                      double* grad, double* alpha, kpcg_info* info) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (t < 1) fail(KPCG_ERR_ARG, "t must be >= 1");
+        if (!grad) fail(KPCG_ERR_ARG, "grad is NULL");
+        kpcg::check_dev_ptr(y, "y");
+        kpcg::check_dev_ptr(probes, "probes");
+        if (alpha) kpcg::check_dev_ptr(alpha, "alpha");
+        const int64_t n = h->n, ld = h->ld;
+        const int c = t + 1;
+        cudaStream_t st = h->stream;
+        double* Bb = h->Bblk.need((size_t)ld * c);
+        double* Sb = h->Sblk.need((size_t)ld * c);
+        kpcg::copy_cols<double>(Bb, ld, y, n, n, 1, st);
+        kpcg::copy_cols<double>(Bb + ld, ld, probes, n, n, t, st);
+        kpcg_info sinfo{};
+        h->P.n = n;
+        const kpcg_status s = kpcg::solve_impl(*h, Bb, ld, c, tol, nullptr, Sb, ld, nullptr, &sinfo);
+        if (s != KPCG_OK) return s;
+        // G_q = dK_q [a, r_1..r_t]
+        const int nq = (h->ard ? h->d : 1) + 1;
+        float* w32 = h->W32.need((size_t)ld * c);
+        kpcg::convert_scale_cols<float, double>(w32, ld, Sb, ld, n, 1, nullptr, 0, st);
+        kpcg::convert_scale_cols<float, double>(w32 + ld, ld, probes, n, n, t, nullptr, 0, st);
+        double* G = h->G.need((size_t)nq * ld * c);
+        kpcg::dkv_f32(h->xs32.p, n, h->dp, h->d, h->ard, h->c0_32(), w32, ld, c, G, ld, h->kvws,
+                      st);
+        // dots: S^T G_q per column (c of them), and S^T [a, r_1..r_t] for the noise term
+        kpcg::copy_cols<double>(Bb, ld, Sb, ld, n, 1, st);
+        const int nblk = kpcg::dot_blocks(n);
+        double* partial = h->partial.need((size_t)nblk * c * (nq + 1));
+        for (int q = 0; q < nq; ++q)
+            kpcg::dot_cols<double>(Sb, ld, G + (size_t)q * ld * c, ld, n, c,
+                                   partial + (size_t)q * nblk * c, nblk, st);
+        kpcg::dot_cols<double>(Sb, ld, Bb, ld, n, c, partial + (size_t)nq * nblk * c, nblk, st);
+        std::vector<double> hp((size_t)nblk * c * (nq + 1));
+        KPCG_CUDA(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        if (alpha) kpcg::copy_cols<double>(alpha, n, Sb, ld, n, 1, st);
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        auto dot = [&](int q, int k) {
+            double s = 0.0;
+            for (int b = 0; b < nblk; ++b) s += hp[((size_t)q * c + k) * nblk + b];
+            return s;
+        };
+        for (int q = 0; q <= nq; ++q) {
+            double tr = 0.0;
+            for (int k = 1; k < c; ++k) tr += dot(q, k);
+            tr /= (double)t;
+            const double quad = dot(q, 0);
+            const double scale = (q == nq) ? h->noise : 1.0;  // dK_y/dlog sigma^2 = sigma^2 I
+            grad[q] = scale * (-0.5 * tr + 0.5 * quad);
+        }
+        if (info) *info = sinfo;
+    });
+    return KPCG_OK;
+}
+
+void kpcg_destroy(kpcg_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->hflags) cudaFreeHost(h->hflags);
+    delete h;
+}
+
+const char* kpcg_last_error(kpcg_t h) {
+    if (!h) return kpcg::g_create_err.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

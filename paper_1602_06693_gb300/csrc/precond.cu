@@ -1,0 +1,601 @@
+// Preconditioners of Sec. 3: Nystrom (Sec. 3.1) and block-Jacobi (Sec. 3.3.1).
+//
+// Nystrom.  P = K_XU K_UU^{-1} K_UX + sigma^2 I, inverted by the matrix
+// inversion lemma as P^{-1} = sigma^{-2} [I - K_XU M^{-1} K_UX] with
+// M = sigma^2 K_UU + K_UX K_XU (the printed inverse drops the sigma^2 on K_UU).
+// K_XU is stored once in FP32; M is formed from that same FP32 block with
+// FP64 products and sums, so the applied operator is exactly the inverse of
+// the SPD matrix K^_XU K_UU^{-1} K^_UX + sigma^2 I built from the stored block.
+// M = L L^T is factored in FP64 and L^{-1} formed explicitly (stored as
+// U = L^{-T}, row-major), so an apply is two skinny products with K_XU and two
+// m x m triangular products, all accumulated in FP64: with sigma^2 small the
+// difference r - K_XU M^{-1} K_UX r cancels almost completely along the
+// leading eigenvectors, and an FP32 accumulation there destroys the
+// preconditioner.
+//
+// Block-Jacobi.  P = bldiag(K_y), contiguous blocks of b rows (the last one
+// shorter).  Each block is factored in FP64 and its inverse factor stored;
+// an apply is two triangular products per block, FP64 accumulation.
+//
+// Factorizations are blocked right-looking Cholesky (diagonal block on one
+// CTA, panel solve and trailing update across the grid), batched over
+// matrices of equal leading dimension.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kpcg_internal.cuh"
+#include "precond.cuh"
+
+namespace kpcg {
+namespace {
+
+constexpr int NB = 32;  // panel width of the blocked Cholesky
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Size of matrix q in a batch of blocks of a length-n_total index range.
+__device__ __forceinline__ int64_t bsize(int64_t q, int64_t b, int64_t n_total) {
+    const int64_t r0 = q * b;
+    return (n_total - r0 < b) ? (n_total - r0) : b;
+}
+
+// Factor the nb x nb diagonal block at (j0, j0) of matrix q in place.
+__global__ void potrf_diag_kernel(double* A, int64_t stride, int64_t b, int64_t n_total,
+                                  int64_t j0, int* status) {
+    __shared__ double S[NB][NB + 1];
+    __shared__ int bad;
+    const int64_t q = blockIdx.x;
+    const int64_t bq = bsize(q, b, n_total);
+    if (j0 >= bq || status[q]) return;
+    const int nb = (int)min((int64_t)NB, bq - j0);
+    double* M = A + q * stride;
+    const int64_t ld = bq;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e / nb, c = e % nb;
+        S[r][c] = M[(j0 + r) * ld + j0 + c];
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double piv = S[j][j];
+            if (!(piv > 0.0) || !isfinite(piv)) {
+                bad = 1;
+            } else {
+                S[j][j] = sqrt(piv);
+            }
+        }
+        __syncthreads();
+        if (bad) {
+            if (threadIdx.x == 0) status[q] = (int)(j0 + j + 1);
+            return;
+        }
+        const double ljj = S[j][j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) S[i][j] /= ljj;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            const int i = e / nb, k = e % nb;
+            if (i > j && k > j && k <= i) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e / nb, c = e % nb;
+        M[(j0 + r) * ld + j0 + c] = (c <= r) ? S[r][c] : 0.0;
+    }
+}
+
+// Panel solve: rows i >= j0+nb of columns j0..j0+nb-1 become L21 = A21 L11^{-T}.
+__global__ void trsm_panel_kernel(double* A, int64_t stride, int64_t b, int64_t n_total,
+                                  int64_t j0, const int* status) {
+    __shared__ double L[NB][NB + 1];
+    const int64_t q = blockIdx.y;
+    const int64_t bq = bsize(q, b, n_total);
+    if (j0 >= bq || status[q]) return;
+    const int nb = (int)min((int64_t)NB, bq - j0);
+    double* M = A + q * stride;
+    const int64_t ld = bq;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e / nb, c = e % nb;
+        L[r][c] = M[(j0 + r) * ld + j0 + c];
+    }
+    __syncthreads();
+    const int64_t i = j0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bq) return;
+    double x[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) x[t] = (t < nb) ? M[i * ld + j0 + t] : 0.0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        if (t < nb) {
+            double s = x[t];
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (u < t) s -= x[u] * L[t][u];
+            x[t] = s / L[t][t];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+        if (t < nb) M[i * ld + j0 + t] = x[t];
+}
+
+// Trailing update A22 -= L21 L21^T on the lower triangle; 32x32 output tiles.
+__global__ void syrk_update_kernel(double* A, int64_t stride, int64_t b, int64_t n_total,
+                                   int64_t j0, const int* status) {
+    __shared__ double Li[32][NB + 1];
+    __shared__ double Lk[32][NB + 1];
+    const int64_t q = blockIdx.z;
+    const int64_t bq = bsize(q, b, n_total);
+    if (j0 >= bq || status[q]) return;
+    const int nb = (int)min((int64_t)NB, bq - j0);
+    const int64_t t0 = j0 + nb;
+    const int64_t ti = blockIdx.y, tk = blockIdx.x;
+    if (tk > ti) return;
+    const int64_t i0 = t0 + ti * 32, k0 = t0 + tk * 32;
+    if (i0 >= bq) return;
+    double* M = A + q * stride;
+    const int64_t ld = bq;
+    for (int e = threadIdx.x; e < 32 * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Li[r][c] = (i0 + r < bq && c < nb) ? M[(i0 + r) * ld + j0 + c] : 0.0;
+        Lk[r][c] = (k0 + r < bq && c < nb) ? M[(k0 + r) * ld + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 each
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const int r = ty * 2 + a, cc = tx * 2 + c2;
+            const int64_t i = i0 + r, k = k0 + cc;
+            if (i < bq && k < bq && k <= i) {
+                double s = 0.0;
+#pragma unroll
+                for (int u = 0; u < NB; ++u) s = fma(Li[r][u], Lk[cc][u], s);
+                M[i * ld + k] -= s;
+            }
+        }
+}
+
+// U = L^{-T}: warp w solves L x = e_j for column j, writing x into row j of U.
+__global__ void trinv_kernel(const double* Lb, double* Ub, int64_t stride, int64_t b,
+                             int64_t n_total, int64_t nmat) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    // Flat column index over the batch: matrix q holds columns [q*b, q*b+bq).
+    const int64_t q = gw / b, j = gw % b;
+    if (q >= nmat) return;
+    const int64_t bq = bsize(q, b, n_total);
+    if (j >= bq) return;
+    const double* L = Lb + q * stride;
+    double* U = Ub + q * stride + j * bq;  // row j of U
+    for (int64_t i = lane; i < j; i += 32) U[i] = 0.0;
+    if (lane == 0) U[j] = 1.0 / L[j * bq + j];
+    __syncwarp();
+    for (int64_t i = j + 1; i < bq; ++i) {
+        const double* Li = L + i * bq;
+        double s = 0.0;
+        for (int64_t k = j + lane; k < i; k += 32) s = fma(Li[k], U[k], s);
+        s = warp_sum(s);
+        if (lane == 0) U[i] = -s / Li[i];
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- Nystrom
+__global__ void gather_rows_f32(const float* __restrict__ src, const int64_t* __restrict__ idx,
+                                int64_t m, int dp, float* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * dp) return;
+    const int64_t a = e / dp;
+    dst[e] = src[idx[a] * dp + (e - a * dp)];
+}
+__global__ void gather_rows_f64(const double* __restrict__ src, const int64_t* __restrict__ idx,
+                                int64_t m, int dp, double* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * dp) return;
+    const int64_t a = e / dp;
+    dst[e] = src[idx[a] * dp + (e - a * dp)];
+}
+
+// part[s][a][b] = sum over rows of split s of KXU[i][a] KXU[i][b], lower tiles.
+constexpr int ST = 64;  // output tile
+constexpr int SR = 32;  // rows per stage
+__global__ void __launch_bounds__(256)
+    syrk_kxu_kernel(const float* __restrict__ KXU, int64_t n, int64_t m, int64_t rows_per_split,
+                    double* __restrict__ part) {
+    __shared__ float Aa[SR][ST];
+    __shared__ float Ab[SR][ST];
+    const int64_t ta = blockIdx.y, tb = blockIdx.x;
+    if (tb > ta) return;
+    const int64_t a0 = ta * ST, b0 = tb * ST;
+    const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
+    const int64_t r1 = min(n, r0 + rows_per_split);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 4 x 4 outputs each
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int64_t rs = r0; rs < r1; rs += SR) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < SR * ST; e += 256) {
+            const int r = e / ST, c = e % ST;
+            const int64_t i = rs + r;
+            Aa[r][c] = (i < r1 && a0 + c < m) ? KXU[i * m + a0 + c] : 0.f;
+            Ab[r][c] = (i < r1 && b0 + c < m) ? KXU[i * m + b0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < SR; ++r) {
+            double va[4], vb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) va[u] = (double)Aa[r][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) vb[v] = (double)Ab[r][tx * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(va[u], vb[v], acc[u][v]);
+        }
+    }
+    double* P = part + (int64_t)blockIdx.z * m * m;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t a = a0 + ty * 4 + u, bb = b0 + tx * 4 + v;
+            if (a < m && bb < m && bb <= a) P[a * m + bb] = acc[u][v];
+        }
+}
+
+// M[a][b] += sum_s part[s][a][b] (lower), then mirror to the upper triangle.
+__global__ void syrk_reduce_kernel(const double* __restrict__ part, int nsplit, int64_t m,
+                                   double* __restrict__ M) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int64_t a = e / m, b = e % m;
+    if (b > a) return;
+    double s = M[e];
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * m * m + e];
+    M[e] = s;
+    M[b * m + a] = s;
+}
+
+__global__ void add_diag_kernel(double* M, int64_t m, double v) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < m) M[a * m + a] += v;
+}
+
+// w_part[s][k][a] = sum_{i in split s} KXU[i][a] R[i][k]   (FP64 products)
+constexpr int PC = 4;  // columns per pass
+template <typename T>
+__global__ void __launch_bounds__(256)
+    nys_proj_kernel(const float* __restrict__ KXU, int64_t n, int64_t m, const T* __restrict__ R,
+                    int64_t ldr, int ncols, int64_t rows_per_split, double* __restrict__ part,
+                    int c_total) {
+    __shared__ double sr[64][PC];
+    const int64_t a = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+    const int64_t r1 = min(n, r0 + rows_per_split);
+    double acc[PC];
+#pragma unroll
+    for (int k = 0; k < PC; ++k) acc[k] = 0.0;
+    for (int64_t rs = r0; rs < r1; rs += 64) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * PC; e += 256) {
+            const int k = e / 64, r = e % 64;
+            sr[r][k] = (rs + r < r1 && k < ncols) ? (double)R[rs + r + (int64_t)k * ldr] : 0.0;
+        }
+        __syncthreads();
+        const int rn = (int)min((int64_t)64, r1 - rs);
+        if (a < m) {
+            for (int r = 0; r < rn; ++r) {
+                const double kv = (double)KXU[(rs + r) * m + a];
+#pragma unroll
+                for (int k = 0; k < PC; ++k) acc[k] = fma(kv, sr[r][k], acc[k]);
+            }
+        }
+    }
+    if (a < m)
+        for (int k = 0; k < ncols; ++k)
+            part[((int64_t)blockIdx.y * c_total + k) * m + a] = acc[k];
+}
+
+__global__ void sum_splits_kernel(const double* __restrict__ part, int nsplit, int64_t len,
+                                  double* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * len + e];
+    out[e] = s;
+}
+
+// y_k = L^{-1} w_k with U = L^{-T} row-major: y_i = sum_{j <= i} U[j][i] w_j.
+__global__ void tri_lower_apply_kernel(const double* __restrict__ U, int64_t m,
+                                       const double* __restrict__ w, double* __restrict__ y) {
+    const int k = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double* wk = w + (int64_t)k * m;
+    double s = 0.0;
+    for (int64_t j = 0; j <= i; ++j) s = fma(U[j * m + i], wk[j], s);
+    y[(int64_t)k * m + i] = s;
+}
+
+// u_k = L^{-T} y_k: u_j = sum_{i >= j} U[j][i] y_i (warp per j).
+__global__ void tri_upper_apply_kernel(const double* __restrict__ U, int64_t m,
+                                       const double* __restrict__ y, double* __restrict__ u) {
+    const int k = blockIdx.y;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const double* yk = y + (int64_t)k * m;
+    const double* Uj = U + j * m;
+    double s = 0.0;
+    for (int64_t i = j + lane; i < m; i += 32) s = fma(Uj[i], yk[i], s);
+    s = warp_sum(s);
+    if (lane == 0) u[(int64_t)k * m + j] = s;
+}
+
+// Z = (R - K_XU u) / sigma^2, warp per row, FP64 accumulation.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    nys_back_kernel(const float* __restrict__ KXU, int64_t n, int64_t m,
+                    const double* __restrict__ u, int c, const T* __restrict__ R, int64_t ldr,
+                    T* __restrict__ Z, int64_t ldz, double inv_noise) {
+    extern __shared__ double su[];  // m * c
+    for (int64_t e = threadIdx.x; e < m * c; e += blockDim.x) su[e] = u[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const float* Ki = KXU + i * m;
+        for (int k = 0; k < c; ++k) {
+            const double* uk = su + (int64_t)k * m;
+            double s = 0.0;
+            for (int64_t a = lane; a < m; a += 32) s = fma((double)Ki[a], uk[a], s);
+            s = warp_sum(s);
+            if (lane == 0)
+                Z[i + (int64_t)k * ldz] = (T)(((double)R[i + (int64_t)k * ldr] - s) * inv_noise);
+        }
+    }
+}
+
+// ---------------------------------------------------------- block-Jacobi
+// Dense block of K_y: A_q[a][b] = s2 exp(-|x'_a - x'_b|^2) + noise [a == b].
+__global__ void bj_fill_kernel(const double* __restrict__ xs, int64_t n, int dp, double c0,
+                               double noise, int64_t b, double* __restrict__ A) {
+    const int64_t q = blockIdx.y;
+    const int64_t bq = bsize(q, b, n);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= bq * bq) return;
+    const int64_t r = e / bq, c = e % bq;
+    const double* xr = xs + (q * b + r) * dp;
+    const double* xc = xs + (q * b + c) * dp;
+    double acc = c0;
+    for (int t = 0; t < dp; ++t) {
+        const double d = xr[t] - xc[t];
+        acc = fma(-d, d, acc);
+    }
+    A[q * b * b + e] = exp(acc) + (r == c ? noise : 0.0);
+}
+
+// z_blk = L^{-T} L^{-1} r_blk for block q, column k (one CTA each).
+template <typename T>
+__global__ void bj_apply_kernel(const double* __restrict__ Ub, int64_t n, int64_t b,
+                                const T* __restrict__ R, int64_t ldr, T* __restrict__ Z,
+                                int64_t ldz) {
+    extern __shared__ double sm[];  // 2 * b
+    const int64_t q = blockIdx.x;
+    const int k = blockIdx.y;
+    const int64_t bq = bsize(q, b, n);
+    const int64_t r0 = q * b;
+    const double* U = Ub + q * b * b;
+    double* rv = sm;
+    double* yv = sm + b;
+    for (int64_t i = threadIdx.x; i < bq; i += blockDim.x)
+        rv[i] = (double)R[r0 + i + (int64_t)k * ldr];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < bq; i += blockDim.x) {
+        double s = 0.0;
+        for (int64_t j = 0; j <= i; ++j) s = fma(U[j * bq + i], rv[j], s);
+        yv[i] = s;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    for (int64_t j = threadIdx.x >> 5; j < bq; j += nw) {
+        const double* Uj = U + j * bq;
+        double s = 0.0;
+        for (int64_t i = j + lane; i < bq; i += 32) s = fma(Uj[i], yv[i], s);
+        s = warp_sum(s);
+        if (lane == 0) Z[r0 + j + (int64_t)k * ldz] = (T)s;
+    }
+}
+
+}  // namespace
+
+// Blocked Cholesky of a batch of SPD matrices (in place, lower) and the
+// explicit inverse factor U = L^{-T}.  Returns the first failing status.
+static int factor_and_invert(double* A, double* U, int64_t b, int64_t n_total, int64_t nmat,
+                             int* status_dev, cudaStream_t st) {
+    KPCG_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int) * nmat, st));
+    for (int64_t j0 = 0; j0 < b; j0 += NB) {
+        potrf_diag_kernel<<<(unsigned)nmat, 256, 0, st>>>(A, b * b, b, n_total, j0, status_dev);
+        KPCG_LAUNCHED("potrf_diag_kernel");
+        const int64_t rows = b - j0 - NB;
+        if (rows > 0) {
+            dim3 g1((unsigned)((rows + 127) / 128), (unsigned)nmat);
+            trsm_panel_kernel<<<g1, 128, 0, st>>>(A, b * b, b, n_total, j0, status_dev);
+            KPCG_LAUNCHED("trsm_panel_kernel");
+            const unsigned nt = (unsigned)((rows + 31) / 32);
+            dim3 g2(nt, nt, (unsigned)nmat);
+            syrk_update_kernel<<<g2, 256, 0, st>>>(A, b * b, b, n_total, j0, status_dev);
+            KPCG_LAUNCHED("syrk_update_kernel");
+        }
+    }
+    std::vector<int> hs((size_t)nmat);
+    KPCG_CUDA(cudaMemcpyAsync(hs.data(), status_dev, sizeof(int) * nmat, cudaMemcpyDeviceToHost,
+                              st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q = 0; q < nmat; ++q)
+        if (hs[(size_t)q]) return hs[(size_t)q] + (int)(q * b);
+    const int64_t warps = nmat * b;
+    trinv_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(A, U, b * b, b, n_total,
+                                                                      nmat);
+    KPCG_LAUNCHED("trinv_kernel");
+    return 0;
+}
+
+void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                   float c0_32, double c0_64, double noise, const int64_t* idx_host, int64_t m,
+                   cudaStream_t st) {
+    P.kind = KPCG_PREC_NYSTROM;
+    P.n = n;
+    P.m = m;
+    P.noise = noise;
+    int64_t* idx = P.idx.need((size_t)m);
+    KPCG_CUDA(cudaMemcpyAsync(idx, idx_host, sizeof(int64_t) * m, cudaMemcpyHostToDevice, st));
+    float* us32 = P.us32.need((size_t)m * dp);
+    double* us64 = P.us64.need((size_t)m * dp);
+    const unsigned g = (unsigned)((m * dp + 255) / 256);
+    gather_rows_f32<<<g, 256, 0, st>>>(xs32, idx, m, dp, us32);
+    KPCG_LAUNCHED("gather_rows_f32");
+    gather_rows_f64<<<g, 256, 0, st>>>(xs64, idx, m, dp, us64);
+    KPCG_LAUNCHED("gather_rows_f64");
+    float* KXU = P.KXU.need((size_t)n * m);
+    kxu_f32(xs32, n, us32, m, dp, c0_32, KXU, st);
+    // M0 = sigma^2 K_UU + K_UX K_XU
+    double* M0 = P.M0.need((size_t)m * m);
+    kuu_f64(us64, m, dp, c0_64, noise, 0.0, M0, st);
+    const int64_t tiles = (m + ST - 1) / ST;
+    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 4095) / 4096));
+    const int64_t rps = ((n + nsplit - 1) / nsplit + SR - 1) / SR * SR;
+    nsplit = (int)((n + rps - 1) / rps);
+    double* part = P.scratch.need((size_t)nsplit * m * m);
+    dim3 gs((unsigned)tiles, (unsigned)tiles, (unsigned)nsplit);
+    syrk_kxu_kernel<<<gs, 256, 0, st>>>(KXU, n, m, rps, part);
+    KPCG_LAUNCHED("syrk_kxu_kernel");
+    syrk_reduce_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, nsplit, m, M0);
+    KPCG_LAUNCHED("syrk_reduce_kernel");
+    // trace for the jitter ladder
+    std::vector<double> diag((size_t)m);
+    KPCG_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), M0, sizeof(double) * (m + 1),
+                                sizeof(double), (size_t)m, cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    double tr = 0.0;
+    for (double v : diag) tr += v;
+    double* M = P.M.need((size_t)m * m);
+    double* U = P.U.need((size_t)m * m);
+    int* status = P.status.need(1);
+    int rc = 1;
+    P.jitter = 0.0;
+    for (int k = -1; k <= 6 && rc; ++k) {
+        P.jitter = (k < 0) ? 0.0 : 1e-12 * tr / (double)m * std::pow(10.0, (double)k);
+        KPCG_CUDA(cudaMemcpyAsync(M, M0, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+        if (P.jitter > 0.0) {
+            add_diag_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(M, m, P.jitter);
+            KPCG_LAUNCHED("add_diag_kernel");
+        }
+        rc = factor_and_invert(M, U, m, m, 1, status, st);
+    }
+    if (rc) fail(KPCG_ERR_NOT_SPD, "Nystrom inner matrix is not positive definite after jitter");
+    P.ready = true;
+}
+
+void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
+                        double noise, int64_t b, cudaStream_t st) {
+    P.kind = KPCG_PREC_BLOCK_JACOBI;
+    P.n = n;
+    P.b = b;
+    P.noise = noise;
+    const int64_t nb = (n + b - 1) / b;
+    double* A = P.M.need((size_t)nb * b * b);
+    double* U = P.U.need((size_t)nb * b * b);
+    dim3 g((unsigned)((b * b + 255) / 256), (unsigned)nb);
+    bj_fill_kernel<<<g, 256, 0, st>>>(xs64, n, dp, c0_64, noise, b, A);
+    KPCG_LAUNCHED("bj_fill_kernel");
+    int* status = P.status.need((size_t)nb);
+    const int rc = factor_and_invert(A, U, b, n, nb, status, st);
+    if (rc)
+        fail(KPCG_ERR_NOT_SPD,
+             "block of K_y not positive definite near row " + std::to_string(rc - 1));
+    P.ready = true;
+}
+
+template <typename T>
+static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z,
+                          int64_t ldz, cudaStream_t st) {
+    const int64_t n = P.n, m = P.m;
+    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 1023) / 1024));
+    const int64_t rps = (n + nsplit - 1) / nsplit;
+    nsplit = (int)((n + rps - 1) / rps);
+    double* part = const_cast<PrecondState&>(P).wpart.need((size_t)nsplit * c * m);
+    double* w = const_cast<PrecondState&>(P).w.need((size_t)c * m);
+    double* y = const_cast<PrecondState&>(P).y.need((size_t)c * m);
+    for (int k0 = 0; k0 < c; k0 += PC) {
+        const int nc = std::min(PC, c - k0);
+        dim3 g((unsigned)((m + 255) / 256), (unsigned)nsplit);
+        nys_proj_kernel<T><<<g, 256, 0, st>>>(P.KXU.p, n, m, R + (int64_t)k0 * ldr, ldr, nc, rps,
+                                              part + (int64_t)k0 * m, c);
+        KPCG_LAUNCHED("nys_proj_kernel");
+    }
+    sum_splits_kernel<<<(unsigned)((c * m + 255) / 256), 256, 0, st>>>(part, nsplit, c * m, w);
+    KPCG_LAUNCHED("sum_splits_kernel");
+    tri_lower_apply_kernel<<<dim3((unsigned)((m + 127) / 128), c), 128, 0, st>>>(P.U.p, m, w, y);
+    KPCG_LAUNCHED("tri_lower_apply_kernel");
+    tri_upper_apply_kernel<<<dim3((unsigned)((m * 32 + 255) / 256), c), 256, 0, st>>>(P.U.p, m, y,
+                                                                                     w);
+    KPCG_LAUNCHED("tri_upper_apply_kernel");
+    const size_t smem = sizeof(double) * (size_t)m * c;
+    if (smem > 200 * 1024) fail(KPCG_ERR_ARG, "Nystrom apply: m * c too large");
+    if (smem > 48 * 1024)
+        KPCG_CUDA(cudaFuncSetAttribute(nys_back_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 8);
+    nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, w, c, R, ldr, Z, ldz,
+                                                  1.0 / P.noise);
+    KPCG_LAUNCHED("nys_back_kernel");
+}
+
+template <typename T>
+static void bj_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
+                     cudaStream_t st) {
+    const int64_t nb = (P.n + P.b - 1) / P.b;
+    const size_t smem = sizeof(double) * 2 * (size_t)P.b;
+    if (smem > 48 * 1024)
+        KPCG_CUDA(cudaFuncSetAttribute(bj_apply_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bj_apply_kernel<T><<<dim3((unsigned)nb, c), 256, smem, st>>>(P.U.p, P.n, P.b, R, ldr, Z, ldz);
+    KPCG_LAUNCHED("bj_apply_kernel");
+}
+
+template <typename T>
+static void apply_any(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
+                      cudaStream_t st) {
+    if (P.kind == KPCG_PREC_NYSTROM && P.ready)
+        nystrom_apply<T>(P, R, ldr, c, Z, ldz, st);
+    else if (P.kind == KPCG_PREC_BLOCK_JACOBI && P.ready)
+        bj_apply<T>(P, R, ldr, c, Z, ldz, st);
+    else
+        copy_cols<T>(Z, ldz, R, ldr, P.n, c, st);
+}
+
+void precond_apply_f64(const PrecondState& P, const double* R, int64_t ldr, int c, double* Z,
+                       int64_t ldz, cudaStream_t st) {
+    apply_any<double>(P, R, ldr, c, Z, ldz, st);
+}
+void precond_apply_f32(const PrecondState& P, const float* R, int64_t ldr, int c, float* Z,
+                       int64_t ldz, cudaStream_t st) {
+    apply_any<float>(P, R, ldr, c, Z, ldz, st);
+}
+
+}  // namespace kpcg

@@ -1,0 +1,81 @@
+"""CPU-side checks of the C ABI boundary: the library builds for sm_103a,
+loads, and exports every entry point that include/kpcg.h declares.  No
+compute call is made (there is no GPU here)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "kpcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kpcg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1602_06693_gb300 import build
+    build.build()
+    return build.LIB
+
+
+def test_header_declares_core_calls():
+    names = _declared()
+    for core in ("kpcg_create", "kpcg_precond", "kpcg_solve", "kpcg_grad", "kpcg_destroy"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    import ctypes
+    L = ctypes.CDLL(built)
+    missing = [s for s in _declared() if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol(built):
+    import paper_1602_06693_gb300 as kpcg
+    from paper_1602_06693_gb300 import binding
+    assert sorted(binding.SYMBOLS) == _declared()
+    assert sorted(kpcg.exported_symbols()) == _declared()
+
+
+def test_default_options_and_status_strings(built):
+    import paper_1602_06693_gb300 as kpcg
+    o = kpcg.default_options()
+    assert o.max_iter == 100000 and o.tol_mode == 0 and 0 < o.inner_tol < 1
+    L = kpcg.lib()
+    assert L.kpcg_status_string(0) == b"KPCG_OK"
+    assert L.kpcg_status_string(6) == b"KPCG_ERR_NO_CONVERGENCE"
+
+
+def test_create_rejects_host_pointer_without_gpu(built):
+    # A host pointer is refused with KPCG_ERR_ARG (or a CUDA error when no
+    # driver is present); the library never falls back to the CPU.
+    import ctypes
+    import numpy as np
+    import paper_1602_06693_gb300 as kpcg
+    L = kpcg.lib()
+    X = np.zeros((4, 2), dtype=np.float32)
+    lt = np.zeros(3)
+    h = ctypes.c_void_p()
+    st = L.kpcg_create(ctypes.c_void_p(X.ctypes.data), 4, 2,
+                       lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, 0.1, None, None,
+                       ctypes.byref(h))
+    assert st != 0 and not h.value
+    assert L.kpcg_last_error(None)
+
+
+def test_oracle_and_library_share_no_code():
+    # The oracle is plain C in oracle/, the CUDA path lives in the package:
+    # neither includes or imports the other.
+    csrc = os.path.join(ROOT, "paper_1602_06693_gb300")
+    for dirpath, _, files in os.walk(csrc):
+        for f in files:
+            if f.endswith((".cu", ".cuh", ".py", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f == "__init__.py", f
+    otxt = open(os.path.join(ROOT, "oracle", "kpcg_oracle.c")).read()
+    assert "kpcg.h" not in otxt and "csrc" not in otxt

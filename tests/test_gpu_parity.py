@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Every input is seeded and synthetic (``synthetic``); expected values come
+from ``oracle`` only.  Tolerances:
+  * FP64 products: 1e-12 relative (both sides FP64, direct differences;
+    the GPU centres X before scaling, which only reorders rounding).
+  * FP32 products: 2e-5 relative.  Each FP32 entry carries ~2^-22 from
+    ex2.approx plus |arg| * 2^-24 from the FP32 inputs; sums of n terms
+    stay within 2e-5 of the norm for the sizes tested.
+  * Solves: FP64-recomputed relative residual <= 1e-8 and solution error
+    <= 1e-5 against the oracle's dense Cholesky solve.
+  * Gradients: 1e-4 relative against the oracle's stochastic gradient with
+    the same probes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def kpcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1602_06693_gb300 as k
+    from paper_1602_06693_gb300 import build
+    build.build()
+    return k
+
+
+DEV = "cuda:0"
+
+
+def _cm(a, dtype=torch.float64):
+    """numpy (n, c) -> column-major CUDA tensor."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        return torch.from_numpy(a.copy()).to(DEV, dtype)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(DEV, dtype).t()
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _solver(kpcg, p, precision=None, **kw):
+    opt = kpcg.default_options(**kw)
+    if precision is not None:
+        opt.precision = precision
+    return kpcg.Solver(torch.from_numpy(p.X).to(DEV), p.log_theta, p.noise, ard=p.ard,
+                       options=opt)
+
+
+def _problem(n, d, seed, noise=0.05, ard=True, dist="normal", ell=None):
+    if ell is None:
+        ell = "loguniform" if ard else 1.0
+    return synthetic.make_problem(n, d, seed, dist=dist, ard=ard, ell=ell, noise=noise)
+
+
+# ------------------------------------------------------------------ K.V
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 17),
+                                   (700, 32, 2), (513, 12, 9)])
+def test_matvec_f64_matches_oracle(kpcg, n, d, c):
+    p = _problem(n, d, seed=n + d)
+    V = synthetic.rng(5).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(_cm(V)))
+    assert _rel(out, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (255, 2, 1), (1000, 8, 3), (4099, 16, 17),
+                                   (700, 32, 5)])
+def test_matvec_f32_matches_oracle(kpcg, n, d, c):
+    p = _problem(n, d, seed=7 * n + d)
+    V = synthetic.rng(6).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=0))
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= 2e-5
+
+
+def test_matvec_isotropic_and_leading_dimension(kpcg):
+    p = _problem(300, 5, seed=3, ard=False, ell=0.7)
+    V = synthetic.rng(1).standard_normal((300, 2))
+    ell, s2 = oracle.split_theta(p.log_theta, 5, False)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    big = torch.zeros((2, 320), dtype=torch.float64, device=DEV)
+    big[:, :300] = torch.from_numpy(V.T.copy()).to(DEV)
+    Vld = big.t()[:300]  # leading dimension 320
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(Vld))
+    assert _rel(out, ref) <= 1e-12
+
+
+# ------------------------------------------------------- preconditioners
+def test_block_jacobi_apply_matches_oracle(kpcg):
+    p = _problem(1100, 4, seed=11, noise=0.01)
+    ell, s2 = oracle.split_theta(p.log_theta, 4, True)
+    P = oracle.BlockJacobi(p.X, ell, s2, p.noise, 256)  # blocks 256 x4 + 76
+    R = synthetic.rng(2).standard_normal((1100, 3))
+    with _solver(kpcg, p) as s:
+        s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, 256)
+        out = _np(s.precond_apply(_cm(R)))
+    assert _rel(out, P.apply(R)) <= 1e-9
+
+
+def test_nystrom_apply_matches_oracle(kpcg):
+    # The GPU stores K_XU in FP32 (relative perturbation <= 2^-24 (1+|arg|));
+    # P^-1 moves by at most about kappa(P) times that: with noise 0.1 and
+    # m = 64 this stays below 1e-4.
+    p = _problem(2000, 6, seed=12, noise=0.1)
+    ell, s2 = oracle.split_theta(p.log_theta, 6, True)
+    idx = synthetic.inducing_subset(2000, 64, seed=3)
+    P = oracle.Nystrom(p.X, ell, s2, p.noise, idx)
+    R = synthetic.rng(4).standard_normal((2000, 2))
+    with _solver(kpcg, p) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, len(idx), idx)
+        out = _np(s.precond_apply(_cm(R)))
+    assert _rel(out, P.apply(R)) <= 1e-4
+
+
+def test_nystrom_with_all_points_solves_in_one_step(kpcg):
+    # m = n makes P = K_y (Sec. 3.1), so PCG stops after one iteration.
+    p = _problem(64, 8, seed=7, noise=0.1, ell=1.0)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 64, np.arange(64))
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-10)
+    assert st == 0 and it[0] <= 2 and info.max_rel_res <= 1e-10
+
+
+# ------------------------------------------------------------------ solves
+@pytest.fixture(scope="module")
+def config1_ref():
+    p = synthetic.config1(seed=0)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    return p, oracle.dense_solve(p.X, ell, s2, p.noise, p.y)
+
+
+def test_config1_fp64_nystrom_solve(kpcg, config1_ref):
+    p, ref = config1_ref
+    idx = synthetic.inducing_subset(p.n, 256, seed=1)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 256, idx)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    x = _np(x)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    res = _rel(oracle.kyv(p.X, ell, s2, p.noise, x), p.y)
+    assert st == 0 and info.max_rel_res <= 1e-8 and res <= 1e-8
+    assert _rel(x, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["FP32_IR", "FP64"])
+def test_config1_other_precisions(kpcg, config1_ref, precision):
+    p, ref = config1_ref
+    prec = getattr(kpcg, "KPCG_" + precision)
+    idx = synthetic.inducing_subset(p.n, 256, seed=1)
+    with _solver(kpcg, p, precision=prec) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 256, idx)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    assert st == 0 and info.max_rel_res <= 1e-8
+    assert _rel(_np(x), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["nystrom", "bj", "none"])
+def test_ill_conditioned_mixed_precision_solve(kpcg, kind):
+    # The uniform-cube ARD workload with noise 1e-4, scaled down to n = 2048.
+    p = synthetic.config2(seed=0, n=2048)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    ref = oracle.dense_solve(p.X, ell, s2, p.noise, p.y)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+        if kind == "nystrom":
+            s.precond(kpcg.KPCG_PREC_NYSTROM, 512, synthetic.inducing_subset(p.n, 512, seed=1))
+        elif kind == "bj":
+            s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, 512)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    x = _np(x)
+    assert st == 0 and info.max_rel_res <= 1e-8, info.as_dict()
+    assert _rel(oracle.kyv(p.X, ell, s2, p.noise, x), p.y) <= 1e-8
+    assert _rel(x, ref) <= 1e-5
+
+
+def test_multi_rhs_block_with_zero_column_and_warm_start(kpcg):
+    p = _problem(1500, 5, seed=21, noise=0.02)
+    ell, s2 = oracle.split_theta(p.log_theta, 5, True)
+    B = np.column_stack([p.y, np.zeros(1500), synthetic.rademacher(1500, 3, 9)])
+    ref = oracle.dense_solve(p.X, ell, s2, p.noise, B)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 100, synthetic.inducing_subset(1500, 100, 2))
+        x, it, info, st = s.solve(_cm(B), tol=1e-9)
+        x = _np(x)
+        assert st == 0 and it[1] == 0 and np.all(x[:, 1] == 0)
+        for k in range(5):
+            if k != 1:
+                assert _rel(x[:, k], ref[:, k]) <= 1e-6
+        # starting from the solution: nothing left to do
+        x2, it2, info2, st2 = s.solve(_cm(B), tol=1e-8, X0=_cm(x))
+        assert st2 == 0 and info2.iters_total == 0
+
+
+def test_plain_fp32_pcg_reaches_fp32_accuracy(kpcg):
+    p = _problem(3000, 4, seed=5, noise=0.1)
+    ell, s2 = oracle.split_theta(p.log_theta, 4, True)
+    ref = oracle.dense_solve(p.X, ell, s2, p.noise, p.y)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP32) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 128, synthetic.inducing_subset(3000, 128, 0))
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-5)
+    assert st == 0 and info.max_rel_res <= 1e-5
+    assert _rel(_np(x), ref) <= 1e-3
+
+
+def test_paper_absolute_stop_rule(kpcg):
+    p = _problem(800, 3, seed=8, noise=0.01)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64, tol_mode=1) as s:
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-10)  # ||r||^2 < n 1e-10 (Sec. 4)
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    r = p.y - oracle.kyv(p.X, ell, s2, p.noise, _np(x))
+    assert st == 0 and r @ r < 800 * 1e-10
+
+
+def test_full_size_mixed_precision_solve_sampled_rows(kpcg):
+    # The n = 65536, d = 8, noise 1e-4 uniform-cube ARD system with Nystrom
+    # m = 1024, as timed by the benchmark.  The residual is checked on 48
+    # sampled rows, each recomputed by the oracle row by row in FP64.
+    p = synthetic.config2(seed=0)
+    idx = synthetic.inducing_subset(p.n, 1024, seed=1)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 1024, idx)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    x = _np(x)
+    assert st == 0 and info.max_rel_res <= 1e-8, info.as_dict()
+    rows = np.sort(synthetic.rng(3).choice(p.n, 48, replace=False))
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    Krow = oracle.gram(p.X[rows], p.X, ell, s2)
+    r = p.y[rows] - (Krow @ x + p.noise * x[rows])
+    # per-row bound implied by the global one: |r_i| <= ||r|| <= 1e-8 ||y||
+    assert np.abs(r).max() <= 1e-8 * np.linalg.norm(p.y)
+
+
+# ------------------------------------------------------------- gradients
+def test_dkv_matches_oracle(kpcg):
+    p = _problem(900, 6, seed=31)
+    W = synthetic.rng(8).standard_normal((900, 5))
+    ell, s2 = oracle.split_theta(p.log_theta, 6, True)
+    ref = oracle.dkv(p.X, ell, s2, W)  # (d+1, n, c)
+    with _solver(kpcg, p) as s:
+        G = _np(s.dkv(_cm(W)))
+    for q in range(7):
+        assert _rel(G[q], ref[q]) <= 2e-5, q
+
+
+def test_dkv_isotropic_pools_dimensions(kpcg):
+    p = _problem(400, 3, seed=32, ard=False, ell=0.8)
+    W = synthetic.rng(9).standard_normal((400, 2))
+    ell, s2 = oracle.split_theta(p.log_theta, 3, False)
+    ref = oracle.dkv(p.X, ell, s2, W)
+    with _solver(kpcg, p) as s:
+        G = _np(s.dkv(_cm(W)))
+    assert G.shape[0] == 2
+    assert _rel(G[0], ref[:3].sum(axis=0)) <= 2e-5
+    assert _rel(G[1], ref[3]) <= 2e-5
+
+
+@pytest.mark.parametrize("ard", [True, False])
+def test_stochastic_gradient_matches_oracle(kpcg, ard):
+    n, t = 1200, 8
+    p = _problem(n, 4, seed=41, noise=0.05, ard=ard, ell=None if ard else 0.9)
+    R = synthetic.rademacher(n, t, seed=5)
+    gref = oracle.grad_stochastic(p.X, p.log_theta, p.noise, p.y, R, ard=ard)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 120, synthetic.inducing_subset(n, 120, 1))
+        g, alpha, info = s.grad(_cm(p.y), _cm(R), tol=1e-10, want_alpha=True)
+    assert g.shape == gref.shape
+    np.testing.assert_allclose(g, gref, rtol=1e-4, atol=1e-4 * np.abs(gref).max())
+    ell, s2 = oracle.split_theta(p.log_theta, 4, ard)
+    assert _rel(_np(alpha), oracle.dense_solve(p.X, ell, s2, p.noise, p.y)) <= 1e-6
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_arguments_are_reported(kpcg):
+    p = _problem(50, 2, seed=1)
+    X = torch.from_numpy(p.X).to(DEV)
+    with pytest.raises(kpcg.KpcgError) as e:
+        kpcg.Solver(X, p.log_theta, -1.0)
+    assert e.value.name == "KPCG_ERR_ARG"
+    with _solver(kpcg, p) as s:
+        with pytest.raises(kpcg.KpcgError):
+            s.precond(kpcg.KPCG_PREC_NYSTROM, 3, np.array([0, 0, 1]))  # not distinct
+        with pytest.raises(kpcg.KpcgError):
+            s.precond(kpcg.KPCG_PREC_NYSTROM, 2, np.array([0, 50]))  # out of range
+        with pytest.raises(kpcg.KpcgError):
+            s.set_theta(np.array([np.nan, 0.0, 0.0]), 0.1)
+
+
+def test_iteration_cap_reports_no_convergence(kpcg):
+    p = _problem(2000, 3, seed=2, noise=1e-4)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64, max_iter=3) as s:
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-10, raise_on_error=False)
+    assert st == 6 and info.iters_total <= 3 and np.all(np.isfinite(_np(x)))
