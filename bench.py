@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: PCG time-to-relative-residual 1e-8 on the n = 65536 kernel system.
+
+Workload (one "step"): the ARD-RBF system (K + sigma^2 I) alpha = y with
+n = 65536, d = 8, X ~ U[0,1]^8, l_r ~ LogUniform(0.3, 3), s = 1, sigma^2 = 1e-4
+(seeded, synthetic), Nystrom preconditioner with m = 1024 random inducing
+points built inside the step, solved to ||y - K_y alpha|| <= 1e-8 ||y|| by the
+mixed-precision solver (outer flexible CG in FP64, inner FP32 PCG).  Inputs are
+resident in HBM when the timed region starts; L2 is flushed between steps.
+
+Printed: one JSON line with the time per solve (seconds, lower is better), the
+end-to-end time through the C ABI from host buffers, the roofline of the
+dominant kernel, the FP64 CPU oracle's time on a bounded sample of the same
+workload, and the plain-FP32 PCG comparison on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kpcg|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic  # noqa: E402
+
+N_FULL, D, M_INDUCING, TOL = 65536, 8, 1024, 1e-8
+METRIC = "PCG time-to-rel-res 1e-8 at n=65k vs plain FP32; K.V TFLOP/s vs roofline"
+WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum sin(x)+N(0,0.01); "
+            "Nystrom m=1024 built in-step; tol 1e-8 rel; 1 RHS")
+# Algorithmic work of one K.V entry (i, j) with c right-hand sides: d subtractions,
+# d multiplies and d adds for the squared distance, a multiply-add for the exponent,
+# one exponential, and c multiply-adds for the contraction.
+def flops_per_entry(d, c):
+    return 3 * d + 2 + 1 + 2 * c
+
+
+def sm_clock_probe():
+    """Start an nvidia-smi sampler; returns (stop_fn -> dict)."""
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    dev = os.environ.get("LOCAL_RANK", "0")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return lambda: {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    lines = []
+
+    def reader():
+        for ln in proc.stdout:
+            lines.append(ln.strip())
+
+    th = threading.Thread(target=reader, daemon=True)
+    th.start()
+
+    def stop():
+        proc.terminate()
+        try:
+            proc.wait(timeout=5)
+        except Exception:
+            proc.kill()
+        th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+    return stop
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(n=N_FULL, iters=2):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: its Nystrom
+    set-up plus `iters` PCG iterations at full size.  Scaled to a whole solve
+    with the iteration count the oracle's own complete run recorded."""
+    import oracle
+    p = synthetic.config2(seed=0, n=n)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    idx = synthetic.inducing_subset(n, M_INDUCING, seed=1)
+    t0 = time.perf_counter()
+    P = oracle.Nystrom(p.X, ell, s2, p.noise, idx)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pcg(p.X, ell, s2, p.noise, p.y, precond=P, tol=1e-30, max_iter=iters)
+    t_iters = time.perf_counter() - t0
+    # or_pcg also spends one K_y x for r0 and one for the final residual: iters + 2 products
+    per_iter = t_iters / (iters + 2)
+    rec_path = os.path.join(ROOT, "tests", "golden", f"oracle_pcg_n{n}.json")
+    n_iter, src = None, None
+    if os.path.exists(rec_path):
+        with open(rec_path) as f:
+            rec = json.load(f)
+        n_iter, src = int(rec["iterations"]), os.path.relpath(rec_path, ROOT)
+    est = t_setup + per_iter * (n_iter + 2) if n_iter else None
+    return {
+        "value": est,
+        "unit": "s",
+        "cores": oracle.num_threads(),
+        "kind": "oracle",
+        "sample": (f"FP64 oracle Nystrom set-up + {iters} PCG iterations at n={n} "
+                   f"({t_setup:.1f} s + {t_iters:.1f} s); whole solve = set-up + "
+                   f"{n_iter} iterations x {per_iter:.2f} s"
+                   + (f" (iteration count from {src})" if src else " (no recorded count)")),
+        "setup_s": t_setup,
+        "s_per_iteration": per_iter,
+    }
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    vals = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        base = oracle_sample(iters=1)
+        if s >= args.warmup:
+            vals.append(base["value"])
+    v = statistics.mean(vals) if vals and None not in vals else None
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3 if v else None,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {k: base[k] for k in ("kind", "cores", "sample")} | {"value": v,
+                                                                               "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------- GPU
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kpcg", choices=["kpcg", "reference"])
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--skip-baselines", action="store_true")
+    ap.add_argument("--fp32-max-iter", type=int, default=3000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = {"auto": kpcg.KPCG_FP32_IR, "fp32_ir": kpcg.KPCG_FP32_IR,
+            "tf32_ir": kpcg.KPCG_TF32_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+
+    # replicas: each rank solves its own seeded instance of the same workload
+    p = synthetic.config2(seed=rank, n=args.n)
+    idx = synthetic.inducing_subset(p.n, M_INDUCING, seed=1 + rank)
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    opt = kpcg.default_options(precision=prec, profile=1)
+    solver = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        solver.set_theta(p.log_theta, p.noise)  # drop the preconditioner: rebuilt in-step
+        solver.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
+        x, it, info, st = solver.solve(y, tol=TOL, raise_on_error=False)
+        return x, it, info, st
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+
+    stop_clock = sm_clock_probe()
+    times, infos = [], []
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, it, info, st = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append((info, st))
+    clocks = stop_clock()
+    t_step = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    info, st = infos[-1]
+
+    # roofline of the dominant kernel class, from the library's event timers
+    cats = {"kv_inner": (info.kv_inner_ms, info.kv_inner_calls),
+            "kv_outer_fp64": (info.kv_outer_ms, info.kv_outer_calls),
+            "precond_apply": (info.precond_ms, info.precond_calls)}
+    dom = max(cats, key=lambda k: cats[k][0])
+    ms, calls = cats[dom]
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if dom.startswith("kv"):
+        flops = flops_per_entry(D, 1) * float(p.n) ** 2
+        achieved = flops / (ms / calls / 1e3) / 1e12
+        if dom == "kv_outer_fp64":
+            peak = 1.25  # nominal GB300 FP64 rate (no FP64 figure is measured)
+            peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
+        else:
+            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+            peak_src = f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz"
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_src, "calls": calls, "avg_ms": ms / calls,
+                "flops_per_call": flops}
+    else:
+        # Nystrom apply streams K_XU (n x m FP32) twice and reads/writes n-vectors
+        bytes_ = 2 * 4.0 * p.n * M_INDUCING + 3 * 4.0 * p.n
+        achieved = bytes_ / (ms / calls / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "calls": calls,
+                "avg_ms": ms / calls}
+
+    # end to end through the C ABI from host buffers
+    Xh = torch.from_numpy(p.X).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(3.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Xd = Xh.to(dev, non_blocking=True)
+        yd = yh.to(dev, non_blocking=True)
+        s2 = kpcg.Solver(Xd, p.log_theta, p.noise, ard=True, options=opt)
+        s2.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
+        xs, _, _, _ = s2.solve(yd, tol=TOL, raise_on_error=False)
+        xh.copy_(xs, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(time.perf_counter() - t0)
+        s2.close()
+    e2e = {"value": statistics.mean(e2e_times), "unit": "s",
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + idx.nbytes),
+           "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.skip_baselines:
+        # plain FP32 PCG on the same GPU, same preconditioner
+        o32 = kpcg.default_options(precision=kpcg.KPCG_FP32, max_iter=args.fp32_max_iter,
+                                   max_restarts=0)
+        s32 = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=o32)
+        t0 = time.perf_counter()
+        s32.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
+        x32, it32, inf32, st32 = s32.solve(y, tol=TOL, raise_on_error=False)
+        torch.cuda.synchronize(dev)
+        t32 = time.perf_counter() - t0
+        extra["fp32_pcg"] = {"status": st32, "time_s": t32, "iters": int(inf32.iters_total),
+                             "final_rel_res_fp64": inf32.max_rel_res,
+                             "reached_tol": bool(st32 == 0),
+                             "note": f"plain FP32 PCG, capped at {args.fp32_max_iter} iterations"}
+        s32.close()
+        try:
+            extra["cpu_baseline"] = oracle_sample()
+        except Exception as e:  # the baseline never blocks the GPU line
+            extra["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+
+    launches_per_step = int(info.launches)  # counted by the library inside the solve
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "precision": args.precision},
+        "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
+                  "max_rel_res_fp64": info.max_rel_res, "setup_ms": info.setup_ms,
+                  "kv_inner_ms": info.kv_inner_ms, "kv_inner_calls": info.kv_inner_calls,
+                  "kv_outer_ms": info.kv_outer_ms, "kv_outer_calls": info.kv_outer_calls,
+                  "precond_ms": info.precond_ms, "precond_calls": info.precond_calls,
+                  "step_times_s": times},
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -62,32 +62,53 @@ typedef enum {
     KPCG_FP64 = 0,     /* FP64 entries, vectors and scalars throughout           */
     KPCG_FP32 = 1,     /* plain FP32 PCG: FP32 entries (direct differences),
                           FP32 vectors; no refinement                            */
-    KPCG_FP32_IR = 2,  /* inner FP32 PCG refined by FP64 outer residuals         */
-    KPCG_TF32_IR = 3   /* inner PCG on the tensor-core K.V (tcgen05, TF32 split
-                          distances, FP32 accumulate) refined by FP64 residuals  */
+    KPCG_FP32_IR = 2,  /* mixed: outer flexible CG (Notay) in FP64 whose
+                          preconditioner is an inner FP32 PCG on the shifted
+                          operator K + sigma^2 (1 + inner_shift) I               */
+    KPCG_TF32_IR = 3   /* as KPCG_FP32_IR, the inner K.V on the tensor cores
+                          (tcgen05, TF32 split distances, FP32 accumulate)       */
 } kpcg_precision;
 
 typedef struct {
-    int32_t max_iter;     /* CG iterations per solve (all inner ones in IR
+    int32_t max_iter;     /* CG iterations per solve (all inner ones in mixed
                              modes); default 100000 (the paper's cap, Sec. 4)  */
-    int32_t precision;    /* kpcg_precision; default KPCG_TF32_IR              */
+    int32_t precision;    /* kpcg_precision; default KPCG_FP32_IR              */
     int32_t tol_mode;     /* 0: ||b - K_y x|| <= tol ||b|| per column (default);
                              1: the paper's absolute ||r||^2 < n*tol (Sec. 4)  */
-    int32_t max_outer;    /* refinement steps in IR modes; default 40          */
-    double inner_tol;     /* relative reduction asked of each inner solve in
-                             IR modes; default 1e-4                            */
+    int32_t max_outer;    /* outer flexible-CG steps in mixed modes; def. 60   */
+    double inner_tol;     /* relative residual reduction asked of each inner
+                             solve in mixed modes; default 1e-2               */
     int32_t check_every;  /* host polls convergence every k iterations; def. 4 */
-    int32_t max_restarts; /* residual-replacement restarts in non-IR modes;
-                             default 5                                         */
+    int32_t max_restarts; /* residual-replacement restarts in single-precision
+                             modes; default 5                                  */
+    double inner_shift;   /* mixed modes: the inner operator and the
+                             preconditioner use noise sigma^2 (1 + inner_shift),
+                             which keeps the reduced-precision inner system
+                             positive definite; default 1.0                    */
+    int32_t inner_max_iter; /* CG iterations per inner solve; default 2000    */
+    int32_t fcg_window;   /* A-orthogonal directions kept by the outer
+                             flexible CG; default 16                           */
+    int32_t profile;      /* 1: time every K.V and preconditioner call with CUDA
+                             events on the handle's stream and report the sums
+                             in kpcg_info; default 0                           */
 } kpcg_options;
 
 typedef struct {
     int32_t iters_total;  /* CG iterations run (sum over inner solves)          */
-    int32_t outer_steps;  /* FP64 residual evaluations (IR modes), else restarts */
+    int32_t outer_steps;  /* outer flexible-CG steps (mixed modes), else restarts */
     double max_rel_res;   /* max over columns of ||b - K_y x|| / ||b||,
                              recomputed in FP64 on the device at return        */
     double time_ms;       /* wall time of the call on the host                  */
     double setup_ms;      /* part of time_ms spent in preconditioner set-up     */
+    /* Filled when opt.profile = 1 (device time from CUDA events), else 0:     */
+    double kv_inner_ms;   /* reduced-precision K.V calls (mixed modes) or the
+                             working-precision K.V calls (single modes)        */
+    int32_t kv_inner_calls;
+    int32_t kv_outer_calls;
+    double kv_outer_ms;   /* FP64 K.V calls of the outer loop and residuals    */
+    double precond_ms;    /* preconditioner applications                       */
+    int32_t precond_calls;
+    int32_t launches;     /* CUDA kernels this call launched (always filled)   */
 } kpcg_info;
 
 /* Fill *opt with the defaults documented in kpcg_options. */
@@ -107,7 +128,8 @@ kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_
                         void* stream, kpcg_t* out);
 
 /* Replace the hyperparameters (host log_theta, same length as at create).
- * Drops the preconditioner, which must be rebuilt with kpcg_precond. */
+ * The preconditioner is rebuilt for the new theta, from the last
+ * kpcg_precond request, at the next call that needs it. */
 kpcg_status kpcg_set_theta(kpcg_t h, const double* log_theta, double noise_var);
 
 /* Replace the options (host struct). */
@@ -123,7 +145,10 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt);
  *   KPCG_PREC_BLOCK_JACOBI: size = b, idx ignored; contiguous blocks of b rows,
  *     the last one shorter, P = bldiag(K_y) (Sec. 3.3.1).
  *   KPCG_PREC_NONE: removes the preconditioner.
- * Returns KPCG_ERR_NOT_SPD if a factorization fails. */
+ * In the mixed modes the preconditioner approximates the inner operator, so
+ * it is built with noise sigma^2 (1 + inner_shift); it is rebuilt when the
+ * mode or the shift changes.  Returns KPCG_ERR_NOT_SPD if a factorization
+ * fails (the handle is then left without a preconditioner). */
 kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx);
 
 /* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
@@ -138,7 +163,8 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 
-/* Z = P^{-1} R with the current preconditioner (device float64). */
+/* Z = P^{-1} R with the preconditioner as built for the current mode
+ * (device float64). */
 kpcg_status kpcg_precond_apply_f64(kpcg_t h, const double* R, int64_t ldr, int32_t c, double* Z,
                                    int64_t ldz);
 

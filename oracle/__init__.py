@@ -66,7 +66,7 @@ def _load():
             lib.or_bj_apply.argtypes = [_i64, _i64, _d, _d, _i64, _int, _d, _i64]
             lib.or_pcg.argtypes = [_d, _i64, _int, _d, ctypes.c_double, ctypes.c_double, _int,
                                    _d, _d, _i64, _d, _i64, _d, _i64, _int, ctypes.c_double, _int,
-                                   _int, _d, _d, _i64, ctypes.POINTER(ctypes.c_int), _d]
+                                   _int, _d, _d, _i64, ctypes.POINTER(ctypes.c_int), _d, _d]
             lib.or_pcg.restype = _int
             _lib = lib
     return _lib
@@ -238,11 +238,14 @@ class BlockJacobi:
         return Z[:, 0] if np.ndim(R) == 1 else Z
 
 
-def pcg(X, ell, s2, noise, B, *, precond=None, tol=1e-8, tol_mode=0, max_iter=100000, X0=None):
+def pcg(X, ell, s2, noise, B, *, precond=None, tol=1e-8, tol_mode=0, max_iter=100000, X0=None,
+        history=False):
     """Algorithm 1 (textbook form) on each column of B.
 
     Returns (Xsol, iters, relres, rc): iters per column (-1 = breakdown),
     relres = recomputed ||b - K_y x|| / ||b||, rc 0 ok / 1 max_iter / 2 breakdown.
+    With history=True a fifth item holds the first column's recursive
+    relative residual before each iteration.
     """
     Xd = _f64c(X)
     n, d = Xd.shape
@@ -259,13 +262,16 @@ def pcg(X, ell, s2, noise, B, *, precond=None, tol=1e-8, tol_mode=0, max_iter=10
     m = precond.m if kind == 1 else 0
     b = precond.b if kind == 2 else 0
     nul = ctypes.cast(None, _d)
+    hist = np.full(max_iter + 1, np.nan) if history else None
     rc = _load().or_pcg(_p(Xd), n, d, _p(_f64c(ell)), float(s2), float(noise), kind,
                         _p(KXU) if KXU is not None else nul, _p(LM) if LM is not None else nul, m,
                         _p(Lbj) if Lbj is not None else nul, b, _p(Bf), n, c, float(tol),
                         int(tol_mode), int(max_iter), _p(X0f) if X0f is not None else nul,
-                        _p(out), n, iters, _p(rel))
+                        _p(out), n, iters, _p(rel), _p(hist) if history else nul)
     it = np.array(list(iters), dtype=np.int64)
     sol = out[:, 0] if np.ndim(B) == 1 else out
+    if history:
+        return sol, it, rel, int(rc), hist[: max(int(it[0]), 0) + 1]
     return sol, it, rel, int(rc)
 
 

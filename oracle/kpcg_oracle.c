@@ -263,6 +263,8 @@ void or_bj_apply(int64_t n, int64_t b, const double* Lbj, const double* R, int64
  * iters[k] receives the CG iterations of column k (-1 on breakdown),
  * relres[k] the recomputed ||b - K_y x|| / ||b||.  Returns 0 if every
  * column converged, 1 if some hit max_iter, 2 on a breakdown.
+ * hist (nullable, max_iter + 1 entries) receives, for the first column, the
+ * recursive ||r_i|| / ||b|| before each iteration i (entry 0: initial).
  * --------------------------------------------------------------------- */
 typedef struct {
     int kind;
@@ -290,7 +292,8 @@ static double dotc(const double* a, const double* b, int64_t n) {
 int or_pcg(const double* X, int64_t n, int d, const double* ell, double s2, double sigma2, int kind,
            const double* KXU, const double* LM, int64_t m, const double* Lbj, int64_t b,
            const double* B, int64_t ldb, int c, double tol, int tol_mode, int max_iter,
-           const double* X0, double* Xout, int64_t ldx, int* iters, double* relres) {
+           const double* X0, double* Xout, int64_t ldx, int* iters, double* relres,
+           double* hist) {
     precond_t P = {kind, n, m, b, sigma2, KXU, LM, Lbj};
     int rc = 0;
     double* x = (double*)malloc(sizeof(double) * (size_t)n);
@@ -309,6 +312,7 @@ int or_pcg(const double* X, int64_t n, int d, const double* ell, double s2, doub
             continue;
         }
         double thr2 = (tol_mode == 1) ? (double)n * tol : tol * tol * bnorm * bnorm;
+        double* hk = (k == 0) ? hist : NULL;
         int restarts = 0, it = 0, done = 0, broke = 0;
         while (!done) {
             /* (re)start: r = b - K_y x */
@@ -319,6 +323,7 @@ int or_pcg(const double* X, int64_t n, int d, const double* ell, double s2, doub
             papply(&P, r, n, 1, z, n);
             for (int64_t i = 0; i < n; ++i) p[i] = z[i];
             double rho = dotc(r, z, n);
+            if (hk) hk[it] = sqrt(dotc(r, r, n)) / bnorm;
             int conv = 0;
             while (it < max_iter) {
                 or_kyv(X, n, d, ell, s2, sigma2, p, n, 1, q, n);
@@ -330,7 +335,9 @@ int or_pcg(const double* X, int64_t n, int d, const double* ell, double s2, doub
                     x[i] += alpha * p[i];
                     r[i] -= alpha * q[i];
                 }
-                if (dotc(r, r, n) <= thr2) { conv = 1; break; }
+                double rr = dotc(r, r, n);
+                if (hk) hk[it] = sqrt(rr) / bnorm;
+                if (rr <= thr2) { conv = 1; break; }
                 papply(&P, r, n, 1, z, n);
                 double rho1 = dotc(r, z, n);
                 double beta = rho1 / rho;

@@ -41,6 +41,10 @@ class Options(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("check_every", ctypes.c_int32),
         ("max_restarts", ctypes.c_int32),
+        ("inner_shift", ctypes.c_double),
+        ("inner_max_iter", ctypes.c_int32),
+        ("fcg_window", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
     ]
 
 
@@ -51,6 +55,13 @@ class Info(ctypes.Structure):
         ("max_rel_res", ctypes.c_double),
         ("time_ms", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
+        ("kv_inner_ms", ctypes.c_double),
+        ("kv_inner_calls", ctypes.c_int32),
+        ("kv_outer_calls", ctypes.c_int32),
+        ("kv_outer_ms", ctypes.c_double),
+        ("precond_ms", ctypes.c_double),
+        ("precond_calls", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
     ]
 
     def as_dict(self):

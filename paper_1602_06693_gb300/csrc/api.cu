@@ -25,6 +25,10 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
              std::to_string(line) + ")");
 }
 
+static thread_local long long g_launches = 0;
+void note_launch() { ++g_launches; }
+long long launch_count() { return g_launches; }
+
 int padded_dim(int d) {
     if (d <= 4) return 4;
     if (d <= 8) return 8;
@@ -201,7 +205,9 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
 static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const double* X, int64_t ldx,
                          double* R, std::vector<double>& rr, std::vector<double>& bb) {
     cudaStream_t st = h.stream;
-    kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, X, ldx, c, B, ldb, R, h.ld, h.kvws, st);
+    h.prof.time(Profiler::KV_OUTER, st, [&] {
+        kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, X, ldx, c, B, ldb, R, h.ld, h.kvws, st);
+    });
     const int nblk = dot_blocks(h.n);
     double* partial = h.partial.need((size_t)nblk * c * 2);
     dot_cols<double>(R, h.ld, R, h.ld, h.n, c, partial, nblk, st);
@@ -224,10 +230,211 @@ static bool col_converged(double rr, double bb, double tol, int tol_mode, int64_
     return tol_mode == 1 ? rr < (double)n * tol : rr <= tol * tol * bb;
 }
 
+
+// Noise of the system the preconditioner approximates: sigma^2 for the
+// single-precision solvers, the shifted inner noise for the mixed ones.
+static double precond_noise(const Ctx& h) {
+    const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TF32_IR;
+    return mixed ? h.noise * (1.0 + h.opt.inner_shift) : h.noise;
+}
+
+static void build_precond(Ctx& h) {
+    h.P.reset();
+    const double nz = precond_noise(h);
+    if (h.pkind == KPCG_PREC_NYSTROM)
+        nystrom_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), nz,
+                      h.pidx.data(), h.psize, h.stream);
+    else if (h.pkind == KPCG_PREC_BLOCK_JACOBI)
+        block_jacobi_setup(h.P, h.xs64.p, h.n, h.dp, h.c0_64(), nz,
+                           std::min<int64_t>(h.psize, h.n), h.stream);
+    h.P.n = h.n;
+    h.P.noise = nz;
+    KPCG_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+// Rebuild the preconditioner if theta, the noise or the mode changed since.
+static double ensure_precond(Ctx& h) {
+    h.P.n = h.n;
+    if (h.pkind == KPCG_PREC_NONE) return 0.0;
+    if (h.P.ready && h.P.noise == precond_noise(h)) return 0.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    build_precond(h);
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Mixed precision.  Outer: flexible CG (Notay's FCG, the outer loop the
+// paper uses around an inexact inner solve, Sec. 3.3.2) in FP64 with the
+// FP64 operator; the A-orthogonalisation runs over a window of the last
+// fcg_window directions.  Its preconditioner is an inner PCG in FP32 on the
+// shifted operator K + sigma^2 (1 + shift) I, solved to inner_tol on the
+// normalised residual.  The shift keeps the FP32 system positive definite
+// when the FP32 rounding of K is not small against sigma^2; the outer loop
+// removes the difference.  Columns are independent throughout.
+static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double tol,
+                             const double* X0, double* Xout, int64_t ldx,
+                             std::vector<int>& iters_col, int& iters_total, int& steps,
+                             std::vector<double>& rr, std::vector<double>& bb) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n, ld = h.ld;
+    const int W = std::max(1, h.opt.fcg_window);
+    const bool tc = (h.opt.precision == KPCG_TF32_IR);
+    const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
+    double* R = h.R64.need((size_t)ld * c);
+    double* Pw = h.fcgP.need((size_t)W * ld * c);
+    double* APw = h.fcgAP.need((size_t)W * ld * c);
+    double* Z = h.Q64.need((size_t)ld * c);
+    float* b32 = h.c32.b.need((size_t)ld * c);
+    float* d32 = h.c32.x.need((size_t)ld * c);
+    double* cs = h.colscale.need((size_t)c * (W + 2));
+    const int nblk = dot_blocks(n);
+    double* partial = h.partial.need((size_t)nblk * c * (W + 2));
+    std::vector<double> hp;
+    auto dots = [&](int nd, const std::vector<std::pair<const double*, const double*>>& pairs,
+                    std::vector<double>& out) {
+        for (int t = 0; t < nd; ++t)
+            dot_cols<double>(pairs[t].first, ld, pairs[t].second, ld, n, c,
+                             partial + (size_t)t * nblk * c, nblk, st);
+        hp.resize((size_t)nd * nblk * c);
+        KPCG_CUDA(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        out.assign((size_t)nd * c, 0.0);
+        for (int t = 0; t < nd; ++t)
+            for (int k = 0; k < c; ++k)
+                for (int b2 = 0; b2 < nblk; ++b2)
+                    out[(size_t)t * c + k] += hp[((size_t)t * c + k) * nblk + b2];
+    };
+    if (X0)
+        copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
+    else
+        fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
+    residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+    std::vector<double> pAp((size_t)W * c, 1.0), coef((size_t)c), d;
+    std::vector<int> dead((size_t)c, 0);
+    int nwin = 0, head = 0, stall = 0, recheck = 0;
+    double best = INFINITY;
+    kpcg_status status = KPCG_OK;
+    for (int outer = 0;; ++outer) {
+        bool all = true;
+        double worst = 0.0;
+        std::vector<double> scale((size_t)c, 0.0);
+        for (int k = 0; k < c; ++k) {
+            const bool ok = dead[k] || col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
+            all = all && ok;
+            scale[k] = ok ? 0.0 : std::sqrt(rr[k]);
+            if (bb[k] > 0 && !dead[k]) worst = std::max(worst, std::sqrt(rr[k] / bb[k]));
+        }
+        steps = outer;
+        if (all) {
+            // certify on the recomputed residual; continue from it if the
+            // recursive one drifted
+            if (recheck) break;
+            residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+            recheck = 1;
+            nwin = 0;
+            --outer;
+            continue;
+        }
+        recheck = 0;
+        if (outer >= h.opt.max_outer || iters_total >= h.opt.max_iter) {
+            status = KPCG_ERR_NO_CONVERGENCE;
+            break;
+        }
+        if (worst < best * 0.9) {
+            best = worst;
+            stall = 0;
+        } else if (++stall >= 4) {
+            status = KPCG_ERR_NO_CONVERGENCE;
+            break;
+        }
+        // z = ||r|| * M(r / ||r||): inner FP32 PCG on the shifted operator
+        KPCG_CUDA(cudaMemcpyAsync(cs, scale.data(), sizeof(double) * c, cudaMemcpyHostToDevice,
+                                  st));
+        convert_scale_cols<float, double>(b32, ld, R, ld, n, c, cs, 1, st);
+        std::vector<int> its;
+        int br = 0;
+        const int budget = std::min(h.opt.inner_max_iter, h.opt.max_iter - iters_total);
+        const int ran = pcg_core<float>(
+            h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, std::max(1, budget),
+            [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+                h.prof.time(Profiler::KV_INNER, st, [&] {
+                    if (tc)
+                        kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
+                    else
+                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), inner_noise, V, ldv, cc, O, ldo,
+                               h.kvws, st);
+                });
+            },
+            [&](const float* Rr, int64_t ldr, int cc, float* Zz, int64_t ldz) {
+                h.prof.time(Profiler::PRECOND, st, [&] {
+                    precond_apply_f32(h.P, Rr, ldr, cc, Zz, ldz, st);
+                });
+            },
+            h.c32, its, br);
+        iters_total += ran;
+        for (int k = 0; k < c; ++k) iters_col[k] += (its[k] < 0 ? -1 - its[k] : its[k]);
+        convert_scale_cols<double, float>(Z, ld, d32, ld, n, c, cs, 0, st);
+        // p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j over the window
+        double* p = Pw + (size_t)head * ld * c;
+        double* q = APw + (size_t)head * ld * c;
+        if (nwin > 0) {
+            std::vector<std::pair<const double*, const double*>> pr;
+            std::vector<int> slot;
+            for (int t = 0; t < nwin; ++t) {
+                const int j = (head - 1 - t + W) % W;
+                slot.push_back(j);
+                pr.push_back({Z, APw + (size_t)j * ld * c});
+            }
+            dots(nwin, pr, d);
+            std::vector<double> hc((size_t)nwin * c);
+            for (int t = 0; t < nwin; ++t)
+                for (int k = 0; k < c; ++k)
+                    hc[(size_t)t * c + k] = -d[(size_t)t * c + k] / pAp[(size_t)slot[t] * c + k];
+            KPCG_CUDA(cudaMemcpyAsync(cs + c, hc.data(), sizeof(double) * hc.size(),
+                                      cudaMemcpyHostToDevice, st));
+            copy_cols<double>(p, ld, Z, ld, n, c, st);
+            for (int t = 0; t < nwin; ++t)
+                axpy_cols_f64(p, ld, Pw + (size_t)slot[t] * ld * c, ld, n, c,
+                              cs + c + (size_t)t * c, st);
+        } else {
+            copy_cols<double>(p, ld, Z, ld, n, c, st);
+        }
+        h.prof.time(Profiler::KV_OUTER, st, [&] {
+            kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, p, ld, c, nullptr, 0, q, ld, h.kvws, st);
+        });
+        dots(2, {{p, q}, {p, R}}, d);
+        std::vector<double> al((size_t)c, 0.0), nal((size_t)c);
+        for (int k = 0; k < c; ++k) {
+            const double pq = d[k], pr = d[(size_t)c + k];
+            pAp[(size_t)head * c + k] = (pq > 0.0) ? pq : 1.0;
+            if (scale[k] > 0.0 && pq > 0.0 && std::isfinite(pq) && std::isfinite(pr))
+                al[k] = pr / pq;
+            else if (scale[k] > 0.0 && !(pq > 0.0))
+                dead[k] = 1;  // breakdown of the outer recurrence for this column
+            nal[k] = -al[k];
+        }
+        KPCG_CUDA(cudaMemcpyAsync(cs + c, al.data(), sizeof(double) * c, cudaMemcpyHostToDevice,
+                                  st));
+        KPCG_CUDA(cudaMemcpyAsync(cs + 2 * c, nal.data(), sizeof(double) * c,
+                                  cudaMemcpyHostToDevice, st));
+        axpy_cols_f64(Xout, ldx, p, ld, n, c, cs + c, st);
+        axpy_cols_f64(R, ld, q, ld, n, c, cs + 2 * c, st);
+        head = (head + 1) % W;
+        nwin = std::min(nwin + 1, W);
+        dots(1, {{R, R}}, rr);
+    }
+    for (int k = 0; k < c; ++k)
+        if (dead[k] && status == KPCG_OK) status = KPCG_ERR_BREAKDOWN;
+    return status;
+}
+
 static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                               const double* X0, double* Xout, int64_t ldx, int32_t* iters_host,
                               kpcg_info* info) {
     const auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = launch_count();
+    const double setup_ms = ensure_precond(h);
+    h.prof.on = (h.opt.profile != 0);
     cudaStream_t st = h.stream;
     const int64_t n = h.n, ld = h.ld;
     const int prec = h.opt.precision;
@@ -265,22 +472,30 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
                 ran = pcg_core<double>(
                     h, c, B, ldb, Xout, ldx, x0_zero, tol, h.opt.tol_mode, budget,
                     [&](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
-                        kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, V, ldv, cc, nullptr, 0, O,
-                               ldo, h.kvws, st);
+                        h.prof.time(Profiler::KV_INNER, st, [&] {
+                            kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, V, ldv, cc, nullptr, 0,
+                                   O, ldo, h.kvws, st);
+                        });
                     },
                     [&](const double* Rr, int64_t ldr, int cc, double* Z, int64_t ldz) {
-                        precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, st);
+                        h.prof.time(Profiler::PRECOND, st, [&] {
+                            precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, st);
+                        });
                     },
                     h.c64, its, br);
             } else {
                 ran = pcg_core<float>(
                     h, c, b32, ld, x32, ld, x0_zero, tol, h.opt.tol_mode, budget,
                     [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
-                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O, ldo,
-                               h.kvws, st);
+                        h.prof.time(Profiler::KV_INNER, st, [&] {
+                            kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O,
+                                   ldo, h.kvws, st);
+                        });
                     },
                     [&](const float* Rr, int64_t ldr, int cc, float* Z, int64_t ldz) {
-                        precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
+                        h.prof.time(Profiler::PRECOND, st, [&] {
+                            precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
+                        });
                     },
                     h.c32, its, br);
             }
@@ -324,70 +539,11 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
         }
         if (!f64) convert_scale_cols<double, float>(Xout, ldx, x32, ld, n, c, nullptr, 0, st);
     } else {
-        // Mixed precision: FP64 outer residuals, reduced-precision inner PCG
-        // on the normalised residual, x += ||r|| d (iterative refinement).
-        if (X0)
-            copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
-        else
-            fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
-        float* b32 = h.c32.b.need((size_t)ld * c);
-        float* d32 = h.c32.x.need((size_t)ld * c);
-        double* cs = h.colscale.need((size_t)c);
-        std::vector<double> hcs((size_t)c);
-        double best = INFINITY;
-        int stall = 0;
-        const bool tc = (prec == KPCG_TF32_IR);
-        for (int outer = 0;; ++outer) {
-            residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
-            bool all = true;
-            double worst = 0.0;
-            for (int k = 0; k < c; ++k) {
-                const bool ok = col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
-                all = all && ok;
-                hcs[k] = ok ? 0.0 : std::sqrt(rr[k]);
-                if (bb[k] > 0) worst = std::max(worst, std::sqrt(rr[k] / bb[k]));
-            }
-            steps = outer;
-            if (all) break;
-            if (outer >= h.opt.max_outer || iters_total >= h.opt.max_iter) {
-                status = KPCG_ERR_NO_CONVERGENCE;
-                break;
-            }
-            if (worst < best * 0.9) {
-                best = worst;
-                stall = 0;
-            } else if (++stall >= 3) {
-                status = KPCG_ERR_NO_CONVERGENCE;
-                break;
-            }
-            KPCG_CUDA(cudaMemcpyAsync(cs, hcs.data(), sizeof(double) * c, cudaMemcpyHostToDevice,
-                                      st));
-            convert_scale_cols<float, double>(b32, ld, R, ld, n, c, cs, 1, st);
-            std::vector<int> its;
-            int br = 0;
-            const int budget = h.opt.max_iter - iters_total;
-            const int ran = pcg_core<float>(
-                h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, budget,
-                [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
-                    if (tc)
-                        kv_tc_apply(h, V, ldv, cc, O, ldo);
-                    else
-                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O, ldo,
-                               h.kvws, st);
-                },
-                [&](const float* Rr, int64_t ldr, int cc, float* Z, int64_t ldz) {
-                    precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
-                },
-                h.c32, its, br);
-            iters_total += ran;
-            for (int k = 0; k < c; ++k) iters_col[k] += (its[k] < 0 ? -1 - its[k] : its[k]);
-            // a breakdown in the inner solve still leaves a usable correction
-            axpy_scaled_f64(Xout, ldx, d32, ld, n, c, cs, st);
-        }
+        status = fcg_solve(h, B, ldb, c, tol, X0, Xout, ldx, iters_col, iters_total, steps, rr, bb);
     }
     // FP64 residual of what is returned
     double maxrel = 0.0;
-    if (prec == KPCG_FP64 || prec == KPCG_FP32 || status != KPCG_OK || rr.empty())
+    if (prec == KPCG_FP64 || prec == KPCG_FP32 || rr.empty())
         residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
     bool all = true;
     for (int k = 0; k < c; ++k) {
@@ -404,7 +560,23 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
         info->time_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                 .count();
-        info->setup_ms = 0.0;
+        info->setup_ms = setup_ms;
+        double ms[Profiler::NCAT];
+        int calls[Profiler::NCAT];
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        h.prof.collect(ms, calls);
+        info->kv_inner_ms = ms[Profiler::KV_INNER];
+        info->kv_inner_calls = calls[Profiler::KV_INNER];
+        info->kv_outer_ms = ms[Profiler::KV_OUTER];
+        info->kv_outer_calls = calls[Profiler::KV_OUTER];
+        info->precond_ms = ms[Profiler::PRECOND];
+        info->precond_calls = calls[Profiler::PRECOND];
+        info->launches = (int)(launch_count() - launches0);
+    } else {
+        double ms[Profiler::NCAT];
+        int calls[Profiler::NCAT];
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        h.prof.collect(ms, calls);
     }
     if (status != KPCG_OK)
         h.err = std::string(kpcg_status_string(status)) +
@@ -439,10 +611,14 @@ void kpcg_default_options(kpcg_options* opt) {
     opt->max_iter = 100000;
     opt->precision = KPCG_FP32_IR;
     opt->tol_mode = 0;
-    opt->max_outer = 40;
-    opt->inner_tol = 1e-4;
+    opt->max_outer = 60;
+    opt->inner_tol = 1e-2;
     opt->check_every = 4;
     opt->max_restarts = 5;
+    opt->inner_shift = 1.0;
+    opt->inner_max_iter = 2000;
+    opt->fcg_window = 16;
+    opt->profile = 0;
 }
 
 const char* kpcg_status_string(kpcg_status s) {
@@ -467,6 +643,10 @@ static void check_opts(const kpcg_options* o) {
         fail(KPCG_ERR_ARG, "invalid precision");
     if (o->tol_mode != 0 && o->tol_mode != 1) fail(KPCG_ERR_ARG, "invalid tol_mode");
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) fail(KPCG_ERR_ARG, "inner_tol not in (0,1)");
+    if (!(o->inner_shift >= 0.0) || !std::isfinite(o->inner_shift))
+        fail(KPCG_ERR_ARG, "inner_shift must be >= 0");
+    if (o->inner_max_iter < 1 || o->fcg_window < 1 || o->fcg_window > 64)
+        fail(KPCG_ERR_ARG, "inner_max_iter >= 1 and fcg_window in [1, 64] required");
 }
 
 kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_theta, int32_t ard,
@@ -544,8 +724,6 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt) {
 kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx) {
     if (!h) return KPCG_ERR_ARG;
     KPCG_GUARD(h, {
-        h->P.reset();
-        if (kind == KPCG_PREC_NONE) return KPCG_OK;
         if (kind == KPCG_PREC_NYSTROM) {
             if (size < 1 || size > h->n || size > 4096)
                 fail(KPCG_ERR_ARG, "Nystrom m must be in [1, min(n, 4096)]");
@@ -555,16 +733,28 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
                 if (a && idx[a] <= idx[a - 1])
                     fail(KPCG_ERR_ARG, "inducing indices must be sorted and distinct");
             }
-            kpcg::nystrom_setup(h->P, h->xs32.p, h->xs64.p, h->n, h->dp, h->c0_32(), h->c0_64(),
-                                h->noise, idx, size, h->stream);
+            h->pidx.assign(idx, idx + size);
         } else if (kind == KPCG_PREC_BLOCK_JACOBI) {
             if (size < 1 || size > 4096) fail(KPCG_ERR_ARG, "block size must be in [1, 4096]");
-            kpcg::block_jacobi_setup(h->P, h->xs64.p, h->n, h->dp, h->c0_64(), h->noise,
-                                     std::min<int64_t>(size, h->n), h->stream);
+            h->pidx.clear();
+        } else if (kind == KPCG_PREC_NONE) {
+            h->pidx.clear();
         } else {
             fail(KPCG_ERR_ARG, "unknown preconditioner kind");
         }
-        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+        h->pkind = KPCG_PREC_NONE;
+        h->P.reset();
+        h->pkind = kind;
+        h->psize = size;
+        if (kind != KPCG_PREC_NONE) {
+            try {
+                kpcg::build_precond(*h);
+            } catch (...) {
+                h->pkind = KPCG_PREC_NONE;
+                h->P.reset();
+                throw;
+            }
+        }
     });
     return KPCG_OK;
 }
@@ -598,7 +788,7 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
         } else if (impl == 1) {
             if (!kpcg::kv_tc_supported(h->dp))
                 fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
-            kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo);
+            kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
         } else {
             fail(KPCG_ERR_ARG, "unknown impl");
         }
@@ -615,7 +805,7 @@ kpcg_status kpcg_precond_apply_f64(kpcg_t h, const double* R, int64_t ldr, int32
         if (c == 0) return KPCG_OK;
         kpcg::check_dev_ptr(R, "R");
         kpcg::check_dev_ptr(Z, "Z");
-        h->P.n = h->n;
+        kpcg::ensure_precond(*h);
         kpcg::precond_apply_f64(h->P, R, ldr, c, Z, ldz, h->stream);
         KPCG_CUDA(cudaStreamSynchronize(h->stream));
     });

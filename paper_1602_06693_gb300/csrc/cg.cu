@@ -192,6 +192,16 @@ __global__ void axpy_scaled_kernel(double* __restrict__ X, int64_t ldx, const fl
         X[i + (int64_t)k * ldx] += f * (double)D[i + (int64_t)k * ldd];
 }
 
+__global__ void axpy_cols_kernel(double* __restrict__ Y, int64_t ldy, const double* __restrict__ X,
+                                 int64_t ldx, int64_t n, const double* __restrict__ coef) {
+    const int k = blockIdx.y;
+    const double f = coef[k];
+    if (f == 0.0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Y[i + (int64_t)k * ldy] = fma(f, X[i + (int64_t)k * ldx], Y[i + (int64_t)k * ldy]);
+}
+
 unsigned grid_x(int64_t n) {
     int64_t g = (n + 255) / 256;
     if (g > 4096) g = 4096;
@@ -256,6 +266,13 @@ void axpy_scaled_f64(double* X, int64_t ldx, const float* D, int64_t ldd, int64_
     if (n <= 0 || c <= 0) return;
     axpy_scaled_kernel<<<dim3(grid_x(n), c), 256, 0, st>>>(X, ldx, D, ldd, n, colscale);
     KPCG_LAUNCHED("axpy_scaled_kernel");
+}
+
+void axpy_cols_f64(double* Y, int64_t ldy, const double* X, int64_t ldx, int64_t n, int c,
+                   const double* coef, cudaStream_t st) {
+    if (n <= 0 || c <= 0) return;
+    axpy_cols_kernel<<<dim3(grid_x(n), c), 256, 0, st>>>(Y, ldy, X, ldx, n, coef);
+    KPCG_LAUNCHED("axpy_cols_kernel");
 }
 
 void fill_zero_cols(void* p, size_t elem, int64_t ld, int64_t n, int c, cudaStream_t st) {

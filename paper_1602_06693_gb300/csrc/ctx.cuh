@@ -16,6 +16,59 @@ struct CgBufs {
     DevBuf<T> x, r, z, p, q, b;
 };
 
+// Device-time accounting of the hot calls (opt.profile): CUDA events around
+// each call on the handle's stream, summed when the call returns.
+struct Profiler {
+    enum { KV_INNER = 0, KV_OUTER = 1, PRECOND = 2, NCAT = 3 };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[NCAT];
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        KPCG_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    template <typename F>
+    void time(int cat, cudaStream_t st, F&& f) {
+        if (!on) {
+            f();
+            return;
+        }
+        cudaEvent_t a = get(), b = get();
+        KPCG_CUDA(cudaEventRecord(a, st));
+        f();
+        KPCG_CUDA(cudaEventRecord(b, st));
+        spans[cat].push_back({a, b});
+    }
+    // Sum and recycle; the stream must have finished.
+    void collect(double ms[NCAT], int calls[NCAT]) {
+        for (int c = 0; c < NCAT; ++c) {
+            ms[c] = 0.0;
+            calls[c] = (int)spans[c].size();
+            for (auto& s : spans[c]) {
+                float t = 0.f;
+                if (cudaEventElapsedTime(&t, s.first, s.second) == cudaSuccess) ms[c] += t;
+                pool.push_back(s.first);
+                pool.push_back(s.second);
+            }
+            spans[c].clear();
+        }
+    }
+    ~Profiler() {
+        for (int c = 0; c < NCAT; ++c)
+            for (auto& s : spans[c]) {
+                cudaEventDestroy(s.first);
+                cudaEventDestroy(s.second);
+            }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -32,12 +85,17 @@ struct Ctx {
     PrecondState P;
     CgBufs<double> c64;
     CgBufs<float> c32;
-    DevBuf<double> R64, Q64, Bblk, Sblk, G, colscale;
+    DevBuf<double> R64, Q64, Bblk, Sblk, G, colscale, fcgP, fcgAP;
+    // preconditioner request, replayed when the noise it needs changes
+    int pkind = KPCG_PREC_NONE;
+    int64_t psize = 0;
+    std::vector<int64_t> pidx;
     DevBuf<float> W32;
     DevBuf<double> partial;
     DevBuf<double> scal;
     DevBuf<int> iscal;
     int* hflags = nullptr;  // pinned host [active, broken]
+    Profiler prof;
     std::string err;
 
     double c0_64() const { return std::log(s2); }
@@ -45,6 +103,6 @@ struct Ctx {
 };
 
 // Tensor-core K.V on the handle's inputs (kv_tc.cu).
-void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo);
+void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise);
 
 }  // namespace kpcg

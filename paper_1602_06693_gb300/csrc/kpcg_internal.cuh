@@ -20,7 +20,11 @@ struct Error {
 [[noreturn]] void fail(kpcg_status s, const std::string& msg);
 void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define KPCG_CUDA(call) ::kpcg::cuda_check((call), #call, __FILE__, __LINE__)
-#define KPCG_LAUNCHED(name) ::kpcg::cuda_check(cudaGetLastError(), name, __FILE__, __LINE__)
+// Checks a kernel launch and counts it (per host thread).
+void note_launch();
+long long launch_count();
+#define KPCG_LAUNCHED(name) \
+    (::kpcg::note_launch(), ::kpcg::cuda_check(cudaGetLastError(), name, __FILE__, __LINE__))
 
 // A device allocation owned by RAII.
 template <typename T>
@@ -125,6 +129,9 @@ void convert_scale_cols(TD* dst, int64_t ldd, const TS* src, int64_t lds, int64_
                         const double* colscale, int invert, cudaStream_t st);
 void axpy_scaled_f64(double* X, int64_t ldx, const float* D, int64_t ldd, int64_t n, int c,
                      const double* colscale, cudaStream_t st);
+// Y[:, k] += coef[k] X[:, k]  (device coefficients).
+void axpy_cols_f64(double* Y, int64_t ldy, const double* X, int64_t ldx, int64_t n, int c,
+                   const double* coef, cudaStream_t st);
 void fill_zero_cols(void* p, size_t elem, int64_t ld, int64_t n, int c, cudaStream_t st);
 int dot_blocks(int64_t n);
 

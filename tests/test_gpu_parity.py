@@ -113,7 +113,7 @@ def test_block_jacobi_apply_matches_oracle(kpcg):
     ell, s2 = oracle.split_theta(p.log_theta, 4, True)
     P = oracle.BlockJacobi(p.X, ell, s2, p.noise, 256)  # blocks 256 x4 + 76
     R = synthetic.rng(2).standard_normal((1100, 3))
-    with _solver(kpcg, p) as s:
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
         s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, 256)
         out = _np(s.precond_apply(_cm(R)))
     assert _rel(out, P.apply(R)) <= 1e-9
@@ -128,9 +128,14 @@ def test_nystrom_apply_matches_oracle(kpcg):
     idx = synthetic.inducing_subset(2000, 64, seed=3)
     P = oracle.Nystrom(p.X, ell, s2, p.noise, idx)
     R = synthetic.rng(4).standard_normal((2000, 2))
-    with _solver(kpcg, p) as s:
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
         s.precond(kpcg.KPCG_PREC_NYSTROM, len(idx), idx)
         out = _np(s.precond_apply(_cm(R)))
+        # the mixed modes build it for the shifted inner noise sigma^2 (1 + shift)
+        s.set_options(kpcg.default_options(precision=kpcg.KPCG_FP32_IR, inner_shift=0.5))
+        out2 = _np(s.precond_apply(_cm(R)))
+    P2 = oracle.Nystrom(p.X, ell, s2, 1.5 * p.noise, idx)
+    assert _rel(out2, P2.apply(R)) <= 1e-4
     assert _rel(out, P.apply(R)) <= 1e-4
 
 
