@@ -97,6 +97,7 @@ static void ctx_rescale(Ctx& h) {
         inv[q] = std::exp(-lt);
     }
     h.s2 = std::exp(h.log_theta.back());
+    ++h.theta_version;
     KPCG_CUDA(cudaMemcpyAsync(h.inv_ell.p, inv.data(), sizeof(double) * h.d,
                               cudaMemcpyHostToDevice, h.stream));
     const int64_t tot = h.n * h.dp;
@@ -425,6 +426,8 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
     }
     for (int k = 0; k < c; ++k)
         if (dead[k] && status == KPCG_OK) status = KPCG_ERR_BREAKDOWN;
+    if (tc && kv_tc_error(h))
+        fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
     return status;
 }
 
@@ -789,6 +792,8 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             if (!kpcg::kv_tc_supported(h->dp))
                 fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
             kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         } else {
             fail(KPCG_ERR_ARG, "unknown impl");
         }

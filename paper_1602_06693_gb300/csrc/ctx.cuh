@@ -96,6 +96,11 @@ struct Ctx {
     DevBuf<int> iscal;
     int* hflags = nullptr;  // pinned host [active, broken]
     Profiler prof;
+    // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
+    int theta_version = 0, tc_version = -1, tc_kch = 0;
+    DevBuf<uint16_t> tcA, tcB;
+    DevBuf<float> tcV, tcPart;
+    DevBuf<int> tc_err;
     std::string err;
 
     double c0_64() const { return std::log(s2); }
@@ -104,5 +109,8 @@ struct Ctx {
 
 // Tensor-core K.V on the handle's inputs (kv_tc.cu).
 void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise);
+// Nonzero if a bounded wait inside the tensor-core kernel expired since the
+// last call (the flag is cleared).
+int kv_tc_error(Ctx& h);
 
 }  // namespace kpcg

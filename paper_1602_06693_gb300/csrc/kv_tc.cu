@@ -1,9 +1,548 @@
-// Tensor-core K.V (placeholder until the tcgen05 kernel lands).
+// Tensor-core K.V for sm_103a: tcgen05 MMA with TMEM accumulators.
+//
+// O = K V + noise V with K_ij = s^2 exp(-1/2 sum_r (x_ir - x_jr)^2 / l_r^2)
+// (Eq. 1), entries rebuilt per 128 x 128 tile and never stored (the matrix-free
+// product CG needs, Sec. 2.1).
+//
+// Exponent on the tensor cores.  With x' = (x - mu) / l * sqrt(log2(e)/2) the
+// entry is exp2(a_ij), a_ij = log2(s^2) - |x'_i|^2 - |x'_j|^2 + 2 x'_i.x'_j.
+// Every row is split (in FP64) into three BF16 parts x' = h + m + l and
+// q = log2(s^2)/2 - |x'|^2 likewise; the augmented rows
+//     A_i = [ h  h  m  h  l  m | 1 1 1 | qh qm ql ]
+//     B_j = 2[ h  m  h  l  h  m ] | qh qm ql | 1 1 1 ]
+// make one BF16 MMA chain (FP32 accumulate) produce a_ij directly: the six
+// cross products carry 2 x'_i.x'_j to about 2^-24 relative, which keeps the
+// error of K at FP32 level (a two-way TF32 split is twice as large, a single
+// BF16 or TF32 rounding is useless against a small noise term).  K-dim is
+// 6d + 6, padded to 64 (d <= 9) or 128 (d <= 20).  Padding rows of B carry
+// q = -1e30 so their entries vanish.
+//
+// Data movement.  A prep kernel writes A and B in HBM already in the 128-byte
+// swizzled K-major shared-memory layout, one 16 KB block per 128 rows and 64
+// columns, so a tile moves with a single bulk copy (cp.async.bulk, TMA engine)
+// that completes on an mbarrier.  V tiles move the same way.
+//
+// Roles (10 warps): warp 0 issues bulk copies into a 4-stage ring, warp 1
+// owns TMEM (2 x 128 columns: double-buffered accumulators) and issues the
+// MMAs from one thread, warps 2..9 drain TMEM with tcgen05.ld, apply exp2 on
+// the MUFU and contract with V in FP32 registers.  Each thread owns one row
+// and 64 of the 128 columns of a tile.  Every wait is bounded (globaltimer);
+// on expiry the kernel records an error code, drains its own work and frees
+// TMEM.  Column ranges of K are split across CTAs and added by a second,
+// deterministic kernel.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
 #include "ctx.cuh"
 
 namespace kpcg {
-bool kv_tc_supported(int) { return false; }
-void kv_tc_apply(Ctx&, const float*, int64_t, int, float*, int64_t, float) {
-    fail(KPCG_ERR_ARG, "tensor-core K.V is not available in this build");
+namespace {
+
+constexpr int TM = 128;          // rows per tile (MMA M)
+constexpr int TN = 128;          // columns per tile (MMA N)
+constexpr int KC = 64;           // bf16 per 128-byte swizzle row
+constexpr int SUB = TM * KC;     // elements per 16 KB sub-tile
+constexpr int NSTAGE = 4;
+constexpr int NWARPS = 10;
+constexpr int NEPI = 8;          // epilogue warps
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            su32(b)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 "
+        "%0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on the phase of the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t deadline) {
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(b, parity)) return true;
+        if ((it & 255u) == 0 && gtimer() > deadline) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused: swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, K-major A and B.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], "
+        "%1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(b))
+        : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float ex2(float a) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
+// Byte offset of element (r, k) inside a 128-row x 64-col swizzled sub-tile.
+__device__ __forceinline__ uint32_t swz_off(int r, int k) {
+    const int chunk = (k >> 3) ^ (r & 7);
+    return (uint32_t)(r * 128 + chunk * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split3(double v, __nv_bfloat16& h, __nv_bfloat16& m,
+                                       __nv_bfloat16& l) {
+    h = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(h);
+    m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
+    l = __double2bfloat16(r2);
+}
+
+// One thread per row: build the augmented A and B rows (see file comment).
+__global__ void tc_prep_kernel(const double* __restrict__ xs64, int64_t n, int64_t n_pad, int d,
+                               int dp, int kch, double scale, double c0,
+                               __nv_bfloat16* __restrict__ Aop, __nv_bfloat16* __restrict__ Bop) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const int kdim = kch * KC;
+    const int64_t tile = i / TM;
+    const int r = (int)(i % TM);
+    uint8_t* abase = reinterpret_cast<uint8_t*>(Aop) + (size_t)tile * kch * SUB * 2;
+    uint8_t* bbase = reinterpret_cast<uint8_t*>(Bop) + (size_t)tile * kch * SUB * 2;
+    auto put = [&](uint8_t* base, int k, __nv_bfloat16 v) {
+        const int kc = k / KC, kk = k % KC;
+        *reinterpret_cast<__nv_bfloat16*>(base + (size_t)kc * SUB * 2 + swz_off(r, kk)) = v;
+    };
+    const __nv_bfloat16 z = __float2bfloat16(0.f), one = __float2bfloat16(1.f);
+    for (int k = 0; k < kdim; ++k) {
+        put(abase, k, z);
+        put(bbase, k, z);
+    }
+    if (i >= n) {  // padding column of K: exp2(-huge) = 0
+        put(bbase, 6 * d, __float2bfloat16(-1e30f));
+        return;
+    }
+    double nrm = 0.0;
+    for (int q = 0; q < d; ++q) {
+        const double x = xs64[i * dp + q] * scale;
+        nrm += x * x;
+        __nv_bfloat16 h, m, l;
+        split3(x, h, m, l);
+        const __nv_bfloat16 h2 = __float2bfloat16(2.f * __bfloat162float(h));
+        const __nv_bfloat16 m2 = __float2bfloat16(2.f * __bfloat162float(m));
+        const __nv_bfloat16 l2 = __float2bfloat16(2.f * __bfloat162float(l));
+        put(abase, 0 * d + q, h);
+        put(bbase, 0 * d + q, h2);
+        put(abase, 1 * d + q, h);
+        put(bbase, 1 * d + q, m2);
+        put(abase, 2 * d + q, m);
+        put(bbase, 2 * d + q, h2);
+        put(abase, 3 * d + q, h);
+        put(bbase, 3 * d + q, l2);
+        put(abase, 4 * d + q, l);
+        put(bbase, 4 * d + q, h2);
+        put(abase, 5 * d + q, m);
+        put(bbase, 5 * d + q, m2);
+    }
+    __nv_bfloat16 qh, qm, ql;
+    split3(0.5 * c0 - nrm, qh, qm, ql);
+    put(abase, 6 * d + 0, one);
+    put(abase, 6 * d + 1, one);
+    put(abase, 6 * d + 2, one);
+    put(bbase, 6 * d + 0, qh);
+    put(bbase, 6 * d + 1, qm);
+    put(bbase, 6 * d + 2, ql);
+    put(abase, 6 * d + 3, qh);
+    put(abase, 6 * d + 4, qm);
+    put(abase, 6 * d + 5, ql);
+    put(bbase, 6 * d + 3, one);
+    put(bbase, 6 * d + 4, one);
+    put(bbase, 6 * d + 5, one);
+}
+
+__global__ void tc_stage_v_kernel(const float* __restrict__ V, int64_t ldv, int64_t n,
+                                  int64_t n_pad, float* __restrict__ Vs) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Vs[i + k * n_pad] = (i < n) ? V[i + k * ldv] : 0.f;
+}
+
+template <int KCH, int CB>
+struct TcSmem {
+    static constexpr uint32_t kSub = SUB * 2;                    // 16 KB
+    static constexpr uint32_t kA = KCH * kSub;                   // A tile
+    static constexpr uint32_t kBst = KCH * kSub;                 // B part of a stage
+    static constexpr uint32_t kVst = CB * TN * 4;                // V part of a stage
+    static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
+    static constexpr uint32_t kBars = 1024;
+    static constexpr uint32_t kTotal = 1024 /*align slack*/ + kA + NSTAGE * kStage + kBars;
+};
+
+template <int KCH, int CB>
+__global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
+    kv_tc_kernel(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
+                 const float* __restrict__ Vs, int64_t n, int64_t n_pad, int ncols,
+                 int tiles_per_split, float* __restrict__ part, int* __restrict__ err) {
+    using S = TcSmem<KCH, CB>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sStage = smem + S::kA;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kA + NSTAGE * S::kStage);
+    uint64_t* full = bars;                  // [NSTAGE] bulk copies landed
+    uint64_t* empty = bars + NSTAGE;        // [NSTAGE] MMA done + epilogue done with V
+    uint64_t* tfull = bars + 2 * NSTAGE;    // [2] accumulator ready
+    uint64_t* tempty = bars + 2 * NSTAGE + 2;  // [2] accumulator drained
+    uint64_t* afull = bars + 2 * NSTAGE + 4;
+    uint64_t* done = bars + 2 * NSTAGE + 5;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 6);
+    float* comb = reinterpret_cast<float*>(sStage);  // reused after the loop: [CB][TM]
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t rt = blockIdx.x;  // row tile
+    const int64_t n_ct = n_pad / TN;
+    const int64_t jt0 = (int64_t)blockIdx.y * tiles_per_split;
+    const int64_t jt1 = min(n_ct, jt0 + tiles_per_split);
+    const int ntiles = (int)max((int64_t)0, jt1 - jt0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1 + NEPI);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], NEPI);
+        }
+        mbar_init(afull, 1);
+        mbar_init(done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                su32(tmem_slot)),
+            "r"(2 * TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint64_t deadline = gtimer() + kWaitNs;
+    int fail = 0;
+    float acc[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) acc[k] = 0.f;
+    const int quarter = warp & 3;         // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;     // epilogue: column half of a tile
+    const int row = quarter * 32 + lane;  // epilogue: row of the tile
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // A tile once, then B + V tiles through the ring
+            mbar_expect_tx(afull, S::kA);
+            bulk_g2s(sA, Aop + (size_t)rt * KCH * SUB, S::kA, afull);
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % NSTAGE;
+                if (!mbar_wait(&empty[s], ((uint32_t)(t / NSTAGE) & 1u) ^ 1u, deadline)) {
+                    fail = 1;
+                    break;
+                }
+                const int64_t jt = jt0 + t;
+                uint8_t* st = sStage + (size_t)s * S::kStage;
+                mbar_expect_tx(&full[s], S::kBst + (uint32_t)ncols * TN * 4);
+                bulk_g2s(st, Bop + (size_t)jt * KCH * SUB, S::kBst, &full[s]);
+                for (int k = 0; k < ncols; ++k)
+                    bulk_g2s(st + S::kBst + (size_t)k * TN * 4, Vs + (size_t)k * n_pad + jt * TN,
+                             TN * 4, &full[s]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (!mbar_wait(afull, 0, deadline)) fail = 1;
+            fence_after();
+            const uint32_t a0 = su32(sA);
+            for (int t = 0; t < ntiles && !fail; ++t) {
+                const int s = t % NSTAGE, b = t & 1;
+                if (!mbar_wait(&full[s], (uint32_t)(t / NSTAGE) & 1u, deadline) ||
+                    !mbar_wait(&tempty[b], ((uint32_t)(t >> 1) & 1u) ^ 1u, deadline)) {
+                    fail = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t b0 = su32(sStage + (size_t)s * S::kStage);
+                const uint32_t dt = tmem + (uint32_t)(b * TN);
+#pragma unroll
+                for (int kc = 0; kc < KCH; ++kc)
+#pragma unroll
+                    for (int kk = 0; kk < KC / 16; ++kk) {
+                        const uint32_t off = (uint32_t)kc * S::kSub + (uint32_t)kk * 32;
+                        mma_bf16(dt, sdesc(a0 + off), sdesc(b0 + off), (kc | kk) ? 1u : 0u);
+                    }
+                mma_commit(&tfull[b]);
+                mma_commit(&empty[s]);
+            }
+            // drain: this commit arrives once every MMA issued above has finished
+            mma_commit(done);
+            if (!mbar_wait(done, 0, gtimer() + kWaitNs)) fail = 1;
+        }
+    } else {
+        for (int t = 0; t < ntiles; ++t) {
+            const int s = t % NSTAGE, b = t & 1;
+            // warp-uniform decision: the TMEM loads below are .sync.aligned
+            const bool ok = __all_sync(0xffffffffu,
+                                       mbar_wait(&tfull[b], (uint32_t)(t >> 1) & 1u, deadline));
+            if (!ok) {
+                fail = 1;
+                break;
+            }
+            fence_after();
+            const float* vst =
+                reinterpret_cast<const float*>(sStage + (size_t)s * S::kStage + S::kBst);
+#pragma unroll 1
+            for (int ch = 0; ch < 4; ++ch) {
+                const int col0 = half * 64 + ch * 16;
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + col0), r);
+                float ev[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) ev[j] = ex2(__uint_as_float(r[j]));
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
+                    float a = acc[k];
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float4 v = vp[j4];
+                        a = fmaf(ev[4 * j4 + 0], v.x, a);
+                        a = fmaf(ev[4 * j4 + 1], v.y, a);
+                        a = fmaf(ev[4 * j4 + 2], v.z, a);
+                        a = fmaf(ev[4 * j4 + 3], v.w, a);
+                    }
+                    acc[k] = a;
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&tempty[b]);
+                mbar_arrive(&empty[s]);
+            }
+        }
+    }
+    // every role ends here
+    if (fail) atomicExch(&s_fail, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // add the two column halves of each row (ring memory is free now)
+    if (warp >= 2 && half == 1)
+#pragma unroll
+        for (int k = 0; k < CB; ++k) comb[k * TM + row] = acc[k];
+    __syncthreads();
+    if (warp >= 2 && half == 0) {
+        const int64_t i = rt * TM + row;
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+            const float v = acc[k] + comb[k * TM + row];
+            if (k < ncols && i < n) part[((size_t)blockIdx.y * CB + k) * n_pad + i] = v;
+        }
+    }
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * TN));
+    }
+}
+
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int64_t n_pad, int nsplit,
+                                 int cb, int ncols, const float* __restrict__ V, int64_t ldv,
+                                 float noise, float* __restrict__ O, int64_t ldo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n || k >= ncols) return;
+    float s = noise * V[i + (int64_t)k * ldv];
+    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * cb + k) * n_pad + i];
+    O[i + (int64_t)k * ldo] = s;
+}
+
+int sm_count_tc() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+        if (cached <= 0) cached = 148;
+    }
+    return cached;
+}
+
+template <int KCH, int CB>
+void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* Vs,
+               int64_t n_pad, int ncols, float* part, int nsplit, int tps, int* err,
+               cudaStream_t st) {
+    using S = TcSmem<KCH, CB>;
+    static bool attr = false;
+    if (!attr) {
+        KPCG_CUDA(cudaFuncSetAttribute(kv_tc_kernel<KCH, CB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal));
+        attr = true;
+    }
+    dim3 grid((unsigned)(n_pad / TM), (unsigned)nsplit);
+    kv_tc_kernel<KCH, CB><<<grid, NWARPS * 32, S::kTotal, st>>>(A, B, Vs, h.n, n_pad, ncols, tps,
+                                                                part, err);
+    KPCG_LAUNCHED("kv_tc_kernel");
+}
+
+}  // namespace
+
+bool kv_tc_supported(int dp) { return dp <= 16; }
+
+void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int64_t n_pad = ((n + TM - 1) / TM) * TM;
+    const int kch = (6 * h.d + 6 <= KC) ? 1 : 2;
+    if (6 * h.d + 6 > 2 * KC) fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
+    // operands for the current theta
+    if (h.tc_version != h.theta_version || h.tc_kch != kch) {
+        h.tcA.need((size_t)n_pad * kch * KC);
+        h.tcB.need((size_t)n_pad * kch * KC);
+        tc_prep_kernel<<<(unsigned)((n_pad + 127) / 128), 128, 0, st>>>(
+            h.xs64.p, n, n_pad, h.d, h.dp, kch, std::sqrt(kLog2e), std::log2(h.s2),
+            reinterpret_cast<__nv_bfloat16*>(h.tcA.p), reinterpret_cast<__nv_bfloat16*>(h.tcB.p));
+        KPCG_LAUNCHED("tc_prep_kernel");
+        h.tc_version = h.theta_version;
+        h.tc_kch = kch;
+        int* e = h.tc_err.need(1);
+        KPCG_CUDA(cudaMemsetAsync(e, 0, sizeof(int), st));
+    }
+    const int n_ct = (int)(n_pad / TN);
+    const int n_rt = (int)(n_pad / TM);
+    // splits of the column range: about four waves of two CTAs per SM
+    int nsplit = std::max(1, std::min(n_ct, (sm_count_tc() * 4 + n_rt - 1) / n_rt));
+    const int tps = (n_ct + nsplit - 1) / nsplit;
+    nsplit = (n_ct + tps - 1) / tps;
+    const int max_cb = 8;
+    float* Vs = h.tcV.need((size_t)n_pad * max_cb);
+    float* part = h.tcPart.need((size_t)nsplit * max_cb * n_pad);
+    for (int k0 = 0; k0 < c;) {
+        const int rem = c - k0;
+        const int cb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int ncols = std::min(cb, rem);
+        tc_stage_v_kernel<<<dim3((unsigned)std::min<int64_t>((n_pad + 255) / 256, 2048),
+                                 (unsigned)ncols),
+                            256, 0, st>>>(V + (int64_t)k0 * ldv, ldv, n, n_pad, Vs);
+        KPCG_LAUNCHED("tc_stage_v_kernel");
+        const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(h.tcA.p);
+        const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(h.tcB.p);
+#define KPCG_TC_CASE(KCHV, CBV)                                                             \
+    if (kch == KCHV && cb == CBV)                                                           \
+        launch_tc<KCHV, CBV>(h, A, B, Vs, n_pad, ncols, part, nsplit, tps, h.tc_err.p, st);
+        KPCG_TC_CASE(1, 1)
+        KPCG_TC_CASE(1, 2)
+        KPCG_TC_CASE(1, 4)
+        KPCG_TC_CASE(1, 8)
+        KPCG_TC_CASE(2, 1)
+        KPCG_TC_CASE(2, 2)
+        KPCG_TC_CASE(2, 4)
+        KPCG_TC_CASE(2, 8)
+#undef KPCG_TC_CASE
+        tc_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)ncols), 256, 0, st>>>(
+            part, n_pad, nsplit, cb, ncols, V + (int64_t)k0 * ldv, ldv, noise,
+            O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("tc_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
+int kv_tc_error(Ctx& h) {
+    if (!h.tc_err.p) return 0;
+    int e = 0;
+    KPCG_CUDA(cudaMemcpyAsync(&e, h.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    KPCG_CUDA(cudaStreamSynchronize(h.stream));
+    if (e) KPCG_CUDA(cudaMemsetAsync(h.tc_err.p, 0, sizeof(int), h.stream));
+    return e;
+}
+
 }  // namespace kpcg

@@ -274,39 +274,64 @@ __global__ void add_diag_kernel(double* M, int64_t m, double v) {
     if (a < m) M[a * m + a] += v;
 }
 
-// w_part[s][k][a] = sum_{i in split s} KXU[i][a] R[i][k]   (FP64 products)
+// Compensated dot-product accumulation (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", 2005, algorithm Dot2): each product is split exactly into
+// p + pi by an FMA (TwoProduct), p is added to the running sum s with Knuth's
+// TwoSum, and all rounding errors are gathered in c.  s + c is as accurate as
+// a dot product computed in twice the FP32 precision, at FP32-pipe speed.
+struct Acc2 {
+    float s, c;
+};
+__device__ __forceinline__ void dot2_add(Acc2& a, float x, float y) {
+    const float p = x * y;
+    const float pi = fmaf(x, y, -p);
+    const float t = a.s + p;
+    const float z = t - a.s;
+    const float sg = (a.s - (t - z)) + (p - z);
+    a.s = t;
+    a.c += pi + sg;
+}
+
+// w_part[s][k][a] = sum_{i in split s} KXU[i][a] R[i][k], compensated FP32.
 constexpr int PC = 4;  // columns per pass
 template <typename T>
 __global__ void __launch_bounds__(256)
     nys_proj_kernel(const float* __restrict__ KXU, int64_t n, int64_t m, const T* __restrict__ R,
                     int64_t ldr, int ncols, int64_t rows_per_split, double* __restrict__ part,
                     int c_total) {
-    __shared__ double sr[64][PC];
+    __shared__ float2 sr[128][PC];  // r split into float hi + lo
     const int64_t a = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
     const int64_t r1 = min(n, r0 + rows_per_split);
-    double acc[PC];
+    Acc2 acc[PC];
 #pragma unroll
-    for (int k = 0; k < PC; ++k) acc[k] = 0.0;
-    for (int64_t rs = r0; rs < r1; rs += 64) {
+    for (int k = 0; k < PC; ++k) acc[k] = {0.f, 0.f};
+    for (int64_t rs = r0; rs < r1; rs += 128) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 64 * PC; e += 256) {
-            const int k = e / 64, r = e % 64;
-            sr[r][k] = (rs + r < r1 && k < ncols) ? (double)R[rs + r + (int64_t)k * ldr] : 0.0;
+        for (int e = threadIdx.x; e < 128 * PC; e += 256) {
+            const int k = e / 128, r = e % 128;
+            double v = (rs + r < r1 && k < ncols) ? (double)R[rs + r + (int64_t)k * ldr] : 0.0;
+            const float hi = (float)v;
+            sr[r][k] = make_float2(hi, (float)(v - (double)hi));
         }
         __syncthreads();
-        const int rn = (int)min((int64_t)64, r1 - rs);
+        const int rn = (int)min((int64_t)128, r1 - rs);
         if (a < m) {
+            const float* Kp = KXU + rs * m + a;
+#pragma unroll 4
             for (int r = 0; r < rn; ++r) {
-                const double kv = (double)KXU[(rs + r) * m + a];
+                const float kv = __ldg(Kp + (int64_t)r * m);
 #pragma unroll
-                for (int k = 0; k < PC; ++k) acc[k] = fma(kv, sr[r][k], acc[k]);
+                for (int k = 0; k < PC; ++k) {
+                    dot2_add(acc[k], kv, sr[r][k].x);
+                    acc[k].c = fmaf(kv, sr[r][k].y, acc[k].c);
+                }
             }
         }
     }
     if (a < m)
         for (int k = 0; k < ncols; ++k)
-            part[((int64_t)blockIdx.y * c_total + k) * m + a] = acc[k];
+            part[((int64_t)blockIdx.y * c_total + k) * m + a] = (double)acc[k].s + (double)acc[k].c;
 }
 
 __global__ void sum_splits_kernel(const double* __restrict__ part, int nsplit, int64_t len,
@@ -345,24 +370,37 @@ __global__ void tri_upper_apply_kernel(const double* __restrict__ U, int64_t m,
     if (lane == 0) u[(int64_t)k * m + j] = s;
 }
 
-// Z = (R - K_XU u) / sigma^2, warp per row, FP64 accumulation.
+// Z = (R - K_XU u) / sigma^2, warp per row; u is split into FP32 hi + lo and
+// the row sum accumulated with Dot2, lanes combined in FP64.
+__global__ void split_u_kernel(const double* __restrict__ u, int64_t len, float2* __restrict__ o) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    const double v = u[e];
+    const float hi = (float)v;
+    o[e] = make_float2(hi, (float)(v - (double)hi));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     nys_back_kernel(const float* __restrict__ KXU, int64_t n, int64_t m,
-                    const double* __restrict__ u, int c, const T* __restrict__ R, int64_t ldr,
+                    const float2* __restrict__ u2, int c, const T* __restrict__ R, int64_t ldr,
                     T* __restrict__ Z, int64_t ldz, double inv_noise) {
-    extern __shared__ double su[];  // m * c
-    for (int64_t e = threadIdx.x; e < m * c; e += blockDim.x) su[e] = u[e];
+    extern __shared__ float2 su[];  // m * c
+    for (int64_t e = threadIdx.x; e < m * c; e += blockDim.x) su[e] = u2[e];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const float* Ki = KXU + i * m;
         for (int k = 0; k < c; ++k) {
-            const double* uk = su + (int64_t)k * m;
-            double s = 0.0;
-            for (int64_t a = lane; a < m; a += 32) s = fma((double)Ki[a], uk[a], s);
-            s = warp_sum(s);
+            const float2* uk = su + (int64_t)k * m;
+            Acc2 acc = {0.f, 0.f};
+            for (int64_t a = lane; a < m; a += 32) {
+                const float kv = __ldg(Ki + a);
+                dot2_add(acc, kv, uk[a].x);
+                acc.c = fmaf(kv, uk[a].y, acc.c);
+            }
+            double s = warp_sum((double)acc.s + (double)acc.c);
             if (lane == 0)
                 Z[i + (int64_t)k * ldz] = (T)(((double)R[i + (int64_t)k * ldr] - s) * inv_noise);
         }
@@ -535,7 +573,9 @@ template <typename T>
 static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z,
                           int64_t ldz, cudaStream_t st) {
     const int64_t n = P.n, m = P.m;
-    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 1023) / 1024));
+    const int64_t ablk = (m + 255) / 256;
+    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((152 * 4 + ablk - 1) / ablk,
+                                                             (n + 127) / 128));
     const int64_t rps = (n + nsplit - 1) / nsplit;
     nsplit = (int)((n + rps - 1) / rps);
     double* part = const_cast<PrecondState&>(P).wpart.need((size_t)nsplit * c * m);
@@ -555,13 +595,16 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     tri_upper_apply_kernel<<<dim3((unsigned)((m * 32 + 255) / 256), c), 256, 0, st>>>(P.U.p, m, y,
                                                                                      w);
     KPCG_LAUNCHED("tri_upper_apply_kernel");
-    const size_t smem = sizeof(double) * (size_t)m * c;
+    const size_t smem = sizeof(float2) * (size_t)m * c;
     if (smem > 200 * 1024) fail(KPCG_ERR_ARG, "Nystrom apply: m * c too large");
     if (smem > 48 * 1024)
         KPCG_CUDA(cudaFuncSetAttribute(nys_back_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 8);
-    nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, w, c, R, ldr, Z, ldz,
+    float2* u2 = reinterpret_cast<float2*>(y);  // y is free again: reuse it for split u
+    split_u_kernel<<<(unsigned)((c * m + 255) / 256), 256, 0, st>>>(w, c * m, u2);
+    KPCG_LAUNCHED("split_u_kernel");
+    int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 16);
+    nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, u2, c, R, ldr, Z, ldz,
                                                   1.0 / P.noise);
     KPCG_LAUNCHED("nys_back_kernel");
 }

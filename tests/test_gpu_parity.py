@@ -94,6 +94,35 @@ def test_matvec_f32_matches_oracle(kpcg, n, d, c):
         assert _rel(out[:, k], ref[:, k]) <= 2e-5
 
 
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 9),
+                                   (300, 9, 17), (129, 5, 8), (8192, 8, 1)])
+def test_matvec_tensor_core_matches_oracle(kpcg, n, d, c):
+    # BF16 x3 split exponent on tcgen05, FP32 accumulate: per-entry error
+    # ~ ln2 * 2^-24 * (|x'_i|^2 + |x'_j|^2 + 2|x'_i.x'_j|), well inside 2e-5.
+    p = _problem(n, d, seed=11 * n + d)
+    V = synthetic.rng(7).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=1))
+        again = _np(s.matvec_f32(_cm(V, torch.float32), impl=1))
+    np.testing.assert_array_equal(out, again)  # deterministic
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= 2e-5, k
+
+
+def test_tensor_core_follows_theta_changes(kpcg):
+    p = _problem(777, 6, seed=3)
+    V = synthetic.rng(8).standard_normal(777)
+    with _solver(kpcg, p) as s:
+        s.matvec_f32(_cm(V, torch.float32), impl=1)
+        lt = p.log_theta + 0.3
+        s.set_theta(lt, 2 * p.noise)
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=1))
+    ell, s2 = oracle.split_theta(lt, 6, True)
+    assert _rel(out, oracle.kyv(p.X, ell, s2, 2 * p.noise, V)) <= 2e-5
+
+
 def test_matvec_isotropic_and_leading_dimension(kpcg):
     p = _problem(300, 5, seed=3, ard=False, ell=0.7)
     V = synthetic.rng(1).standard_normal((300, 2))
