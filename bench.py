@@ -195,7 +195,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     prec = {"auto": kpcg.KPCG_FP32_IR, "fp32_ir": kpcg.KPCG_FP32_IR,
-            "tf32_ir": kpcg.KPCG_TF32_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+            "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
 
     # replicas: each rank solves its own seeded instance of the same workload
     p = synthetic.config2(seed=rank, n=args.n)

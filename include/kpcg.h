@@ -65,8 +65,14 @@ typedef enum {
     KPCG_FP32_IR = 2,  /* mixed: outer flexible CG (Notay) in FP64 whose
                           preconditioner is an inner FP32 PCG on the shifted
                           operator K + sigma^2 (1 + inner_shift) I               */
-    KPCG_TF32_IR = 3   /* as KPCG_FP32_IR, the inner K.V on the tensor cores
-                          (tcgen05, TF32 split distances, FP32 accumulate)       */
+    KPCG_TC_IR = 3,    /* as KPCG_FP32_IR, the inner K.V on the tensor cores:
+                          tcgen05 BF16 MMAs on a three-way split of the scaled
+                          inputs form the exponent in FP32 (TMEM), exp2 on the
+                          MUFU; requires d <= 16                                 */
+    KPCG_DF64 = 4      /* FP64 vectors and scalars; iterations use the
+                          double-float K.V (FP32-pair arithmetic on the FP32
+                          pipe, about 44 bits); stop and restart decisions use
+                          the native FP64 residual                               */
 } kpcg_precision;
 
 typedef struct {
@@ -152,14 +158,18 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt);
 kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx);
 
 /* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
- * matrix-free product of Sec. 2.1, entries built in FP64 from X. */
+ * matrix-free product of Sec. 2.1.  impl 0: entries and sums in native FP64;
+ * impl 1: the double-float kernel of KPCG_DF64 (FP32-pair arithmetic, about
+ * 44 bits per entry, sums carried as FP32 pairs and added in FP64). */
 kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
-                            int64_t ldo);
+                            int64_t ldo, int32_t impl);
 
 /* O = (K + sigma^2 I) V in reduced precision (device float32).
  * impl 0: FP32 entries by direct differences on the CUDA cores;
- * impl 1: tensor-core distances (tcgen05, TF32 hi/lo split), FP32 exp and
- *         accumulation -- the kernel KPCG_TF32_IR iterates with. */
+ * impl 1: the tensor-core kernel KPCG_TC_IR iterates with (tcgen05 BF16x3
+ *         split exponent, FP32 accumulate, exp2 and contraction in FP32);
+ *         d <= 16, else KPCG_ERR_ARG.  A bounded wait that expires inside
+ *         the kernel returns KPCG_ERR_TIMEOUT. */
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 

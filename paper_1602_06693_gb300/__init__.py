@@ -7,12 +7,13 @@ is no CPU fallback: if the library or a GPU is missing, the binding raises.
 """
 from .binding import (  # noqa: F401
     KPCG_FP32,
+    KPCG_DF64,
     KPCG_FP32_IR,
     KPCG_FP64,
     KPCG_PREC_BLOCK_JACOBI,
     KPCG_PREC_NONE,
     KPCG_PREC_NYSTROM,
-    KPCG_TF32_IR,
+    KPCG_TC_IR,
     KpcgError,
     Options,
     Solver,

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
 KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI = 0, 1, 2
-KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TF32_IR = 0, 1, 2, 3
+KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64 = 0, 1, 2, 3, 4
 
 _STATUS = {
     0: "KPCG_OK", 1: "KPCG_ERR_ARG", 2: "KPCG_ERR_CUDA", 3: "KPCG_ERR_OOM",
@@ -105,7 +105,7 @@ def lib():
         L.kpcg_set_theta.argtypes = [vp, pdbl, dbl]
         L.kpcg_set_options.argtypes = [vp, ctypes.POINTER(Options)]
         L.kpcg_precond.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int64)]
-        L.kpcg_matvec_f64.argtypes = [vp, vp, i64, i32, vp, i64]
+        L.kpcg_matvec_f64.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_matvec_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_precond_apply_f64.argtypes = [vp, vp, i64, i32, vp, i64]
         L.kpcg_solve.argtypes = [vp, vp, i64, i32, dbl, vp, vp, i64,
@@ -236,14 +236,14 @@ class Solver:
             p = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         self._check(lib().kpcg_precond(self._h, int(kind), int(size), p))
 
-    def matvec_f64(self, V, out=None):
+    def matvec_f64(self, V, impl=0, out=None):
         torch = _torch()
         V, ldv, c = _colmajor(V, "V")
         O = out if out is not None else (torch.empty_like(V) if V.dim() == 1 else
                                          fortran_empty(self.n, c, torch.float64, V.device))
         O_, ldo, _ = _colmajor(O, "out")
         self._check(lib().kpcg_matvec_f64(self._h, _dptr(V, torch.float64, "V"), ldv, c,
-                                          _dptr(O_, torch.float64, "out"), ldo))
+                                          _dptr(O_, torch.float64, "out"), ldo, int(impl)))
         return O
 
     def matvec_f32(self, V, impl=0, out=None):

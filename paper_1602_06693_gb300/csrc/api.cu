@@ -235,7 +235,7 @@ static bool col_converged(double rr, double bb, double tol, int tol_mode, int64_
 // Noise of the system the preconditioner approximates: sigma^2 for the
 // single-precision solvers, the shifted inner noise for the mixed ones.
 static double precond_noise(const Ctx& h) {
-    const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TF32_IR;
+    const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TC_IR;
     return mixed ? h.noise * (1.0 + h.opt.inner_shift) : h.noise;
 }
 
@@ -278,7 +278,7 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
     cudaStream_t st = h.stream;
     const int64_t n = h.n, ld = h.ld;
     const int W = std::max(1, h.opt.fcg_window);
-    const bool tc = (h.opt.precision == KPCG_TF32_IR);
+    const bool tc = (h.opt.precision == KPCG_TC_IR);
     const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
     double* R = h.R64.need((size_t)ld * c);
     double* Pw = h.fcgP.need((size_t)W * ld * c);
@@ -441,17 +441,19 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
     cudaStream_t st = h.stream;
     const int64_t n = h.n, ld = h.ld;
     const int prec = h.opt.precision;
-    if (prec == KPCG_TF32_IR && !kv_tc_supported(h.dp))
+    if (prec == KPCG_TC_IR && !kv_tc_supported(h.dp))
         fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
     std::vector<int> iters_col((size_t)c, 0);
     int iters_total = 0, steps = 0, broken = 0;
     kpcg_status status = KPCG_OK;
     std::vector<double> rr, bb;
+    bool rr_current = false;  // rr/bb hold the FP64 residual of the current Xout
     double* R = h.R64.need((size_t)ld * c);
 
-    if (prec == KPCG_FP64 || prec == KPCG_FP32) {
+    if (prec == KPCG_FP64 || prec == KPCG_FP32 || prec == KPCG_DF64) {
         // Plain PCG in one precision with residual replacement restarts.
-        const bool f64 = (prec == KPCG_FP64);
+        const bool f64 = (prec != KPCG_FP32);
+        const bool dfk = (prec == KPCG_DF64);
         if (f64) {
             if (X0)
                 copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
@@ -476,8 +478,11 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
                     h, c, B, ldb, Xout, ldx, x0_zero, tol, h.opt.tol_mode, budget,
                     [&](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
                         h.prof.time(Profiler::KV_INNER, st, [&] {
-                            kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, V, ldv, cc, nullptr, 0,
-                                   O, ldo, h.kvws, st);
+                            if (dfk)
+                                kv_df(h, V, ldv, cc, nullptr, 0, O, ldo, h.noise);
+                            else
+                                kv_f64(h.xs64.p, n, h.dp, h.c0_64(), h.noise, V, ldv, cc, nullptr,
+                                       0, O, ldo, h.kvws, st);
                         });
                     },
                     [&](const double* Rr, int64_t ldr, int cc, double* Z, int64_t ldz) {
@@ -506,11 +511,13 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
             for (int k = 0; k < c; ++k) iters_col[k] += std::abs(its[k] < 0 ? -1 - its[k] : its[k]);
             broken += br;
             x0_zero = false;
+            rr_current = false;
             if (br) break;
             // true residual in the working precision decides a restart
             bool all = true;
             if (f64) {
                 residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+                rr_current = true;
             } else {
                 float* q32 = h.c32.q.need((size_t)ld * c);
                 float* r32 = h.c32.r.need((size_t)ld * c);
@@ -543,11 +550,12 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
         if (!f64) convert_scale_cols<double, float>(Xout, ldx, x32, ld, n, c, nullptr, 0, st);
     } else {
         status = fcg_solve(h, B, ldb, c, tol, X0, Xout, ldx, iters_col, iters_total, steps, rr, bb);
+        rr_current = (status == KPCG_OK);  // converged exits certify on a recomputed residual
     }
-    // FP64 residual of what is returned
+    // FP64 residual of what is returned (the single-precision FP32 solver
+    // checked its own operator only)
     double maxrel = 0.0;
-    if (prec == KPCG_FP64 || prec == KPCG_FP32 || rr.empty())
-        residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+    if (!rr_current || prec == KPCG_FP32) residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
     bool all = true;
     for (int k = 0; k < c; ++k) {
         if (bb[k] > 0) maxrel = std::max(maxrel, std::sqrt(rr[k] / bb[k]));
@@ -642,7 +650,7 @@ const char* kpcg_status_string(kpcg_status s) {
 static void check_opts(const kpcg_options* o) {
     if (o->max_iter < 0 || o->max_outer < 0 || o->check_every < 1 || o->max_restarts < 0)
         fail(KPCG_ERR_ARG, "invalid options");
-    if (o->precision < KPCG_FP64 || o->precision > KPCG_TF32_IR)
+    if (o->precision < KPCG_FP64 || o->precision > KPCG_DF64)
         fail(KPCG_ERR_ARG, "invalid precision");
     if (o->tol_mode != 0 && o->tol_mode != 1) fail(KPCG_ERR_ARG, "invalid tol_mode");
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) fail(KPCG_ERR_ARG, "inner_tol not in (0,1)");
@@ -763,15 +771,20 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
 }
 
 kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
-                            int64_t ldo) {
+                            int64_t ldo, int32_t impl) {
     if (!h) return KPCG_ERR_ARG;
     KPCG_GUARD(h, {
         if (c < 0 || ldv < h->n || ldo < h->n) fail(KPCG_ERR_ARG, "bad sizes");
         if (c == 0) return KPCG_OK;
         kpcg::check_dev_ptr(V, "V");
         kpcg::check_dev_ptr(O, "O");
-        kpcg::kv_f64(h->xs64.p, h->n, h->dp, h->c0_64(), h->noise, V, ldv, c, nullptr, 0, O, ldo,
-                     h->kvws, h->stream);
+        if (impl == 0)
+            kpcg::kv_f64(h->xs64.p, h->n, h->dp, h->c0_64(), h->noise, V, ldv, c, nullptr, 0, O,
+                         ldo, h->kvws, h->stream);
+        else if (impl == 1)
+            kpcg::kv_df(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
+        else
+            fail(KPCG_ERR_ARG, "unknown impl");
         KPCG_CUDA(cudaStreamSynchronize(h->stream));
     });
     return KPCG_OK;

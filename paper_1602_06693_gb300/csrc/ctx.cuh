@@ -101,6 +101,12 @@ struct Ctx {
     DevBuf<uint16_t> tcA, tcB;
     DevBuf<float> tcV, tcPart;
     DevBuf<int> tc_err;
+    // double-float operands (kv_df.cu), rebuilt when theta changes
+    int df_version = -1;
+    float df_c0h = 0.f, df_c0l = 0.f;
+    DevBuf<float> xdf;
+    DevBuf<float2> df_tab;
+    DevBuf<double> df_grid;
     std::string err;
 
     double c0_64() const { return std::log(s2); }
@@ -109,6 +115,10 @@ struct Ctx {
 
 // Tensor-core K.V on the handle's inputs (kv_tc.cu).
 void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise);
+// O = K V + noise V (or B - that when B != nullptr) with the double-float
+// kernel (kv_df.cu); FP64 in and out.
+void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb, double* O,
+           int64_t ldo, double noise);
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);

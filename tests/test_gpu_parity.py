@@ -81,6 +81,22 @@ def test_matvec_f64_matches_oracle(kpcg, n, d, c):
     assert _rel(out, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 6),
+                                   (700, 32, 2), (513, 12, 5), (6000, 8, 1)])
+def test_matvec_double_float_matches_oracle(kpcg, n, d, c):
+    # FP32-pair entries: exact grid differences, TwoSum accumulation and a
+    # table-driven exp2 keep each entry within about 2^-40 of FP64, so the
+    # products agree with the oracle far below FP32 rounding.
+    p = _problem(n, d, seed=13 * n + d)
+    V = synthetic.rng(9).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(_cm(V), impl=1))
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= 1e-11, k
+
+
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (255, 2, 1), (1000, 8, 3), (4099, 16, 17),
                                    (700, 32, 5)])
 def test_matvec_f32_matches_oracle(kpcg, n, d, c):
@@ -266,13 +282,30 @@ def test_paper_absolute_stop_rule(kpcg):
     assert st == 0 and r @ r < 800 * 1e-10
 
 
-def test_full_size_mixed_precision_solve_sampled_rows(kpcg):
+@pytest.mark.parametrize("kind", ["nystrom", "bj"])
+def test_ill_conditioned_double_float_solve(kpcg, kind):
+    p = synthetic.config2(seed=0, n=2048)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    ref = oracle.dense_solve(p.X, ell, s2, p.noise, p.y)
+    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+        if kind == "nystrom":
+            s.precond(kpcg.KPCG_PREC_NYSTROM, 512, synthetic.inducing_subset(p.n, 512, seed=1))
+        else:
+            s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, 512)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    x = _np(x)
+    assert st == 0 and info.max_rel_res <= 1e-8, info.as_dict()
+    assert _rel(oracle.kyv(p.X, ell, s2, p.noise, x), p.y) <= 1e-8
+    assert _rel(x, ref) <= 1e-5
+
+
+def test_full_size_double_float_solve_sampled_rows(kpcg):
     # The n = 65536, d = 8, noise 1e-4 uniform-cube ARD system with Nystrom
     # m = 1024, as timed by the benchmark.  The residual is checked on 48
     # sampled rows, each recomputed by the oracle row by row in FP64.
     p = synthetic.config2(seed=0)
     idx = synthetic.inducing_subset(p.n, 1024, seed=1)
-    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
         s.precond(kpcg.KPCG_PREC_NYSTROM, 1024, idx)
         x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
     x = _np(x)
