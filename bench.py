@@ -38,11 +38,19 @@ N_FULL, D, M_INDUCING, TOL = 65536, 8, 1024, 1e-8
 METRIC = "PCG time-to-rel-res 1e-8 at n=65k vs plain FP32; K.V TFLOP/s vs roofline"
 WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum sin(x)+N(0,0.01); "
             "Nystrom m=1024 built in-step; tol 1e-8 rel; 1 RHS")
-# Algorithmic work of one K.V entry (i, j) with c right-hand sides: d subtractions,
-# d multiplies and d adds for the squared distance, a multiply-add for the exponent,
-# one exponential, and c multiply-adds for the contraction.
-def flops_per_entry(d, c):
-    return 3 * d + 2 + 1 + 2 * c
+# Algorithmic work of one K.V entry (i, j) with c right-hand sides, in FP32-pipe
+# instructions of the double-float kernel: per dimension 16 (exact difference,
+# three-part low difference, TwoProduct, two FMAs, TwoSum into the exponent),
+# 33 for the table-driven exp2 of a double-float, 12 per column for the split
+# product and its TwoSum accumulation.
+def df_ops_per_entry(d, c):
+    return 16 * d + 33 + 12 * c
+
+
+# Native-FP64 kernel: d subtractions and d FMAs for the distance, the FP64 exp
+# (counted as one operation) and c FMAs.
+def fp64_ops_per_entry(d, c):
+    return 2 * d + 1 + c
 
 
 def sm_clock_probe():
@@ -194,7 +202,7 @@ def main():
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    prec = {"auto": kpcg.KPCG_FP32_IR, "fp32_ir": kpcg.KPCG_FP32_IR,
+    prec = {"auto": kpcg.KPCG_DF64, "df64": kpcg.KPCG_DF64, "fp32_ir": kpcg.KPCG_FP32_IR,
             "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
 
     # replicas: each rank solves its own seeded instance of the same workload
@@ -251,24 +259,29 @@ def main():
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if dom.startswith("kv"):
-        flops = flops_per_entry(D, 1) * float(p.n) ** 2
-        achieved = flops / (ms / calls / 1e3) / 1e12
-        if dom == "kv_outer_fp64":
-            peak = 1.25  # nominal GB300 FP64 rate (no FP64 figure is measured)
-            peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
+        entries = float(p.n) ** 2
+        if dom == "kv_inner" and prec == kpcg.KPCG_DF64:
+            ops = df_ops_per_entry(D, 1) * entries
+            peak = 152 * 128 * sm_max * 1e6 / 1e12
+            peak_src = (f"FP32 pipe issue rate: 152 SMs x 128 lanes x {sm_max:.0f} MHz "
+                        "(unit counts and max clock; no measured FP32 figure)")
+            kname = "kv_df_kernel (double-float K.V)"
         else:
-            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-            peak_src = f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz"
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            ops = fp64_ops_per_entry(D, 1) * entries
+            peak = 1.25 / 2  # 1.25 TFLOP/s nominal FP64 = 0.625 T FMA-class op/s
+            peak_src = "nominal GB300 FP64 rate, 1.25 TFLOP/s = 0.625 Top/s"
+            kname = "kv_simt_kernel<double> (native FP64 K.V)"
+        achieved = ops / (ms / calls / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "Top/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": peak_src, "calls": calls, "avg_ms": ms / calls,
-                "flops_per_call": flops}
+                "ops_per_call": ops}
     else:
         # Nystrom apply streams K_XU (n x m FP32) twice and reads/writes n-vectors
-        bytes_ = 2 * 4.0 * p.n * M_INDUCING + 3 * 4.0 * p.n
+        bytes_ = 2 * 4.0 * p.n * M_INDUCING + 3 * 8.0 * p.n
         achieved = bytes_ / (ms / calls / 1e3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+        roof = {"bound": "hbm", "kernel": "Nystrom apply", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "calls": calls,
                 "avg_ms": ms / calls}

@@ -131,10 +131,14 @@ static void check_dev_ptr(const void* p, const char* name) {
 // Per-column batched PCG (Algorithm 1, textbook recurrence) in vector type T.
 // X holds x0 on entry (zero if x0_zero) and the iterate on return.
 // Returns the number of iterations run (max over columns).
+// R0 (nullable, leading dimension h.ld) is the residual B - K_y X of the
+// entry X when the caller has it, e.g. recomputed with a more accurate
+// operator than `matvec`; then the recursion starts from it.
 template <typename T, typename MV, typename PC>
 static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, bool x0_zero,
                     double tol, int tol_mode, int max_iter, MV&& matvec, PC&& precond,
-                    CgBufs<T>& bufs, std::vector<int>& iters_out, int& broken) {
+                    CgBufs<T>& bufs, std::vector<int>& iters_out, int& broken,
+                    const T* R0 = nullptr) {
     const int64_t n = h.n, ld = h.ld;
     cudaStream_t st = h.stream;
     T* r = bufs.r.need((size_t)ld * c);
@@ -154,6 +158,8 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
     if (x0_zero) {
         fill_zero_cols(X, sizeof(T), ldx, n, c, st);
         copy_cols<T>(r, ld, B, ldb, n, c, st);
+    } else if (R0) {
+        copy_cols<T>(r, ld, R0, ld, n, c, st);
     } else {
         matvec(X, ldx, c, q, ld);
         sub_cols_t_kernel<T><<<dim3(gx(n), c), 256, 0, st>>>(r, ld, B, ldb, q, ld, n);
@@ -490,7 +496,7 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
                             precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, st);
                         });
                     },
-                    h.c64, its, br);
+                    h.c64, its, br, rr_current ? R : nullptr);
             } else {
                 ran = pcg_core<float>(
                     h, c, b32, ld, x32, ld, x0_zero, tol, h.opt.tol_mode, budget,

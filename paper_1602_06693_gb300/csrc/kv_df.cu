@@ -5,11 +5,16 @@
 // K_ij = s^2 exp(-1/2 sum_r (x_ir - x_jr)^2 / l_r^2) (Eq. 1) as an unevaluated
 // sum of two FP32 numbers (hi + lo), which keeps about 44 bits:
 //
-//  * Inputs.  x' = (x - mu) / l * sqrt(log2(e)/2) is split per dimension r into
-//    hi, a multiple of 2^(k_r - 23) with |x'| < 2^k_r (so hi_i - hi_j is exact
-//    in FP32), and lo = fl(x' - hi).
-//  * Squared distance.  delta = D + E with D = hi_i - hi_j exact, E = lo_i -
-//    lo_j; delta^2 = D*D (split exactly by an FMA, "TwoProduct") + 2 D E + E^2,
+//  * Inputs.  x' = (x - mu) / l * sqrt(log2(e)/2) (FP64) is split per
+//    dimension r into hi, a multiple of 2^(k_r - 23) with |x'| < 2^k_r (so
+//    hi_i - hi_j is exact in FP32), lo = fl(x' - hi) and lo2 = fl(x' - hi - lo):
+//    the three parts hold the FP64 value exactly, so the only per-point error
+//    is the FP64 rounding of x' itself.  (With two parts, the 2^-48 rounding of
+//    lo is a per-point, hence structured, perturbation of K; multiplied by a
+//    solution with |alpha| >> |y| it limited the residual to about 1e-7.)
+//  * Squared distance.  delta = D + E with D = hi_i - hi_j exact, E = (lo_i -
+//    lo_j) + (lo2_i - lo2_j); delta^2 = D*D (split exactly by an FMA,
+//    "TwoProduct") + 2 D E + E^2,
 //    accumulated into the exponent a = log2(s^2) - |x'_i - x'_j|^2 with Knuth's
 //    TwoSum, so no rounding of the running sum is lost.
 //  * exp2 of a double-float (table-driven method of P. T. P. Tang, "Table-
@@ -114,20 +119,20 @@ __device__ __forceinline__ DF df_exp2(float ah, float al, const float2* __restri
 
 template <int DP, int CB>
 __global__ void __launch_bounds__(KT)
-    kv_df_kernel(const float2* __restrict__ xs, int64_t n, float c0h, float c0l,
+    kv_df_kernel(const float4* __restrict__ xs, int64_t n, float c0h, float c0l,
                  const double* __restrict__ V, int64_t ldv, int ncols,
                  const float2* __restrict__ gtab, double* __restrict__ part, int64_t ldp,
                  int64_t cps) {
     __shared__ float2 tab[NTAB];
-    __shared__ float2 sx[TJ * DP];
+    __shared__ float4 sx[TJ * DP];
     __shared__ float2 sv[TJ * CB];
     for (int e = threadIdx.x; e < NTAB; e += KT) tab[e] = gtab[e];
     const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
     const int64_t j0 = (int64_t)blockIdx.y * cps;
     const int64_t j1 = min(n, j0 + cps);
-    float2 xi[DP];
+    float4 xi[DP];
 #pragma unroll
-    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : make_float2(0.f, 0.f);
+    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     float S[CB], C[CB];
 #pragma unroll
     for (int k = 0; k < CB; ++k) S[k] = C[k] = 0.f;
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(KT)
         __syncthreads();
         for (int e = threadIdx.x; e < TJ * DP; e += KT) {
             const int jj = e / DP;
-            sx[e] = (jj < jn) ? xs[(jt + jj) * DP + (e - jj * DP)] : make_float2(0.f, 0.f);
+            sx[e] = (jj < jn) ? xs[(jt + jj) * DP + (e - jj * DP)] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int e = threadIdx.x; e < TJ * CB; e += KT) {
             const int k = e / TJ, jj = e - k * TJ;
@@ -149,9 +154,9 @@ __global__ void __launch_bounds__(KT)
             float ah = c0h, al = c0l;
 #pragma unroll
             for (int q = 0; q < DP; ++q) {
-                const float2 xj = sx[jj * DP + q];
+                const float4 xj = sx[jj * DP + q];
                 const float D = xi[q].x - xj.x;  // exact
-                const float E = xi[q].y - xj.y;
+                const float E = (xi[q].y - xj.y) + (xi[q].z - xj.z);
                 const float P = D * D;
                 float Pe = fmaf(D, D, -P);
                 Pe = fmaf(2.f * D, E, Pe);
@@ -205,16 +210,18 @@ __global__ void colmax_kernel(const double* __restrict__ xs64, int64_t n, int dp
     if (threadIdx.x == 0) out[q] = sh[0];
 }
 
-// hi = x' rounded to the grid 2^(k_r - 23), lo = fl(x' - hi).
+// hi = x' rounded to the grid 2^(k_r - 23), lo = fl(x' - hi), lo2 = x' - hi - lo.
 __global__ void df_prep_kernel(const double* __restrict__ xs64, int64_t n, int dp, double scale,
-                               const double* __restrict__ grid, float2* __restrict__ out) {
+                               const double* __restrict__ grid, float4* __restrict__ out) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * dp) return;
     const int q = (int)(e % dp);
     const double x = xs64[e] * scale;
     const double g = grid[q];
     const double hi = rint(x / g) * g;
-    out[e] = make_float2((float)hi, (float)(x - hi));
+    const float lo = (float)(x - hi);
+    const float lo2 = (float)(x - hi - (double)lo);
+    out[e] = make_float4((float)hi, lo, lo2, 0.f);
 }
 
 struct DfSplit {
@@ -237,7 +244,7 @@ DfSplit df_plan(int64_t n) {
 }
 
 template <int DP, int CB>
-void df_launch(const float2* xs, int64_t n, float c0h, float c0l, const double* V, int64_t ldv,
+void df_launch(const float4* xs, int64_t n, float c0h, float c0l, const double* V, int64_t ldv,
                int ncols, const float2* tab, double* part, const DfSplit& s, cudaStream_t st) {
     kv_df_kernel<DP, CB><<<dim3(s.nrb, s.nsplit), KT, 0, st>>>(xs, n, c0h, c0l, V, ldv, ncols,
                                                                tab, part, s.ldp, s.cps);
@@ -245,7 +252,7 @@ void df_launch(const float2* xs, int64_t n, float c0h, float c0l, const double* 
 }
 
 template <int DP>
-void df_launch_cb(int cb, const float2* xs, int64_t n, float c0h, float c0l, const double* V,
+void df_launch_cb(int cb, const float4* xs, int64_t n, float c0h, float c0l, const double* V,
                   int64_t ldv, int ncols, const float2* tab, double* part, const DfSplit& s,
                   cudaStream_t st) {
     switch (cb) {
@@ -290,7 +297,7 @@ static void df_prepare(Ctx& h) {
     }
     KPCG_CUDA(cudaMemcpyAsync(mx + h.dp, grid.data(), sizeof(double) * h.dp,
                               cudaMemcpyHostToDevice, st));
-    float2* xdf = reinterpret_cast<float2*>(h.xdf.need((size_t)n * h.dp * 2));
+    float4* xdf = reinterpret_cast<float4*>(h.xdf.need((size_t)n * h.dp * 4));
     df_prep_kernel<<<(unsigned)((n * h.dp + 255) / 256), 256, 0, st>>>(h.xs64.p, n, h.dp, scale,
                                                                        mx + h.dp, xdf);
     KPCG_LAUNCHED("df_prep_kernel");
@@ -309,7 +316,7 @@ void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t
     const DfSplit s = df_plan(n);
     const int max_cb = 4;
     double* part = h.kvws.part64.need((size_t)s.nsplit * max_cb * s.ldp);
-    const float2* xs = reinterpret_cast<const float2*>(h.xdf.p);
+    const float4* xs = reinterpret_cast<const float4*>(h.xdf.p);
     const float2* tab = reinterpret_cast<const float2*>(h.df_tab.p);
     for (int k0 = 0; k0 < c;) {
         const int rem = c - k0;
