@@ -204,6 +204,31 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
 kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
                       double* grad, double* alpha, kpcg_info* info);
 
+/* The native-FP64 product O = (K + sigma^2 I) V of kpcg_matvec_f64 (impl 0)
+ * for callers that cannot allocate device memory: for example a host program
+ * whose GPU memory is entirely reserved by another allocator (a framework's
+ * pool that has claimed the device), or a latency-critical caller that must
+ * not pay cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; it is a deployment variant of the product of Sec. 2.1.
+ *   X: device float32 n x d row-major; log_theta: host, d+1 (ard) or 2 values
+ *   as in kpcg_create; V, O: device float64, column-major, ldv/ldo >= n;
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * It allocates nothing: its scratch (column means, scaled inputs, split
+ * partial sums) is one static device array of 16 MiB that every GPU loading
+ * the library holds until exit.  Sizes needing more are rejected with
+ * KPCG_ERR_ARG and a message; on a 152-SM GPU every n below 74 880 fits for
+ * d <= 8 (131 064 for d <= 4, 43 680 for d <= 16, 24 960 for d <= 32).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) while the
+ * device is current; make that first call before any stream capture.  Every
+ * call shares the array and leaves its contents behind, so calls that overlap
+ * on the GPU (other streams, other host threads) race: serialise them.  The
+ * call returns after the stream has finished its work.  On error the message
+ * is available from kpcg_last_error(NULL). */
+kpcg_status kpcg_matvec_f64_noalloc(const float* X, int64_t n, int32_t d,
+                                    const double* log_theta, int32_t ard, double noise_var,
+                                    const double* V, int64_t ldv, int32_t c, double* O,
+                                    int64_t ldo, void* stream);
+
 /* Release the handle and every device buffer it owns.  NULL is ignored. */
 void kpcg_destroy(kpcg_t h);
 

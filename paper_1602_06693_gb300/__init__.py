@@ -23,4 +23,5 @@ from .binding import (  # noqa: F401
     fortran_empty,
     lib,
     library_path,
+    matvec_f64_noalloc,
 )

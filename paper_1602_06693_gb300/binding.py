@@ -28,7 +28,7 @@ SYMBOLS = (
     "kpcg_default_options", "kpcg_status_string", "kpcg_create", "kpcg_set_theta",
     "kpcg_set_options", "kpcg_precond", "kpcg_matvec_f64", "kpcg_matvec_f32",
     "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
-    "kpcg_last_error",
+    "kpcg_last_error", "kpcg_matvec_f64_noalloc",
 )
 
 
@@ -112,6 +112,8 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
         L.kpcg_dkv.argtypes = [vp, vp, i64, i32, vp, i64]
         L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, pdbl, vp, ctypes.POINTER(Info)]
+        L.kpcg_matvec_f64_noalloc.argtypes = [vp, i64, i32, pdbl, i32, dbl, vp, i64, i32, vp,
+                                              i64, vp]
         L.kpcg_destroy.argtypes = [vp]
         L.kpcg_destroy.restype = None
         L.kpcg_last_error.argtypes = [vp]
@@ -127,6 +129,30 @@ def exported_symbols():
     """Names from include/kpcg.h that the loaded library exports."""
     L = lib()
     return [s for s in SYMBOLS if hasattr(L, s)]
+
+
+def matvec_f64_noalloc(X, log_theta, noise, V, ard=True, out=None, stream=None):
+    """kpcg_matvec_f64_noalloc: (K + noise I) V in FP64 without device allocation
+    inside the library (its scratch is a static device array)."""
+    torch = _torch()
+    if X.dtype != torch.float32 or not X.is_cuda or not X.is_contiguous():
+        raise TypeError("X must be a contiguous float32 CUDA tensor (n x d row-major)")
+    n, d = int(X.shape[0]), int(X.shape[1])
+    V, ldv, c = _colmajor(V, "V")
+    O = out if out is not None else (torch.empty_like(V) if V.dim() == 1 else
+                                     fortran_empty(n, c, torch.float64, V.device))
+    O_, ldo, _ = _colmajor(O, "out")
+    lt = np.ascontiguousarray(log_theta, dtype=np.float64)
+    st = stream if stream is not None else torch.cuda.current_stream(X.device)
+    L = lib()
+    rc = L.kpcg_matvec_f64_noalloc(ctypes.c_void_p(X.data_ptr()), n, d,
+                                   lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(ard),
+                                   float(noise), _dptr(V, torch.float64, "V"), ldv, c,
+                                   _dptr(O_, torch.float64, "out"), ldo,
+                                   ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise KpcgError(rc, L.kpcg_last_error(None).decode())
+    return O
 
 
 def default_options(**kw) -> Options:

@@ -90,6 +90,9 @@ unsigned gx(int64_t n) {
 
 static thread_local std::string g_create_err;
 
+// Message reported by kpcg_last_error(NULL) for calls that have no handle.
+void set_handleless_error(const std::string& msg) { g_create_err = msg; }
+
 static void ctx_rescale(Ctx& h) {
     std::vector<double> inv(h.d);
     for (int q = 0; q < h.d; ++q) {

@@ -18,6 +18,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(kpcg_status s, const std::string& msg);
+void set_handleless_error(const std::string& msg);
 void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define KPCG_CUDA(call) ::kpcg::cuda_check((call), #call, __FILE__, __LINE__)
 // Checks a kernel launch and counts it (per host thread).
@@ -73,6 +74,11 @@ struct KvWorkspace {
 void kv_f64(const double* xs, int64_t n, int dp, double c0, double noise, const double* V,
             int64_t ldv, int c, const double* B, int64_t ldb, double* O, int64_t ldo,
             KvWorkspace& ws, cudaStream_t st);
+// The FP64 product with caller-provided partial-sum scratch of at least
+// kv_f64_scratch_elems(n) doubles (column blocks of up to four).
+size_t kv_f64_scratch_elems(int64_t n);
+void kv_f64_into(const double* xs, int64_t n, int dp, double c0, double noise, const double* V,
+                 int64_t ldv, int c, double* O, int64_t ldo, double* part, cudaStream_t st);
 void kv_f32(const float* xs, int64_t n, int dp, float c0, float noise, const float* V,
             int64_t ldv, int c, float* O, int64_t ldo, KvWorkspace& ws, cudaStream_t st);
 

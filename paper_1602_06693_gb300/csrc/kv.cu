@@ -342,6 +342,38 @@ void dkv_launch(int cb, const float* xs, int64_t n, int nq, int ard, float c0, c
 
 }  // namespace
 
+size_t kv_f64_scratch_elems(int64_t n) {
+    if (n <= 0) return 0;
+    const Split s = plan(n, KT);
+    return (size_t)s.nsplit * 4 * (size_t)s.ldp;
+}
+
+void kv_f64_into(const double* xs, int64_t n, int dp, double c0, double noise, const double* V,
+                 int64_t ldv, int c, double* O, int64_t ldo, double* part, cudaStream_t st) {
+    if (n <= 0 || c <= 0) return;
+    const Split s = plan(n, KT);
+    for (int k0 = 0; k0 < c;) {
+        const int rem = c - k0;
+        const int cb = rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int ncols = std::min(cb, rem);
+        const double* Vk = V + (int64_t)k0 * ldv;
+        switch (dp) {
+            case 4: launch_cb<double, 4>(cb, xs, n, c0, Vk, ldv, ncols, part, s, 1, st); break;
+            case 8: launch_cb<double, 8>(cb, xs, n, c0, Vk, ldv, ncols, part, s, 1, st); break;
+            case 12: launch_cb<double, 12>(cb, xs, n, c0, Vk, ldv, ncols, part, s, 1, st); break;
+            case 16: launch_cb<double, 16>(cb, xs, n, c0, Vk, ldv, ncols, part, s, 1, st); break;
+            case 32: launch_cb<double, 32>(cb, xs, n, c0, Vk, ldv, ncols, part, s, 1, st); break;
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+        dim3 rg((unsigned)((n + 255) / 256), (unsigned)ncols);
+        kv_reduce_kernel<double><<<rg, 256, 0, st>>>(part, s.ldp, s.nsplit, cb, ncols, Vk, ldv,
+                                                     noise, nullptr, 0, O + (int64_t)k0 * ldo,
+                                                     ldo, n);
+        KPCG_LAUNCHED("kv_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
 void kv_f64(const double* xs, int64_t n, int dp, double c0, double noise, const double* V,
             int64_t ldv, int c, const double* B, int64_t ldb, double* O, int64_t ldo,
             KvWorkspace& ws, cudaStream_t st) {
