@@ -38,13 +38,14 @@ N_FULL, D, M_INDUCING, TOL = 65536, 8, 1024, 1e-8
 METRIC = "PCG time-to-rel-res 1e-8 at n=65k vs plain FP32; K.V TFLOP/s vs roofline"
 WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum sin(x)+N(0,0.01); "
             "Nystrom m=1024 built in-step; tol 1e-8 rel; 1 RHS")
-# Algorithmic work of one K.V entry (i, j) with c right-hand sides, in FP32-pipe
-# instructions of the double-float kernel: per dimension 16 (exact difference,
-# three-part low difference, TwoProduct, two FMAs, TwoSum into the exponent),
-# 33 for the table-driven exp2 of a double-float, 12 per column for the split
-# product and its TwoSum accumulation.
-def df_ops_per_entry(d, c):
-    return 16 * d + 33 + 12 * c
+# Algorithmic work of one double-float K.V, in FP32-pipe instructions.  K is
+# symmetric, so each of the n(n+1)/2 distinct entries is evaluated once: per
+# dimension 16 (exact difference, three-part low difference, TwoProduct, two
+# FMAs, TwoSum into the exponent) plus 33 for the table-driven exp2 of a
+# double-float; every (i, j) then costs 12 per right-hand side (split product
+# and TwoSum accumulation).
+def df_ops_per_product(n, d, c):
+    return n * (n + 1) / 2 * (16 * d + 33) + float(n) * n * 12 * c
 
 
 # Native-FP64 kernel: d subtractions and d FMAs for the distance, the FP64 exp
@@ -261,11 +262,11 @@ def main():
     if dom.startswith("kv"):
         entries = float(p.n) ** 2
         if dom == "kv_inner" and prec == kpcg.KPCG_DF64:
-            ops = df_ops_per_entry(D, 1) * entries
+            ops = df_ops_per_product(p.n, D, 1)
             peak = 152 * 128 * sm_max * 1e6 / 1e12
             peak_src = (f"FP32 pipe issue rate: 152 SMs x 128 lanes x {sm_max:.0f} MHz "
                         "(unit counts and max clock; no measured FP32 figure)")
-            kname = "kv_df_kernel (double-float K.V)"
+            kname = "kv_df_sym_kernel (double-float K.V, symmetric tile pairs)"
         else:
             ops = fp64_ops_per_entry(D, 1) * entries
             peak = 1.25 / 2  # 1.25 TFLOP/s nominal FP64 = 0.625 T FMA-class op/s

@@ -107,6 +107,11 @@ struct Ctx {
     DevBuf<float> xdf;
     DevBuf<float2> df_tab;
     DevBuf<double> df_grid;
+    bool df_symmetric = true;  // symmetric tile-pair kernel (cleared by tests of the other)
+    int64_t df_sym_n = -1;
+    int df_sym_G = 0, df_nwork = 0;
+    DevBuf<int> df_work;
+    DevBuf<double> df_prow, df_pcol;
     std::string err;
 
     double c0_64() const { return std::log(s2); }
@@ -119,6 +124,10 @@ void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t l
 // kernel (kv_df.cu); FP64 in and out.
 void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb, double* O,
            int64_t ldo, double noise);
+// Native-FP64 product on symmetric tile pairs (kv_df.cu); falls back to the
+// row-split kernel for small n or d > 16.  Same arguments as kv_df.
+void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb,
+                double* O, int64_t ldo, double noise);
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);

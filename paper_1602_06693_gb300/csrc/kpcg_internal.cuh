@@ -89,6 +89,9 @@ bool kv_tc_supported(int dp);
 // Cross-kernel block K(X, U) (n x m row-major), FP32 entries from FP32-scaled inputs.
 void kxu_f32(const float* xs, int64_t n, const float* us, int64_t m, int dp, float c0,
              float* KXU, cudaStream_t st);
+// Cross block K(X, U) (n x m row-major) with FP64 entries stored as FP32 pairs.
+void kxu_pair_f64(const double* xs, int64_t n, const double* us, int64_t m, int dp, double c0,
+                  float2* KXU, cudaStream_t st);
 // Square FP64 block s2 * K(U, U) (m x m row-major) plus diag_add on the diagonal.
 void kuu_f64(const double* us, int64_t m, int dp, double c0, double scale, double diag_add,
              double* A, cudaStream_t st);

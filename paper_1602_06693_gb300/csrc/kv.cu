@@ -217,6 +217,22 @@ __global__ void kxu_f32_kernel(const float* __restrict__ xs, int64_t n,
     KXU[e] = kexp<float>(acc);
 }
 
+__global__ void kxu_pair_kernel(const double* __restrict__ xs, int64_t n,
+                                const double* __restrict__ us, int64_t m, int dp, double c0,
+                                float2* __restrict__ KXU) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    const int64_t i = e / m, a = e - i * m;
+    double acc = c0;
+    for (int q = 0; q < dp; ++q) {
+        const double t = xs[i * dp + q] - us[a * dp + q];
+        acc = fma(-t, t, acc);
+    }
+    const double v = exp(acc);
+    const float hi = (float)v;
+    KXU[e] = make_float2(hi, (float)(v - (double)hi));
+}
+
 __global__ void kuu_f64_kernel(const double* __restrict__ us, int64_t m, int dp, double c0,
                                double scale, double diag_add, double* __restrict__ A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -391,6 +407,14 @@ void kxu_f32(const float* xs, int64_t n, const float* us, int64_t m, int dp, flo
     if (tot == 0) return;
     kxu_f32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xs, n, us, m, dp, c0, KXU);
     KPCG_LAUNCHED("kxu_f32_kernel");
+}
+
+void kxu_pair_f64(const double* xs, int64_t n, const double* us, int64_t m, int dp, double c0,
+                  float2* KXU, cudaStream_t st) {
+    const int64_t tot = n * m;
+    if (tot == 0) return;
+    kxu_pair_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xs, n, us, m, dp, c0, KXU);
+    KPCG_LAUNCHED("kxu_pair_kernel");
 }
 
 void kuu_f64(const double* us, int64_t m, int dp, double c0, double scale, double diag_add,

@@ -77,6 +77,14 @@ __device__ __forceinline__ void df_acc(float& S, float& C, float P, float Pe) {
     C += err + Pe;
 }
 
+// Fold the compensation into the sum (Fast2Sum), keeping C small so its own
+// FP32 roundings stay below 2^-48 of the sum over long accumulations.
+__device__ __forceinline__ void df_renorm(float& S, float& C) {
+    const float s = S + C;
+    C = C - (s - S);
+    S = s;
+}
+
 // 2^(ah + al) as a double-float; zero below 2^-126.
 __device__ __forceinline__ DF df_exp2(float ah, float al, const float2* __restrict__ tab) {
     // renormalise
@@ -173,6 +181,9 @@ __global__ void __launch_bounds__(KT)
                 Pe = fmaf(e.l, v.x, Pe);
                 df_acc(S[k], C[k], P, Pe);
             }
+            if ((jj & 31) == 31)
+#pragma unroll
+                for (int k = 0; k < CB; ++k) df_renorm(S[k], C[k]);
         }
     }
     if (i < n) {
@@ -180,6 +191,229 @@ __global__ void __launch_bounds__(KT)
         for (int k = 0; k < CB; ++k)
             if (k < ncols) part[((int64_t)blockIdx.y * CB + k) * ldp + i] = (double)S[k] + (double)C[k];
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// Symmetric variant: K is symmetric, so each entry of an off-diagonal 128 x 128
+// tile pair (I, J), I < J, is evaluated once and used twice: for the row sums
+// of tile I (thread-owned rows, as above) and, through a shared-memory
+// transpose of the products e_ij v_i, for the column sums of tile J.  A CTA
+// walks a run of J tiles for one I.  Row partials go to prow[I][chunk], column
+// partials to pcol[J][I]; a second kernel adds them in a fixed order.
+constexpr int ST = 128;   // tile edge
+constexpr int SCW = 32;   // columns per transpose chunk
+
+template <int DP, int CB>
+__global__ void __launch_bounds__(ST)
+    kv_df_sym_kernel(const float4* __restrict__ xs, int64_t n, int nt, float c0h, float c0l,
+                     const double* __restrict__ V, int64_t ldv, int ncols,
+                     const float2* __restrict__ gtab, const int4* __restrict__ work, int G,
+                     int nchunk, double* __restrict__ prow, double* __restrict__ pcol) {
+    // dynamic shared memory: x_J tile, exp2 table, V_J, transpose buffer, reductions
+    extern __shared__ float4 dsm[];
+    float4* sx = dsm;                                                    // ST * DP
+    float2* tab = reinterpret_cast<float2*>(sx + ST * DP);               // NTAB (+1 pad)
+    float2* sv = tab + NTAB + 1;                                         // ST * CB
+    float2 (*W)[ST][SCW + 1] = reinterpret_cast<float2 (*)[ST][SCW + 1]>(sv + ST * CB);
+    float2 (*red)[4][SCW] = reinterpret_cast<float2 (*)[4][SCW]>(&W[CB][0][0]);
+    for (int e = threadIdx.x; e < NTAB; e += ST) tab[e] = gtab[e];
+    const int4 wk = work[blockIdx.x];  // (I, J0, J1, chunk)
+    const int I = wk.x;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int64_t i = (int64_t)I * ST + t;
+    float4 xi[DP];
+#pragma unroll
+    for (int q = 0; q < DP; ++q)
+        xi[q] = (i < n) ? xs[i * DP + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 vi[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        const double v = (i < n && k < ncols) ? V[i + (int64_t)k * ldv] : 0.0;
+        const float vh = (float)v;
+        vi[k] = make_float2(vh, (float)(v - (double)vh));
+    }
+    float S[CB], C[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) S[k] = C[k] = 0.f;
+    for (int J = wk.y; J < wk.z; ++J) {
+        __syncthreads();
+        for (int e = t; e < ST * DP; e += ST) {
+            const int jj = e / DP;
+            const int64_t j = (int64_t)J * ST + jj;
+            sx[e] = (j < n) ? xs[j * DP + (e - jj * DP)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = t; e < ST * CB; e += ST) {
+            const int k = e / ST, jj = e - k * ST;
+            const int64_t j = (int64_t)J * ST + jj;
+            const double v = (j < n && k < ncols) ? V[j + (int64_t)k * ldv] : 0.0;
+            const float vh = (float)v;
+            sv[jj * CB + k] = make_float2(vh, (float)(v - (double)vh));
+        }
+        __syncthreads();
+        const bool mirror = (J != I);
+        for (int c0 = 0; c0 < ST; c0 += SCW) {
+            for (int jj = 0; jj < SCW; ++jj) {
+                const int jc = c0 + jj;
+                float ah = c0h, al = c0l;
+#pragma unroll
+                for (int q = 0; q < DP; ++q) {
+                    const float4 xj = sx[jc * DP + q];
+                    const float D = xi[q].x - xj.x;  // exact
+                    const float E = (xi[q].y - xj.y) + (xi[q].z - xj.z);
+                    const float P = D * D;
+                    float Pe = fmaf(D, D, -P);
+                    Pe = fmaf(D, E + E, Pe);
+                    Pe = fmaf(E, E, Pe);
+                    df_sub(ah, al, P, Pe);
+                }
+                const DF e = df_exp2(ah, al, tab);
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    const float2 v = sv[jc * CB + k];
+                    const float P = e.h * v.x;
+                    float Pe = fmaf(e.h, v.x, -P);
+                    Pe = fmaf(e.h, v.y, Pe);
+                    Pe = fmaf(e.l, v.x, Pe);
+                    df_acc(S[k], C[k], P, Pe);
+                    if (mirror) {
+                        const float Q = e.h * vi[k].x;
+                        float Qe = fmaf(e.h, vi[k].x, -Q);
+                        Qe = fmaf(e.h, vi[k].y, Qe);
+                        Qe = fmaf(e.l, vi[k].x, Qe);
+                        W[k][t][jj] = make_float2(Q, Qe);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CB; ++k) df_renorm(S[k], C[k]);
+            if (mirror) {
+                __syncthreads();
+                // column sums: warp w adds rows 32w..32w+31 of column `lane`
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    float cs = 0.f, cc = 0.f;
+                    for (int r = 0; r < 32; ++r) {
+                        const float2 w = W[k][warp * 32 + r][lane];
+                        df_acc(cs, cc, w.x, w.y);
+                    }
+                    red[k][warp][lane] = make_float2(cs, cc);
+                }
+                __syncthreads();
+                if (warp == 0) {
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        float cs = 0.f, cc = 0.f;
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) df_acc(cs, cc, red[k][w][lane].x, red[k][w][lane].y);
+                        pcol[(((size_t)J * nt + I) * CB + k) * ST + c0 + lane] =
+                            (double)cs + (double)cc;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k)
+        prow[(((size_t)I * nchunk + wk.w) * CB + k) * ST + t] = (double)S[k] + (double)C[k];
+}
+
+
+// Native-FP64 symmetric variant (used for the FP64 residuals): the same tile
+// pairs, transpose and reduction, entries exp(c0 - |x'_i - x'_j|^2) in FP64.
+template <int DP, int CB>
+__global__ void __launch_bounds__(ST)
+    kv_f64_sym_kernel(const double* __restrict__ xs, int64_t n, int nt, double c0,
+                      const double* __restrict__ V, int64_t ldv, int ncols,
+                      const int4* __restrict__ work, int G, int nchunk,
+                      double* __restrict__ prow, double* __restrict__ pcol) {
+    extern __shared__ double dsm64[];
+    double* sx = dsm64;                 // ST * DP
+    double* sv = sx + ST * DP;          // ST * CB
+    double (*W)[ST][SCW + 1] = reinterpret_cast<double (*)[ST][SCW + 1]>(sv + ST * CB);
+    double (*red)[4][SCW] = reinterpret_cast<double (*)[4][SCW]>(&W[CB][0][0]);
+    const int4 wk = work[blockIdx.x];
+    const int I = wk.x;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int64_t i = (int64_t)I * ST + t;
+    double xi[DP];
+#pragma unroll
+    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : 0.0;
+    double vi[CB], S[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        vi[k] = (i < n && k < ncols) ? V[i + (int64_t)k * ldv] : 0.0;
+        S[k] = 0.0;
+    }
+    for (int J = wk.y; J < wk.z; ++J) {
+        __syncthreads();
+        for (int e = t; e < ST * DP; e += ST) {
+            const int jj = e / DP;
+            const int64_t j = (int64_t)J * ST + jj;
+            sx[e] = (j < n) ? xs[j * DP + (e - jj * DP)] : 0.0;
+        }
+        for (int e = t; e < ST * CB; e += ST) {
+            const int k = e / ST, jj = e - k * ST;
+            const int64_t j = (int64_t)J * ST + jj;
+            sv[jj * CB + k] = (j < n && k < ncols) ? V[j + (int64_t)k * ldv] : 0.0;
+        }
+        __syncthreads();
+        const bool mirror = (J != I);
+        for (int cst = 0; cst < ST; cst += SCW) {
+            for (int jj = 0; jj < SCW; ++jj) {
+                const int jc = cst + jj;
+                double a = c0;
+#pragma unroll
+                for (int q = 0; q < DP; ++q) {
+                    const double dlt = xi[q] - sx[jc * DP + q];
+                    a = fma(-dlt, dlt, a);
+                }
+                const double e = exp(a);
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    S[k] = fma(e, sv[jc * CB + k], S[k]);
+                    if (mirror) W[k][t][jj] = e * vi[k];
+                }
+            }
+            if (mirror) {
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    double cs = 0.0;
+                    for (int r = 0; r < 32; ++r) cs += W[k][warp * 32 + r][lane];
+                    red[k][warp][lane] = cs;
+                }
+                __syncthreads();
+                if (warp == 0) {
+#pragma unroll
+                    for (int k = 0; k < CB; ++k)
+                        pcol[(((size_t)J * nt + I) * CB + k) * ST + cst + lane] =
+                            ((red[k][0][lane] + red[k][1][lane]) + red[k][2][lane]) +
+                            red[k][3][lane];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k) prow[(((size_t)I * nchunk + wk.w) * CB + k) * ST + t] = S[k];
+}
+
+__global__ void kv_df_sym_reduce_kernel(const double* __restrict__ prow,
+                                        const double* __restrict__ pcol, int nt, int G,
+                                        int nchunk, int cb, int ncols,
+                                        const double* __restrict__ V, int64_t ldv, double noise,
+                                        const double* __restrict__ B, int64_t ldb,
+                                        double* __restrict__ O, int64_t ldo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n || k >= ncols) return;
+    const int T = (int)(i / ST), r = (int)(i % ST);
+    double s = noise * V[i + (int64_t)k * ldv];
+    for (int ch = T / G; ch < nchunk; ++ch) s += prow[(((size_t)T * nchunk + ch) * cb + k) * ST + r];
+    for (int I = 0; I < T; ++I) s += pcol[(((size_t)T * nt + I) * cb + k) * ST + r];
+    O[i + (int64_t)k * ldo] = B ? (B[i + (int64_t)k * ldb] - s) : s;
 }
 
 __global__ void kv_df_reduce_kernel(const double* __restrict__ part, int64_t ldp, int nsplit,
@@ -307,10 +541,174 @@ static void df_prepare(Ctx& h) {
     h.df_version = h.theta_version;
 }
 
+template <int DP, int CB>
+static size_t df_sym_smem() {
+    return sizeof(float4) * ST * DP + sizeof(float2) * (NTAB + 1) + sizeof(float2) * ST * CB +
+           sizeof(float2) * CB * ST * (SCW + 1) + sizeof(float2) * CB * 4 * SCW;
+}
+
+template <int DP, int CB>
+static void df_sym_launch1(const float4* xs, int64_t n, int nt, float c0h, float c0l,
+                           const double* V, int64_t ldv, int ncols, const float2* tab,
+                           const int4* work, int nwork, int G, int nchunk, double* prow,
+                           double* pcol, cudaStream_t st) {
+    const size_t smem = df_sym_smem<DP, CB>();
+    static bool attr = false;
+    if (!attr) {
+        KPCG_CUDA(cudaFuncSetAttribute(kv_df_sym_kernel<DP, CB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    kv_df_sym_kernel<DP, CB><<<nwork, ST, smem, st>>>(xs, n, nt, c0h, c0l, V, ldv, ncols, tab,
+                                                      work, G, nchunk, prow, pcol);
+    KPCG_LAUNCHED("kv_df_sym_kernel");
+}
+
+template <int DP>
+static void df_sym_launch(int cb, const float4* xs, int64_t n, int nt, float c0h, float c0l,
+                          const double* V, int64_t ldv, int ncols, const float2* tab,
+                          const int4* work, int nwork, int G, int nchunk, double* prow,
+                          double* pcol, cudaStream_t st) {
+    if (cb == 1)
+        df_sym_launch1<DP, 1>(xs, n, nt, c0h, c0l, V, ldv, ncols, tab, work, nwork, G, nchunk,
+                              prow, pcol, st);
+    else
+        df_sym_launch1<DP, 2>(xs, n, nt, c0h, c0l, V, ldv, ncols, tab, work, nwork, G, nchunk,
+                              prow, pcol, st);
+}
+
+// Symmetric product, column blocks of two.  Work items (I, J0, J1, chunk) cover
+// the upper triangle of tile pairs in runs of G tiles, cached per n.
+// Work list (I, J0, J1, chunk) over the upper triangle of tile pairs, in runs
+// of G tiles, cached per n.  Returns G; nchunk = ceil(nt / G).
+static int ensure_sym_work(Ctx& h, int nt) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    // runs of G tiles: about sixteen CTAs of work per SM
+    int G = std::max(1, (int)((int64_t)nt * (nt + 1) / 2 / ((int64_t)sm_count_df() * 16)));
+    G = std::min(G, 16);
+    if (h.df_sym_n != n || h.df_sym_G != G) {
+        std::vector<int4> w;
+        for (int I = 0; I < nt; ++I)
+            for (int J0 = I; J0 < nt;) {
+                const int ch = J0 / G;
+                const int J1 = std::min(nt, (ch + 1) * G);
+                w.push_back(make_int4(I, J0, J1, ch));
+                J0 = J1;
+            }
+        int4* dw = reinterpret_cast<int4*>(h.df_work.need(w.size() * 4));
+        KPCG_CUDA(cudaMemcpyAsync(dw, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice,
+                                  st));
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        h.df_sym_n = n;
+        h.df_sym_G = G;
+        h.df_nwork = (int)w.size();
+    }
+    return G;
+}
+
+static void kv_df_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb,
+                      double* O, int64_t ldo, double noise) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int nt = (int)((n + ST - 1) / ST);
+    const int G = ensure_sym_work(h, nt);
+    const int nchunk = (nt + G - 1) / G;
+    const int max_cb = 2;
+    double* prow = h.df_prow.need((size_t)nt * nchunk * max_cb * ST);
+    double* pcol = h.df_pcol.need((size_t)nt * nt * max_cb * ST);
+    const float4* xs = reinterpret_cast<const float4*>(h.xdf.p);
+    const float2* tab = reinterpret_cast<const float2*>(h.df_tab.p);
+    const int4* work = reinterpret_cast<const int4*>(h.df_work.p);
+    for (int k0 = 0; k0 < c;) {
+        const int cb = (c - k0 >= 2) ? 2 : 1;
+        const int ncols = cb;
+        const double* Vk = V + (int64_t)k0 * ldv;
+        switch (h.dp) {
+            case 4: df_sym_launch<4>(cb, xs, n, nt, h.df_c0h, h.df_c0l, Vk, ldv, ncols, tab, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 8: df_sym_launch<8>(cb, xs, n, nt, h.df_c0h, h.df_c0l, Vk, ldv, ncols, tab, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 12: df_sym_launch<12>(cb, xs, n, nt, h.df_c0h, h.df_c0l, Vk, ldv, ncols, tab, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 16: df_sym_launch<16>(cb, xs, n, nt, h.df_c0h, h.df_c0l, Vk, ldv, ncols, tab, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+        kv_df_sym_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)ncols), 256, 0, st>>>(
+            prow, pcol, nt, G, nchunk, cb, ncols, Vk, ldv, noise,
+            B ? B + (int64_t)k0 * ldb : nullptr, ldb, O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("kv_df_sym_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
+template <int DP, int CB>
+static void f64_sym_launch1(const double* xs, int64_t n, int nt, double c0, const double* V,
+                            int64_t ldv, int ncols, const int4* work, int nwork, int G, int nchunk,
+                            double* prow, double* pcol, cudaStream_t st) {
+    const size_t smem = sizeof(double) * (ST * DP + ST * CB + CB * ST * (SCW + 1) + CB * 4 * SCW);
+    static bool attr = false;
+    if (!attr) {
+        KPCG_CUDA(cudaFuncSetAttribute(kv_f64_sym_kernel<DP, CB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    kv_f64_sym_kernel<DP, CB><<<nwork, ST, smem, st>>>(xs, n, nt, c0, V, ldv, ncols, work, G,
+                                                       nchunk, prow, pcol);
+    KPCG_LAUNCHED("kv_f64_sym_kernel");
+}
+
+template <int DP>
+static void f64_sym_launch(int cb, const double* xs, int64_t n, int nt, double c0, const double* V,
+                           int64_t ldv, int ncols, const int4* work, int nwork, int G, int nchunk,
+                           double* prow, double* pcol, cudaStream_t st) {
+    if (cb == 1)
+        f64_sym_launch1<DP, 1>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+    else
+        f64_sym_launch1<DP, 2>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+}
+
+void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb,
+                double* O, int64_t ldo, double noise) {
+    if (h.n <= 0 || c <= 0) return;
+    if (!(h.dp <= 16 && h.n >= 4 * ST)) {
+        kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), noise, V, ldv, c, B, ldb, O, ldo, h.kvws, h.stream);
+        return;
+    }
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int nt = (int)((n + ST - 1) / ST);
+    const int G = ensure_sym_work(h, nt);
+    const int nchunk = (nt + G - 1) / G;
+    const int max_cb = 2;
+    double* prow = h.df_prow.need((size_t)nt * nchunk * max_cb * ST);
+    double* pcol = h.df_pcol.need((size_t)nt * nt * max_cb * ST);
+    const int4* work = reinterpret_cast<const int4*>(h.df_work.p);
+    const double c0 = h.c0_64();
+    for (int k0 = 0; k0 < c;) {
+        const int cb = (c - k0 >= 2) ? 2 : 1;
+        const double* Vk = V + (int64_t)k0 * ldv;
+        switch (h.dp) {
+            case 4: f64_sym_launch<4>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 8: f64_sym_launch<8>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 12: f64_sym_launch<12>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 16: f64_sym_launch<16>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+        kv_df_sym_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)cb), 256, 0, st>>>(
+            prow, pcol, nt, G, nchunk, cb, cb, Vk, ldv, noise, B ? B + (int64_t)k0 * ldb : nullptr,
+            ldb, O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("kv_df_sym_reduce_kernel");
+        k0 += cb;
+    }
+}
+
 void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb, double* O,
            int64_t ldo, double noise) {
     if (h.n <= 0 || c <= 0) return;
     df_prepare(h);
+    // The symmetric kernel pays off once there are several tile pairs per SM.
+    if (h.dp <= 16 && h.n >= 4 * ST && h.df_symmetric) {
+        kv_df_sym(h, V, ldv, c, B, ldb, O, ldo, noise);
+        return;
+    }
     cudaStream_t st = h.stream;
     const int64_t n = h.n;
     const DfSplit s = df_plan(n);

@@ -4,13 +4,14 @@
 // inversion lemma as P^{-1} = sigma^{-2} [I - K_XU M^{-1} K_UX] with
 // M = sigma^2 K_UU + K_UX K_XU (the printed inverse drops the sigma^2 on K_UU).
 // K_XU is stored once in FP32; M is formed from that same FP32 block with
-// FP64 products and sums, so the applied operator is exactly the inverse of
-// the SPD matrix K^_XU K_UU^{-1} K^_UX + sigma^2 I built from the stored block.
-// M = L L^T is factored in FP64 and L^{-1} formed explicitly (stored as
-// U = L^{-T}, row-major), so an apply is two skinny products with K_XU and two
-// m x m triangular products, all accumulated in FP64: with sigma^2 small the
-// difference r - K_XU M^{-1} K_UX r cancels almost completely along the
-// leading eigenvectors, and an FP32 accumulation there destroys the
+// exact products and compensated (double-FP32) sums, so the applied operator
+// is, to that accuracy, the inverse of the SPD matrix K^_XU K_UU^{-1} K^_UX +
+// sigma^2 I built from the stored block.  M = L L^T is factored in FP64 and
+// L^{-1} formed explicitly (stored as U = L^{-T}, row-major), so an apply is
+// two skinny products with K_XU and two m x m triangular products.  The skinny
+// products use compensated FP32 (Dot2) and the rest FP64: with sigma^2 small
+// the difference r - K_XU M^{-1} K_UX r cancels almost completely along the
+// leading eigenvectors, and a plain FP32 accumulation there destroys the
 // preconditioner.
 //
 // Block-Jacobi.  P = bldiag(K_y), contiguous blocks of b rows (the last one
@@ -206,44 +207,62 @@ __global__ void gather_rows_f64(const double* __restrict__ src, const int64_t* _
 }
 
 // part[s][a][b] = sum over rows of split s of KXU[i][a] KXU[i][b], lower tiles.
+// Entries are FP32 pairs (hi + lo, an FP64 value split exactly); products are
+// split by TwoProduct and accumulated with the compensated Dot2 scheme (see
+// dot2_add below), leaving as FP64: FP64-class sums at FP32-pipe speed.
 constexpr int ST = 64;  // output tile
 constexpr int SR = 32;  // rows per stage
+struct Acc2s {
+    float s, c;
+};
+__device__ __forceinline__ void dot2s(Acc2s& a, float x, float y) {
+    const float p = x * y;
+    const float pi = fmaf(x, y, -p);
+    const float t = a.s + p;
+    const float z = t - a.s;
+    a.c += pi + ((a.s - (t - z)) + (p - z));
+    a.s = t;
+}
 __global__ void __launch_bounds__(256)
-    syrk_kxu_kernel(const float* __restrict__ KXU, int64_t n, int64_t m, int64_t rows_per_split,
+    syrk_kxu_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m, int64_t rows_per_split,
                     double* __restrict__ part) {
-    __shared__ float Aa[SR][ST];
-    __shared__ float Ab[SR][ST];
+    __shared__ float2 Aa[SR][ST];
+    __shared__ float2 Ab[SR][ST];
     const int64_t ta = blockIdx.y, tb = blockIdx.x;
     if (tb > ta) return;
     const int64_t a0 = ta * ST, b0 = tb * ST;
     const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
     const int64_t r1 = min(n, r0 + rows_per_split);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 4 x 4 outputs each
-    double acc[4][4];
+    Acc2s acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+        for (int v = 0; v < 4; ++v) acc[u][v] = {0.f, 0.f};
     for (int64_t rs = r0; rs < r1; rs += SR) {
         __syncthreads();
         for (int e = threadIdx.x; e < SR * ST; e += 256) {
             const int r = e / ST, c = e % ST;
             const int64_t i = rs + r;
-            Aa[r][c] = (i < r1 && a0 + c < m) ? KXU[i * m + a0 + c] : 0.f;
-            Ab[r][c] = (i < r1 && b0 + c < m) ? KXU[i * m + b0 + c] : 0.f;
+            Aa[r][c] = (i < r1 && a0 + c < m) ? KXU[i * m + a0 + c] : make_float2(0.f, 0.f);
+            Ab[r][c] = (i < r1 && b0 + c < m) ? KXU[i * m + b0 + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int r = 0; r < SR; ++r) {
-            double va[4], vb[4];
+            float2 va[4], vb[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) va[u] = (double)Aa[r][ty * 4 + u];
+            for (int u = 0; u < 4; ++u) va[u] = Aa[r][ty * 4 + u];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) vb[v] = (double)Ab[r][tx * 4 + v];
+            for (int v = 0; v < 4; ++v) vb[v] = Ab[r][tx * 4 + v];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fma(va[u], vb[v], acc[u][v]);
+                for (int v = 0; v < 4; ++v) {
+                    // (ha + la)(hb + lb): exact ha*hb by TwoProduct, cross terms into c
+                    dot2s(acc[u][v], va[u].x, vb[v].x);
+                    acc[u][v].c = fmaf(va[u].x, vb[v].y, fmaf(va[u].y, vb[v].x, acc[u][v].c));
+                }
         }
     }
     double* P = part + (int64_t)blockIdx.z * m * m;
@@ -252,7 +271,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int64_t a = a0 + ty * 4 + u, bb = b0 + tx * 4 + v;
-            if (a < m && bb < m && bb <= a) P[a * m + bb] = acc[u][v];
+            if (a < m && bb < m && bb <= a) P[a * m + bb] = (double)acc[u][v].s + (double)acc[u][v].c;
         }
 }
 
@@ -292,11 +311,12 @@ __device__ __forceinline__ void dot2_add(Acc2& a, float x, float y) {
     a.c += pi + sg;
 }
 
-// w_part[s][k][a] = sum_{i in split s} KXU[i][a] R[i][k], compensated FP32.
+// w_part[s][k][a] = sum_{i in split s} KXU[i][a] R[i][k]; K_XU and R enter as
+// FP32 pairs, products are split exactly and accumulated with Dot2.
 constexpr int PC = 4;  // columns per pass
 template <typename T>
 __global__ void __launch_bounds__(256)
-    nys_proj_kernel(const float* __restrict__ KXU, int64_t n, int64_t m, const T* __restrict__ R,
+    nys_proj_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m, const T* __restrict__ R,
                     int64_t ldr, int ncols, int64_t rows_per_split, double* __restrict__ part,
                     int c_total) {
     __shared__ float2 sr[128][PC];  // r split into float hi + lo
@@ -317,14 +337,14 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         const int rn = (int)min((int64_t)128, r1 - rs);
         if (a < m) {
-            const float* Kp = KXU + rs * m + a;
+            const float2* Kp = KXU + rs * m + a;
 #pragma unroll 4
             for (int r = 0; r < rn; ++r) {
-                const float kv = __ldg(Kp + (int64_t)r * m);
+                const float2 kv = __ldg(Kp + (int64_t)r * m);
 #pragma unroll
                 for (int k = 0; k < PC; ++k) {
-                    dot2_add(acc[k], kv, sr[r][k].x);
-                    acc[k].c = fmaf(kv, sr[r][k].y, acc[k].c);
+                    dot2_add(acc[k], kv.x, sr[r][k].x);
+                    acc[k].c = fmaf(kv.x, sr[r][k].y, fmaf(kv.y, sr[r][k].x, acc[k].c));
                 }
             }
         }
@@ -344,15 +364,26 @@ __global__ void sum_splits_kernel(const double* __restrict__ part, int nsplit, i
 }
 
 // y_k = L^{-1} w_k with U = L^{-T} row-major: y_i = sum_{j <= i} U[j][i] w_j.
-__global__ void tri_lower_apply_kernel(const double* __restrict__ U, int64_t m,
-                                       const double* __restrict__ w, double* __restrict__ y) {
+// A CTA owns 32 consecutive i; its 32 warps stride over j (coalesced rows of
+// U), and the 32 partial sums of each i are added in a fixed order.
+__global__ void __launch_bounds__(1024)
+    tri_lower_apply_kernel(const double* __restrict__ U, int64_t m, const double* __restrict__ w,
+                           double* __restrict__ y) {
+    __shared__ double part[32][33];
     const int k = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     const double* wk = w + (int64_t)k * m;
     double s = 0.0;
-    for (int64_t j = 0; j <= i; ++j) s = fma(U[j * m + i], wk[j], s);
-    y[(int64_t)k * m + i] = s;
+    if (i < m)
+        for (int64_t j = g; j <= i; j += 32) s = fma(U[j * m + i], wk[j], s);
+    part[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && i < m) {
+        double t = 0.0;
+        for (int q = 0; q < 32; ++q) t += part[q][lane];
+        y[(int64_t)k * m + i] = t;
+    }
 }
 
 // u_k = L^{-T} y_k: u_j = sum_{i >= j} U[j][i] y_i (warp per j).
@@ -371,7 +402,7 @@ __global__ void tri_upper_apply_kernel(const double* __restrict__ U, int64_t m,
 }
 
 // Z = (R - K_XU u) / sigma^2, warp per row; u is split into FP32 hi + lo and
-// the row sum accumulated with Dot2, lanes combined in FP64.
+// the row sum of the pair products accumulated with Dot2, lanes combined in FP64.
 __global__ void split_u_kernel(const double* __restrict__ u, int64_t len, float2* __restrict__ o) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= len) return;
@@ -382,7 +413,7 @@ __global__ void split_u_kernel(const double* __restrict__ u, int64_t len, float2
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    nys_back_kernel(const float* __restrict__ KXU, int64_t n, int64_t m,
+    nys_back_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
                     const float2* __restrict__ u2, int c, const T* __restrict__ R, int64_t ldr,
                     T* __restrict__ Z, int64_t ldz, double inv_noise) {
     extern __shared__ float2 su[];  // m * c
@@ -391,14 +422,14 @@ __global__ void __launch_bounds__(256)
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        const float* Ki = KXU + i * m;
+        const float2* Ki = KXU + i * m;
         for (int k = 0; k < c; ++k) {
             const float2* uk = su + (int64_t)k * m;
             Acc2 acc = {0.f, 0.f};
             for (int64_t a = lane; a < m; a += 32) {
-                const float kv = __ldg(Ki + a);
-                dot2_add(acc, kv, uk[a].x);
-                acc.c = fmaf(kv, uk[a].y, acc.c);
+                const float2 kv = __ldg(Ki + a);
+                dot2_add(acc, kv.x, uk[a].x);
+                acc.c = fmaf(kv.x, uk[a].y, fmaf(kv.y, uk[a].x, acc.c));
             }
             double s = warp_sum((double)acc.s + (double)acc.c);
             if (lane == 0)
@@ -509,8 +540,11 @@ void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64
     KPCG_LAUNCHED("gather_rows_f32");
     gather_rows_f64<<<g, 256, 0, st>>>(xs64, idx, m, dp, us64);
     KPCG_LAUNCHED("gather_rows_f64");
-    float* KXU = P.KXU.need((size_t)n * m);
-    kxu_f32(xs32, n, us32, m, dp, c0_32, KXU, st);
+    // K_XU in FP64 entries (direct differences), stored as exact FP32 pairs: at
+    // small noise the preconditioner needs FP64-accurate entries (an FP32
+    // rounding of K_XU alone raised the PCG iteration count by 10-50%).
+    float2* KXU = P.KXU.need((size_t)n * m);
+    kxu_pair_f64(xs64, n, us64, m, dp, c0_64, KXU, st);
     // M0 = sigma^2 K_UU + K_UX K_XU
     double* M0 = P.M0.need((size_t)m * m);
     kuu_f64(us64, m, dp, c0_64, noise, 0.0, M0, st);
@@ -590,7 +624,7 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     }
     sum_splits_kernel<<<(unsigned)((c * m + 255) / 256), 256, 0, st>>>(part, nsplit, c * m, w);
     KPCG_LAUNCHED("sum_splits_kernel");
-    tri_lower_apply_kernel<<<dim3((unsigned)((m + 127) / 128), c), 128, 0, st>>>(P.U.p, m, w, y);
+    tri_lower_apply_kernel<<<dim3((unsigned)((m + 31) / 32), c), 1024, 0, st>>>(P.U.p, m, w, y);
     KPCG_LAUNCHED("tri_lower_apply_kernel");
     tri_upper_apply_kernel<<<dim3((unsigned)((m * 32 + 255) / 256), c), 256, 0, st>>>(P.U.p, m, y,
                                                                                      w);

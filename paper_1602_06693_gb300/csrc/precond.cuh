@@ -16,7 +16,7 @@ struct PrecondState {
     DevBuf<int64_t> idx;     // inducing rows (Nystrom)
     DevBuf<float> us32;      // scaled inducing rows, FP32
     DevBuf<double> us64;     // scaled inducing rows, FP64
-    DevBuf<float> KXU;       // n x m row-major, FP32
+    DevBuf<float2> KXU;      // n x m row-major, FP64 entries as FP32 pairs (hi, lo)
     DevBuf<double> M0;       // sigma^2 K_UU + K_UX K_XU before jitter
     DevBuf<double> M;        // Cholesky factor(s) L
     DevBuf<double> U;        // L^{-T}, row-major (per block for block-Jacobi)
