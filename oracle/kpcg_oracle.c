@@ -116,11 +116,11 @@ void or_dkv(const double* X, int64_t n, int d, const double* ell, double s2, con
  * from): A = L L^T, lower triangle of the row-major n x n matrix A is
  * overwritten by L, the strict upper triangle is zeroed.  Returns 0, or
  * j+1 when the j-th pivot is not positive. */
-int or_chol(double* A, int64_t n) {
+static int chol_thr(double* A, int64_t n, double thr) {
     for (int64_t j = 0; j < n; ++j) {
         double s = A[j * n + j];
         for (int64_t k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-        if (!(s > 0.0)) return (int)(j + 1);
+        if (!(s > thr)) return (int)(j + 1);
         double ljj = sqrt(s);
         A[j * n + j] = ljj;
 #pragma omp parallel for schedule(static)
@@ -134,6 +134,8 @@ int or_chol(double* A, int64_t n) {
         for (int64_t j = i + 1; j < n; ++j) A[i * n + j] = 0.0;
     return 0;
 }
+
+int or_chol(double* A, int64_t n) { return chol_thr(A, n, 0.0); }
 
 /* Solve L L^T x = b in place for c columns (column-major B, leading dim ldb). */
 void or_chol_solve(const double* L, int64_t n, double* B, int64_t ldb, int c) {
@@ -160,9 +162,15 @@ void or_chol_solve(const double* L, int64_t n, double* B, int64_t ldb, int c) {
  *   P^{-1} = sigma2^{-1} [ I - K_XU (sigma2 K_UU + K_UX K_XU)^{-1} K_UX ].
  * (The printed inverse omits the factor sigma2 on K_UU; it is only right for
  * sigma2 = 1.)  M = sigma2 K_UU + K_UX K_XU is SPD and is factored once.
- * If the factorization fails, jitter 1e-12 * tr(M)/m * 10^k, k = 0..6, is
- * added to the diagonal; the paper does not discuss this case.
+ * The paper does not discuss the factorization of M.  With a small noise M
+ * is nearly singular (condition numbers ~1e13 seen), where whether a
+ * Cholesky factorization "succeeds" depends on rounding details.  The rule
+ * here is deterministic: a factorization is accepted only if every pivot
+ * exceeds NYS_PIVOT_TOL * max_k M_kk; otherwise jitter 1e-12 * tr(M)/m * 10^k,
+ * k = 0..6, is added to the diagonal and the next level tried.
  * --------------------------------------------------------------------- */
+#define NYS_PIVOT_TOL 3e-12
+
 int or_nys_setup(const double* X, int64_t n, int d, const double* ell, double s2, double sigma2,
                  const int64_t* idx, int64_t m, double* KXU, double* M, double* jitter_out) {
     double* U = (double*)malloc(sizeof(double) * (size_t)(m * d));
@@ -176,15 +184,18 @@ int or_nys_setup(const double* X, int64_t n, int d, const double* ell, double s2
             for (int64_t i = 0; i < n; ++i) t += KXU[i * m + a] * KXU[i * m + b];
             M0[a * m + b] = t;
         }
-    double tr = 0.0;
-    for (int64_t a = 0; a < m; ++a) tr += M0[a * m + a];
+    double tr = 0.0, dmax = 0.0;
+    for (int64_t a = 0; a < m; ++a) {
+        tr += M0[a * m + a];
+        if (M0[a * m + a] > dmax) dmax = M0[a * m + a];
+    }
     int status = 1;
     double jit = 0.0;
     for (int k = -1; k <= 6 && status != 0; ++k) {
         jit = (k < 0) ? 0.0 : 1e-12 * tr / (double)m * pow(10.0, k);
         memcpy(M, M0, sizeof(double) * (size_t)(m * m));
         for (int64_t a = 0; a < m; ++a) M[a * m + a] += jit;
-        status = or_chol(M, m);
+        status = chol_thr(M, m, NYS_PIVOT_TOL * dmax);
     }
     if (jitter_out) *jitter_out = jit;
     free(U);
