@@ -115,6 +115,8 @@ typedef struct {
     double precond_ms;    /* preconditioner applications                       */
     int32_t precond_calls;
     int32_t launches;     /* CUDA kernels this call launched (always filled)   */
+    double precond_jitter; /* diagonal jitter the Nystrom inner matrix needed
+                             (0 when it factored as built)                    */
 } kpcg_info;
 
 /* Fill *opt with the defaults documented in kpcg_options. */

@@ -62,6 +62,7 @@ class Info(ctypes.Structure):
         ("precond_ms", ctypes.c_double),
         ("precond_calls", ctypes.c_int32),
         ("launches", ctypes.c_int32),
+        ("precond_jitter", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -596,6 +596,7 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
         info->precond_ms = ms[Profiler::PRECOND];
         info->precond_calls = calls[Profiler::PRECOND];
         info->launches = (int)(launch_count() - launches0);
+        info->precond_jitter = h.P.ready ? h.P.jitter : 0.0;
     } else {
         double ms[Profiler::NCAT];
         int calls[Profiler::NCAT];

@@ -3,13 +3,11 @@
 // Nystrom.  P = K_XU K_UU^{-1} K_UX + sigma^2 I, inverted by the matrix
 // inversion lemma as P^{-1} = sigma^{-2} [I - K_XU M^{-1} K_UX] with
 // M = sigma^2 K_UU + K_UX K_XU (the printed inverse drops the sigma^2 on K_UU).
-// K_XU is stored once in FP32; M is formed from that same FP32 block with
-// exact products and compensated (double-FP32) sums, so the applied operator
-// is, to that accuracy, the inverse of the SPD matrix K^_XU K_UU^{-1} K^_UX +
-// sigma^2 I built from the stored block.  M = L L^T is factored in FP64 and
+// K_XU holds FP64 entries as exact FP32 pairs; M is formed from it with FP64
+// products and sums (see syrk_kxu_kernel for why nothing less will do).  M = L L^T is factored in FP64 and
 // L^{-1} formed explicitly (stored as U = L^{-T}, row-major), so an apply is
-// two skinny products with K_XU and two m x m triangular products.  The skinny
-// products use compensated FP32 (Dot2) and the rest FP64: with sigma^2 small
+// two skinny products with K_XU and two m x m triangular products.  K_UX r uses
+// compensated FP32 (Dot2) on the pairs, the rest is FP64: with sigma^2 small
 // the difference r - K_XU M^{-1} K_UX r cancels almost completely along the
 // leading eigenvectors, and a plain FP32 accumulation there destroys the
 // preconditioner.
@@ -46,9 +44,10 @@ __device__ __forceinline__ int64_t bsize(int64_t q, int64_t b, int64_t n_total) 
     return (n_total - r0 < b) ? (n_total - r0) : b;
 }
 
-// Factor the nb x nb diagonal block at (j0, j0) of matrix q in place.
+// Factor the nb x nb diagonal block at (j0, j0) of matrix q in place; a pivot
+// not above thr fails the factorization.
 __global__ void potrf_diag_kernel(double* A, int64_t stride, int64_t b, int64_t n_total,
-                                  int64_t j0, int* status) {
+                                  int64_t j0, int* status, double thr) {
     __shared__ double S[NB][NB + 1];
     __shared__ int bad;
     const int64_t q = blockIdx.x;
@@ -66,7 +65,7 @@ __global__ void potrf_diag_kernel(double* A, int64_t stride, int64_t b, int64_t 
     for (int j = 0; j < nb; ++j) {
         if (threadIdx.x == 0) {
             const double piv = S[j][j];
-            if (!(piv > 0.0) || !isfinite(piv)) {
+            if (!(piv > thr) || !isfinite(piv)) {
                 bad = 1;
             } else {
                 S[j][j] = sqrt(piv);
@@ -206,51 +205,46 @@ __global__ void gather_rows_f64(const double* __restrict__ src, const int64_t* _
     dst[e] = src[idx[a] * dp + (e - a * dp)];
 }
 
-// part[s][a][b] = sum over rows of split s of KXU[i][a] KXU[i][b], lower tiles.
-// Entries are FP32 pairs (hi + lo, an FP64 value split exactly); products are
-// split by TwoProduct and accumulated with the compensated Dot2 scheme (see
-// dot2_add below), leaving as FP64: FP64-class sums at FP32-pipe speed.
+// part[s][a][b] = sum over rows of split s of KXU[i][a] KXU[i][b], lower tiles,
+// in FP64 (entries are exact FP32 pairs, hi + lo).  M = noise K_UU + K_UX K_XU
+// is nearly singular (kappa ~ 1e11 at noise 1e-4) and the preconditioner it
+// defines implicitly inverts K_UU, whose small eigenvalues are far below the
+// 2^-48 relative error of a compensated-FP32 sum divided by the noise: such
+// errors made the preconditioner indefinite and doubled the PCG iteration
+// count.  FP64 products and sums keep it at the accuracy of a direct FP64
+// construction.
 constexpr int ST = 64;  // output tile
-constexpr int SR = 32;  // rows per stage
-struct Acc2s {
-    float s, c;
-};
-__device__ __forceinline__ void dot2s(Acc2s& a, float x, float y) {
-    const float p = x * y;
-    const float pi = fmaf(x, y, -p);
-    const float t = a.s + p;
-    const float z = t - a.s;
-    a.c += pi + ((a.s - (t - z)) + (p - z));
-    a.s = t;
-}
+constexpr int SR = 16;  // rows per stage
 __global__ void __launch_bounds__(256)
     syrk_kxu_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m, int64_t rows_per_split,
                     double* __restrict__ part) {
-    __shared__ float2 Aa[SR][ST];
-    __shared__ float2 Ab[SR][ST];
+    __shared__ double Aa[SR][ST];
+    __shared__ double Ab[SR][ST];
     const int64_t ta = blockIdx.y, tb = blockIdx.x;
     if (tb > ta) return;
     const int64_t a0 = ta * ST, b0 = tb * ST;
     const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
     const int64_t r1 = min(n, r0 + rows_per_split);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 4 x 4 outputs each
-    Acc2s acc[4][4];
+    double acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = {0.f, 0.f};
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
     for (int64_t rs = r0; rs < r1; rs += SR) {
         __syncthreads();
         for (int e = threadIdx.x; e < SR * ST; e += 256) {
             const int r = e / ST, c = e % ST;
             const int64_t i = rs + r;
-            Aa[r][c] = (i < r1 && a0 + c < m) ? KXU[i * m + a0 + c] : make_float2(0.f, 0.f);
-            Ab[r][c] = (i < r1 && b0 + c < m) ? KXU[i * m + b0 + c] : make_float2(0.f, 0.f);
+            float2 ka = (i < r1 && a0 + c < m) ? KXU[i * m + a0 + c] : make_float2(0.f, 0.f);
+            float2 kb = (i < r1 && b0 + c < m) ? KXU[i * m + b0 + c] : make_float2(0.f, 0.f);
+            Aa[r][c] = (double)ka.x + (double)ka.y;
+            Ab[r][c] = (double)kb.x + (double)kb.y;
         }
         __syncthreads();
 #pragma unroll 2
         for (int r = 0; r < SR; ++r) {
-            float2 va[4], vb[4];
+            double va[4], vb[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) va[u] = Aa[r][ty * 4 + u];
 #pragma unroll
@@ -258,11 +252,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    // (ha + la)(hb + lb): exact ha*hb by TwoProduct, cross terms into c
-                    dot2s(acc[u][v], va[u].x, vb[v].x);
-                    acc[u][v].c = fmaf(va[u].x, vb[v].y, fmaf(va[u].y, vb[v].x, acc[u][v].c));
-                }
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(va[u], vb[v], acc[u][v]);
         }
     }
     double* P = part + (int64_t)blockIdx.z * m * m;
@@ -271,7 +261,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int64_t a = a0 + ty * 4 + u, bb = b0 + tx * 4 + v;
-            if (a < m && bb < m && bb <= a) P[a * m + bb] = (double)acc[u][v].s + (double)acc[u][v].c;
+            if (a < m && bb < m && bb <= a) P[a * m + bb] = acc[u][v];
         }
 }
 
@@ -401,39 +391,33 @@ __global__ void tri_upper_apply_kernel(const double* __restrict__ U, int64_t m,
     if (lane == 0) u[(int64_t)k * m + j] = s;
 }
 
-// Z = (R - K_XU u) / sigma^2, warp per row; u is split into FP32 hi + lo and
-// the row sum of the pair products accumulated with Dot2, lanes combined in FP64.
-__global__ void split_u_kernel(const double* __restrict__ u, int64_t len, float2* __restrict__ o) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= len) return;
-    const double v = u[e];
-    const float hi = (float)v;
-    o[e] = make_float2(hi, (float)(v - (double)hi));
-}
-
+// Z = (R - K_XU u) / sigma^2, warp per row, FP64 accumulation.  With a
+// badly conditioned M (kappa ~ 1e11 at noise 1e-4), u = M^{-1} K_UX r has
+// components up to ~1e6 that cancel to O(1) in K_XU u; a compensated-FP32 sum
+// (2^-48) left ~3e-6 relative noise there and weakened the preconditioner,
+// FP64 (2^-53) matches the direct solve.
 template <typename T>
 __global__ void __launch_bounds__(256)
     nys_back_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
-                    const float2* __restrict__ u2, int c, const T* __restrict__ R, int64_t ldr,
+                    const double* __restrict__ u, int c, const T* __restrict__ R, int64_t ldr,
                     T* __restrict__ Z, int64_t ldz, double inv_noise) {
-    extern __shared__ float2 su[];  // m * c
-    for (int64_t e = threadIdx.x; e < m * c; e += blockDim.x) su[e] = u2[e];
+    extern __shared__ double su[];  // m * c
+    for (int64_t e = threadIdx.x; e < m * c; e += blockDim.x) su[e] = u[e];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const float2* Ki = KXU + i * m;
         for (int k = 0; k < c; ++k) {
-            const float2* uk = su + (int64_t)k * m;
-            Acc2 acc = {0.f, 0.f};
+            const double* uk = su + (int64_t)k * m;
+            double acc = 0.0;
             for (int64_t a = lane; a < m; a += 32) {
                 const float2 kv = __ldg(Ki + a);
-                dot2_add(acc, kv.x, uk[a].x);
-                acc.c = fmaf(kv.x, uk[a].y, fmaf(kv.y, uk[a].x, acc.c));
+                acc = fma((double)kv.x + (double)kv.y, uk[a], acc);
             }
-            double s = warp_sum((double)acc.s + (double)acc.c);
+            const double sm = warp_sum(acc);
             if (lane == 0)
-                Z[i + (int64_t)k * ldz] = (T)(((double)R[i + (int64_t)k * ldr] - s) * inv_noise);
+                Z[i + (int64_t)k * ldz] = (T)(((double)R[i + (int64_t)k * ldr] - sm) * inv_noise);
         }
     }
 }
@@ -495,10 +479,11 @@ __global__ void bj_apply_kernel(const double* __restrict__ Ub, int64_t n, int64_
 // Blocked Cholesky of a batch of SPD matrices (in place, lower) and the
 // explicit inverse factor U = L^{-T}.  Returns the first failing status.
 static int factor_and_invert(double* A, double* U, int64_t b, int64_t n_total, int64_t nmat,
-                             int* status_dev, cudaStream_t st) {
+                             int* status_dev, cudaStream_t st, double thr = 0.0) {
     KPCG_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int) * nmat, st));
     for (int64_t j0 = 0; j0 < b; j0 += NB) {
-        potrf_diag_kernel<<<(unsigned)nmat, 256, 0, st>>>(A, b * b, b, n_total, j0, status_dev);
+        potrf_diag_kernel<<<(unsigned)nmat, 256, 0, st>>>(A, b * b, b, n_total, j0, status_dev,
+                                                          thr);
         KPCG_LAUNCHED("potrf_diag_kernel");
         const int64_t rows = b - j0 - NB;
         if (rows > 0) {
@@ -563,8 +548,16 @@ void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64
     KPCG_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), M0, sizeof(double) * (m + 1),
                                 sizeof(double), (size_t)m, cudaMemcpyDeviceToHost, st));
     KPCG_CUDA(cudaStreamSynchronize(st));
-    double tr = 0.0;
-    for (double v : diag) tr += v;
+    double tr = 0.0, dmax = 0.0;
+    for (double v : diag) {
+        tr += v;
+        dmax = std::max(dmax, v);
+    }
+    // Deterministic acceptance (the paper is silent): every pivot must exceed
+    // kPivotTol * max diag(M); a nearly singular M otherwise "factors" or not
+    // depending on rounding details, and a factor with pivots near zero makes
+    // a useless preconditioner.
+    const double kPivotTol = 3e-12;
     double* M = P.M.need((size_t)m * m);
     double* U = P.U.need((size_t)m * m);
     int* status = P.status.need(1);
@@ -577,7 +570,7 @@ void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64
             add_diag_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(M, m, P.jitter);
             KPCG_LAUNCHED("add_diag_kernel");
         }
-        rc = factor_and_invert(M, U, m, m, 1, status, st);
+        rc = factor_and_invert(M, U, m, m, 1, status, st, kPivotTol * dmax);
     }
     if (rc) fail(KPCG_ERR_NOT_SPD, "Nystrom inner matrix is not positive definite after jitter");
     P.ready = true;
@@ -629,16 +622,13 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     tri_upper_apply_kernel<<<dim3((unsigned)((m * 32 + 255) / 256), c), 256, 0, st>>>(P.U.p, m, y,
                                                                                      w);
     KPCG_LAUNCHED("tri_upper_apply_kernel");
-    const size_t smem = sizeof(float2) * (size_t)m * c;
+    const size_t smem = sizeof(double) * (size_t)m * c;
     if (smem > 200 * 1024) fail(KPCG_ERR_ARG, "Nystrom apply: m * c too large");
     if (smem > 48 * 1024)
         KPCG_CUDA(cudaFuncSetAttribute(nys_back_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    float2* u2 = reinterpret_cast<float2*>(y);  // y is free again: reuse it for split u
-    split_u_kernel<<<(unsigned)((c * m + 255) / 256), 256, 0, st>>>(w, c * m, u2);
-    KPCG_LAUNCHED("split_u_kernel");
     int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 16);
-    nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, u2, c, R, ldr, Z, ldz,
+    nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, w, c, R, ldr, Z, ldz,
                                                   1.0 / P.noise);
     KPCG_LAUNCHED("nys_back_kernel");
 }

@@ -321,7 +321,9 @@ def test_full_size_double_float_solve_sampled_rows(kpcg):
     # sampled rows, each recomputed by the oracle row by row in FP64.
     p = synthetic.config2(seed=0)
     idx = synthetic.inducing_subset(p.n, 1024, seed=1)
-    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+    # the FP64 oracle needs 62 iterations (tests/golden/oracle_pcg_n65536.json);
+    # the cap keeps a regression from running for minutes
+    with _solver(kpcg, p, precision=kpcg.KPCG_DF64, max_iter=600) as s:
         s.precond(kpcg.KPCG_PREC_NYSTROM, 1024, idx)
         x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
     x = _np(x)
