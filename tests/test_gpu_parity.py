@@ -184,8 +184,10 @@ def test_nystrom_apply_matches_oracle(kpcg):
 
 
 def test_nystrom_apply_small_noise_many_inducing(kpcg):
-    # noise 1e-4 with m = n/2: the regime where an FP32 K_XU visibly weakened
-    # the preconditioner (more PCG iterations than the oracle).
+    # noise 1e-4 with m = n/2: M has condition ~1e11, so two FP64
+    # constructions of P^-1 differ by up to ~kappa(M) eps ~ 1e-5 relative
+    # (tolerance 1e-4); the decisive check is that PCG with the GPU's
+    # preconditioner needs the oracle's iteration count.
     p = synthetic.config2(seed=0, n=2048)
     ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
     idx = synthetic.inducing_subset(2048, 1024, seed=1)
@@ -195,7 +197,7 @@ def test_nystrom_apply_small_noise_many_inducing(kpcg):
         s.precond(kpcg.KPCG_PREC_NYSTROM, 1024, idx)
         out = _np(s.precond_apply(_cm(R)))
         x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
-    assert _rel(out, P.apply(R)) <= 1e-6
+    assert _rel(out, P.apply(R)) <= 1e-4
     _, it_ref, _, _ = oracle.pcg(p.X, ell, s2, p.noise, p.y, precond=P, tol=1e-8)
     assert st == 0 and abs(int(it[0]) - int(it_ref[0])) <= 3, (it, it_ref)
 
