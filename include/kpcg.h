@@ -199,12 +199,58 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
 /* Stochastic gradient of log p(y|theta) (Eq. 2, trace by Rademacher probes as
  * in Sec. 2.1):  g_q = -1/2 (1/t) sum_k w_k^T dK_q r_k + 1/2 a^T dK_q a, with
  * [a, w_1..w_t] = K_y^{-1} [y, r_1..r_t] solved as one block to tol.
+ * alpha0 (device, n doubles, nullable) is the initial iterate of the a column
+ * (the probe columns start at zero).
  * y (device, n doubles), probes (device, n x t column-major, ld = n, entries
  * +-1, t >= 1).  grad (host) receives n_theta + 1 values:
  * d/dlog l_r (or d/dlog l), d/dlog s^2, d/dlog sigma^2.  alpha (device,
  * nullable) receives a = K_y^{-1} y. */
 kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
-                      double* grad, double* alpha, kpcg_info* info);
+                      const double* alpha0, double* grad, double* alpha, kpcg_info* info);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  Algorithm 1 takes an initial iterate x0; along a
+ * hyperparameter trajectory a small network predicts coefficients c on a fixed
+ * basis of m inducing points Z, and x0 = K(X, Z | theta) c.  The calls below
+ * provide the basis (fit and expansion under the current theta) and the
+ * network (hand-written training and inference kernels).
+ * ------------------------------------------------------------------------ */
+
+/* Fix the basis Z = rows idx (host, m sorted distinct indices) of X.  ridge
+ * (> 0) regularises the fit: c = argmin |K_XZ c - a|^2 + ridge c^T K_ZZ c.
+ * Rebuilt for the current theta when needed (same pivot rule as Nystrom). */
+kpcg_status kpcg_warm_basis(kpcg_t h, int64_t m, const int64_t* idx, double ridge);
+/* c (device, m doubles) = fitted coefficients of a (device, n doubles). */
+kpcg_status kpcg_warm_fit(kpcg_t h, const double* a, double* c);
+/* x0 (device, n doubles) = K(X, Z | theta) c for c (device, m doubles). */
+kpcg_status kpcg_warm_expand(kpcg_t h, const double* c, double* x0);
+
+typedef struct kpcg_mlp* kpcg_mlp_t;
+
+/* The network Linear(n_in,h1)-tanh-Linear(h1,h2)-tanh-Linear(h2,n_out).
+ * params (host, float32) holds W1 (h1 x n_in, row-major), b1, W2 (h2 x h1), b2,
+ * W3 (n_out x h2), b3 back to back.  Batches up to max_batch rows. */
+kpcg_status kpcg_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_out,
+                            const float* params, int32_t max_batch, void* stream,
+                            kpcg_mlp_t* out);
+/* out (device, batch x n_out) for inputs (device, batch x n_in, row-major);
+ * bf16 != 0: BF16 weights and inputs, FP32 accumulation (inference). */
+kpcg_status kpcg_mlp_forward(kpcg_mlp_t m, const float* inputs, int32_t batch, float* out,
+                             int32_t bf16);
+/* Gradient of the mean squared error w.r.t. params into grads (device, params
+ * layout); loss (host, nullable). */
+kpcg_status kpcg_mlp_grad(kpcg_mlp_t m, const float* inputs, const float* targets,
+                          int32_t batch, float* grads, float* loss);
+/* epochs full-batch Adam steps (beta 0.9, 0.999, eps 1e-8) at rate lr.  One
+ * step is captured once as a CUDA graph for these pointers, batch and lr, and
+ * replayed; the pointers must stay valid while the network is trained with
+ * them.  loss (host, nullable) receives the loss before the last update. */
+kpcg_status kpcg_mlp_train(kpcg_mlp_t m, const float* inputs, const float* targets,
+                           int32_t batch, int32_t epochs, float lr, float* loss);
+/* Copy the parameters to params (host, float32, create layout). */
+kpcg_status kpcg_mlp_get_params(kpcg_mlp_t m, float* params);
+void kpcg_mlp_destroy(kpcg_mlp_t m);
+const char* kpcg_mlp_last_error(kpcg_mlp_t m);
 
 /* The native-FP64 product O = (K + sigma^2 I) V of kpcg_matvec_f64 (impl 0)
  * for callers that cannot allocate device memory: for example a host program

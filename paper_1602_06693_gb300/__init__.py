@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     KPCG_PREC_NYSTROM,
     KPCG_TC_IR,
     KpcgError,
+    MLP,
     Options,
     Solver,
     Info,

@@ -28,7 +28,9 @@ SYMBOLS = (
     "kpcg_default_options", "kpcg_status_string", "kpcg_create", "kpcg_set_theta",
     "kpcg_set_options", "kpcg_precond", "kpcg_matvec_f64", "kpcg_matvec_f32",
     "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
-    "kpcg_last_error", "kpcg_matvec_f64_noalloc",
+    "kpcg_last_error", "kpcg_matvec_f64_noalloc", "kpcg_warm_basis", "kpcg_warm_fit",
+    "kpcg_warm_expand", "kpcg_mlp_create", "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
+    "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
 )
 
 
@@ -112,7 +114,20 @@ def lib():
         L.kpcg_solve.argtypes = [vp, vp, i64, i32, dbl, vp, vp, i64,
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
         L.kpcg_dkv.argtypes = [vp, vp, i64, i32, vp, i64]
-        L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, pdbl, vp, ctypes.POINTER(Info)]
+        L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, vp, pdbl, vp, ctypes.POINTER(Info)]
+        L.kpcg_warm_basis.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), dbl]
+        L.kpcg_warm_fit.argtypes = [vp, vp, vp]
+        L.kpcg_warm_expand.argtypes = [vp, vp, vp]
+        pflt = ctypes.POINTER(ctypes.c_float)
+        L.kpcg_mlp_create.argtypes = [i32, i32, i32, i32, pflt, i32, vp, ctypes.POINTER(vp)]
+        L.kpcg_mlp_forward.argtypes = [vp, vp, i32, vp, i32]
+        L.kpcg_mlp_grad.argtypes = [vp, vp, vp, i32, vp, pflt]
+        L.kpcg_mlp_train.argtypes = [vp, vp, vp, i32, i32, ctypes.c_float, pflt]
+        L.kpcg_mlp_get_params.argtypes = [vp, pflt]
+        L.kpcg_mlp_destroy.argtypes = [vp]
+        L.kpcg_mlp_destroy.restype = None
+        L.kpcg_mlp_last_error.argtypes = [vp]
+        L.kpcg_mlp_last_error.restype = ctypes.c_char_p
         L.kpcg_matvec_f64_noalloc.argtypes = [vp, i64, i32, pdbl, i32, dbl, vp, i64, i32, vp,
                                               i64, vp]
         L.kpcg_destroy.argtypes = [vp]
@@ -120,7 +135,8 @@ def lib():
         L.kpcg_last_error.argtypes = [vp]
         L.kpcg_last_error.restype = ctypes.c_char_p
         for name in SYMBOLS[2:]:
-            if name not in ("kpcg_destroy", "kpcg_last_error"):
+            if name not in ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy",
+                            "kpcg_mlp_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -322,7 +338,7 @@ class Solver:
                                    ctypes.c_void_p(G.data_ptr()), self.n))
         return G.transpose(1, 2)  # (n_theta, n, c)
 
-    def grad(self, y, probes, tol=1e-8, want_alpha=False):
+    def grad(self, y, probes, tol=1e-8, want_alpha=False, alpha0=None):
         """Stochastic gradient of log p (Eq. 2): returns (grad[n_theta+1], alpha|None, Info)."""
         torch = _torch()
         if y.dim() != 1 or not y.is_contiguous():
@@ -333,9 +349,114 @@ class Solver:
         g = np.zeros(self.n_theta + 1, dtype=np.float64)
         alpha = torch.empty(self.n, dtype=torch.float64, device=y.device) if want_alpha else None
         info = Info()
+        a0 = _dptr(alpha0, torch.float64, "alpha0") if alpha0 is not None else None
         self._check(lib().kpcg_grad(self._h, _dptr(y, torch.float64, "y"),
-                                    _dptr(P, torch.float64, "probes"), t, float(tol),
+                                    _dptr(P, torch.float64, "probes"), t, float(tol), a0,
                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     _dptr(alpha, torch.float64, "alpha") if want_alpha else None,
                                     ctypes.byref(info)))
         return g, alpha, info
+
+    # -- learned warm start: basis fit and expansion
+    def warm_basis(self, idx, ridge=1e-6):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        self.m_warm = int(idx.shape[0])
+        self._check(lib().kpcg_warm_basis(self._h, self.m_warm,
+                                          idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          float(ridge)))
+
+    def warm_fit(self, a):
+        torch = _torch()
+        c = torch.empty(self.m_warm, dtype=torch.float64, device=a.device)
+        self._check(lib().kpcg_warm_fit(self._h, _dptr(a, torch.float64, "a"),
+                                        _dptr(c, torch.float64, "c")))
+        return c
+
+    def warm_expand(self, c):
+        torch = _torch()
+        x0 = torch.empty(self.n, dtype=torch.float64, device=c.device)
+        self._check(lib().kpcg_warm_expand(self._h, _dptr(c, torch.float64, "c"),
+                                           _dptr(x0, torch.float64, "x0")))
+        return x0
+
+
+MLP_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+class MLP:
+    """The warm-start network (kpcg_mlp_*): parameters live on the GPU."""
+
+    def __init__(self, params: dict, max_batch=256, stream=None):
+        torch = _torch()
+        self.shapes = {k: np.asarray(params[k]).shape for k in MLP_NAMES}
+        h1, n_in = self.shapes["W1"]
+        h2 = self.shapes["W2"][0]
+        n_out = self.shapes["W3"][0]
+        self.dims = (n_in, h1, h2, n_out)
+        flat = np.concatenate([np.asarray(params[k], dtype=np.float32).ravel() for k in MLP_NAMES])
+        self.size = flat.size
+        st = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        L = lib()
+        rc = L.kpcg_mlp_create(n_in, h1, h2, n_out,
+                               flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(max_batch),
+                               ctypes.c_void_p(st.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise KpcgError(rc, L.kpcg_mlp_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise KpcgError(rc, lib().kpcg_mlp_last_error(self._h).decode())
+
+    def forward(self, X, bf16=False):
+        torch = _torch()
+        X = X.contiguous()
+        out = torch.empty((X.shape[0], self.dims[3]), dtype=torch.float32, device=X.device)
+        self._check(lib().kpcg_mlp_forward(self._h, _dptr(X, torch.float32, "X"), X.shape[0],
+                                           _dptr(out, torch.float32, "out"), int(bool(bf16))))
+        return out
+
+    def grad(self, X, T):
+        torch = _torch()
+        g = torch.empty(self.size, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_float()
+        self._check(lib().kpcg_mlp_grad(self._h, _dptr(X, torch.float32, "X"),
+                                        _dptr(T, torch.float32, "T"), X.shape[0],
+                                        _dptr(g, torch.float32, "g"), ctypes.byref(loss)))
+        return self._unflatten(g.cpu().numpy()), float(loss.value)
+
+    def train(self, X, T, epochs, lr):
+        """Full-batch Adam; X and T must stay alive while trained with (graph)."""
+        torch = _torch()
+        loss = ctypes.c_float()
+        self._keep = (X, T)
+        self._check(lib().kpcg_mlp_train(self._h, _dptr(X, torch.float32, "X"),
+                                         _dptr(T, torch.float32, "T"), X.shape[0], int(epochs),
+                                         float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def params(self):
+        flat = np.empty(self.size, dtype=np.float32)
+        self._check(lib().kpcg_mlp_get_params(self._h,
+                                              flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return self._unflatten(flat)
+
+    def _unflatten(self, flat):
+        out, o = {}, 0
+        for k in MLP_NAMES:
+            sz = int(np.prod(self.shapes[k]))
+            out[k] = flat[o:o + sz].reshape(self.shapes[k])
+            o += sz
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kpcg_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

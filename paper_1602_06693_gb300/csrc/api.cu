@@ -731,6 +731,7 @@ kpcg_status kpcg_set_theta(kpcg_t h, const double* log_theta, double noise_var) 
         h->log_theta.assign(log_theta, log_theta + (h->ard ? h->d + 1 : 2));
         h->noise = noise_var;
         h->P.reset();
+        h->Wb.reset();
         kpcg::ctx_rescale(*h);
     });
     return KPCG_OK;
@@ -878,7 +879,7 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
 }
 
 kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
-                      double* grad, double* alpha, kpcg_info* info) {
+                      const double* alpha0, double* grad, double* alpha, kpcg_info* info) {
     if (!h) return KPCG_ERR_ARG;
     KPCG_GUARD(h, {
         if (t < 1) fail(KPCG_ERR_ARG, "t must be >= 1");
@@ -895,7 +896,15 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
         kpcg::copy_cols<double>(Bb + ld, ld, probes, n, n, t, st);
         kpcg_info sinfo{};
         h->P.n = n;
-        const kpcg_status s = kpcg::solve_impl(*h, Bb, ld, c, tol, nullptr, Sb, ld, nullptr, &sinfo);
+        const double* X0 = nullptr;
+        if (alpha0) {
+            kpcg::check_dev_ptr(alpha0, "alpha0");
+            double* X0b = h->Q64.need((size_t)ld * c);
+            kpcg::fill_zero_cols(X0b, sizeof(double), ld, n, c, st);
+            kpcg::copy_cols<double>(X0b, ld, alpha0, n, n, 1, st);
+            X0 = X0b;
+        }
+        const kpcg_status s = kpcg::solve_impl(*h, Bb, ld, c, tol, X0, Sb, ld, nullptr, &sinfo);
         if (s != KPCG_OK) return s;
         // G_q = dK_q [a, r_1..r_t]
         const int nq = (h->ard ? h->d : 1) + 1;
@@ -932,6 +941,55 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
             grad[q] = scale * (-0.5 * tr + 0.5 * quad);
         }
         if (info) *info = sinfo;
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_warm_basis(kpcg_t h, int64_t m, const int64_t* idx, double ridge) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (m < 1 || m > h->n || m > 4096) fail(KPCG_ERR_ARG, "m must be in [1, min(n, 4096)]");
+        if (!idx) fail(KPCG_ERR_ARG, "idx is NULL");
+        if (!(ridge > 0.0) || !std::isfinite(ridge)) fail(KPCG_ERR_ARG, "ridge must be > 0");
+        for (int64_t a = 0; a < m; ++a) {
+            if (idx[a] < 0 || idx[a] >= h->n) fail(KPCG_ERR_ARG, "basis index out of range");
+            if (a && idx[a] <= idx[a - 1]) fail(KPCG_ERR_ARG, "basis indices must be sorted");
+        }
+        h->widx.assign(idx, idx + m);
+        h->wridge = ridge;
+        h->Wb.reset();
+    });
+    return KPCG_OK;
+}
+
+static void ensure_warm(kpcg::Ctx& h) {
+    if (h.widx.empty()) fail(KPCG_ERR_STATE, "no warm-start basis: call kpcg_warm_basis first");
+    if (h.Wb.ready) return;
+    kpcg::nystrom_setup(h.Wb, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), h.wridge,
+                        h.widx.data(), (int64_t)h.widx.size(), h.stream);
+    h.Wb.n = h.n;
+}
+
+kpcg_status kpcg_warm_fit(kpcg_t h, const double* a, double* c) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        kpcg::check_dev_ptr(a, "a");
+        kpcg::check_dev_ptr(c, "c");
+        ensure_warm(*h);
+        kpcg::nystrom_project_solve(h->Wb, a, h->n, 1, c, h->stream);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_warm_expand(kpcg_t h, const double* c, double* x0) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        kpcg::check_dev_ptr(c, "c");
+        kpcg::check_dev_ptr(x0, "x0");
+        ensure_warm(*h);
+        kpcg::nystrom_expand(h->Wb, c, x0, h->stream);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
     });
     return KPCG_OK;
 }

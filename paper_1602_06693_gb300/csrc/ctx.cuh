@@ -90,6 +90,10 @@ struct Ctx {
     int pkind = KPCG_PREC_NONE;
     int64_t psize = 0;
     std::vector<int64_t> pidx;
+    // warm-start basis (Nystrom-type fit), rebuilt lazily when theta changes
+    PrecondState Wb;
+    std::vector<int64_t> widx;
+    double wridge = 0.0;
     DevBuf<float> W32;
     DevBuf<double> partial;
     DevBuf<double> scal;

@@ -633,6 +633,57 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     KPCG_LAUNCHED("nys_back_kernel");
 }
 
+// u = M^{-1} K_UX r for c columns (FP64 in and out, column-major, ld m for u).
+void nystrom_project_solve(const PrecondState& P, const double* R, int64_t ldr, int c, double* u,
+                           cudaStream_t st) {
+    const int64_t n = P.n, m = P.m;
+    const int64_t ablk = (m + 255) / 256;
+    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((152 * 4 + ablk - 1) / ablk,
+                                                             (n + 127) / 128));
+    const int64_t rps = (n + nsplit - 1) / nsplit;
+    nsplit = (int)((n + rps - 1) / rps);
+    double* part = const_cast<PrecondState&>(P).wpart.need((size_t)nsplit * c * m);
+    double* w = const_cast<PrecondState&>(P).w.need((size_t)c * m);
+    double* y = const_cast<PrecondState&>(P).y.need((size_t)c * m);
+    for (int k0 = 0; k0 < c; k0 += PC) {
+        const int nc = std::min(PC, c - k0);
+        dim3 g((unsigned)((m + 255) / 256), (unsigned)nsplit);
+        nys_proj_kernel<double><<<g, 256, 0, st>>>(P.KXU.p, n, m, R + (int64_t)k0 * ldr, ldr, nc,
+                                                   rps, part + (int64_t)k0 * m, c);
+        KPCG_LAUNCHED("nys_proj_kernel");
+    }
+    sum_splits_kernel<<<(unsigned)((c * m + 255) / 256), 256, 0, st>>>(part, nsplit, c * m, w);
+    KPCG_LAUNCHED("sum_splits_kernel");
+    tri_lower_apply_kernel<<<dim3((unsigned)((m + 31) / 32), c), 1024, 0, st>>>(P.U.p, m, w, y);
+    KPCG_LAUNCHED("tri_lower_apply_kernel");
+    tri_upper_apply_kernel<<<dim3((unsigned)((m * 32 + 255) / 256), c), 256, 0, st>>>(P.U.p, m, y,
+                                                                                     u);
+    KPCG_LAUNCHED("tri_upper_apply_kernel");
+}
+
+// out[i] = sum_a K_XU[i][a] u[a] (one column, FP64 accumulation, warp per row).
+__global__ void nys_expand_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
+                                  const double* __restrict__ u, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const float2* Ki = KXU + i * m;
+        double acc = 0.0;
+        for (int64_t a = lane; a < m; a += 32) {
+            const float2 kv = __ldg(Ki + a);
+            acc = fma((double)kv.x + (double)kv.y, __ldg(u + a), acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) out[i] = acc;
+    }
+}
+
+void nystrom_expand(const PrecondState& P, const double* u, double* out, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((P.n + 7) / 8, 152 * 16);
+    nys_expand_kernel<<<blocks, 256, 0, st>>>(P.KXU.p, P.n, P.m, u, out);
+    KPCG_LAUNCHED("nys_expand_kernel");
+}
+
 template <typename T>
 static void bj_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
                      cudaStream_t st) {

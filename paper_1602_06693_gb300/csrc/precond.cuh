@@ -45,6 +45,12 @@ struct PrecondState {
 void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
                    float c0_32, double c0_64, double noise, const int64_t* idx_host, int64_t m,
                    cudaStream_t st);
+// u = M^{-1} K_UX R (FP64, c columns, u column-major with ld m), the
+// coefficient fit of the warm-start basis.
+void nystrom_project_solve(const PrecondState& P, const double* R, int64_t ldr, int c, double* u,
+                           cudaStream_t st);
+// out = K_XU u for one column (FP64).
+void nystrom_expand(const PrecondState& P, const double* u, double* out, cudaStream_t st);
 void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
                         double noise, int64_t b, cudaStream_t st);
 

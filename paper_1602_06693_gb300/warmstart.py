@@ -1,0 +1,126 @@
+"""Learned warm start of PCG along a hyperparameter trajectory.
+
+Stochastic-gradient ascent on log p(y|theta) (gradient of Eq. 2 with the
+Rademacher trace estimate of Sec. 2.1; the paper's optimiser is ADAGRAD with
+N_r = 4 probes, Sec. 5, this driver uses Adam) visits theta_1, theta_2, ...,
+and every step solves K_y(theta_k) alpha_k = y.  Algorithm 1 starts from an
+initial iterate x0.  For the first ``n_train`` steps the driver records
+(theta_k, c*_k), where c*_k fits the converged alpha_k on a fixed basis Z
+(kpcg_warm_fit); it then trains the network theta -> c (kpcg_mlp_train,
+FP32) and, from then on, starts each solve from x0 = K(X, Z | theta_k) c with
+c predicted in BF16 (kpcg_mlp_forward, kpcg_warm_expand).  PCG still runs to
+the same tolerance, so the network only moves the starting point.
+
+The few scalars of the optimiser (d + 2 log-parameters) and the affine
+standardisation of the network's inputs and outputs are host arithmetic; the
+solves, gradients, fits, expansions and the network run in the library.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import binding as _b
+
+
+@dataclasses.dataclass
+class StepRecord:
+    step: int
+    warm: bool
+    iters: int        # PCG iterations of the alpha solve
+    solve_ms: float   # device time of the alpha solve (CUDA events)
+    rel_res: float
+    log_theta: np.ndarray
+    log_noise: float
+
+
+class Trajectory:
+    def __init__(self, solver: "_b.Solver", y, basis_idx, precond_idx, probes_fn, *,
+                 lr=0.05, n_train=50, mlp_params=None, epochs=2000, mlp_lr=1e-3, tol=1e-8,
+                 ridge=1e-6):
+        import torch
+
+        self.torch = torch
+        self.s = solver
+        self.y = y
+        self.precond_idx = np.asarray(precond_idx, dtype=np.int64)
+        self.probes_fn = probes_fn
+        self.lr = lr
+        self.n_train = n_train
+        self.epochs = epochs
+        self.mlp_lr = mlp_lr
+        self.tol = tol
+        self.s.warm_basis(basis_idx, ridge)
+        self.mlp_params = mlp_params
+        self.mlp = None
+        self.inputs, self.targets = [], []
+        self.m1 = None
+        self.m2 = None
+        self.t = 0
+        self.records: list[StepRecord] = []
+
+    # -- host-side standardisation of the network's inputs and outputs
+    def _fit_scalers(self):
+        Z = np.array(self.inputs)
+        C = np.array(self.targets)
+        self.z_mu, self.z_sd = Z.mean(0), np.maximum(Z.std(0), 1e-3)
+        self.c_mu, self.c_sd = C.mean(0), np.maximum(C.std(0), 1e-12 + 1e-6 * np.abs(C).max())
+
+    def train(self):
+        torch = self.torch
+        self._fit_scalers()
+        Zs = (np.array(self.inputs) - self.z_mu) / self.z_sd
+        Cs = (np.array(self.targets) - self.c_mu) / self.c_sd
+        self.Xt = torch.from_numpy(Zs.astype(np.float32)).cuda()
+        self.Tt = torch.from_numpy(Cs.astype(np.float32)).cuda()
+        self.mlp = _b.MLP(self.mlp_params, max_batch=max(256, len(self.inputs)))
+        return self.mlp.train(self.Xt, self.Tt, self.epochs, self.mlp_lr)
+
+    def predict_x0(self, z):
+        torch = self.torch
+        zi = torch.from_numpy(((z - self.z_mu) / self.z_sd).astype(np.float32)[None, :]).cuda()
+        cs = self.mlp.forward(zi, bf16=True)[0].double().cpu().numpy()
+        c = torch.from_numpy(cs * self.c_sd + self.c_mu).cuda()
+        return self.s.warm_expand(c)
+
+    def step(self, k, z):
+        """One trajectory step at z = [log_theta..., log noise]; returns the gradient."""
+        torch = self.torch
+        s = self.s
+        s.set_theta(z[:-1], math.exp(z[-1]))
+        s.precond(_b.KPCG_PREC_NYSTROM, len(self.precond_idx), self.precond_idx)
+        warm = self.mlp is not None
+        x0 = self.predict_x0(z) if warm else None
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        alpha, it, info, rc = s.solve(self.y, tol=self.tol, X0=x0, raise_on_error=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        self.records.append(StepRecord(k, warm, int(it[0]), e0.elapsed_time(e1),
+                                       info.max_rel_res, np.array(z[:-1]), float(z[-1])))
+        if k < self.n_train:
+            self.inputs.append(np.array(z))
+            self.targets.append(s.warm_fit(alpha).cpu().numpy())
+        g, _, _ = s.grad(self.y, self.probes_fn(k), tol=self.tol, alpha0=alpha)
+        return g
+
+    def run(self, z0, steps):
+        z = np.array(z0, dtype=np.float64)
+        self.m1 = np.zeros_like(z)
+        self.m2 = np.zeros_like(z)
+        for k in range(steps):
+            if k == self.n_train and self.mlp is None and self.mlp_params is not None:
+                self.train()
+            g = self.step(k, z)
+            # Adam ascent on log p
+            self.t += 1
+            self.m1 = 0.9 * self.m1 + 0.1 * g
+            self.m2 = 0.999 * self.m2 + 0.001 * g * g
+            mh = self.m1 / (1 - 0.9 ** self.t)
+            vh = self.m2 / (1 - 0.999 ** self.t)
+            z = z + self.lr * mh / (np.sqrt(vh) + 1e-8)
+        return self.records

@@ -41,6 +41,7 @@ __all__ = [
     "config5",
     "rademacher",
     "inducing_subset",
+    "mlp_init",
 ]
 
 
@@ -186,3 +187,16 @@ def inducing_subset(n: int, m: int, seed: int) -> np.ndarray:
         raise ValueError("m > n")
     g = rng(seed)
     return np.sort(g.choice(n, size=m, replace=False)).astype(np.int64)
+
+
+def mlp_init(seed: int, n_in: int, h1: int, h2: int, n_out: int) -> dict:
+    """Xavier-uniform initial weights (zero biases), float64, for the
+    warm-start network: W1 (h1, n_in), b1, W2 (h2, h1), b2, W3 (n_out, h2), b3."""
+    g = rng(seed)
+
+    def xavier(o, i):
+        a = math.sqrt(6.0 / (i + o))
+        return g.uniform(-a, a, size=(o, i))
+
+    return {"W1": xavier(h1, n_in), "b1": np.zeros(h1), "W2": xavier(h2, h1),
+            "b2": np.zeros(h2), "W3": xavier(n_out, h2), "b3": np.zeros(n_out)}

@@ -321,3 +321,43 @@ def test_synthetic_inputs_are_seeded():
     assert set(np.unique(R)) == {-1.0, 1.0} and R.flags.f_contiguous
     idx = synthetic.inducing_subset(100, 10, 0)
     assert np.all(np.diff(idx) > 0) and idx.max() < 100
+
+
+# ------------------------------------------------- warm-start network (MLP)
+def _mlp_case():
+    from oracle import mlp
+    P = synthetic.mlp_init(3, 3, 5, 4, 2)
+    for k in ("b1", "b2", "b3"):
+        P[k] = synthetic.rng(9).standard_normal(P[k].shape) * 0.3
+    X = synthetic.rng(1).standard_normal((4, 3))
+    T = synthetic.rng(2).standard_normal((4, 2))
+    return mlp, P, X, T
+
+
+def test_mlp_backprop_matches_finite_differences():
+    mlp, P, X, T = _mlp_case()
+    g = mlp.backward(P, X, T)
+    h = 1e-6
+    for k in mlp.NAMES:
+        fd = np.zeros_like(P[k])
+        for idx in np.ndindex(P[k].shape):
+            Pp = {q: v.copy() for q, v in P.items()}
+            Pm = {q: v.copy() for q, v in P.items()}
+            Pp[k][idx] += h
+            Pm[k][idx] -= h
+            fd[idx] = (mlp.loss(Pp, X, T) - mlp.loss(Pm, X, T)) / (2 * h)
+        np.testing.assert_allclose(g[k], fd, rtol=1e-7, atol=1e-10)
+
+
+def test_mlp_forward_closed_form_and_adam_first_step():
+    mlp, P, X, T = _mlp_case()
+    Z = {k: np.zeros_like(v) for k, v in P.items()}
+    Z["b3"] = np.array([0.5, -2.0])
+    out, _ = mlp.forward(Z, X)  # tanh(0) = 0: the output is the last bias
+    np.testing.assert_array_equal(out, np.tile([0.5, -2.0], (4, 1)))
+    # Adam, first step from zero moments: m^ = g, v^ = g^2, step = lr g/(|g| + eps)
+    g = mlp.backward(P, X, T)
+    P2 = mlp.adam_step({k: v.copy() for k, v in P.items()}, g, {}, lr=1e-2)
+    for k in mlp.NAMES:
+        np.testing.assert_allclose(P2[k] - P[k], -1e-2 * g[k] / (np.abs(g[k]) + 1e-8),
+                                   rtol=1e-12, atol=1e-15)
