@@ -277,6 +277,69 @@ kpcg_status kpcg_matvec_f64_noalloc(const float* X, int64_t n, int32_t d,
                                     const double* V, int64_t ldv, int32_t c, double* O,
                                     int64_t ldo, void* stream);
 
+/* ---- Many independent systems of uneven size, solved together ----------
+ * Each problem is an independent system (K_p + sigma_p^2 I) x = b of Eq. 1
+ * with its own inputs, hyperparameters and Nystrom preconditioner (Sec. 3.1);
+ * every one of its c right-hand sides runs its own CG (Algorithm 1) and stops
+ * on its own.  The solve is the mixed-precision one (KPCG_TC_IR): an FP64
+ * flexible-CG outer loop whose products use the double-float kernel, around an
+ * inner FP32 PCG whose products with K are ONE persistent tensor-core launch
+ * over the tiles of all problems, and whose preconditioner applies are one
+ * batched launch sequence.
+ *
+ * Block layout: every batch vector is a device float64 (or float32 for the
+ * test entry points) column-major ld x (nprob * c) array, ld >= max_p n_p;
+ * column p*c + k holds the k-th vector of problem p in rows 0 .. n_p-1.  Rows
+ * n_p .. ld-1 of an input are ignored, of an output set to zero. */
+typedef struct kpcg_batch* kpcg_batch_t;
+typedef struct {
+    const float* X;          /* device, n x d row-major, copied by create */
+    int64_t n;
+    int32_t d;               /* 1 .. 16 */
+    int32_t ard;
+    const double* log_theta; /* host, d+1 (ard) or 2 values as in kpcg_create */
+    double noise_var;        /* sigma^2 > 0 */
+    int64_t m;               /* Nystrom inducing points, 0 = no preconditioner */
+    const int64_t* idx;      /* host, m sorted distinct row indices (NULL when m = 0) */
+} kpcg_problem;
+
+/* Copies every problem (one internal handle each; see kpcg_create and
+ * kpcg_precond for their checks).  opt: NULL = defaults with precision
+ * KPCG_TC_IR; any other precision is rejected.  stream: cudaStream_t. */
+kpcg_status kpcg_batch_create(int32_t nprob, const kpcg_problem* probs,
+                              const kpcg_options* opt, void* stream, kpcg_batch_t* out);
+/* Solve every system for its c right-hand sides B (device, block layout) to
+ * ||b - K_y x|| <= tol ||b|| per column, the residual recomputed in FP64-class
+ * arithmetic (double-float products, ~1e-12 relative to FP64).  X: device,
+ * block layout (caller-owned).  iters, rel_res (host, nprob*c, nullable):
+ * inner PCG iterations and final relative residual per column.  Returns
+ * KPCG_ERR_NO_CONVERGENCE (X holds the last iterate) if a column missed tol. */
+kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_t c, double tol,
+                             double* X, int32_t* iters, double* rel_res, kpcg_info* info);
+/* The batched tensor-core product O = (K_p + sigma_p^2 (1 + inner_shift) I) V
+ * for every problem (device float32, block layout): the inner operator of the
+ * solve, exposed for tests and benchmarks. */
+kpcg_status kpcg_batch_matvec_f32(kpcg_batch_t b, const float* V, int64_t ld, int32_t c,
+                                  float* O);
+/* The batched preconditioner apply Z = P_p^{-1} R (device float32, block
+ * layout); problems without inducing points return Z = R. */
+kpcg_status kpcg_batch_precond_apply_f32(kpcg_batch_t b, const float* R, int64_t ld, int32_t c,
+                                         float* Z);
+/* Autotuner of the batched product for c columns per problem: times each
+ * candidate length of the work-list items (1 .. 64 column tiles of 128) on one
+ * persistent CTA per SM with CUDA events and keeps the fastest.  Runs by itself
+ * before the first product unless kpcg_batch_set_tiling fixed the tiling.
+ * Outputs (host, nullable): the chosen length, CTAs, and its time in ms. */
+kpcg_status kpcg_batch_tune(kpcg_batch_t b, int32_t c, int32_t* tiles_per_item, int32_t* ctas,
+                            float* best_ms);
+/* Fix the tiling (ctas = 0: one CTA per SM); disables the autotuner. */
+kpcg_status kpcg_batch_set_tiling(kpcg_batch_t b, int32_t tiles_per_item, int32_t ctas);
+/* max_p n_p: the smallest valid ld. */
+int64_t kpcg_batch_max_n(kpcg_batch_t b);
+void kpcg_batch_destroy(kpcg_batch_t b);
+/* Message of the last failing call on b (NULL: of the last failed create). */
+const char* kpcg_batch_last_error(kpcg_batch_t b);
+
 /* Release the handle and every device buffer it owns.  NULL is ignored. */
 void kpcg_destroy(kpcg_t h);
 

@@ -14,9 +14,11 @@ from .binding import (  # noqa: F401
     KPCG_PREC_NONE,
     KPCG_PREC_NYSTROM,
     KPCG_TC_IR,
+    Batch,
     KpcgError,
     MLP,
     Options,
+    Problem,
     Solver,
     Info,
     default_options,

@@ -30,8 +30,14 @@ SYMBOLS = (
     "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
     "kpcg_last_error", "kpcg_matvec_f64_noalloc", "kpcg_warm_basis", "kpcg_warm_fit",
     "kpcg_warm_expand", "kpcg_mlp_create", "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
-    "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
+    "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error", "kpcg_batch_create",
+    "kpcg_batch_solve", "kpcg_batch_matvec_f32", "kpcg_batch_precond_apply_f32",
+    "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_max_n", "kpcg_batch_destroy",
+    "kpcg_batch_last_error",
 )
+
+_NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
+              "kpcg_batch_max_n", "kpcg_batch_destroy", "kpcg_batch_last_error")
 
 
 class Options(ctypes.Structure):
@@ -69,6 +75,14 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Problem(ctypes.Structure):
+    """kpcg_problem: one system of a batch."""
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("ard", ctypes.c_int32), ("log_theta", ctypes.POINTER(ctypes.c_double)),
+                ("noise_var", ctypes.c_double), ("m", ctypes.c_int64),
+                ("idx", ctypes.POINTER(ctypes.c_int64))]
 
 
 class KpcgError(RuntimeError):
@@ -130,13 +144,27 @@ def lib():
         L.kpcg_mlp_last_error.restype = ctypes.c_char_p
         L.kpcg_matvec_f64_noalloc.argtypes = [vp, i64, i32, pdbl, i32, dbl, vp, i64, i32, vp,
                                               i64, vp]
+        L.kpcg_batch_create.argtypes = [i32, ctypes.POINTER(Problem), ctypes.POINTER(Options), vp,
+                                        ctypes.POINTER(vp)]
+        L.kpcg_batch_solve.argtypes = [vp, vp, i64, i32, dbl, vp, ctypes.POINTER(ctypes.c_int32),
+                                       pdbl, ctypes.POINTER(Info)]
+        L.kpcg_batch_matvec_f32.argtypes = [vp, vp, i64, i32, vp]
+        L.kpcg_batch_precond_apply_f32.argtypes = [vp, vp, i64, i32, vp]
+        L.kpcg_batch_tune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), pflt]
+        L.kpcg_batch_set_tiling.argtypes = [vp, i32, i32]
+        L.kpcg_batch_max_n.argtypes = [vp]
+        L.kpcg_batch_max_n.restype = ctypes.c_int64
+        L.kpcg_batch_destroy.argtypes = [vp]
+        L.kpcg_batch_destroy.restype = None
+        L.kpcg_batch_last_error.argtypes = [vp]
+        L.kpcg_batch_last_error.restype = ctypes.c_char_p
         L.kpcg_destroy.argtypes = [vp]
         L.kpcg_destroy.restype = None
         L.kpcg_last_error.argtypes = [vp]
         L.kpcg_last_error.restype = ctypes.c_char_p
         for name in SYMBOLS[2:]:
-            if name not in ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy",
-                            "kpcg_mlp_last_error"):
+            if name not in _NO_STATUS:
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -460,3 +488,133 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent systems of uneven size (kpcg_batch_*).
+
+    problems: sequence of (X, log_theta, noise, idx) with X a (n_p, d_p) float32
+    CUDA tensor and idx the sorted inducing rows (None: no preconditioner).
+    Block tensors are (ld, P*c) column-major float64/float32 CUDA tensors with
+    ld = max_n; ``block``/``unblock`` convert from/to per-problem (n_p, c) arrays.
+    """
+
+    def __init__(self, problems, ard=True, options: Options | None = None, stream=None):
+        torch = _torch()
+        self._keep = []
+        arr = (Problem * len(problems))()
+        self.ns = []
+        for k, (X, log_theta, noise, idx) in enumerate(problems):
+            X = X.contiguous()
+            if X.dtype != torch.float32 or not X.is_cuda:
+                raise ValueError("X must be a float32 CUDA tensor")
+            lt = np.ascontiguousarray(log_theta, dtype=np.float64)
+            ix = None if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
+            self._keep += [X, lt, ix]
+            arr[k].X = X.data_ptr()
+            arr[k].n = X.shape[0]
+            arr[k].d = X.shape[1]
+            arr[k].ard = 1 if ard else 0
+            arr[k].log_theta = lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[k].noise_var = float(noise)
+            arr[k].m = 0 if ix is None else ix.shape[0]
+            arr[k].idx = (ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if ix is not None
+                          else ctypes.POINTER(ctypes.c_int64)())
+            self.ns.append(int(X.shape[0]))
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        h = ctypes.c_void_p()
+        L = lib()
+        rc = L.kpcg_batch_create(len(problems), arr,
+                                 ctypes.byref(options) if options is not None else None,
+                                 ctypes.c_void_p(st.cuda_stream), ctypes.byref(h))
+        self._keep = None
+        if rc != 0:
+            raise KpcgError(rc, L.kpcg_batch_last_error(None).decode())
+        self._h = h
+        self.P = len(problems)
+        self.ld = int(L.kpcg_batch_max_n(h))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise KpcgError(rc, lib().kpcg_batch_last_error(self._h).decode())
+
+    def empty(self, c, dtype):
+        torch = _torch()
+        return torch.zeros((self.P * c, self.ld), dtype=dtype, device="cuda").t()
+
+    def block(self, vectors, dtype=None):
+        """Per-problem (n_p, c) arrays/tensors -> (ld, P*c) column-major block."""
+        torch = _torch()
+        c = vectors[0].shape[1] if vectors[0].ndim == 2 else 1
+        dtype = dtype or torch.float64
+        out = self.empty(c, dtype)
+        for p, v in enumerate(vectors):
+            t = torch.as_tensor(np.asarray(v) if not torch.is_tensor(v) else v).to(
+                device="cuda", dtype=dtype).reshape(self.ns[p], c)
+            out[: self.ns[p], p * c:(p + 1) * c] = t
+        return out
+
+    def unblock(self, Bk, c):
+        return [Bk[: self.ns[p], p * c:(p + 1) * c] for p in range(self.P)]
+
+    def _blk(self, T, c, dtype, name):
+        torch = _torch()
+        if T.dtype != dtype or T.stride(0) != 1 or T.shape[1] != self.P * c or T.shape[0] < self.ld:
+            raise ValueError(f"{name} must be a column-major ({self.ld}, {self.P * c}) {dtype} block")
+        return T.data_ptr(), T.stride(1)
+
+    def solve(self, B, c, tol=1e-8, raise_on_error=True):
+        """Returns (X block, iters (P, c), rel_res (P, c), Info, status)."""
+        torch = _torch()
+        pb, ld = self._blk(B, c, torch.float64, "B")
+        X = torch.zeros((self.P * c, ld), dtype=torch.float64, device="cuda").t()
+        it = (ctypes.c_int32 * (self.P * c))()
+        rel = (ctypes.c_double * (self.P * c))()
+        info = Info()
+        rc = lib().kpcg_batch_solve(self._h, pb, ld, c, float(tol), X.data_ptr(), it, rel,
+                                    ctypes.byref(info))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        return (X, np.array(list(it)).reshape(self.P, c), np.array(list(rel)).reshape(self.P, c),
+                info, rc)
+
+    def matvec_f32(self, V, c):
+        torch = _torch()
+        pv, ld = self._blk(V, c, torch.float32, "V")
+        O = torch.zeros((self.P * c, ld), dtype=torch.float32, device="cuda").t()
+        self._check(lib().kpcg_batch_matvec_f32(self._h, pv, ld, c, O.data_ptr()))
+        return O
+
+    def precond_apply_f32(self, R, c):
+        torch = _torch()
+        pr, ld = self._blk(R, c, torch.float32, "R")
+        Z = torch.zeros((self.P * c, ld), dtype=torch.float32, device="cuda").t()
+        self._check(lib().kpcg_batch_precond_apply_f32(self._h, pr, ld, c, Z.data_ptr()))
+        return Z
+
+    def tune(self, c):
+        g, n, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        self._check(lib().kpcg_batch_tune(self._h, c, ctypes.byref(g), ctypes.byref(n),
+                                          ctypes.byref(ms)))
+        return int(g.value), int(n.value), float(ms.value)
+
+    def set_tiling(self, tiles_per_item, ctas=0):
+        self._check(lib().kpcg_batch_set_tiling(self._h, int(tiles_per_item), int(ctas)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kpcg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

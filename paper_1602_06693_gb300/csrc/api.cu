@@ -12,6 +12,7 @@
 #include "kpcg_internal.cuh"
 #include "ctx.cuh"
 #include "precond.cuh"
+#include "solver.cuh"
 
 namespace kpcg {
 
@@ -155,6 +156,7 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
     CgScalars S{sc, sc + c, sc + 2 * c, sc + 3 * c, sc + 4 * c, sc + 5 * c, isc, isc + c,
                 isc + 2 * c};
     KPCG_CUDA(cudaMemsetAsync(S.flags, 0, 2 * sizeof(int), st));
+    ActiveScope active_scope(h, S.active);
 
     dot_cols<T>(B, ldb, B, ldb, n, c, partial, nblk, st);
     finalize(partial, nblk, c, FIN_NORM_B, S, tol, tol_mode, n, nullptr, st);
@@ -235,7 +237,7 @@ static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const doub
         }
 }
 
-static bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
+bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
     if (bb == 0.0) return true;
     return tol_mode == 1 ? rr < (double)n * tol : rr <= tol * tol * bb;
 }
@@ -263,7 +265,7 @@ static void build_precond(Ctx& h) {
 }
 
 // Rebuild the preconditioner if theta, the noise or the mode changed since.
-static double ensure_precond(Ctx& h) {
+double ensure_precond(Ctx& h) {
     h.P.n = h.n;
     if (h.pkind == KPCG_PREC_NONE) return 0.0;
     if (h.P.ready && h.P.noise == precond_noise(h)) return 0.0;
@@ -280,15 +282,13 @@ static double ensure_precond(Ctx& h) {
 // normalised residual.  The shift keeps the FP32 system positive definite
 // when the FP32 rounding of K is not small against sigma^2; the outer loop
 // removes the difference.  Columns are independent throughout.
-static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double tol,
-                             const double* X0, double* Xout, int64_t ldx,
-                             std::vector<int>& iters_col, int& iters_total, int& steps,
-                             std::vector<double>& rr, std::vector<double>& bb) {
+kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb, int c,
+                      double tol, const double* X0, double* Xout, int64_t ldx,
+                      std::vector<int>& iters_col, int& iters_total, int& steps,
+                      std::vector<double>& rr, std::vector<double>& bb) {
     cudaStream_t st = h.stream;
     const int64_t n = h.n, ld = h.ld;
     const int W = std::max(1, h.opt.fcg_window);
-    const bool tc = (h.opt.precision == KPCG_TC_IR);
-    const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
     double* R = h.R64.need((size_t)ld * c);
     double* Pw = h.fcgP.need((size_t)W * ld * c);
     double* APw = h.fcgAP.need((size_t)W * ld * c);
@@ -318,7 +318,7 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
         copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
     else
         fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
-    residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+    ops.residual(B, ldb, c, Xout, ldx, R, rr, bb);
     std::vector<double> pAp((size_t)W * c, 1.0), coef((size_t)c), d;
     std::vector<int> dead((size_t)c, 0);
     int nwin = 0, head = 0, stall = 0, recheck = 0;
@@ -339,7 +339,7 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
             // certify on the recomputed residual; continue from it if the
             // recursive one drifted
             if (recheck) break;
-            residual_f64(h, B, ldb, c, Xout, ldx, R, rr, bb);
+            ops.residual(B, ldb, c, Xout, ldx, R, rr, bb);
             recheck = 1;
             nwin = 0;
             --outer;
@@ -367,18 +367,10 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
         const int ran = pcg_core<float>(
             h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, std::max(1, budget),
             [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
-                h.prof.time(Profiler::KV_INNER, st, [&] {
-                    if (tc)
-                        kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
-                    else
-                        kv_f32(h.xs32.p, n, h.dp, h.c0_32(), inner_noise, V, ldv, cc, O, ldo,
-                               h.kvws, st);
-                });
+                h.prof.time(Profiler::KV_INNER, st, [&] { ops.inner_mv(V, ldv, cc, O, ldo); });
             },
             [&](const float* Rr, int64_t ldr, int cc, float* Zz, int64_t ldz) {
-                h.prof.time(Profiler::PRECOND, st, [&] {
-                    precond_apply_f32(h.P, Rr, ldr, cc, Zz, ldz, st);
-                });
+                h.prof.time(Profiler::PRECOND, st, [&] { ops.inner_pc(Rr, ldr, cc, Zz, ldz); });
             },
             h.c32, its, br);
         iters_total += ran;
@@ -409,9 +401,7 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
         } else {
             copy_cols<double>(p, ld, Z, ld, n, c, st);
         }
-        h.prof.time(Profiler::KV_OUTER, st, [&] {
-            kv_f64_sym(h, p, ld, c, nullptr, 0, q, ld, h.noise);
-        });
+        h.prof.time(Profiler::KV_OUTER, st, [&] { ops.outer_mv(p, ld, c, q, ld); });
         dots(2, {{p, q}, {p, R}}, d);
         std::vector<double> al((size_t)c, 0.0), nal((size_t)c);
         for (int k = 0; k < c; ++k) {
@@ -435,9 +425,37 @@ static kpcg_status fcg_solve(Ctx& h, const double* B, int64_t ldb, int c, double
     }
     for (int k = 0; k < c; ++k)
         if (dead[k] && status == KPCG_OK) status = KPCG_ERR_BREAKDOWN;
-    if (tc && kv_tc_error(h))
+    if (ops.timed_out && ops.timed_out())
         fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
     return status;
+}
+
+// The operators of the single-problem mixed-precision solve.
+static MixedOps single_ops(Ctx& h) {
+    MixedOps o;
+    const bool tc = (h.opt.precision == KPCG_TC_IR);
+    const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
+    Ctx* hp = &h;
+    o.inner_mv = [hp, tc, inner_noise](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+        Ctx& h = *hp;
+        if (tc)
+            kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
+        else
+            kv_f32(h.xs32.p, h.n, h.dp, h.c0_32(), inner_noise, V, ldv, cc, O, ldo, h.kvws,
+                   h.stream);
+    };
+    o.inner_pc = [hp](const float* R, int64_t ldr, int cc, float* Z, int64_t ldz) {
+        precond_apply_f32(hp->P, R, ldr, cc, Z, ldz, hp->stream);
+    };
+    o.outer_mv = [hp](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
+        kv_f64_sym(*hp, V, ldv, cc, nullptr, 0, O, ldo, hp->noise);
+    };
+    o.residual = [hp](const double* B, int64_t ldb, int cc, const double* X, int64_t ldx,
+                      double* R, std::vector<double>& rr, std::vector<double>& bb) {
+        residual_f64(*hp, B, ldb, cc, X, ldx, R, rr, bb);
+    };
+    if (tc) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
+    return o;
 }
 
 static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
@@ -562,7 +580,8 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
         }
         if (!f64) convert_scale_cols<double, float>(Xout, ldx, x32, ld, n, c, nullptr, 0, st);
     } else {
-        status = fcg_solve(h, B, ldb, c, tol, X0, Xout, ldx, iters_col, iters_total, steps, rr, bb);
+        status = fcg_solve(h, single_ops(h), B, ldb, c, tol, X0, Xout, ldx, iters_col, iters_total,
+                           steps, rr, bb);
         rr_current = (status == KPCG_OK);  // converged exits certify on a recomputed residual
     }
     // FP64 residual of what is returned (the single-precision FP32 solver
@@ -614,7 +633,6 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
 using kpcg::Ctx;
 using kpcg::fail;
 
-struct kpcg_ctx : kpcg::Ctx {};
 
 #define KPCG_GUARD(hptr, ...)                                               \
     try {                                                                   \

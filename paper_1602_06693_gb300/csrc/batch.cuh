@@ -1,0 +1,85 @@
+// Many independent kernel systems of uneven size solved together
+// (kv_tc.cu: batched tensor-core K.V; precond.cu: batched Nystrom apply;
+// batch.cu: the solver and the C ABI).
+//
+// Layout.  Problem p with n_p rows and c right-hand sides owns columns
+// p*c .. p*c+c-1 of every batch vector, an ld x (P c) column-major block with
+// ld >= max_p n_p; rows n_p .. ld-1 of its columns are zero and stay zero.
+// Every (problem, column) pair is therefore an ordinary column to the CG
+// kernels, with its own alpha, beta and stop test (Algorithm 1 per column).
+#pragma once
+
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace kpcg {
+
+// ---------------------------------------------------------------- K.V
+struct TcBatchProb {
+    const uint16_t* A;  // augmented BF16 operands (tc_prepare), pre-swizzled
+    const uint16_t* B;
+    int64_t voff;       // first row of the problem in the staged V / partial rows
+    int32_t n, n_pad, kch, rt_base;
+    float noise;        // diagonal added by the product
+    int32_t pad_;
+};
+// Tiles [jt0, jt0 + nt) of row tile rt of problem prob.
+struct TcBatchItem {
+    int32_t prob, rt, jt0, nt;
+};
+
+struct TcBatch {
+    int P = 0, G = 0, grid = 0, nitems = 0;
+    int64_t nv = 0;  // sum of the padded sizes
+    std::vector<TcBatchProb> hprobs;
+    DevBuf<TcBatchProb> probs;
+    DevBuf<TcBatchItem> items;
+    DevBuf<int32_t> rt_first, rt_count;  // per (problem, row tile): its items
+    DevBuf<float> Vs, part;
+    DevBuf<int> err;
+};
+
+// Operands of the tensor-core product for the handle's current theta.
+void tc_prepare(Ctx& h);
+int sm_count_tc();
+// Work list: every row tile of every problem, its column tiles cut into
+// items of at most G tiles; grid = CTAs of the persistent launch (0: one per SM).
+void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<float>& noise,
+                   int G, int grid, cudaStream_t st);
+// O = (K_p + noise_p I) V for every problem (columns p*c ..), rows n_p .. nrows-1
+// of O set to zero.  active (nullable, P*c flags): problems with no active
+// column are skipped and their columns of O set to zero.
+void kv_tc_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                 int64_t nrows, const int* active, cudaStream_t st);
+// Nonzero if a bounded wait of the batched kernel expired (flag cleared).
+int kv_tc_batch_error(TcBatch& b, cudaStream_t st);
+
+// ------------------------------------------------------ Nystrom apply
+struct NysBatchProb {
+    const float2* KXU;  // n x m, FP64 entries as FP32 pairs
+    const double* U;    // L^{-T}, m x m row-major
+    int64_t n, m;
+    int64_t wbase;      // offset of the problem in w / y (c * m doubles)
+    int64_t pbase;      // offset of the problem in the split partials
+    int32_t nsplit, rows_per_split;
+    double inv_noise;
+};
+struct NysBatch {
+    int P = 0, c = 0;
+    int64_t mmax = 0, wtotal = 0, ptotal = 0;
+    int nsplit_max = 0;
+    std::vector<NysBatchProb> hprobs;
+    DevBuf<NysBatchProb> probs;
+    DevBuf<double> part, w, y;
+};
+// Tables for c columns per problem from the problems' Nystrom states
+// (problems without one get m = 0 and the identity).
+void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
+                    cudaStream_t st);
+// Z = P_p^{-1} R for every problem (FP32 vectors, FP64 inside), rows n_p ..
+// nrows-1 zero; problems with no active column are skipped (Z = 0).
+void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_t ldz,
+                     int64_t nrows, const int* active, cudaStream_t st);
+
+}  // namespace kpcg

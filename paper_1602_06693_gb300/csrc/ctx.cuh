@@ -99,6 +99,7 @@ struct Ctx {
     DevBuf<double> scal;
     DevBuf<int> iscal;
     int* hflags = nullptr;  // pinned host [active, broken]
+    const int* cg_active = nullptr;  // device flags of the columns the running CG iterates
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;
@@ -137,3 +138,6 @@ void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, in
 int kv_tc_error(Ctx& h);
 
 }  // namespace kpcg
+
+// The opaque handle of the C ABI.
+struct kpcg_ctx : kpcg::Ctx {};

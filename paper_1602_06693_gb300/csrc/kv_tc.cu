@@ -35,6 +35,7 @@
 
 #include <algorithm>
 
+#include "batch.cuh"
 #include "ctx.cuh"
 
 namespace kpcg {
@@ -446,16 +447,6 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int64_t n_pad, 
     O[i + (int64_t)k * ldo] = s;
 }
 
-int sm_count_tc() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-        if (cached <= 0) cached = 148;
-    }
-    return cached;
-}
 
 template <int KCH, int CB>
 void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* Vs,
@@ -476,15 +467,25 @@ void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, con
 
 }  // namespace
 
+int sm_count_tc() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+        if (cached <= 0) cached = 148;
+    }
+    return cached;
+}
+
 bool kv_tc_supported(int dp) { return dp <= 16; }
 
-void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise) {
+void tc_prepare(Ctx& h) {
     cudaStream_t st = h.stream;
     const int64_t n = h.n;
     const int64_t n_pad = ((n + TM - 1) / TM) * TM;
     const int kch = (6 * h.d + 6 <= KC) ? 1 : 2;
     if (6 * h.d + 6 > 2 * KC) fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
-    // operands for the current theta
     if (h.tc_version != h.theta_version || h.tc_kch != kch) {
         h.tcA.need((size_t)n_pad * kch * KC);
         h.tcB.need((size_t)n_pad * kch * KC);
@@ -497,6 +498,14 @@ void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t l
         int* e = h.tc_err.need(1);
         KPCG_CUDA(cudaMemsetAsync(e, 0, sizeof(int), st));
     }
+}
+
+void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int64_t n_pad = ((n + TM - 1) / TM) * TM;
+    tc_prepare(h);
+    const int kch = h.tc_kch;
     const int n_ct = (int)(n_pad / TN);
     const int n_rt = (int)(n_pad / TM);
     // splits of the column range: about four waves of two CTAs per SM
@@ -534,6 +543,402 @@ void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t l
         KPCG_LAUNCHED("tc_reduce_kernel");
         k0 += ncols;
     }
+}
+
+// ------------------------------------------------------------------------
+// Batched product over many problems of uneven size: one persistent launch
+// walks a flat work list of (problem, row tile, run of column tiles) items.
+// The three roles walk the same items in the same order, so the ring and
+// accumulator phases simply continue from one item to the next; the A tile of
+// an item is reloaded once the MMAs of the previous item have finished with
+// it (aempty).  The K-dim (64 or 128) is per problem.  Each epilogue thread
+// writes the partial of its row and column half per item; a second kernel
+// adds the items of a row tile in a fixed order.
+namespace {
+
+constexpr int kMaxKch = 2;
+
+template <int CB>
+struct TcBSmem {
+    static constexpr uint32_t kSub = SUB * 2;
+    static constexpr uint32_t kA = kMaxKch * kSub;
+    static constexpr uint32_t kBst = kMaxKch * kSub;
+    static constexpr uint32_t kVst = CB * TN * 4;
+    static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
+    static constexpr uint32_t kBars = 1024;
+    static constexpr uint32_t kTotal = 1024 + kA + NSTAGE * kStage + kBars;
+};
+
+__device__ __forceinline__ bool prob_live(const int* __restrict__ active, int p, int cpp) {
+    if (!active) return true;
+    for (int k = 0; k < cpp; ++k)
+        if (active[p * cpp + k]) return true;
+    return false;
+}
+
+template <int CB>
+__global__ void __launch_bounds__(NWARPS * 32, 1)
+    kv_tc_batch_kernel(const TcBatchProb* __restrict__ probs,
+                       const TcBatchItem* __restrict__ items, int nitems,
+                       const float* __restrict__ Vs, int64_t nv, int ncols,
+                       const int* __restrict__ active, int cpp, float* __restrict__ part,
+                       int* __restrict__ err) {
+    using S = TcBSmem<CB>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sStage = smem + S::kA;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kA + NSTAGE * S::kStage);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NSTAGE;
+    uint64_t* tfull = bars + 2 * NSTAGE;
+    uint64_t* tempty = bars + 2 * NSTAGE + 2;
+    uint64_t* afull = bars + 2 * NSTAGE + 4;
+    uint64_t* aempty = bars + 2 * NSTAGE + 5;
+    uint64_t* done = bars + 2 * NSTAGE + 6;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 7);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1 + NEPI);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], NEPI);
+        }
+        mbar_init(afull, 1);
+        mbar_init(aempty, 1);
+        mbar_init(done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                su32(tmem_slot)),
+            "r"(2 * TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint64_t deadline = gtimer() + kWaitNs;
+    int fail = 0;
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t t = 0, u = 0;
+            for (int it = blockIdx.x; it < nitems && !fail; it += gridDim.x) {
+                const TcBatchItem w = items[it];
+                if (!prob_live(active, w.prob, cpp)) continue;
+                const TcBatchProb pb = probs[w.prob];
+                const uint32_t abytes = (uint32_t)pb.kch * S::kSub;
+                if (!mbar_wait(aempty, (u & 1u) ^ 1u, deadline)) {
+                    fail = 1;
+                    break;
+                }
+                mbar_expect_tx(afull, abytes);
+                bulk_g2s(sA, pb.A + (size_t)w.rt * pb.kch * SUB, abytes, afull);
+                ++u;
+                for (int j = 0; j < w.nt; ++j) {
+                    const int s = (int)(t % NSTAGE);
+                    if (!mbar_wait(&empty[s], ((t / NSTAGE) & 1u) ^ 1u, deadline)) {
+                        fail = 1;
+                        break;
+                    }
+                    const int64_t jt = (int64_t)w.jt0 + j;
+                    uint8_t* st = sStage + (size_t)s * S::kStage;
+                    mbar_expect_tx(&full[s], abytes + (uint32_t)ncols * TN * 4);
+                    bulk_g2s(st, pb.B + (size_t)jt * pb.kch * SUB, abytes, &full[s]);
+                    for (int k = 0; k < ncols; ++k)
+                        bulk_g2s(st + S::kBst + (size_t)k * TN * 4,
+                                 Vs + (size_t)k * nv + pb.voff + jt * TN, TN * 4, &full[s]);
+                    ++t;
+                }
+            }
+            // let the copies this thread issued land before the CTA exits
+            const uint64_t dl2 = gtimer() + 200000000ull;
+            for (uint32_t q = (t > (uint32_t)NSTAGE ? t - NSTAGE : 0u); q < t; ++q)
+                (void)mbar_wait(&full[q % NSTAGE], (q / NSTAGE) & 1u, dl2);
+            if (u > 0) (void)mbar_wait(afull, (u - 1) & 1u, dl2);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t t = 0, u = 0;
+            const uint32_t a0 = su32(sA);
+            for (int it = blockIdx.x; it < nitems && !fail; it += gridDim.x) {
+                const TcBatchItem w = items[it];
+                if (!prob_live(active, w.prob, cpp)) continue;
+                const int kch = probs[w.prob].kch;
+                if (!mbar_wait(afull, u & 1u, deadline)) {
+                    fail = 1;
+                    break;
+                }
+                ++u;
+                fence_after();
+                for (int j = 0; j < w.nt; ++j) {
+                    const int s = (int)(t % NSTAGE), b = (int)(t & 1u);
+                    if (!mbar_wait(&full[s], (t / NSTAGE) & 1u, deadline) ||
+                        !mbar_wait(&tempty[b], ((t >> 1) & 1u) ^ 1u, deadline)) {
+                        fail = 1;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t b0 = su32(sStage + (size_t)s * S::kStage);
+                    const uint32_t dt = tmem + (uint32_t)(b * TN);
+                    for (int kc = 0; kc < kch; ++kc)
+#pragma unroll
+                        for (int kk = 0; kk < KC / 16; ++kk) {
+                            const uint32_t off = (uint32_t)kc * S::kSub + (uint32_t)kk * 32;
+                            mma_bf16(dt, sdesc(a0 + off), sdesc(b0 + off), (kc | kk) ? 1u : 0u);
+                        }
+                    mma_commit(&tfull[b]);
+                    mma_commit(&empty[s]);
+                    ++t;
+                }
+                if (fail) break;
+                mma_commit(aempty);  // the A tile is free once these MMAs finished
+            }
+            mma_commit(done);
+            if (!mbar_wait(done, 0, gtimer() + kWaitNs)) fail = 1;
+        }
+    } else {
+        uint32_t t = 0;
+        for (int it = blockIdx.x; it < nitems && !fail; it += gridDim.x) {
+            const TcBatchItem w = items[it];
+            if (!prob_live(active, w.prob, cpp)) continue;
+            float acc[CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) acc[k] = 0.f;
+            for (int j = 0; j < w.nt; ++j) {
+                const int s = (int)(t % NSTAGE), b = (int)(t & 1u);
+                const bool ok = __all_sync(
+                    0xffffffffu, mbar_wait(&tfull[b], (t >> 1) & 1u, deadline));
+                if (!ok) {
+                    fail = 1;
+                    break;
+                }
+                fence_after();
+                const float* vst =
+                    reinterpret_cast<const float*>(sStage + (size_t)s * S::kStage + S::kBst);
+#pragma unroll 1
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int col0 = half * 64 + ch * 16;
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + col0),
+                              r);
+                    float ev[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) ev[q] = ex2(__uint_as_float(r[q]));
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        if (k < ncols) {
+                            const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
+                            float a = acc[k];
+#pragma unroll
+                            for (int j4 = 0; j4 < 4; ++j4) {
+                                const float4 v = vp[j4];
+                                a = fmaf(ev[4 * j4 + 0], v.x, a);
+                                a = fmaf(ev[4 * j4 + 1], v.y, a);
+                                a = fmaf(ev[4 * j4 + 2], v.z, a);
+                                a = fmaf(ev[4 * j4 + 3], v.w, a);
+                            }
+                            acc[k] = a;
+                        }
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&tempty[b]);
+                    mbar_arrive(&empty[s]);
+                }
+                ++t;
+            }
+            if (fail) break;
+            const int64_t base = ((int64_t)it * 2 + half) * CB;
+#pragma unroll
+            for (int k = 0; k < CB; ++k)
+                if (k < ncols) part[(base + k) * TM + row] = acc[k];
+        }
+    }
+    if (fail) atomicExch(&s_fail, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * TN));
+    }
+}
+
+// Vs[k][voff_p + i] = V[i][p*cpp + k0 + k] (zero past n_p).
+__global__ void tc_batch_stage_v_kernel(const TcBatchProb* __restrict__ probs,
+                                        const float* __restrict__ V, int64_t ldv, int cpp, int k0,
+                                        int ncols, int64_t nv, float* __restrict__ Vs) {
+    const int p = blockIdx.y;
+    const TcBatchProb pb = probs[p];
+    for (int k = 0; k < ncols; ++k) {
+        const float* v = V + ((int64_t)p * cpp + k0 + k) * ldv;
+        float* o = Vs + (int64_t)k * nv + pb.voff;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pb.n_pad;
+             i += (int64_t)gridDim.x * blockDim.x)
+            o[i] = (i < pb.n) ? v[i] : 0.f;
+    }
+}
+
+// O[i][p*cpp + k0 + k] = noise_p V + sum over the items of row tile i/128 in
+// order (both column halves); zero past n_p and for skipped problems.
+__global__ void tc_batch_reduce_kernel(const TcBatchProb* __restrict__ probs,
+                                       const int32_t* __restrict__ rt_first,
+                                       const int32_t* __restrict__ rt_count,
+                                       const float* __restrict__ part, int cb, int ncols, int cpp,
+                                       int k0, const float* __restrict__ V, int64_t ldv,
+                                       float* __restrict__ O, int64_t ldo, int64_t nrows,
+                                       const int* __restrict__ active) {
+    const int p = blockIdx.y / ncols, k = blockIdx.y % ncols;
+    const TcBatchProb pb = probs[p];
+    const bool live = prob_live(active, p, cpp);
+    const int64_t col = (int64_t)p * cpp + k0 + k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (live && i < pb.n) {
+            const int rt = (int)(i / TM), r = (int)(i % TM);
+            const int f = rt_first[pb.rt_base + rt], cnt = rt_count[pb.rt_base + rt];
+            float s = pb.noise * V[col * ldv + i];
+            for (int q = 0; q < cnt; ++q) {
+                const int64_t base = (int64_t)(f + q) * 2 * cb;
+                s += part[(base + k) * TM + r] + part[(base + cb + k) * TM + r];
+            }
+            v = s;
+        }
+        O[col * ldo + i] = v;
+    }
+}
+
+template <int CB>
+void launch_tc_batch(TcBatch& b, int ncols, const int* active, int cpp, cudaStream_t st) {
+    using S = TcBSmem<CB>;
+    static bool attr = false;
+    if (!attr) {
+        KPCG_CUDA(cudaFuncSetAttribute(kv_tc_batch_kernel<CB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal));
+        attr = true;
+    }
+    const int grid = std::max(1, std::min(b.grid, b.nitems));
+    kv_tc_batch_kernel<CB><<<grid, NWARPS * 32, S::kTotal, st>>>(
+        b.probs.p, b.items.p, b.nitems, b.Vs.p, b.nv, ncols, active, cpp, b.part.p, b.err.p);
+    KPCG_LAUNCHED("kv_tc_batch_kernel");
+}
+
+}  // namespace
+
+void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<float>& noise,
+                   int G, int grid, cudaStream_t st) {
+    if (G < 1) fail(KPCG_ERR_ARG, "tiles per item must be >= 1");
+    b.P = (int)subs.size();
+    b.G = G;
+    b.grid = grid > 0 ? grid : sm_count_tc();
+    b.hprobs.assign((size_t)b.P, TcBatchProb{});
+    std::vector<TcBatchItem> items;
+    std::vector<int32_t> first, count;
+    int64_t voff = 0;
+    int32_t rt_base = 0;
+    for (int p = 0; p < b.P; ++p) {
+        Ctx& h = *subs[(size_t)p];
+        tc_prepare(h);
+        const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
+        const int n_t = (int)(n_pad / TM);
+        TcBatchProb& pb = b.hprobs[(size_t)p];
+        pb.A = h.tcA.p;
+        pb.B = h.tcB.p;
+        pb.voff = voff;
+        pb.n = (int32_t)h.n;
+        pb.n_pad = (int32_t)n_pad;
+        pb.kch = h.tc_kch;
+        pb.rt_base = rt_base;
+        pb.noise = noise[(size_t)p];
+        for (int rt = 0; rt < n_t; ++rt) {
+            first.push_back((int32_t)items.size());
+            int cnt = 0;
+            for (int jt0 = 0; jt0 < n_t; jt0 += G, ++cnt)
+                items.push_back(TcBatchItem{p, rt, jt0, std::min(G, n_t - jt0)});
+            count.push_back(cnt);
+        }
+        voff += n_pad;
+        rt_base += n_t;
+    }
+    b.nv = voff;
+    b.nitems = (int)items.size();
+    b.probs.need(b.hprobs.size());
+    b.items.need(items.size());
+    b.rt_first.need(first.size());
+    b.rt_count.need(count.size());
+    KPCG_CUDA(cudaMemcpyAsync(b.probs.p, b.hprobs.data(), sizeof(TcBatchProb) * b.hprobs.size(),
+                              cudaMemcpyHostToDevice, st));
+    KPCG_CUDA(cudaMemcpyAsync(b.items.p, items.data(), sizeof(TcBatchItem) * items.size(),
+                              cudaMemcpyHostToDevice, st));
+    KPCG_CUDA(cudaMemcpyAsync(b.rt_first.p, first.data(), sizeof(int32_t) * first.size(),
+                              cudaMemcpyHostToDevice, st));
+    KPCG_CUDA(cudaMemcpyAsync(b.rt_count.p, count.data(), sizeof(int32_t) * count.size(),
+                              cudaMemcpyHostToDevice, st));
+    b.Vs.need((size_t)b.nv * 16);
+    b.part.need((size_t)b.nitems * 2 * 16 * TM);
+    if (!b.err.p) {
+        b.err.need(1);
+        KPCG_CUDA(cudaMemsetAsync(b.err.p, 0, sizeof(int), st));
+    }
+    // the host vectors above are released at return: finish the copies first
+    KPCG_CUDA(cudaStreamSynchronize(st));
+}
+
+void kv_tc_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                 int64_t nrows, const int* active, cudaStream_t st) {
+    if (b.P == 0) return;
+    int64_t nmax_pad = 0;
+    for (const auto& pb : b.hprobs) nmax_pad = std::max<int64_t>(nmax_pad, pb.n_pad);
+    for (int k0 = 0; k0 < c;) {
+        const int rem = c - k0;
+        const int cb = rem > 8 ? 16 : rem > 4 ? 8 : rem > 2 ? 4 : rem > 1 ? 2 : 1;
+        const int ncols = std::min(cb, rem);
+        tc_batch_stage_v_kernel<<<dim3((unsigned)std::min<int64_t>((nmax_pad + 255) / 256, 64),
+                                       (unsigned)b.P),
+                                  256, 0, st>>>(b.probs.p, V, ldv, c, k0, ncols, b.nv, b.Vs.p);
+        KPCG_LAUNCHED("tc_batch_stage_v_kernel");
+        switch (cb) {
+            case 1: launch_tc_batch<1>(b, ncols, active, c, st); break;
+            case 2: launch_tc_batch<2>(b, ncols, active, c, st); break;
+            case 4: launch_tc_batch<4>(b, ncols, active, c, st); break;
+            case 8: launch_tc_batch<8>(b, ncols, active, c, st); break;
+            default: launch_tc_batch<16>(b, ncols, active, c, st); break;
+        }
+        tc_batch_reduce_kernel<<<dim3((unsigned)std::min<int64_t>((nrows + 255) / 256, 64),
+                                      (unsigned)(b.P * ncols)),
+                                 256, 0, st>>>(b.probs.p, b.rt_first.p, b.rt_count.p, b.part.p, cb,
+                                               ncols, c, k0, V, ldv, O, ldo, nrows, active);
+        KPCG_LAUNCHED("tc_batch_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
+int kv_tc_batch_error(TcBatch& b, cudaStream_t st) {
+    if (!b.err.p) return 0;
+    int e = 0;
+    KPCG_CUDA(cudaMemcpyAsync(&e, b.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    if (e) KPCG_CUDA(cudaMemsetAsync(b.err.p, 0, sizeof(int), st));
+    return e;
 }
 
 int kv_tc_error(Ctx& h) {

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "kpcg_internal.cuh"
+#include "batch.cuh"
 #include "precond.cuh"
 
 namespace kpcg {
@@ -714,6 +715,237 @@ void precond_apply_f64(const PrecondState& P, const double* R, int64_t ldr, int 
 void precond_apply_f32(const PrecondState& P, const float* R, int64_t ldr, int c, float* Z,
                        int64_t ldz, cudaStream_t st) {
     apply_any<float>(P, R, ldr, c, Z, ldz, st);
+}
+
+
+// ------------------------------------------------------------------------
+// Batched Nystrom apply over many problems (batch layout: problem p owns
+// columns p*c .. p*c+c-1).  Same arithmetic as the single-problem apply:
+// w = K_UX r with Dot2 on FP32 pairs, y = L^{-1} w, u = L^{-T} y (FP64),
+// z = (r - K_XU u) / sigma^2 with FP64 accumulation.  Grids carry the problem
+// index; blocks past a problem's sizes, and problems with no active column,
+// return at once.
+namespace {
+
+constexpr int kSplitRows = 512;
+
+__device__ __forceinline__ bool nb_live(const int* __restrict__ active, int p, int c) {
+    if (!active) return true;
+    for (int k = 0; k < c; ++k)
+        if (active[p * c + k]) return true;
+    return false;
+}
+
+// part[pbase + (split * c + k) * m + a] for columns k0 .. k0+ncols-1
+__global__ void __launch_bounds__(256)
+    nys_batch_proj_kernel(const NysBatchProb* __restrict__ probs, int c, const float* __restrict__ R,
+                          int64_t ldr, int k0, int ncols, const int* __restrict__ active,
+                          double* __restrict__ part) {
+    __shared__ float2 sr[128][PC];
+    const int p = blockIdx.z;
+    const NysBatchProb pb = probs[p];
+    if (pb.m == 0 || (int)blockIdx.y >= pb.nsplit || (int64_t)blockIdx.x * 256 >= pb.m ||
+        !nb_live(active, p, c))
+        return;
+    const int64_t m = pb.m;
+    const int64_t a = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * pb.rows_per_split;
+    const int64_t r1 = min(pb.n, r0 + pb.rows_per_split);
+    const float* Rp = R + ((int64_t)p * c + k0) * ldr;
+    Acc2 acc[PC];
+#pragma unroll
+    for (int k = 0; k < PC; ++k) acc[k] = {0.f, 0.f};
+    for (int64_t rs = r0; rs < r1; rs += 128) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 128 * PC; e += 256) {
+            const int k = e / 128, r = e % 128;
+            const float v = (rs + r < r1 && k < ncols) ? Rp[rs + r + (int64_t)k * ldr] : 0.f;
+            sr[r][k] = make_float2(v, 0.f);
+        }
+        __syncthreads();
+        const int rn = (int)min((int64_t)128, r1 - rs);
+        if (a < m) {
+            const float2* Kp = pb.KXU + rs * m + a;
+#pragma unroll 4
+            for (int r = 0; r < rn; ++r) {
+                const float2 kv = __ldg(Kp + (int64_t)r * m);
+#pragma unroll
+                for (int k = 0; k < PC; ++k) {
+                    dot2_add(acc[k], kv.x, sr[r][k].x);
+                    acc[k].c = fmaf(kv.y, sr[r][k].x, acc[k].c);
+                }
+            }
+        }
+    }
+    if (a < m)
+        for (int k = 0; k < ncols; ++k)
+            part[pb.pbase + ((int64_t)blockIdx.y * c + k0 + k) * m + a] =
+                (double)acc[k].s + (double)acc[k].c;
+}
+
+__global__ void nys_batch_sum_kernel(const NysBatchProb* __restrict__ probs, int c,
+                                     const int* __restrict__ active,
+                                     const double* __restrict__ part, double* __restrict__ w) {
+    const int p = blockIdx.y;
+    const NysBatchProb pb = probs[p];
+    const int64_t len = (int64_t)c * pb.m;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len || !nb_live(active, p, c)) return;
+    double s = 0.0;
+    for (int sp = 0; sp < pb.nsplit; ++sp) s += part[pb.pbase + (int64_t)sp * len + e];
+    w[pb.wbase + e] = s;
+}
+
+// y = L^{-1} w per problem and column (same scheme as tri_lower_apply_kernel)
+__global__ void __launch_bounds__(1024)
+    nys_batch_lower_kernel(const NysBatchProb* __restrict__ probs, int c,
+                           const int* __restrict__ active, const double* __restrict__ w,
+                           double* __restrict__ y) {
+    __shared__ double part[32][33];
+    const int p = blockIdx.z, k = blockIdx.y;
+    const NysBatchProb pb = probs[p];
+    const int64_t m = pb.m;
+    if ((int64_t)blockIdx.x * 32 >= m || !nb_live(active, p, c)) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    const double* wk = w + pb.wbase + (int64_t)k * m;
+    double s = 0.0;
+    if (i < m)
+        for (int64_t j = g; j <= i; j += 32) s = fma(pb.U[j * m + i], wk[j], s);
+    part[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && i < m) {
+        double t = 0.0;
+        for (int q = 0; q < 32; ++q) t += part[q][lane];
+        y[pb.wbase + (int64_t)k * m + i] = t;
+    }
+}
+
+// u = L^{-T} y (warp per entry), written over w
+__global__ void nys_batch_upper_kernel(const NysBatchProb* __restrict__ probs, int c,
+                                       const int* __restrict__ active,
+                                       const double* __restrict__ y, double* __restrict__ u) {
+    const int p = blockIdx.z, k = blockIdx.y;
+    const NysBatchProb pb = probs[p];
+    const int64_t m = pb.m;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= m || !nb_live(active, p, c)) return;
+    const double* yk = y + pb.wbase + (int64_t)k * m;
+    const double* Uj = pb.U + j * m;
+    double s = 0.0;
+    for (int64_t i = j + lane; i < m; i += 32) s = fma(Uj[i], yk[i], s);
+    s = warp_sum(s);
+    if (lane == 0) u[pb.wbase + (int64_t)k * m + j] = s;
+}
+
+// z = (r - K_XU u) / sigma^2 (warp per row), zero past n_p and for skipped
+// problems; m = 0 means no preconditioner (z = r).
+__global__ void __launch_bounds__(256)
+    nys_batch_back_kernel(const NysBatchProb* __restrict__ probs, int c,
+                          const int* __restrict__ active, const double* __restrict__ u,
+                          const float* __restrict__ R, int64_t ldr, float* __restrict__ Z,
+                          int64_t ldz, int64_t nrows) {
+    const int p = blockIdx.y;
+    const NysBatchProb pb = probs[p];
+    const bool live = nb_live(active, p, c);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float* Rp = R + (int64_t)p * c * ldr;
+    float* Zp = Z + (int64_t)p * c * ldz;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nrows;
+         i += warps) {
+        if (!live || i >= pb.n) {
+            if (lane < c)
+                for (int k = lane; k < c; k += 32) Zp[i + (int64_t)k * ldz] = 0.f;
+            continue;
+        }
+        if (pb.m == 0) {
+            for (int k = lane; k < c; k += 32) Zp[i + (int64_t)k * ldz] = Rp[i + (int64_t)k * ldr];
+            continue;
+        }
+        const float2* Ki = pb.KXU + i * pb.m;
+        for (int k = 0; k < c; ++k) {
+            const double* uk = u + pb.wbase + (int64_t)k * pb.m;
+            double acc = 0.0;
+            for (int64_t a = lane; a < pb.m; a += 32) {
+                const float2 kv = __ldg(Ki + a);
+                acc = fma((double)kv.x + (double)kv.y, __ldg(uk + a), acc);
+            }
+            const double sm = warp_sum(acc);
+            if (lane == 0)
+                Zp[i + (int64_t)k * ldz] =
+                    (float)(((double)Rp[i + (int64_t)k * ldr] - sm) * pb.inv_noise);
+        }
+    }
+}
+
+}  // namespace
+
+void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
+                    cudaStream_t st) {
+    nb.P = (int)Ps.size();
+    nb.c = c;
+    nb.hprobs.assign((size_t)nb.P, NysBatchProb{});
+    nb.mmax = 0;
+    nb.wtotal = 0;
+    nb.ptotal = 0;
+    nb.nsplit_max = 1;
+    for (int p = 0; p < nb.P; ++p) {
+        const PrecondState& P = *Ps[(size_t)p];
+        NysBatchProb& q = nb.hprobs[(size_t)p];
+        q.n = P.n;
+        const bool on = P.ready && P.kind == KPCG_PREC_NYSTROM;
+        q.m = on ? P.m : 0;
+        q.KXU = on ? P.KXU.p : nullptr;
+        q.U = on ? P.U.p : nullptr;
+        q.inv_noise = on ? 1.0 / P.noise : 1.0;
+        q.rows_per_split = kSplitRows;
+        q.nsplit = (int32_t)std::max<int64_t>(1, (P.n + kSplitRows - 1) / kSplitRows);
+        q.wbase = nb.wtotal;
+        q.pbase = nb.ptotal;
+        nb.wtotal += (int64_t)c * q.m;
+        nb.ptotal += (int64_t)q.nsplit * c * q.m;
+        nb.mmax = std::max(nb.mmax, q.m);
+        nb.nsplit_max = std::max(nb.nsplit_max, (int)q.nsplit);
+    }
+    nb.probs.need(nb.hprobs.size());
+    nb.part.need((size_t)std::max<int64_t>(1, nb.ptotal));
+    nb.w.need((size_t)std::max<int64_t>(1, nb.wtotal));
+    nb.y.need((size_t)std::max<int64_t>(1, nb.wtotal));
+    KPCG_CUDA(cudaMemcpyAsync(nb.probs.p, nb.hprobs.data(), sizeof(NysBatchProb) * nb.hprobs.size(),
+                              cudaMemcpyHostToDevice, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+}
+
+void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_t ldz,
+                     int64_t nrows, const int* active, cudaStream_t st) {
+    if (nb.P == 0) return;
+    const int c = nb.c;
+    if (nb.mmax > 0) {
+        const unsigned ablk = (unsigned)((nb.mmax + 255) / 256);
+        for (int k0 = 0; k0 < c; k0 += PC) {
+            const int nc = std::min(PC, c - k0);
+            nys_batch_proj_kernel<<<dim3(ablk, (unsigned)nb.nsplit_max, (unsigned)nb.P), 256, 0,
+                                    st>>>(nb.probs.p, c, R, ldr, k0, nc, active, nb.part.p);
+            KPCG_LAUNCHED("nys_batch_proj_kernel");
+        }
+        nys_batch_sum_kernel<<<dim3((unsigned)((c * nb.mmax + 255) / 256), (unsigned)nb.P), 256, 0,
+                               st>>>(nb.probs.p, c, active, nb.part.p, nb.w.p);
+        KPCG_LAUNCHED("nys_batch_sum_kernel");
+        nys_batch_lower_kernel<<<dim3((unsigned)((nb.mmax + 31) / 32), (unsigned)c,
+                                      (unsigned)nb.P),
+                                 1024, 0, st>>>(nb.probs.p, c, active, nb.w.p, nb.y.p);
+        KPCG_LAUNCHED("nys_batch_lower_kernel");
+        nys_batch_upper_kernel<<<dim3((unsigned)((nb.mmax * 32 + 255) / 256), (unsigned)c,
+                                      (unsigned)nb.P),
+                                 256, 0, st>>>(nb.probs.p, c, active, nb.y.p, nb.w.p);
+        KPCG_LAUNCHED("nys_batch_upper_kernel");
+    }
+    const unsigned blocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 256);
+    nys_batch_back_kernel<<<dim3(blocks, (unsigned)nb.P), 256, 0, st>>>(
+        nb.probs.p, c, active, nb.w.p, R, ldr, Z, ldz, nrows);
+    KPCG_LAUNCHED("nys_batch_back_kernel");
 }
 
 }  // namespace kpcg

@@ -1,0 +1,46 @@
+// Solver pieces shared by the single-problem handle (api.cu) and the batch
+// of uneven problems (batch.cu).
+#pragma once
+
+#include <functional>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace kpcg {
+
+// The operators of the mixed-precision solve: the flexible-CG outer loop in
+// FP64 (Notay's FCG around an inexact inner solve, Sec. 3.3.2) only sees
+// these, so one loop serves one problem or a batch laid out column by column.
+struct MixedOps {
+    // O = (K + inner noise I) V in FP32, and the inner preconditioner
+    std::function<void(const float*, int64_t, int, float*, int64_t)> inner_mv, inner_pc;
+    // O = K_y V with FP64-class accuracy
+    std::function<void(const double*, int64_t, int, double*, int64_t)> outer_mv;
+    // R = B - K_y X (FP64-class) and the per-column ||R||^2, ||B||^2
+    std::function<void(const double*, int64_t, int, const double*, int64_t, double*,
+                       std::vector<double>&, std::vector<double>&)>
+        residual;
+    // true if a bounded device wait expired since the last query
+    std::function<bool()> timed_out;
+};
+
+// Makes the active-column flags of the running CG visible to the operators
+// (h.cg_active) for the lifetime of one pcg_core call.
+struct ActiveScope {
+    Ctx& h;
+    const int* saved;
+    ActiveScope(Ctx& hh, const int* a) : h(hh), saved(hh.cg_active) { h.cg_active = a; }
+    ~ActiveScope() { h.cg_active = saved; }
+};
+
+kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb, int c,
+                      double tol, const double* X0, double* Xout, int64_t ldx,
+                      std::vector<int>& iters_col, int& iters_total, int& steps,
+                      std::vector<double>& rr, std::vector<double>& bb);
+bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n);
+// (Re)build the handle's preconditioner for the noise its mode needs;
+// returns the host milliseconds spent (0 if it was current).
+double ensure_precond(Ctx& h);
+
+}  // namespace kpcg

@@ -34,12 +34,14 @@ class StepRecord:
     rel_res: float
     log_theta: np.ndarray
     log_noise: float
+    cold_iters: int | None = None  # a cold-started solve at the same theta (compare=True)
+    cold_ms: float | None = None
 
 
 class Trajectory:
     def __init__(self, solver: "_b.Solver", y, basis_idx, precond_idx, probes_fn, *,
                  lr=0.05, n_train=50, mlp_params=None, epochs=2000, mlp_lr=1e-3, tol=1e-8,
-                 ridge=1e-6):
+                 ridge=1e-6, compare=False):
         import torch
 
         self.torch = torch
@@ -52,6 +54,7 @@ class Trajectory:
         self.epochs = epochs
         self.mlp_lr = mlp_lr
         self.tol = tol
+        self.compare = compare
         self.s.warm_basis(basis_idx, ridge)
         self.mlp_params = mlp_params
         self.mlp = None
@@ -85,23 +88,30 @@ class Trajectory:
         c = torch.from_numpy(cs * self.c_sd + self.c_mu).cuda()
         return self.s.warm_expand(c)
 
-    def step(self, k, z):
-        """One trajectory step at z = [log_theta..., log noise]; returns the gradient."""
+    def _timed_solve(self, x0):
         torch = self.torch
-        s = self.s
-        s.set_theta(z[:-1], math.exp(z[-1]))
-        s.precond(_b.KPCG_PREC_NYSTROM, len(self.precond_idx), self.precond_idx)
-        warm = self.mlp is not None
-        x0 = self.predict_x0(z) if warm else None
         st = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        alpha, it, info, rc = s.solve(self.y, tol=self.tol, X0=x0, raise_on_error=False)
+        alpha, it, info, _ = self.s.solve(self.y, tol=self.tol, X0=x0, raise_on_error=False)
         e1.record(st)
         torch.cuda.synchronize()
-        self.records.append(StepRecord(k, warm, int(it[0]), e0.elapsed_time(e1),
-                                       info.max_rel_res, np.array(z[:-1]), float(z[-1])))
+        return alpha, int(it[0]), e0.elapsed_time(e1), info.max_rel_res
+
+    def step(self, k, z):
+        """One trajectory step at z = [log_theta..., log noise]; returns the gradient."""
+        s = self.s
+        s.set_theta(z[:-1], math.exp(z[-1]))
+        s.precond(_b.KPCG_PREC_NYSTROM, len(self.precond_idx), self.precond_idx)
+        warm = self.mlp is not None
+        cold_it = cold_ms = None
+        if warm and self.compare:
+            _, cold_it, cold_ms, _ = self._timed_solve(None)
+        x0 = self.predict_x0(z) if warm else None
+        alpha, it, ms, rel = self._timed_solve(x0)
+        self.records.append(StepRecord(k, warm, it, ms, rel, np.array(z[:-1]), float(z[-1]),
+                                       cold_it, cold_ms))
         if k < self.n_train:
             self.inputs.append(np.array(z))
             self.targets.append(s.warm_fit(alpha).cpu().numpy())

@@ -1,0 +1,166 @@
+"""GPU parity of the batched solver over uneven problems (kpcg_batch_*)
+against the FP64 CPU oracle, problem by problem.
+
+Tolerances: the batched tensor-core product is FP32-class (2e-5 relative per
+column, as the single-problem tensor-core product); the batched Nystrom
+apply works in FP64 on FP32 vectors (1e-5 relative at noise >= 1e-2); solves
+reach an FP64-recomputed relative residual <= 1e-8 per column, and the
+solution error against the oracle's dense solve is <= 1e-5 where the
+system's condition number allows it (kappa * 1e-8 otherwise)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def kpcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1602_06693_gb300 as k
+    from paper_1602_06693_gb300 import build
+    build.build()
+    return k
+
+
+# uneven sizes with ragged last tiles, n = 1 and one problem without inducing points
+SIZES = [(1, 3, 0.1), (130, 2, 0.05), (511, 5, 0.02), (700, 9, 0.3), (1029, 12, 0.01),
+         (257, 16, 0.1), (900, 7, 0.04)]
+
+
+def _problems(sizes, seed=0, m_frac=8, none_at=(0, 5)):
+    out = []
+    for k, (n, d, noise) in enumerate(sizes):
+        p = synthetic.make_problem(n, d, seed + k, dist="normal", ell="loguniform", noise=noise)
+        p.log_theta[:-1] += 0.5 * math.log(d)  # l_r ~ LogU(0.3, 3) * sqrt(d)
+        m = 0 if k in none_at else max(8, min(256, n // m_frac))
+        idx = synthetic.inducing_subset(n, m, seed=100 + k) if m else None
+        out.append((p, idx))
+    return out
+
+
+def _batch(kpcg, probs, **kw):
+    opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, **kw)
+    return kpcg.Batch([(torch.from_numpy(p.X).cuda(), p.log_theta, p.noise, idx)
+                       for p, idx in probs], options=opt)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_batched_product_matches_oracle(kpcg):
+    probs = _problems(SIZES)
+    c, shift = 3, 0.5
+    V = [synthetic.rng(50 + k).standard_normal((p.n, c)) for k, (p, _) in enumerate(probs)]
+    with _batch(kpcg, probs, inner_shift=shift) as b:
+        Vb = b.block(V, torch.float32)
+        O = b.matvec_f32(Vb, c)
+        again = b.matvec_f32(Vb, c)
+        assert torch.equal(O, again)  # fixed-order reduction: deterministic
+        out = [t.double().cpu().numpy() for t in b.unblock(O, c)]
+        assert float(O[:, :].abs().sum()) > 0
+        for p_i, (p, _) in enumerate(probs):  # rows past n_p are zero
+            assert float(O[p.n:, p_i * c:(p_i + 1) * c].abs().max() if p.n < b.ld else 0.0) == 0.0
+    for k, (p, _) in enumerate(probs):
+        ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
+        Vf = V[k].astype(np.float32).astype(np.float64)
+        ref = oracle.kyv(p.X, ell, s2, p.noise * (1 + shift), Vf)
+        for j in range(c):
+            assert _rel(out[k][:, j], ref[:, j]) <= 2e-5, (k, j)
+
+
+def test_batched_product_each_tiling(kpcg):
+    probs = _problems(SIZES[1:5])
+    c = 2
+    V = [synthetic.rng(60 + k).standard_normal((p.n, c)) for k, (p, _) in enumerate(probs)]
+    with _batch(kpcg, probs, inner_shift=0.0) as b:
+        Vb = b.block(V, torch.float32)
+        outs = []
+        for G in (1, 3, 64):
+            b.set_tiling(G)
+            outs.append(b.matvec_f32(Vb, c).double().cpu().numpy())
+        G, ctas, ms = b.tune(c)
+        assert G in (1, 2, 4, 8, 16, 32, 64) and ctas > 0 and ms > 0
+    # different item lengths change only the order of the FP32 partial sums
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() <= 1e-5 * np.abs(outs[0]).max()
+
+
+def test_batched_preconditioner_matches_oracle(kpcg):
+    probs = _problems(SIZES)
+    c, shift = 2, 0.25
+    R = [synthetic.rng(70 + k).standard_normal((p.n, c)) for k, (p, _) in enumerate(probs)]
+    with _batch(kpcg, probs, inner_shift=shift) as b:
+        Z = [t.double().cpu().numpy() for t in b.unblock(b.precond_apply_f32(b.block(R, torch.float32), c), c)]
+    for k, (p, idx) in enumerate(probs):
+        Rf = R[k].astype(np.float32).astype(np.float64)
+        if idx is None:
+            np.testing.assert_array_equal(Z[k], Rf)
+            continue
+        ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
+        ref = oracle.Nystrom(p.X, ell, s2, p.noise * (1 + shift), idx).apply(Rf)
+        assert _rel(Z[k], ref) <= 1e-5, k
+
+
+def _check_solutions(probs, Xs, B, rel_res, tol=1e-8):
+    for k, (p, _) in enumerate(probs):
+        ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
+        x = Xs[k]
+        r = B[k] - oracle.kyv(p.X, ell, s2, p.noise, x)
+        for j in range(B[k].shape[1]):
+            rr = np.linalg.norm(r[:, j]) / np.linalg.norm(B[k][:, j])
+            assert rr <= tol, (k, j, rr)
+            assert rel_res[k, j] <= tol, (k, j)
+
+
+def test_batched_solve_matches_oracle(kpcg):
+    sizes = [(200, 4, 1e-4), (1500, 8, 1e-3), (640, 16, 1e-1), (1100, 3, 3e-3), (333, 10, 1e-2),
+             (1024, 6, 2e-4)]
+    probs = _problems(sizes, seed=20, m_frac=4, none_at=())
+    c = 3
+    B = [np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 200 + k)])
+         for k, (p, _) in enumerate(probs)]
+    with _batch(kpcg, probs, inner_shift=0.25, max_iter=20000, max_outer=40) as b:
+        Xb, iters, rel, info, rc = b.solve(b.block(B), c, tol=1e-8)
+        assert rc == 0
+        Xs = [t.cpu().numpy() for t in b.unblock(Xb, c)]
+        for k, (p, _) in enumerate(probs):
+            assert float(Xb[p.n:, k * c:(k + 1) * c].abs().max() if p.n < b.ld else 0.0) == 0.0
+    _check_solutions(probs, Xs, B, rel)
+    for k, (p, _) in enumerate(probs):
+        ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
+        ref = oracle.dense_solve(p.X, ell, s2, p.noise, B[k])
+        Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
+        w = np.linalg.eigvalsh(Ky)
+        bound = max(1e-5, 1e-8 * w[-1] / w[0])
+        assert _rel(Xs[k], ref) <= bound, (k, _rel(Xs[k], ref), bound)
+    assert info.iters_total > 0 and info.outer_steps >= 1
+
+
+def test_sixty_four_uneven_problems(kpcg):
+    # 64 problems, n ~ LogU[512, 16384], d in 2..16, y plus 8 Rademacher probes each
+    problems = synthetic.config4_problems(seed=0)
+    probs = []
+    for k, p in enumerate(problems):
+        m = min(512, max(64, p.n // 8))
+        probs.append((p, synthetic.inducing_subset(p.n, m, seed=300 + k)))
+    c = 9
+    B = [np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)])
+         for k, (p, _) in enumerate(probs)]
+    with _batch(kpcg, probs, inner_shift=0.25, max_iter=20000, max_outer=40) as b:
+        Xb, iters, rel, info, rc = b.solve(b.block(B), c, tol=1e-8)
+        assert rc == 0, (rc, rel.max())
+        assert rel.max() <= 1e-8
+        order = np.argsort([p.n for p, _ in probs])
+        pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+        Xs = b.unblock(Xb, c)
+        sub = [probs[k] for k in pick]
+        _check_solutions(sub, [Xs[k][:, :1].cpu().numpy() for k in pick], [B[k][:, :1] for k in pick],
+                         rel[pick][:, :1])
