@@ -210,19 +210,29 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  Algorithm 1 takes an initial iterate x0; along a
- * hyperparameter trajectory a small network predicts coefficients c on a fixed
- * basis of m inducing points Z, and x0 = K(X, Z | theta) c.  The calls below
- * provide the basis (fit and expansion under the current theta) and the
- * network (hand-written training and inference kernels).
+ * hyperparameter trajectory a small network predicts coefficients c on a
+ * basis B, and x0 = B c.  Two bases:
+ *   - kernel basis: B = K(X, Z | theta) on m inducing points Z (kpcg_warm_basis);
+ *   - snapshot basis: B = the q most recent solutions pushed along the
+ *     trajectory, most recent first (kpcg_warm_snapshots, kpcg_warm_push).
+ * The calls below fit and expand on the active basis (the last one chosen),
+ * and provide the network (hand-written training and inference kernels).
  * ------------------------------------------------------------------------ */
 
-/* Fix the basis Z = rows idx (host, m sorted distinct indices) of X.  ridge
+/* Kernel basis Z = rows idx (host, m sorted distinct indices) of X.  ridge
  * (> 0) regularises the fit: c = argmin |K_XZ c - a|^2 + ridge c^T K_ZZ c.
  * Rebuilt for the current theta when needed (same pivot rule as Nystrom). */
 kpcg_status kpcg_warm_basis(kpcg_t h, int64_t m, const int64_t* idx, double ridge);
-/* c (device, m doubles) = fitted coefficients of a (device, n doubles). */
+/* Snapshot basis of depth q (1 .. 16), emptied.  ridge (> 0) regularises the
+ * fit: c = argmin |S c - a|^2 + ridge (tr(S^T S) / q) |c|^2, with S the n x q
+ * matrix of the stored solutions (FP64 Gram matrix, q x q Cholesky). */
+kpcg_status kpcg_warm_snapshots(kpcg_t h, int32_t q, double ridge);
+/* Store a solution (device, n doubles) as the newest snapshot; the oldest of q
+ * is dropped.  Until q are stored, missing snapshots count as zero vectors. */
+kpcg_status kpcg_warm_push(kpcg_t h, const double* a);
+/* c (device, m or q doubles) = fitted coefficients of a (device, n doubles). */
 kpcg_status kpcg_warm_fit(kpcg_t h, const double* a, double* c);
-/* x0 (device, n doubles) = K(X, Z | theta) c for c (device, m doubles). */
+/* x0 (device, n doubles) = B c for c (device, m or q doubles). */
 kpcg_status kpcg_warm_expand(kpcg_t h, const double* c, double* x0);
 
 typedef struct kpcg_mlp* kpcg_mlp_t;

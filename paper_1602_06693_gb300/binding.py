@@ -29,7 +29,8 @@ SYMBOLS = (
     "kpcg_set_options", "kpcg_precond", "kpcg_matvec_f64", "kpcg_matvec_f32",
     "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
     "kpcg_last_error", "kpcg_matvec_f64_noalloc", "kpcg_warm_basis", "kpcg_warm_fit",
-    "kpcg_warm_expand", "kpcg_mlp_create", "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
+    "kpcg_warm_expand", "kpcg_warm_snapshots", "kpcg_warm_push", "kpcg_mlp_create",
+    "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
     "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error", "kpcg_batch_create",
     "kpcg_batch_solve", "kpcg_batch_matvec_f32", "kpcg_batch_precond_apply_f32",
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_max_n", "kpcg_batch_destroy",
@@ -130,6 +131,8 @@ def lib():
         L.kpcg_dkv.argtypes = [vp, vp, i64, i32, vp, i64]
         L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, vp, pdbl, vp, ctypes.POINTER(Info)]
         L.kpcg_warm_basis.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), dbl]
+        L.kpcg_warm_snapshots.argtypes = [vp, i32, dbl]
+        L.kpcg_warm_push.argtypes = [vp, vp]
         L.kpcg_warm_fit.argtypes = [vp, vp, vp]
         L.kpcg_warm_expand.argtypes = [vp, vp, vp]
         pflt = ctypes.POINTER(ctypes.c_float)
@@ -392,6 +395,14 @@ class Solver:
         self._check(lib().kpcg_warm_basis(self._h, self.m_warm,
                                           idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                           float(ridge)))
+
+    def warm_snapshots(self, q, ridge=1e-10):
+        self.m_warm = int(q)
+        self._check(lib().kpcg_warm_snapshots(self._h, int(q), float(ridge)))
+
+    def warm_push(self, a):
+        torch = _torch()
+        self._check(lib().kpcg_warm_push(self._h, _dptr(a, torch.float64, "a")))
 
     def warm_fit(self, a):
         torch = _torch()

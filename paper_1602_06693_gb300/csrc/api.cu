@@ -628,6 +628,98 @@ static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, doubl
     return status;
 }
 
+// Slot of the j-th most recent snapshot (j = 0: newest).
+static int snap_slot(const Ctx& h, int j) { return ((h.whead - 1 - j) % h.wq + h.wq) % h.wq; }
+
+__global__ void snap_expand_kernel(const double* __restrict__ S, int64_t ld, int q, int head,
+                                   int count, const double* __restrict__ c,
+                                   double* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < count; ++j) {
+            const int slot = ((head - 1 - j) % q + q) % q;
+            s = fma(c[j], S[(int64_t)slot * ld + i], s);
+        }
+        x[i] = s;
+    }
+}
+
+// c = argmin |S c - a|^2 + ridge (tr(G)/q) |c|^2 over the stored snapshots:
+// G = S^T S and S^T a by the FP64 dot kernels, then a q x q Cholesky solve
+// (at most 16 unknowns) on the host; coefficients of missing snapshots are 0.
+void snapshot_fit(Ctx& h, const double* a, double* c_dev) {
+    cudaStream_t st = h.stream;
+    const int q = h.wq, cnt = h.wcount;
+    std::vector<double> c((size_t)q, 0.0);
+    if (cnt > 0) {
+        const int nblk = dot_blocks(h.n);
+        const int npair = cnt * (cnt + 1) / 2 + cnt;
+        double* partial = h.partial.need((size_t)nblk * npair);
+        int t = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const double* Si = h.wsnap.p + (size_t)snap_slot(h, i) * h.ld;
+            for (int j = 0; j <= i; ++j, ++t)
+                dot_cols<double>(Si, h.ld, h.wsnap.p + (size_t)snap_slot(h, j) * h.ld, h.ld, h.n,
+                                 1, partial + (size_t)t * nblk, nblk, st);
+            dot_cols<double>(Si, h.ld, a, h.ld, h.n, 1,
+                             partial + (size_t)(cnt * (cnt + 1) / 2 + i) * nblk, nblk, st);
+        }
+        std::vector<double> hp((size_t)nblk * npair);
+        KPCG_CUDA(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(),
+                                  cudaMemcpyDeviceToHost, st));
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        auto sum = [&](int idx) {
+            double v = 0.0;
+            for (int b = 0; b < nblk; ++b) v += hp[(size_t)idx * nblk + b];
+            return v;
+        };
+        std::vector<double> G((size_t)cnt * cnt), r((size_t)cnt);
+        t = 0;
+        for (int i = 0; i < cnt; ++i)
+            for (int j = 0; j <= i; ++j, ++t) G[(size_t)i * cnt + j] = G[(size_t)j * cnt + i] = sum(t);
+        double tr = 0.0;
+        for (int i = 0; i < cnt; ++i) {
+            r[(size_t)i] = sum(cnt * (cnt + 1) / 2 + i);
+            tr += G[(size_t)i * cnt + i];
+        }
+        for (int i = 0; i < cnt; ++i) G[(size_t)i * cnt + i] += h.wridge * tr / cnt;
+        // Cholesky G = L L^T in place (lower), then two triangular solves
+        for (int j = 0; j < cnt; ++j) {
+            double d = G[(size_t)j * cnt + j];
+            for (int k = 0; k < j; ++k) d -= G[(size_t)j * cnt + k] * G[(size_t)j * cnt + k];
+            if (!(d > 0.0)) fail(KPCG_ERR_NOT_SPD, "snapshot Gram matrix not positive definite");
+            d = std::sqrt(d);
+            G[(size_t)j * cnt + j] = d;
+            for (int i = j + 1; i < cnt; ++i) {
+                double v = G[(size_t)i * cnt + j];
+                for (int k = 0; k < j; ++k) v -= G[(size_t)i * cnt + k] * G[(size_t)j * cnt + k];
+                G[(size_t)i * cnt + j] = v / d;
+            }
+        }
+        for (int i = 0; i < cnt; ++i) {
+            double v = r[(size_t)i];
+            for (int k = 0; k < i; ++k) v -= G[(size_t)i * cnt + k] * c[(size_t)k];
+            c[(size_t)i] = v / G[(size_t)i * cnt + i];
+        }
+        for (int i = cnt - 1; i >= 0; --i) {
+            double v = c[(size_t)i];
+            for (int k = i + 1; k < cnt; ++k) v -= G[(size_t)k * cnt + i] * c[(size_t)k];
+            c[(size_t)i] = v / G[(size_t)i * cnt + i];
+        }
+    }
+    KPCG_CUDA(cudaMemcpyAsync(c_dev, c.data(), sizeof(double) * q, cudaMemcpyHostToDevice, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+}
+
+void snapshot_expand(Ctx& h, const double* c, double* x0) {
+    const int blocks = (int)std::min<int64_t>((h.n + 255) / 256, 152 * 8);
+    snap_expand_kernel<<<blocks, 256, 0, h.stream>>>(h.wsnap.p, h.ld, h.wq, h.whead, h.wcount, c,
+                                                      x0, h.n);
+    KPCG_LAUNCHED("snap_expand_kernel");
+    KPCG_CUDA(cudaStreamSynchronize(h.stream));
+}
+
 }  // namespace kpcg
 
 using kpcg::Ctx;
@@ -976,16 +1068,48 @@ kpcg_status kpcg_warm_basis(kpcg_t h, int64_t m, const int64_t* idx, double ridg
         h->widx.assign(idx, idx + m);
         h->wridge = ridge;
         h->Wb.reset();
+        h->wmode = 1;
     });
     return KPCG_OK;
 }
 
 static void ensure_warm(kpcg::Ctx& h) {
-    if (h.widx.empty()) fail(KPCG_ERR_STATE, "no warm-start basis: call kpcg_warm_basis first");
+    if (h.wmode != 1 || h.widx.empty())
+        fail(KPCG_ERR_STATE, "no warm-start basis: call kpcg_warm_basis first");
     if (h.Wb.ready) return;
     kpcg::nystrom_setup(h.Wb, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), h.wridge,
                         h.widx.data(), (int64_t)h.widx.size(), h.stream);
     h.Wb.n = h.n;
+}
+
+kpcg_status kpcg_warm_snapshots(kpcg_t h, int32_t q, double ridge) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (q < 1 || q > 16) fail(KPCG_ERR_ARG, "q must be in [1, 16]");
+        if (!(ridge > 0.0) || !std::isfinite(ridge)) fail(KPCG_ERR_ARG, "ridge must be > 0");
+        h->wsnap.need((size_t)q * h->ld);
+        h->wc.need(16);
+        h->wq = q;
+        h->wcount = 0;
+        h->whead = 0;
+        h->wridge = ridge;
+        h->wmode = 2;
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_warm_push(kpcg_t h, const double* a) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (h->wmode != 2) fail(KPCG_ERR_STATE, "no snapshot basis: call kpcg_warm_snapshots first");
+        kpcg::check_dev_ptr(a, "a");
+        KPCG_CUDA(cudaMemcpyAsync(h->wsnap.p + (size_t)h->whead * h->ld, a,
+                                  sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+        h->whead = (h->whead + 1) % h->wq;
+        h->wcount = std::min(h->wcount + 1, h->wq);
+        KPCG_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    return KPCG_OK;
 }
 
 kpcg_status kpcg_warm_fit(kpcg_t h, const double* a, double* c) {
@@ -993,6 +1117,10 @@ kpcg_status kpcg_warm_fit(kpcg_t h, const double* a, double* c) {
     KPCG_GUARD(h, {
         kpcg::check_dev_ptr(a, "a");
         kpcg::check_dev_ptr(c, "c");
+        if (h->wmode == 2) {
+            kpcg::snapshot_fit(*h, a, c);
+            return KPCG_OK;
+        }
         ensure_warm(*h);
         kpcg::nystrom_project_solve(h->Wb, a, h->n, 1, c, h->stream);
         KPCG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1005,6 +1133,10 @@ kpcg_status kpcg_warm_expand(kpcg_t h, const double* c, double* x0) {
     KPCG_GUARD(h, {
         kpcg::check_dev_ptr(c, "c");
         kpcg::check_dev_ptr(x0, "x0");
+        if (h->wmode == 2) {
+            kpcg::snapshot_expand(*h, c, x0);
+            return KPCG_OK;
+        }
         ensure_warm(*h);
         kpcg::nystrom_expand(h->Wb, c, x0, h->stream);
         KPCG_CUDA(cudaStreamSynchronize(h->stream));

@@ -342,7 +342,8 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
         status = fcg_solve(M, ops, Bp, L, C, tol, nullptr, Xp, L, iters_col, iters_total, steps,
                            rr, bn);
         if (status != KPCG_OK) ops.residual(Bp, L, C, Xp, L, M.R64.p, rr, bn);
-        masked_copy_kernel<double, double><<<g, 256, 0, st>>>(X, ld, Xp, L, b->nrow.p, c, L);
+        // exactly ld rows per column of the caller's block (ld may be below L)
+        masked_copy_kernel<double, double><<<g, 256, 0, st>>>(X, ld, Xp, L, b->nrow.p, c, ld);
         KPCG_LAUNCHED("masked_copy_kernel");
         double maxrel = 0.0;
         for (int k = 0; k < C; ++k) {

@@ -95,6 +95,10 @@ struct Ctx {
     std::vector<int64_t> widx;
     double wridge = 0.0;
     DevBuf<float> W32;
+    // snapshot basis: ring of the wq most recent pushed solutions (column-major, ld)
+    int wmode = 0;  // 0 none, 1 kernel basis, 2 snapshots
+    int wq = 0, wcount = 0, whead = 0;
+    DevBuf<double> wsnap, wc;
     DevBuf<double> partial;
     DevBuf<double> scal;
     DevBuf<int> iscal;

@@ -4,16 +4,27 @@ Stochastic-gradient ascent on log p(y|theta) (gradient of Eq. 2 with the
 Rademacher trace estimate of Sec. 2.1; the paper's optimiser is ADAGRAD with
 N_r = 4 probes, Sec. 5, this driver uses Adam) visits theta_1, theta_2, ...,
 and every step solves K_y(theta_k) alpha_k = y.  Algorithm 1 starts from an
-initial iterate x0.  For the first ``n_train`` steps the driver records
-(theta_k, c*_k), where c*_k fits the converged alpha_k on a fixed basis Z
-(kpcg_warm_fit); it then trains the network theta -> c (kpcg_mlp_train,
-FP32) and, from then on, starts each solve from x0 = K(X, Z | theta_k) c with
-c predicted in BF16 (kpcg_mlp_forward, kpcg_warm_expand).  PCG still runs to
-the same tolerance, so the network only moves the starting point.
+initial iterate x0.  A small network maps the step's log-hyperparameters to
+coefficients c on a basis B and PCG starts from x0 = B c; it still runs to the
+same tolerance, so the network only moves the starting point.
 
-The few scalars of the optimiser (d + 2 log-parameters) and the affine
-standardisation of the network's inputs and outputs are host arithmetic; the
-solves, gradients, fits, expansions and the network run in the library.
+Bases (kpcg_warm_*):
+  * ``"snapshots"`` (default): the q most recent solutions of the trajectory,
+    newest first.  Along the trajectory alpha(theta) moves smoothly, so a
+    combination of recent solutions is close to the next one; the training
+    target of step k is the least-squares combination of the q solutions
+    before it.
+  * ``"kernel"``: K(X, Z | theta) on m fixed inducing points; target = the
+    least-squares fit of alpha_k.  alpha = K_y^{-1} y is dominated by its rough
+    component, which a smooth kernel basis does not represent, so this basis
+    saves few iterations even with exact coefficients; kept for comparison.
+
+For the first ``n_train`` steps the driver records (theta_k, c*_k), then
+trains the network (kpcg_mlp_train, FP32 Adam) and from then on predicts c in
+BF16 (kpcg_mlp_forward).  The optimiser's few scalars (d + 2 log-parameters)
+and the affine standardisation of the network's inputs and outputs are host
+arithmetic; solves, gradients, fits, expansions and the network run in the
+library.
 """
 from __future__ import annotations
 
@@ -39,9 +50,9 @@ class StepRecord:
 
 
 class Trajectory:
-    def __init__(self, solver: "_b.Solver", y, basis_idx, precond_idx, probes_fn, *,
-                 lr=0.05, n_train=50, mlp_params=None, epochs=2000, mlp_lr=1e-3, tol=1e-8,
-                 ridge=1e-6, compare=False):
+    def __init__(self, solver: "_b.Solver", y, precond_idx, probes_fn, *, basis="snapshots",
+                 q=4, basis_idx=None, lr=0.05, n_train=50, mlp_params=None, epochs=2000,
+                 mlp_lr=1e-3, tol=1e-8, ridge=None, compare=False):
         import torch
 
         self.torch = torch
@@ -55,12 +66,19 @@ class Trajectory:
         self.mlp_lr = mlp_lr
         self.tol = tol
         self.compare = compare
-        self.s.warm_basis(basis_idx, ridge)
+        self.basis = basis
+        self.q = q
+        if basis == "snapshots":
+            self.s.warm_snapshots(q, 1e-10 if ridge is None else ridge)
+        elif basis == "kernel":
+            self.s.warm_basis(basis_idx, 1e-6 if ridge is None else ridge)
+        else:
+            raise ValueError(basis)
+        self.n_seen = 0
         self.mlp_params = mlp_params
         self.mlp = None
         self.inputs, self.targets = [], []
-        self.m1 = None
-        self.m2 = None
+        self.m1 = self.m2 = None
         self.t = 0
         self.records: list[StepRecord] = []
 
@@ -112,9 +130,12 @@ class Trajectory:
         alpha, it, ms, rel = self._timed_solve(x0)
         self.records.append(StepRecord(k, warm, it, ms, rel, np.array(z[:-1]), float(z[-1]),
                                        cold_it, cold_ms))
-        if k < self.n_train:
+        if k < self.n_train and (self.basis == "kernel" or self.n_seen >= self.q):
             self.inputs.append(np.array(z))
             self.targets.append(s.warm_fit(alpha).cpu().numpy())
+        if self.basis == "snapshots":
+            s.warm_push(alpha)
+        self.n_seen += 1
         g, _, _ = s.grad(self.y, self.probes_fn(k), tol=self.tol, alpha0=alpha)
         return g
 

@@ -155,9 +155,12 @@ def test_sixty_four_uneven_problems(kpcg):
     B = [np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)])
          for k, (p, _) in enumerate(probs)]
     with _batch(kpcg, probs, inner_shift=0.25, max_iter=20000, max_outer=40) as b:
-        Xb, iters, rel, info, rc = b.solve(b.block(B), c, tol=1e-8)
-        assert rc == 0, (rc, rel.max())
-        assert rel.max() <= 1e-8
+        Xb, iters, rel, info, rc = b.solve(b.block(B), c, tol=1e-8, raise_on_error=False)
+        print(f"64 problems: status {rc}, outer steps {info.outer_steps}, inner iterations "
+              f"{info.iters_total}, {info.time_ms:.1f} ms, max rel residual {rel.max():.2e}")
+        bad = [(k, p.n, p.d, round(p.noise, 6), float(rel[k].max()), int(iters[k].max()))
+               for k, (p, _) in enumerate(probs) if rel[k].max() > 1e-8]
+        assert rc == 0 and not bad, bad[:12]
         order = np.argsort([p.n for p, _ in probs])
         pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
         Xs = b.unblock(Xb, c)
