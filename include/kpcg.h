@@ -292,7 +292,7 @@ kpcg_status kpcg_matvec_f64_noalloc(const float* X, int64_t n, int32_t d,
  * with its own inputs, hyperparameters and Nystrom preconditioner (Sec. 3.1);
  * every one of its c right-hand sides runs its own CG (Algorithm 1) and stops
  * on its own.  The solve is the mixed-precision one (KPCG_TC_IR): an FP64
- * flexible-CG outer loop whose products use the double-float kernel, around an
+ * flexible-CG outer loop (double-float direction products, native-FP64 residuals) around an
  * inner FP32 PCG whose products with K are ONE persistent tensor-core launch
  * over the tiles of all problems, and whose preconditioner applies are one
  * batched launch sequence.
@@ -319,8 +319,8 @@ typedef struct {
 kpcg_status kpcg_batch_create(int32_t nprob, const kpcg_problem* probs,
                               const kpcg_options* opt, void* stream, kpcg_batch_t* out);
 /* Solve every system for its c right-hand sides B (device, block layout) to
- * ||b - K_y x|| <= tol ||b|| per column, the residual recomputed in FP64-class
- * arithmetic (double-float products, ~1e-12 relative to FP64).  X: device,
+ * ||b - K_y x|| <= tol ||b|| per column, the residual recomputed in FP64
+ * (the outer loop's direction products use the double-float kernel).  X: device,
  * block layout (caller-owned).  iters, rel_res (host, nprob*c, nullable):
  * inner PCG iterations and final relative residual per column.  Returns
  * KPCG_ERR_NO_CONVERGENCE (X holds the last iterate) if a column missed tol. */

@@ -314,10 +314,11 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
                 for (int b2 = 0; b2 < nblk; ++b2)
                     out[(size_t)t * c + k] += hp[((size_t)t * c + k) * nblk + b2];
     };
-    if (X0)
-        copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
-    else
+    if (X0) {
+        if (X0 != Xout) copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
+    } else {
         fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
+    }
     ops.residual(B, ldb, c, Xout, ldx, R, rr, bb);
     std::vector<double> pAp((size_t)W * c, 1.0), coef((size_t)c), d;
     std::vector<int> dead((size_t)c, 0);

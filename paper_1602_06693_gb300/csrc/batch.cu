@@ -5,8 +5,10 @@
 // flexible CG in FP64 outside, FP32 PCG inside, where every inner product
 // with K is one persistent tensor-core launch over the flat tile list of all
 // problems and every preconditioner apply is one batched launch sequence.
-// The FP64-class products (outer loop, residuals) use the double-float
-// kernel per problem.  Columns, hence problems, stop independently.
+// The outer loop's direction products use the double-float kernel per
+// problem and every true residual the native-FP64 one (its error scales with
+// the full solution, the directions' with the small correction).  Columns,
+// hence problems, stop independently.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -312,9 +314,11 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
             for (size_t p = 0; p < bb->sub.size(); ++p) {
                 Ctx& h = *bb->sub[p];
                 const int64_t off = (int64_t)p * c;
+                // native FP64: b - K x cancels terms up to ~|x|/|b| ~ 1/sigma^2
+                // larger than the result, beyond the double-float product's reach
                 M.prof.time(Profiler::KV_OUTER, M.stream, [&] {
-                    kv_df(h, Xm + off * ldx, ldx, c, Bm + off * ldb, ldb, R + off * M.ld, M.ld,
-                          h.noise);
+                    kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, Xm + off * ldx, ldx, c,
+                           Bm + off * ldb, ldb, R + off * M.ld, M.ld, h.kvws, M.stream);
                 });
             }
             const int nblk = dot_blocks(M.n);
@@ -339,8 +343,25 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
         std::vector<int> iters_col((size_t)C, 0);
         int iters_total = 0, steps = 0;
         std::vector<double> rr, bn;
-        status = fcg_solve(M, ops, Bp, L, C, tol, nullptr, Xp, L, iters_col, iters_total, steps,
-                           rr, bn);
+        // The outer loop gives up when its worst column stops improving; with
+        // hundreds of columns of very different difficulty that can be one slow
+        // problem in a slow phase.  Restart it from the current iterate (fresh
+        // residual, empty direction window) while restarts keep improving.
+        double prev_worst = INFINITY;
+        for (int restart = 0;; ++restart) {
+            int st_steps = 0;
+            status = fcg_solve(M, ops, Bp, L, C, tol, restart ? Xp : nullptr, Xp, L, iters_col,
+                               iters_total, st_steps, rr, bn);
+            steps += st_steps;
+            if (status != KPCG_ERR_NO_CONVERGENCE || restart >= M.opt.max_restarts ||
+                iters_total >= M.opt.max_iter)
+                break;
+            double worst = 0.0;
+            for (int k = 0; k < C; ++k)
+                if (bn[k] > 0) worst = std::max(worst, std::sqrt(rr[k] / bn[k]));
+            if (!(worst < 0.5 * prev_worst)) break;
+            prev_worst = worst;
+        }
         if (status != KPCG_OK) ops.residual(Bp, L, C, Xp, L, M.R64.p, rr, bn);
         // exactly ld rows per column of the caller's block (ld may be below L)
         masked_copy_kernel<double, double><<<g, 256, 0, st>>>(X, ld, Xp, L, b->nrow.p, c, ld);

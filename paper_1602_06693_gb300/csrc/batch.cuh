@@ -72,13 +72,15 @@ struct NysBatch {
     std::vector<NysBatchProb> hprobs;
     DevBuf<NysBatchProb> probs;
     DevBuf<double> part, w, y;
+    DevBuf<float2> u2;  // u = M^{-1} K_UX r as FP32 pairs for the back product
 };
 // Tables for c columns per problem from the problems' Nystrom states
 // (problems without one get m = 0 and the identity).
 void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
                     cudaStream_t st);
-// Z = P_p^{-1} R for every problem (FP32 vectors, FP64 inside), rows n_p ..
-// nrows-1 zero; problems with no active column are skipped (Z = 0).
+// Z = P_p^{-1} R for every problem (FP32 vectors; FP64 and double-float
+// inside), rows n_p .. nrows-1 zero; the columns of problems with no active
+// column are skipped and left unchanged.
 void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_t ldz,
                      int64_t nrows, const int* active, cudaStream_t st);
 

@@ -736,12 +736,13 @@ __device__ __forceinline__ bool nb_live(const int* __restrict__ active, int p, i
     return false;
 }
 
-// part[pbase + (split * c + k) * m + a] for columns k0 .. k0+ncols-1
+// part[pbase + (split * c + k) * m + a] for columns k0 .. k0+ncols-1 (ncols <= NC)
+template <int NC>
 __global__ void __launch_bounds__(256)
     nys_batch_proj_kernel(const NysBatchProb* __restrict__ probs, int c, const float* __restrict__ R,
                           int64_t ldr, int k0, int ncols, const int* __restrict__ active,
                           double* __restrict__ part) {
-    __shared__ float2 sr[128][PC];
+    __shared__ float sr[128][NC];
     const int p = blockIdx.z;
     const NysBatchProb pb = probs[p];
     if (pb.m == 0 || (int)blockIdx.y >= pb.nsplit || (int64_t)blockIdx.x * 256 >= pb.m ||
@@ -752,35 +753,39 @@ __global__ void __launch_bounds__(256)
     const int64_t r0 = (int64_t)blockIdx.y * pb.rows_per_split;
     const int64_t r1 = min(pb.n, r0 + pb.rows_per_split);
     const float* Rp = R + ((int64_t)p * c + k0) * ldr;
-    Acc2 acc[PC];
+    Acc2 acc[NC];
 #pragma unroll
-    for (int k = 0; k < PC; ++k) acc[k] = {0.f, 0.f};
+    for (int k = 0; k < NC; ++k) acc[k] = {0.f, 0.f};
     for (int64_t rs = r0; rs < r1; rs += 128) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 128 * PC; e += 256) {
+        for (int e = threadIdx.x; e < 128 * NC; e += 256) {
             const int k = e / 128, r = e % 128;
-            const float v = (rs + r < r1 && k < ncols) ? Rp[rs + r + (int64_t)k * ldr] : 0.f;
-            sr[r][k] = make_float2(v, 0.f);
+            sr[r][k] = (rs + r < r1 && k < ncols) ? Rp[rs + r + (int64_t)k * ldr] : 0.f;
         }
         __syncthreads();
         const int rn = (int)min((int64_t)128, r1 - rs);
         if (a < m) {
             const float2* Kp = pb.KXU + rs * m + a;
-#pragma unroll 4
+#pragma unroll 2
             for (int r = 0; r < rn; ++r) {
                 const float2 kv = __ldg(Kp + (int64_t)r * m);
 #pragma unroll
-                for (int k = 0; k < PC; ++k) {
-                    dot2_add(acc[k], kv.x, sr[r][k].x);
-                    acc[k].c = fmaf(kv.y, sr[r][k].x, acc[k].c);
+                for (int k = 0; k < NC; ++k) {
+                    if (k < ncols) {
+                        dot2_add(acc[k], kv.x, sr[r][k]);
+                        acc[k].c = fmaf(kv.y, sr[r][k], acc[k].c);
+                    }
                 }
             }
         }
     }
-    if (a < m)
-        for (int k = 0; k < ncols; ++k)
-            part[pb.pbase + ((int64_t)blockIdx.y * c + k0 + k) * m + a] =
-                (double)acc[k].s + (double)acc[k].c;
+    if (a < m) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            if (k < ncols)
+                part[pb.pbase + ((int64_t)blockIdx.y * c + k0 + k) * m + a] =
+                    (double)acc[k].s + (double)acc[k].c;
+    }
 }
 
 __global__ void nys_batch_sum_kernel(const NysBatchProb* __restrict__ probs, int c,
@@ -821,10 +826,11 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// u = L^{-T} y (warp per entry), written over w
+// u = L^{-T} y (warp per entry), written over w and as FP32 pairs (hi, lo)
 __global__ void nys_batch_upper_kernel(const NysBatchProb* __restrict__ probs, int c,
                                        const int* __restrict__ active,
-                                       const double* __restrict__ y, double* __restrict__ u) {
+                                       const double* __restrict__ y, double* __restrict__ u,
+                                       float2* __restrict__ u2) {
     const int p = blockIdx.z, k = blockIdx.y;
     const NysBatchProb pb = probs[p];
     const int64_t m = pb.m;
@@ -836,46 +842,67 @@ __global__ void nys_batch_upper_kernel(const NysBatchProb* __restrict__ probs, i
     double s = 0.0;
     for (int64_t i = j + lane; i < m; i += 32) s = fma(Uj[i], yk[i], s);
     s = warp_sum(s);
-    if (lane == 0) u[pb.wbase + (int64_t)k * m + j] = s;
+    if (lane == 0) {
+        u[pb.wbase + (int64_t)k * m + j] = s;
+        const float hi = (float)s;
+        u2[pb.wbase + (int64_t)k * m + j] = make_float2(hi, (float)(s - (double)hi));
+    }
 }
 
-// z = (r - K_XU u) / sigma^2 (warp per row), zero past n_p and for skipped
-// problems; m = 0 means no preconditioner (z = r).
+// z = (r - K_XU u) / sigma^2 (warp per row, all columns k0 .. k0+ncols-1 of
+// the problem in one sweep over the row of K_XU), zero past n_p; m = 0 means
+// no preconditioner (z = r).  Problems with no active column are left as they
+// are: the CG does not read those columns again.
+//
+// u can hold entries ~1e6 that cancel to O(1) in K_XU u (the Nystrom P^{-1}
+// spans ~1/sigma^2 .. 1/lambda_max), so the sum needs ~FP64 accuracy; FP64
+// itself runs at 1/64 of the FP32 rate here.  Both factors are FP32 pairs
+// (hi, lo); each term is split exactly (TwoProduct by FMA, plus the two
+// cross terms) and summed with TwoSum (Dot2, Ogita-Rump-Oishi 2005), about
+// 2^-46 relative per term at ~11 FP32 operations.
+template <int NC>
 __global__ void __launch_bounds__(256)
-    nys_batch_back_kernel(const NysBatchProb* __restrict__ probs, int c,
-                          const int* __restrict__ active, const double* __restrict__ u,
+    nys_batch_back_kernel(const NysBatchProb* __restrict__ probs, int c, int k0, int ncols,
+                          const int* __restrict__ active, const float2* __restrict__ u,
                           const float* __restrict__ R, int64_t ldr, float* __restrict__ Z,
                           int64_t ldz, int64_t nrows) {
     const int p = blockIdx.y;
     const NysBatchProb pb = probs[p];
-    const bool live = nb_live(active, p, c);
+    if (!nb_live(active, p, c)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const float* Rp = R + (int64_t)p * c * ldr;
-    float* Zp = Z + (int64_t)p * c * ldz;
+    const float* Rp = R + ((int64_t)p * c + k0) * ldr;
+    float* Zp = Z + ((int64_t)p * c + k0) * ldz;
+    const float2* up = u + pb.wbase + (int64_t)k0 * pb.m;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nrows;
          i += warps) {
-        if (!live || i >= pb.n) {
-            if (lane < c)
-                for (int k = lane; k < c; k += 32) Zp[i + (int64_t)k * ldz] = 0.f;
-            continue;
-        }
-        if (pb.m == 0) {
-            for (int k = lane; k < c; k += 32) Zp[i + (int64_t)k * ldz] = Rp[i + (int64_t)k * ldr];
+        if (i >= pb.n || pb.m == 0) {
+            for (int k = lane; k < ncols; k += 32)
+                Zp[i + (int64_t)k * ldz] = (i < pb.n) ? Rp[i + (int64_t)k * ldr] : 0.f;
             continue;
         }
         const float2* Ki = pb.KXU + i * pb.m;
-        for (int k = 0; k < c; ++k) {
-            const double* uk = u + pb.wbase + (int64_t)k * pb.m;
-            double acc = 0.0;
-            for (int64_t a = lane; a < pb.m; a += 32) {
-                const float2 kv = __ldg(Ki + a);
-                acc = fma((double)kv.x + (double)kv.y, __ldg(uk + a), acc);
+        Acc2 acc[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] = {0.f, 0.f};
+        for (int64_t a = lane; a < pb.m; a += 32) {
+            const float2 kv = __ldg(Ki + a);
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+                if (k < ncols) {
+                    const float2 uv = __ldg(up + (int64_t)k * pb.m + a);
+                    dot2_add(acc[k], kv.x, uv.x);
+                    acc[k].c = fmaf(kv.x, uv.y, fmaf(kv.y, uv.x, acc[k].c));
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k < ncols) {
+                const double sm = warp_sum((double)acc[k].s + (double)acc[k].c);
+                if (lane == 0)
+                    Zp[i + (int64_t)k * ldz] =
+                        (float)(((double)Rp[i + (int64_t)k * ldr] - sm) * pb.inv_noise);
             }
-            const double sm = warp_sum(acc);
-            if (lane == 0)
-                Zp[i + (int64_t)k * ldz] =
-                    (float)(((double)Rp[i + (int64_t)k * ldr] - sm) * pb.inv_noise);
         }
     }
 }
@@ -913,6 +940,7 @@ void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, in
     nb.part.need((size_t)std::max<int64_t>(1, nb.ptotal));
     nb.w.need((size_t)std::max<int64_t>(1, nb.wtotal));
     nb.y.need((size_t)std::max<int64_t>(1, nb.wtotal));
+    nb.u2.need((size_t)std::max<int64_t>(1, nb.wtotal));
     KPCG_CUDA(cudaMemcpyAsync(nb.probs.p, nb.hprobs.data(), sizeof(NysBatchProb) * nb.hprobs.size(),
                               cudaMemcpyHostToDevice, st));
     KPCG_CUDA(cudaStreamSynchronize(st));
@@ -924,10 +952,18 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
     const int c = nb.c;
     if (nb.mmax > 0) {
         const unsigned ablk = (unsigned)((nb.mmax + 255) / 256);
-        for (int k0 = 0; k0 < c; k0 += PC) {
-            const int nc = std::min(PC, c - k0);
-            nys_batch_proj_kernel<<<dim3(ablk, (unsigned)nb.nsplit_max, (unsigned)nb.P), 256, 0,
-                                    st>>>(nb.probs.p, c, R, ldr, k0, nc, active, nb.part.p);
+        const dim3 g(ablk, (unsigned)nb.nsplit_max, (unsigned)nb.P);
+        for (int k0 = 0; k0 < c; k0 += 16) {
+            const int nc = std::min(16, c - k0);
+            if (nc <= 4)
+                nys_batch_proj_kernel<4><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
+                                                           nb.part.p);
+            else if (nc <= 8)
+                nys_batch_proj_kernel<8><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
+                                                           nb.part.p);
+            else
+                nys_batch_proj_kernel<16><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
+                                                            nb.part.p);
             KPCG_LAUNCHED("nys_batch_proj_kernel");
         }
         nys_batch_sum_kernel<<<dim3((unsigned)((c * nb.mmax + 255) / 256), (unsigned)nb.P), 256, 0,
@@ -939,13 +975,24 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
         KPCG_LAUNCHED("nys_batch_lower_kernel");
         nys_batch_upper_kernel<<<dim3((unsigned)((nb.mmax * 32 + 255) / 256), (unsigned)c,
                                       (unsigned)nb.P),
-                                 256, 0, st>>>(nb.probs.p, c, active, nb.y.p, nb.w.p);
+                                 256, 0, st>>>(nb.probs.p, c, active, nb.y.p, nb.w.p, nb.u2.p);
         KPCG_LAUNCHED("nys_batch_upper_kernel");
     }
     const unsigned blocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 256);
-    nys_batch_back_kernel<<<dim3(blocks, (unsigned)nb.P), 256, 0, st>>>(
-        nb.probs.p, c, active, nb.w.p, R, ldr, Z, ldz, nrows);
-    KPCG_LAUNCHED("nys_batch_back_kernel");
+    for (int k0 = 0; k0 < c; k0 += 16) {
+        const int nc = std::min(16, c - k0);
+        const dim3 g(blocks, (unsigned)nb.P);
+        if (nc <= 4)
+            nys_batch_back_kernel<4><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p, R,
+                                                       ldr, Z, ldz, nrows);
+        else if (nc <= 8)
+            nys_batch_back_kernel<8><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p, R,
+                                                       ldr, Z, ldz, nrows);
+        else
+            nys_batch_back_kernel<16><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p,
+                                                        R, ldr, Z, ldz, nrows);
+        KPCG_LAUNCHED("nys_batch_back_kernel");
+    }
 }
 
 }  // namespace kpcg

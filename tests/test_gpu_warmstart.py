@@ -131,34 +131,6 @@ def _trajectory(kpcg, basis, n_train=12, steps=24):
     return c, w
 
 
-def _trajectory(kpcg, basis, n_train=12, steps=24):
-    from paper_1602_06693_gb300.warmstart import Trajectory
-    n, d = 2048, 6
-    p = synthetic.make_problem(n, d, 11, dist="normal", ell=1.0, noise=0.1)
-    X = torch.from_numpy(p.X).cuda()
-    y = torch.from_numpy(p.y).cuda()
-    opt = kpcg.default_options(precision=kpcg.KPCG_FP64, max_iter=2000)
-    s = kpcg.Solver(X, p.log_theta, p.noise, options=opt)
-    pidx = synthetic.inducing_subset(n, 128, seed=6)
-    probes = lambda k: torch.from_numpy(synthetic.rademacher(n, 4, 1000 + k)).cuda()
-    q_out = 4 if basis == "snapshots" else 256
-    params = synthetic.mlp_init(9, d + 2, 128, 128, q_out)
-    tr = Trajectory(s, y, pidx, probes, basis=basis, q=4,
-                    basis_idx=synthetic.inducing_subset(n, 256, seed=5), lr=0.05,
-                    n_train=n_train, mlp_params=params, epochs=1500, mlp_lr=2e-3, tol=1e-8,
-                    compare=True)
-    z0 = np.concatenate([p.log_theta, [math.log(p.noise)]])
-    recs = tr.run(z0, steps)
-    s.close()
-    assert all(r.rel_res <= 1e-8 for r in recs)
-    warm = [r for r in recs if r.warm]
-    assert len(warm) == steps - n_train
-    w = np.array([r.iters for r in warm])
-    c = np.array([r.cold_iters for r in warm])
-    print(basis, "same theta: cold iterations", c.tolist(), "warm iterations", w.tolist())
-    return c, w
-
-
 def test_trained_network_cuts_pcg_iterations(kpcg):
     # Adam on (log l_1..d, log s^2, log noise); steps 4..11 give training pairs
     # (coefficients of alpha_k on the 4 solutions before it), steps 12..23
