@@ -179,6 +179,113 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU
+BATCH_WORKLOAD = ("64 ARD-RBF problems, n~LogU[512,16384], d~U{2..16}, l_r~LogU(0.3,3)*sqrt(d), "
+                  "s^2~LogU(0.5,2), noise~LogU(1e-4,1e-1), X~N(0,I); y plus 8 Rademacher probes "
+                  "each; Nystrom m_p=min(512,max(64,n_p/8)); tol 1e-8 rel per column")
+
+
+def run_batch(args):
+    """64 independent uneven problems (9 right-hand sides each) in one batched
+    mixed-precision solve; a step is one kpcg_batch_solve of the whole batch."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    problems = synthetic.config4_problems(seed=rank)
+    probs, B = [], []
+    c = 9
+    for k, p in enumerate(problems):
+        m = min(512, max(64, p.n // 8))
+        probs.append((torch.from_numpy(p.X).to(dev), p.log_theta, p.noise,
+                      synthetic.inducing_subset(p.n, m, seed=300 + k)))
+        B.append(np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)]))
+    opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=0.25, max_iter=20000,
+                               max_outer=40, profile=1)
+    b = kpcg.Batch(probs, options=opt)
+    G, ctas, tune_ms = b.tune(c)
+    Bb = b.block(B)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        b.solve(Bb, c, tol=TOL, raise_on_error=False)
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+    stop_clock = sm_clock_probe()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X, iters, rel, info, st = b.solve(Bb, c, tol=TOL, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = stop_clock()
+    t_step = statistics.mean(times)
+    # batched tensor-core product: per entry one ex2 and c FMAs on the FP32
+    # side.  Inside the solve, converged problems are skipped, so the average
+    # call does less than a full product; time one full product instead (all
+    # problems, the tuned tiling; staging and reduction included).
+    entries = float(sum(p.n ** 2 for p in problems))
+    ops = entries * (c + 1)
+    Vf = b.empty(c, torch.float32)
+    Vf.normal_()
+    for _ in range(2):
+        b.matvec_f32(Vf, c)
+    torch.cuda.synchronize(dev)
+    ef0 = torch.cuda.Event(enable_timing=True)
+    ef1 = torch.cuda.Event(enable_timing=True)
+    ef0.record(stream)
+    for _ in range(5):
+        b.matvec_f32(Vf, c)
+    ef1.record(stream)
+    torch.cuda.synchronize(dev)
+    avg_ms = ef0.elapsed_time(ef1) / 5
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * sm_max * 1e6 / 1e12
+    achieved = ops / (avg_ms / 1e3) / 1e12
+    # end to end from pinned host buffers through the public API
+    Bh = Bb.cpu().pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Bd = Bh.to(dev, non_blocking=True)
+    Xd, _, _, _, _ = b.solve(Bd, c, tol=TOL, raise_on_error=False)
+    Xh.copy_(Xd, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    line = {
+        "metric": "time to solve 64 uneven problems (9 RHS each) to rel-res 1e-8",
+        "value": t_step, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "preconditioners": "built at the first solve (warm-up), reused",
+                   "tiles_per_item": G, "ctas": ctas, "tune_ms": tune_ms},
+        "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
+                  "max_rel_res_fp64": float(rel.max()), "kv_inner_ms": info.kv_inner_ms,
+                  "kv_inner_calls": info.kv_inner_calls, "kv_outer_ms": info.kv_outer_ms,
+                  "kv_outer_calls": info.kv_outer_calls, "precond_ms": info.precond_ms,
+                  "precond_calls": info.precond_calls, "step_times_s": times},
+        "roofline": {"bound": "alu", "kernel": "kv_tc_batch_kernel (+stage, reduce), full product",
+                     "achieved": achieved, "peak": peak, "unit": "Top/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"FP32 pipe issue rate 152 x 128 x {sm_max:.0f} MHz (unit counts)",
+                     "ops_per_call": ops, "avg_ms": avg_ms},
+        "clocks": clocks,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Bh.numel() * 8),
+                "d2h_bytes_per_step": int(Xh.numel() * 8)},
+        "gpu_launches": int(info.launches),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,9 +296,13 @@ def main():
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
+    ap.add_argument("--workload", default="solve65k", choices=["solve65k", "batch64"],
+                    help="solve65k: the headline single solve; batch64: 64 uneven problems")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg
@@ -273,10 +384,17 @@ def main():
             peak_src = "nominal GB300 FP64 rate, 1.25 TFLOP/s = 0.625 Top/s"
             kname = "kv_simt_kernel<double> (native FP64 K.V)"
         achieved = ops / (ms / calls / 1e3) / 1e12
+        traffic, tsrc = None, None
+        if dom == "kv_inner" and prec == kpcg.KPCG_DF64:
+            # ncu capture at n = 16384 (profiles/kv_df_sym_kernel_n16384.md): 2.29 MB of
+            # DRAM reads, 0 writes; the kernel re-reads nothing from DRAM, so its traffic
+            # is its inputs and grows like n, not n^2
+            traffic = 2.29e6 * p.n / 16384
+            tsrc = "dram read+write per launch, ncu at n=16384 scaled by n (inputs only)"
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "Top/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_src, "calls": calls, "avg_ms": ms / calls,
-                "ops_per_call": ops}
+                "unit": "Top/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": tsrc, "peak_source": peak_src, "calls": calls,
+                "avg_ms": ms / calls, "ops_per_call": ops}
     else:
         # Nystrom apply streams K_XU (n x m FP32) twice and reads/writes n-vectors
         bytes_ = 2 * 4.0 * p.n * M_INDUCING + 3 * 8.0 * p.n
