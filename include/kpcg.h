@@ -342,6 +342,11 @@ kpcg_status kpcg_batch_precond_apply_f32(kpcg_batch_t b, const float* R, int64_t
  * Outputs (host, nullable): the chosen length, CTAs, and its time in ms. */
 kpcg_status kpcg_batch_tune(kpcg_batch_t b, int32_t c, int32_t* tiles_per_item, int32_t* ctas,
                             float* best_ms);
+/* Replace the options of the batch and of its problems (precision must stay
+ * KPCG_TC_IR).  With opt->profile == 0 the inner CG replays chunks of
+ * check_every iterations from a captured CUDA graph; with profiling on it
+ * launches kernel by kernel so each kind can be timed. */
+kpcg_status kpcg_batch_set_options(kpcg_batch_t b, const kpcg_options* opt);
 /* Fix the tiling (ctas = 0: one CTA per SM); disables the autotuner. */
 kpcg_status kpcg_batch_set_tiling(kpcg_batch_t b, int32_t tiles_per_item, int32_t ctas);
 /* max_p n_p: the smallest valid ld. */

@@ -33,7 +33,8 @@ SYMBOLS = (
     "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
     "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error", "kpcg_batch_create",
     "kpcg_batch_solve", "kpcg_batch_matvec_f32", "kpcg_batch_precond_apply_f32",
-    "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_max_n", "kpcg_batch_destroy",
+    "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
+    "kpcg_batch_destroy",
     "kpcg_batch_last_error",
 )
 
@@ -156,6 +157,7 @@ def lib():
         L.kpcg_batch_tune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), pflt]
         L.kpcg_batch_set_tiling.argtypes = [vp, i32, i32]
+        L.kpcg_batch_set_options.argtypes = [vp, ctypes.POINTER(Options)]
         L.kpcg_batch_max_n.argtypes = [vp]
         L.kpcg_batch_max_n.restype = ctypes.c_int64
         L.kpcg_batch_destroy.argtypes = [vp]
@@ -609,6 +611,9 @@ class Batch:
         self._check(lib().kpcg_batch_tune(self._h, c, ctypes.byref(g), ctypes.byref(n),
                                           ctypes.byref(ms)))
         return int(g.value), int(n.value), float(ms.value)
+
+    def set_options(self, options: Options):
+        self._check(lib().kpcg_batch_set_options(self._h, ctypes.byref(options)))
 
     def set_tiling(self, tiles_per_item, ctas=0):
         self._check(lib().kpcg_batch_set_tiling(self._h, int(tiles_per_item), int(ctas)))

@@ -186,7 +186,38 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
     KPCG_CUDA(cudaMemcpyAsync(hf, S.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     KPCG_CUDA(cudaStreamSynchronize(st));
     int active = hf[0];
+    // Graph path (h.use_graph, profiling off): after one plain chunk (which
+    // makes every lazy allocation), `every` whole iterations and the read-back
+    // of the activity flags are captured once into a CUDA graph and replayed.
+    // Iterations past convergence inside a chunk change nothing: stopped
+    // columns have alpha = beta = 0.
+    GraphChunk chunk;
+    const bool graphs = h.use_graph && !h.prof.on;
+    auto body = [&](cudaStream_t s) {
+        matvec(p, ld, c, q, ld);
+        dot_cols<T>(p, ld, q, ld, n, c, partial, nblk, s);
+        finalize(partial, nblk, c, FIN_ALPHA, S, tol, tol_mode, n, nullptr, s);
+        update_xr<T>(X, ldx, r, ld, p, ld, q, ld, n, c, S.alpha, partial, nblk, s);
+        finalize(partial, nblk, c, FIN_RR, S, tol, tol_mode, n, nullptr, s);
+        precond(r, ld, c, z, ld);
+        dot_cols<T>(r, ld, z, ld, n, c, partial, nblk, s);
+        finalize(partial, nblk, c, FIN_BETA, S, tol, tol_mode, n, nullptr, s);
+        update_p<T>(p, ld, z, ld, n, c, S.beta, S.active, s);
+    };
     while (active > 0 && it < max_iter) {
+        if (graphs && it >= every && it + every <= max_iter) {
+            if (!chunk.exec)
+                chunk.capture(h, [&](cudaStream_t cs) {
+                    for (int j = 0; j < every; ++j) body(cs);
+                    KPCG_CUDA(cudaMemcpyAsync(hf, S.flags, 2 * sizeof(int),
+                                              cudaMemcpyDeviceToHost, cs));
+                });
+            KPCG_CUDA(cudaGraphLaunch(chunk.exec, st));
+            KPCG_CUDA(cudaStreamSynchronize(st));
+            it += every;
+            active = hf[0];
+            continue;
+        }
         matvec(p, ld, c, q, ld);
         dot_cols<T>(p, ld, q, ld, n, c, partial, nblk, st);
         finalize(partial, nblk, c, FIN_ALPHA, S, tol, tol_mode, n, nullptr, st);

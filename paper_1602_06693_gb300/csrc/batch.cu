@@ -186,6 +186,7 @@ kpcg_status kpcg_batch_create(int32_t nprob, const kpcg_problem* probs, const kp
         b->M.ld = ((b->nmax + 127) / 128) * 128;
         b->M.opt = o;
         b->M.d = 1;
+        b->M.use_graph = true;
         KPCG_CUDA(cudaHostAlloc((void**)&b->M.hflags, 4 * sizeof(int), cudaHostAllocDefault));
         b->nrow.need(nr.size());
         KPCG_CUDA(cudaMemcpyAsync(b->nrow.p, nr.data(), sizeof(int64_t) * nr.size(),
@@ -201,6 +202,21 @@ kpcg_status kpcg_batch_create(int32_t nprob, const kpcg_problem* probs, const kp
 }
 
 int64_t kpcg_batch_max_n(kpcg_batch_t b) { return b ? b->nmax : 0; }
+
+kpcg_status kpcg_batch_set_options(kpcg_batch_t b, const kpcg_options* opt) {
+    if (!b) return KPCG_ERR_ARG;
+    BATCH_GUARD(b, {
+        if (!opt) fail(KPCG_ERR_ARG, "opt is NULL");
+        if (opt->precision != KPCG_TC_IR)
+            fail(KPCG_ERR_ARG, "batch solves run the tensor-core mixed-precision mode");
+        for (auto* h : b->sub) {
+            const kpcg_status st = kpcg_set_options(h, opt);
+            if (st != KPCG_OK) fail(st, kpcg_last_error(h));
+        }
+        b->M.opt = *opt;
+    });
+    return KPCG_OK;
+}
 
 kpcg_status kpcg_batch_set_tiling(kpcg_batch_t b, int32_t tiles_per_item, int32_t ctas) {
     if (!b) return KPCG_ERR_ARG;

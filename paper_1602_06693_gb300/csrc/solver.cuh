@@ -34,6 +34,44 @@ struct ActiveScope {
     ~ActiveScope() { h.cg_active = saved; }
 };
 
+// One captured chunk of CG iterations.  capture(h, f) records f(cs) on a
+// private non-blocking stream cs (the handle's stream may be the legacy
+// default stream, which cannot be captured) while h.stream points at cs, so
+// operators that launch on h.stream are recorded too; the graph is then
+// launched on the handle's own stream.
+struct GraphChunk {
+    cudaGraphExec_t exec = nullptr;
+    template <typename F>
+    void capture(Ctx& h, F&& f) {
+        cudaStream_t cs = nullptr;
+        KPCG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaStream_t saved = h.stream;
+        h.stream = cs;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            try {
+                f(cs);
+            } catch (...) {
+                cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+                h.stream = saved;
+                cudaStreamDestroy(cs);
+                throw;
+            }
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        h.stream = saved;
+        cudaStreamDestroy(cs);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        KPCG_CUDA(e);
+    }
+    ~GraphChunk() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb, int c,
                       double tol, const double* X0, double* Xout, int64_t ldx,
                       std::vector<int>& iters_col, int& iters_total, int& steps,

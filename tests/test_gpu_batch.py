@@ -144,6 +144,25 @@ def test_batched_solve_matches_oracle(kpcg):
     assert info.iters_total > 0 and info.outer_steps >= 1
 
 
+def test_graph_replay_matches_kernel_by_kernel(kpcg):
+    # the inner CG replayed from captured CUDA graphs (profiling off) runs the
+    # same kernels in the same order as the kernel-by-kernel path
+    sizes = [(300, 4, 1e-3), (900, 8, 1e-2), (513, 12, 1e-1)]
+    probs = _problems(sizes, seed=40, m_frac=4, none_at=())
+    c = 2
+    B = [np.column_stack([p.y, synthetic.rademacher(p.n, 1, 500 + k)])
+         for k, (p, _) in enumerate(probs)]
+    out = []
+    for profile in (1, 0):
+        with _batch(kpcg, probs, inner_shift=0.25, profile=profile, check_every=3) as b:
+            b.set_tiling(8)  # the same summation order on both sides
+            Xb, iters, rel, info, rc = b.solve(b.block(B), c, tol=1e-8)
+            out.append((Xb.cpu().numpy(), iters, rel))
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[1][2].max() <= 1e-8
+
+
 def test_sixty_four_uneven_problems(kpcg):
     # 64 problems, n ~ LogU[512, 16384], d in 2..16, y plus 8 Rademacher probes each
     problems = synthetic.config4_problems(seed=0)
