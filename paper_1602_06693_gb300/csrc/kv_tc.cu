@@ -738,21 +738,21 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                     float ev[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) ev[q] = ex2(__uint_as_float(r[q]));
+                    // every accumulator runs; those past ncols read stale staging
+                    // memory and are never stored (no per-column branch here)
 #pragma unroll
                     for (int k = 0; k < CB; ++k) {
-                        if (k < ncols) {
-                            const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
-                            float a = acc[k];
+                        const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
+                        float a = acc[k];
 #pragma unroll
-                            for (int j4 = 0; j4 < 4; ++j4) {
-                                const float4 v = vp[j4];
-                                a = fmaf(ev[4 * j4 + 0], v.x, a);
-                                a = fmaf(ev[4 * j4 + 1], v.y, a);
-                                a = fmaf(ev[4 * j4 + 2], v.z, a);
-                                a = fmaf(ev[4 * j4 + 3], v.w, a);
-                            }
-                            acc[k] = a;
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            const float4 v = vp[j4];
+                            a = fmaf(ev[4 * j4 + 0], v.x, a);
+                            a = fmaf(ev[4 * j4 + 1], v.y, a);
+                            a = fmaf(ev[4 * j4 + 2], v.z, a);
+                            a = fmaf(ev[4 * j4 + 3], v.w, a);
                         }
+                        acc[k] = a;
                     }
                 }
                 fence_before();
@@ -910,7 +910,8 @@ void kv_tc_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64
     for (const auto& pb : b.hprobs) nmax_pad = std::max<int64_t>(nmax_pad, pb.n_pad);
     for (int k0 = 0; k0 < c;) {
         const int rem = c - k0;
-        const int cb = rem > 8 ? 16 : rem > 4 ? 8 : rem > 2 ? 4 : rem > 1 ? 2 : 1;
+        const int cb = rem > 12 ? 16 : rem > 9 ? 12 : rem == 9 ? 9 : rem > 4 ? 8 : rem > 2 ? 4
+                                                                           : rem;
         const int ncols = std::min(cb, rem);
         tc_batch_stage_v_kernel<<<dim3((unsigned)std::min<int64_t>((nmax_pad + 255) / 256, 64),
                                        (unsigned)b.P),
@@ -921,6 +922,8 @@ void kv_tc_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64
             case 2: launch_tc_batch<2>(b, ncols, active, c, st); break;
             case 4: launch_tc_batch<4>(b, ncols, active, c, st); break;
             case 8: launch_tc_batch<8>(b, ncols, active, c, st); break;
+            case 9: launch_tc_batch<9>(b, ncols, active, c, st); break;
+            case 12: launch_tc_batch<12>(b, ncols, active, c, st); break;
             default: launch_tc_batch<16>(b, ncols, active, c, st); break;
         }
         tc_batch_reduce_kernel<<<dim3((unsigned)std::min<int64_t>((nrows + 255) / 256, 64),
