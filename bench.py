@@ -184,6 +184,9 @@ BATCH_WORKLOAD = ("64 ARD-RBF problems, n~LogU[512,16384], d~U{2..16}, l_r~LogU(
                   "each; Nystrom m_p=min(512,max(64,n_p/8)); tol 1e-8 rel per column")
 
 
+BATCH_SHIFT = 0.25
+
+
 def run_batch(args):
     """64 independent uneven problems (9 right-hand sides each) in one batched
     mixed-precision solve; a step is one kpcg_batch_solve of the whole batch."""
@@ -202,8 +205,12 @@ def run_batch(args):
         probs.append((torch.from_numpy(p.X).to(dev), p.log_theta, p.noise,
                       synthetic.inducing_subset(p.n, m, seed=300 + k)))
         B.append(np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)]))
-    opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=0.25, max_iter=20000,
-                               max_outer=40, profile=1)
+    opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=BATCH_SHIFT,
+                               max_iter=args.batch_max_iter, max_outer=40, profile=1)
+    if args.inner_shift is not None:
+        opt.inner_shift = args.inner_shift
+    if args.inner_tol is not None:
+        opt.inner_tol = args.inner_tol
     b = kpcg.Batch(probs, options=opt)
     G, ctas, tune_ms = b.tune(c)
     Bb = b.block(B)
@@ -270,6 +277,7 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "l2": "flushed between steps (256 MB write)",
                    "preconditioners": "built at the first solve (warm-up), reused",
+                   "inner_shift": opt.inner_shift, "inner_tol": opt.inner_tol,
                    "tiles_per_item": G, "ctas": ctas, "tune_ms": tune_ms},
         "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
                   "max_rel_res_fp64": float(rel.max()), "inner_iterations_in_graphs": True,
@@ -307,6 +315,11 @@ def main():
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
     ap.add_argument("--workload", default="solve65k", choices=["solve65k", "batch64"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
+    ap.add_argument("--batch-max-iter", type=int, default=20000,
+                    help="batch64: cap on inner iterations (short runs for profiling)")
+    ap.add_argument("--inner-shift", type=float, default=None,
+                    help="batch64: shift of the inner operator, in units of each noise")
+    ap.add_argument("--inner-tol", type=float, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

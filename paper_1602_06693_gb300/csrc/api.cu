@@ -28,6 +28,7 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
 
 static thread_local long long g_launches = 0;
 void note_launch() { ++g_launches; }
+void note_launches(long long k) { g_launches += k; }
 long long launch_count() { return g_launches; }
 
 int padded_dim(int d) {
@@ -213,6 +214,7 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
                                               cudaMemcpyDeviceToHost, cs));
                 });
             KPCG_CUDA(cudaGraphLaunch(chunk.exec, st));
+            note_launches(chunk.kernels);
             KPCG_CUDA(cudaStreamSynchronize(st));
             it += every;
             active = hf[0];

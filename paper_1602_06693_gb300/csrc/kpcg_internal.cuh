@@ -23,6 +23,8 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define KPCG_CUDA(call) ::kpcg::cuda_check((call), #call, __FILE__, __LINE__)
 // Checks a kernel launch and counts it (per host thread).
 void note_launch();
+// count k kernel launches made by replaying a captured graph
+void note_launches(long long k);
 long long launch_count();
 #define KPCG_LAUNCHED(name) \
     (::kpcg::note_launch(), ::kpcg::cuda_check(cudaGetLastError(), name, __FILE__, __LINE__))

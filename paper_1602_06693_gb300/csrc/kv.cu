@@ -166,6 +166,14 @@ void launch_cb(int cb, const T* xs, int64_t n, T c0, const T* V, int64_t ldv, in
         case 2: launch_chunk<T, DP, 2>(xs, n, c0, V, ldv, ncols, part, s, rpt, st); break;
         case 4: launch_chunk<T, DP, 4>(xs, n, c0, V, ldv, ncols, part, s, rpt, st); break;
         case 8: launch_chunk<T, DP, 8>(xs, n, c0, V, ldv, ncols, part, s, rpt, st); break;
+        case 16:
+            // FP64 only (one pass over up to 16 columns: the FP64 exp is the
+            // expensive part of an entry, so it is computed once per entry)
+            if constexpr (sizeof(T) == 8 && DP <= 16) {
+                launch_chunk<T, DP, 16>(xs, n, c0, V, ldv, ncols, part, s, rpt, st);
+                break;
+            }
+            fail(KPCG_ERR_ARG, "internal: bad column block");
         default: fail(KPCG_ERR_ARG, "internal: bad column block");
     }
 }
@@ -178,11 +186,11 @@ void kv_generic(const T* xs, int64_t n, int dp, T c0, T noise, const T* V, int64
     // Two rows per thread where registers allow (FP32, d <= 16).
     const int rpt = (sizeof(T) == 4 && dp <= 16) ? 2 : 1;
     const Split s = plan(n, KT * rpt);
-    const int max_cb = 8;
+    const int max_cb = (sizeof(T) == 8 && dp <= 16) ? 16 : 8;
     T* part = partbuf.need((size_t)s.nsplit * max_cb * s.ldp);
     for (int k0 = 0; k0 < c;) {
         const int rem = c - k0;
-        const int cb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int cb = (rem > 8 && max_cb == 16) ? 16 : rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
         const int ncols = std::min(cb, rem);
         const T* Vk = V + (int64_t)k0 * ldv;
         switch (dp) {

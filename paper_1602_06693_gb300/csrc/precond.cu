@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "kpcg_internal.cuh"
@@ -860,12 +861,15 @@ __global__ void nys_batch_upper_kernel(const NysBatchProb* __restrict__ probs, i
 // (hi, lo); each term is split exactly (TwoProduct by FMA, plus the two
 // cross terms) and summed with TwoSum (Dot2, Ogita-Rump-Oishi 2005), about
 // 2^-46 relative per term at ~11 FP32 operations.
-template <int NC>
+// With STAGE the problem's u (ncols x m pairs) is first copied to shared
+// memory: every row of the block reads all of it.
+template <int NC, bool STAGE>
 __global__ void __launch_bounds__(256)
     nys_batch_back_kernel(const NysBatchProb* __restrict__ probs, int c, int k0, int ncols,
                           const int* __restrict__ active, const float2* __restrict__ u,
                           const float* __restrict__ R, int64_t ldr, float* __restrict__ Z,
                           int64_t ldz, int64_t nrows) {
+    extern __shared__ float2 su2[];
     const int p = blockIdx.y;
     const NysBatchProb pb = probs[p];
     if (!nb_live(active, p, c)) return;
@@ -874,6 +878,11 @@ __global__ void __launch_bounds__(256)
     const float* Rp = R + ((int64_t)p * c + k0) * ldr;
     float* Zp = Z + ((int64_t)p * c + k0) * ldz;
     const float2* up = u + pb.wbase + (int64_t)k0 * pb.m;
+    if constexpr (STAGE) {
+        for (int64_t e = threadIdx.x; e < (int64_t)ncols * pb.m; e += blockDim.x) su2[e] = up[e];
+        __syncthreads();
+        up = su2;
+    }
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nrows;
          i += warps) {
         if (i >= pb.n || pb.m == 0) {
@@ -890,7 +899,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int k = 0; k < NC; ++k)
                 if (k < ncols) {
-                    const float2 uv = __ldg(up + (int64_t)k * pb.m + a);
+                    const float2 uv = up[(int64_t)k * pb.m + a];
                     dot2_add(acc[k], kv.x, uv.x);
                     acc[k].c = fmaf(kv.x, uv.y, fmaf(kv.y, uv.x, acc[k].c));
                 }
@@ -908,6 +917,16 @@ __global__ void __launch_bounds__(256)
 }
 
 }  // namespace
+
+// Raise a kernel's dynamic shared-memory limit once per size (the first
+// apply runs outside any graph capture; later ones find it raised).
+static void raise_smem_limit(const void* kern, size_t smem) {
+    static std::map<const void*, size_t> done;
+    size_t& have = done[kern];
+    if (smem <= have) return;
+    KPCG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    have = smem;
+}
 
 void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
                     cudaStream_t st) {
@@ -961,6 +980,9 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
             else if (nc <= 8)
                 nys_batch_proj_kernel<8><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
                                                            nb.part.p);
+            else if (nc <= 9)
+                nys_batch_proj_kernel<9><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
+                                                           nb.part.p);
             else
                 nys_batch_proj_kernel<16><<<g, 256, 0, st>>>(nb.probs.p, c, R, ldr, k0, nc, active,
                                                             nb.part.p);
@@ -982,15 +1004,21 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
     for (int k0 = 0; k0 < c; k0 += 16) {
         const int nc = std::min(16, c - k0);
         const dim3 g(blocks, (unsigned)nb.P);
+        const size_t smem = sizeof(float2) * (size_t)nc * (size_t)nb.mmax;
+        const bool stage = smem <= 200 * 1024;
+        auto go = [&](auto kern) {
+            if (stage && smem > 48 * 1024) raise_smem_limit((const void*)kern, smem);
+            kern<<<g, 256, stage ? smem : 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p, R, ldr,
+                                                   Z, ldz, nrows);
+        };
         if (nc <= 4)
-            nys_batch_back_kernel<4><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p, R,
-                                                       ldr, Z, ldz, nrows);
+            stage ? go(nys_batch_back_kernel<4, true>) : go(nys_batch_back_kernel<4, false>);
         else if (nc <= 8)
-            nys_batch_back_kernel<8><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p, R,
-                                                       ldr, Z, ldz, nrows);
+            stage ? go(nys_batch_back_kernel<8, true>) : go(nys_batch_back_kernel<8, false>);
+        else if (nc <= 9)
+            stage ? go(nys_batch_back_kernel<9, true>) : go(nys_batch_back_kernel<9, false>);
         else
-            nys_batch_back_kernel<16><<<g, 256, 0, st>>>(nb.probs.p, c, k0, nc, active, nb.u2.p,
-                                                        R, ldr, Z, ldz, nrows);
+            stage ? go(nys_batch_back_kernel<16, true>) : go(nys_batch_back_kernel<16, false>);
         KPCG_LAUNCHED("nys_batch_back_kernel");
     }
 }

@@ -41,8 +41,10 @@ struct ActiveScope {
 // launched on the handle's own stream.
 struct GraphChunk {
     cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;  // kernel launches recorded, counted again per replay
     template <typename F>
     void capture(Ctx& h, F&& f) {
+        const long long l0 = launch_count();
         cudaStream_t cs = nullptr;
         KPCG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaStream_t saved = h.stream;
@@ -66,6 +68,9 @@ struct GraphChunk {
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
         KPCG_CUDA(e);
+        // the recording launched nothing: take those counts back, replays add them
+        kernels = launch_count() - l0;
+        note_launches(-kernels);
     }
     ~GraphChunk() {
         if (exec) cudaGraphExecDestroy(exec);
