@@ -201,7 +201,7 @@ def run_batch(args):
     probs, B = [], []
     c = 9
     for k, p in enumerate(problems):
-        m = min(512, max(64, p.n // 8))
+        m = min(args.batch_m_max, max(64, p.n // args.batch_m_div))
         probs.append((torch.from_numpy(p.X).to(dev), p.log_theta, p.noise,
                       synthetic.inducing_subset(p.n, m, seed=300 + k)))
         B.append(np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)]))
@@ -257,6 +257,12 @@ def run_batch(args):
     ef1.record(stream)
     torch.cuda.synchronize(dev)
     avg_ms = ef0.elapsed_time(ef1) / 5
+    ef0.record(stream)
+    for _ in range(5):
+        b.precond_apply_f32(Vf, c)
+    ef1.record(stream)
+    torch.cuda.synchronize(dev)
+    precond_full_ms = ef0.elapsed_time(ef1) / 5
     sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
     peak = 152 * 128 * sm_max * 1e6 / 1e12
     achieved = ops / (avg_ms / 1e3) / 1e12
@@ -278,9 +284,11 @@ def run_batch(args):
         "config": {"workload": BATCH_WORKLOAD, "l2": "flushed between steps (256 MB write)",
                    "preconditioners": "built at the first solve (warm-up), reused",
                    "inner_shift": opt.inner_shift, "inner_tol": opt.inner_tol,
+                   "m_max": args.batch_m_max, "m_div": args.batch_m_div,
                    "tiles_per_item": G, "ctas": ctas, "tune_ms": tune_ms},
         "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
                   "max_rel_res_fp64": float(rel.max()), "inner_iterations_in_graphs": True,
+                  "precond_full_apply_ms": precond_full_ms, "kv_full_product_ms": avg_ms,
                   "step_times_s": times,
                   "profiled_solve": {"time_ms": pinfo.time_ms, "kv_inner_ms": pinfo.kv_inner_ms,
                                      "kv_inner_calls": pinfo.kv_inner_calls,
@@ -320,6 +328,9 @@ def main():
     ap.add_argument("--inner-shift", type=float, default=None,
                     help="batch64: shift of the inner operator, in units of each noise")
     ap.add_argument("--inner-tol", type=float, default=None)
+    ap.add_argument("--batch-m-max", type=int, default=512,
+                    help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
+    ap.add_argument("--batch-m-div", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -435,7 +435,12 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
         } else {
             copy_cols<double>(p, ld, Z, ld, n, c, st);
         }
+        // columns that already meet tol have p = 0 exactly (zero right-hand side
+        // for the inner solve, zero window coefficients); operators may skip them
+        h.outer_cols.assign((size_t)c, 0);
+        for (int k = 0; k < c; ++k) h.outer_cols[(size_t)k] = scale[k] > 0.0 ? 1 : 0;
         h.prof.time(Profiler::KV_OUTER, st, [&] { ops.outer_mv(p, ld, c, q, ld); });
+        h.outer_cols.clear();
         dots(2, {{p, q}, {p, R}}, d);
         std::vector<double> al((size_t)c, 0.0), nal((size_t)c);
         for (int k = 0; k < c; ++k) {

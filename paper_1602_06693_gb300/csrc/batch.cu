@@ -318,9 +318,17 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
             nys_batch_apply(bb->nys, R, ldr, Z, ldz, bb->M.n, bb->M.cg_active, bb->M.stream);
         };
         ops.outer_mv = [bb, c](const double* V, int64_t ldv, int, double* O, int64_t ldo) {
+            const auto& live = bb->M.outer_cols;
             for (size_t p = 0; p < bb->sub.size(); ++p) {
                 Ctx& h = *bb->sub[p];
                 const int64_t off = (int64_t)p * c;
+                bool any = live.empty();
+                for (int k = 0; k < c && !any; ++k) any = live[(size_t)off + k] != 0;
+                if (!any) {  // every direction of this problem is zero: so is K_y p
+                    KPCG_CUDA(cudaMemsetAsync(O + off * ldo, 0, sizeof(double) * (size_t)c * ldo,
+                                              bb->M.stream));
+                    continue;
+                }
                 kv_df(h, V + off * ldv, ldv, c, nullptr, 0, O + off * ldo, ldo, h.noise);
             }
         };

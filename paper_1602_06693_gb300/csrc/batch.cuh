@@ -73,6 +73,8 @@ struct NysBatch {
     DevBuf<NysBatchProb> probs;
     DevBuf<double> part, w, y;
     DevBuf<float2> u2;  // u = M^{-1} K_UX r as FP32 pairs for the back product
+    DevBuf<int4> itemsL, itemsU;  // (problem, column, block) items of the triangular applies
+    int nL = 0, nU = 0;
 };
 // Tables for c columns per problem from the problems' Nystrom states
 // (problems without one get m = 0 and the identity).

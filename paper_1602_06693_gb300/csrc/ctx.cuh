@@ -105,6 +105,7 @@ struct Ctx {
     int* hflags = nullptr;  // pinned host [active, broken]
     const int* cg_active = nullptr;  // device flags of the columns the running CG iterates
     bool use_graph = false;          // replay CG iterations from a captured CUDA graph
+    std::vector<char> outer_cols;    // during an outer product: columns with a nonzero direction
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

@@ -802,51 +802,62 @@ __global__ void nys_batch_sum_kernel(const NysBatchProb* __restrict__ probs, int
     w[pb.wbase + e] = s;
 }
 
-// y = L^{-1} w per problem and column (same scheme as tri_lower_apply_kernel)
+// y = L^{-1} w per problem and column (same scheme as tri_lower_apply_kernel).
+// A bounded grid walks the flat list of (problem, column, 32-row block)
+// items, so items of finished problems cost a flag test, not a CTA.
 __global__ void __launch_bounds__(1024)
     nys_batch_lower_kernel(const NysBatchProb* __restrict__ probs, int c,
-                           const int* __restrict__ active, const double* __restrict__ w,
-                           double* __restrict__ y) {
+                           const int* __restrict__ active, const int4* __restrict__ items,
+                           int nitems, const double* __restrict__ w, double* __restrict__ y) {
     __shared__ double part[32][33];
-    const int p = blockIdx.z, k = blockIdx.y;
-    const NysBatchProb pb = probs[p];
-    const int64_t m = pb.m;
-    if ((int64_t)blockIdx.x * 32 >= m || !nb_live(active, p, c)) return;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
-    const double* wk = w + pb.wbase + (int64_t)k * m;
-    double s = 0.0;
-    if (i < m)
-        for (int64_t j = g; j <= i; j += 32) s = fma(pb.U[j * m + i], wk[j], s);
-    part[g][lane] = s;
-    __syncthreads();
-    if (g == 0 && i < m) {
-        double t = 0.0;
-        for (int q = 0; q < 32; ++q) t += part[q][lane];
-        y[pb.wbase + (int64_t)k * m + i] = t;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 wk = items[it];
+        const int p = wk.x, k = wk.y;
+        if (!nb_live(active, p, c)) continue;  // uniform over the block
+        const NysBatchProb& pb = probs[p];
+        const int64_t m = pb.m;
+        const int64_t i = (int64_t)wk.z * 32 + lane;
+        const double* wk_ = w + pb.wbase + (int64_t)k * m;
+        double s = 0.0;
+        if (i < m)
+            for (int64_t j = g; j <= i; j += 32) s = fma(pb.U[j * m + i], wk_[j], s);
+        part[g][lane] = s;
+        __syncthreads();
+        if (g == 0 && i < m) {
+            double t = 0.0;
+            for (int q = 0; q < 32; ++q) t += part[q][lane];
+            y[pb.wbase + (int64_t)k * m + i] = t;
+        }
+        __syncthreads();
     }
 }
 
-// u = L^{-T} y (warp per entry), written over w and as FP32 pairs (hi, lo)
+// u = L^{-T} y (warp per entry; items of 8 entries), written over w and as
+// FP32 pairs (hi, lo)
 __global__ void nys_batch_upper_kernel(const NysBatchProb* __restrict__ probs, int c,
                                        const int* __restrict__ active,
+                                       const int4* __restrict__ items, int nitems,
                                        const double* __restrict__ y, double* __restrict__ u,
                                        float2* __restrict__ u2) {
-    const int p = blockIdx.z, k = blockIdx.y;
-    const NysBatchProb pb = probs[p];
-    const int64_t m = pb.m;
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= m || !nb_live(active, p, c)) return;
-    const double* yk = y + pb.wbase + (int64_t)k * m;
-    const double* Uj = pb.U + j * m;
-    double s = 0.0;
-    for (int64_t i = j + lane; i < m; i += 32) s = fma(Uj[i], yk[i], s);
-    s = warp_sum(s);
-    if (lane == 0) {
-        u[pb.wbase + (int64_t)k * m + j] = s;
-        const float hi = (float)s;
-        u2[pb.wbase + (int64_t)k * m + j] = make_float2(hi, (float)(s - (double)hi));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 wk = items[it];
+        const int p = wk.x, k = wk.y;
+        const NysBatchProb& pb = probs[p];
+        const int64_t m = pb.m;
+        const int64_t j = (int64_t)wk.z * 8 + warp;
+        if (j >= m || !nb_live(active, p, c)) continue;
+        const double* yk = y + pb.wbase + (int64_t)k * m;
+        const double* Uj = pb.U + j * m;
+        double s = 0.0;
+        for (int64_t i = j + lane; i < m; i += 32) s = fma(Uj[i], yk[i], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            u[pb.wbase + (int64_t)k * m + j] = s;
+            const float hi = (float)s;
+            u2[pb.wbase + (int64_t)k * m + j] = make_float2(hi, (float)(s - (double)hi));
+        }
     }
 }
 
@@ -955,6 +966,24 @@ void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, in
         nb.mmax = std::max(nb.mmax, q.m);
         nb.nsplit_max = std::max(nb.nsplit_max, (int)q.nsplit);
     }
+    std::vector<int4> L, U;
+    for (int p = 0; p < nb.P; ++p) {
+        const int64_t m = nb.hprobs[(size_t)p].m;
+        for (int k = 0; k < c; ++k) {
+            for (int64_t ib = 0; ib * 32 < m; ++ib) L.push_back(make_int4(p, k, (int)ib, 0));
+            for (int64_t jb = 0; jb * 8 < m; ++jb) U.push_back(make_int4(p, k, (int)jb, 0));
+        }
+    }
+    nb.nL = (int)L.size();
+    nb.nU = (int)U.size();
+    nb.itemsL.need(std::max<size_t>(1, L.size()));
+    nb.itemsU.need(std::max<size_t>(1, U.size()));
+    if (!L.empty())
+        KPCG_CUDA(cudaMemcpyAsync(nb.itemsL.p, L.data(), sizeof(int4) * L.size(),
+                                  cudaMemcpyHostToDevice, st));
+    if (!U.empty())
+        KPCG_CUDA(cudaMemcpyAsync(nb.itemsU.p, U.data(), sizeof(int4) * U.size(),
+                                  cudaMemcpyHostToDevice, st));
     nb.probs.need(nb.hprobs.size());
     nb.part.need((size_t)std::max<int64_t>(1, nb.ptotal));
     nb.w.need((size_t)std::max<int64_t>(1, nb.wtotal));
@@ -991,13 +1020,13 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
         nys_batch_sum_kernel<<<dim3((unsigned)((c * nb.mmax + 255) / 256), (unsigned)nb.P), 256, 0,
                                st>>>(nb.probs.p, c, active, nb.part.p, nb.w.p);
         KPCG_LAUNCHED("nys_batch_sum_kernel");
-        nys_batch_lower_kernel<<<dim3((unsigned)((nb.mmax + 31) / 32), (unsigned)c,
-                                      (unsigned)nb.P),
-                                 1024, 0, st>>>(nb.probs.p, c, active, nb.w.p, nb.y.p);
+        nys_batch_lower_kernel<<<(unsigned)std::max(1, std::min(nb.nL, 2 * 152)), 1024, 0,
+                                 st>>>(nb.probs.p, c, active, nb.itemsL.p, nb.nL, nb.w.p,
+                                       nb.y.p);
         KPCG_LAUNCHED("nys_batch_lower_kernel");
-        nys_batch_upper_kernel<<<dim3((unsigned)((nb.mmax * 32 + 255) / 256), (unsigned)c,
-                                      (unsigned)nb.P),
-                                 256, 0, st>>>(nb.probs.p, c, active, nb.y.p, nb.w.p, nb.u2.p);
+        nys_batch_upper_kernel<<<(unsigned)std::max(1, std::min(nb.nU, 8 * 152)), 256, 0,
+                                 st>>>(nb.probs.p, c, active, nb.itemsU.p, nb.nU, nb.y.p, nb.w.p,
+                                       nb.u2.p);
         KPCG_LAUNCHED("nys_batch_upper_kernel");
     }
     const unsigned blocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 256);
