@@ -212,6 +212,25 @@ def run_batch(args):
     if args.inner_tol is not None:
         opt.inner_tol = args.inner_tol
     b = kpcg.Batch(probs, options=opt)
+    if args.probe != "none":
+        b.set_tiling(8)
+        Vf = b.empty(c, torch.float32)
+        Vf.normal_()
+        fn = b.matvec_f32 if args.probe == "kv" else b.precond_apply_f32
+        fn(Vf, c)  # builds the preconditioners / operands
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ms = []
+        for r in range(3):
+            ev[0].record(stream)
+            fn(Vf, c)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(ev[0].elapsed_time(ev[1]))
+        print(json.dumps({"probe": args.probe, "ms": ms, "workload": BATCH_WORKLOAD,
+                          "m_max": args.batch_m_max, "m_div": args.batch_m_div}))
+        b.close()
+        return
     G, ctas, tune_ms = b.tune(c)
     Bb = b.block(B)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -331,6 +350,9 @@ def main():
     ap.add_argument("--batch-m-max", type=int, default=512,
                     help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
     ap.add_argument("--batch-m-div", type=int, default=8)
+    ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
+                    help="batch64: only time full batched products (kv) or preconditioner "
+                         "applies (precond) and exit; a small target for profilers")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
