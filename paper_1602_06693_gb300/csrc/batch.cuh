@@ -64,6 +64,7 @@ struct NysBatchProb {
     int64_t pbase;      // offset of the problem in the split partials
     int32_t nsplit, rows_per_split;
     double inv_noise;
+    float inv_noise_f;
 };
 struct NysBatch {
     int P = 0, c = 0;

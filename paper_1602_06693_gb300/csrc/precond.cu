@@ -915,13 +915,30 @@ __global__ void __launch_bounds__(256)
                     acc[k].c = fmaf(kv.x, uv.y, fmaf(kv.y, uv.x, acc[k].c));
                 }
         }
+        // warp sum of the pairs with TwoSum on every step (FP64 adds would
+        // hold the FP64 pipe, ~1/64 rate, longer than the whole sweep above)
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             if (k < ncols) {
-                const double sm = warp_sum((double)acc[k].s + (double)acc[k].c);
-                if (lane == 0)
-                    Zp[i + (int64_t)k * ldz] =
-                        (float)(((double)Rp[i + (int64_t)k * ldr] - sm) * pb.inv_noise);
+                float hs = acc[k].s, hc = acc[k].c;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float os = __shfl_xor_sync(0xffffffffu, hs, o);
+                    const float oc = __shfl_xor_sync(0xffffffffu, hc, o);
+                    const float t = hs + os;
+                    const float z = t - hs;
+                    const float e = (hs - (t - z)) + (os - z);
+                    hs = t;
+                    hc = hc + oc + e;
+                }
+                if (lane == 0) {
+                    // z = (r - (hs + hc)) / sigma^2: r - hs by TwoSum, then the tails
+                    const float r = Rp[i + (int64_t)k * ldr];
+                    const float d = r - hs;
+                    const float bv = d - r;
+                    const float de = (r - (d - bv)) + (-hs - bv);
+                    Zp[i + (int64_t)k * ldz] = (d + (de - hc)) * pb.inv_noise_f;
+                }
             }
         }
     }
@@ -957,6 +974,7 @@ void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, in
         q.KXU = on ? P.KXU.p : nullptr;
         q.U = on ? P.U.p : nullptr;
         q.inv_noise = on ? 1.0 / P.noise : 1.0;
+        q.inv_noise_f = (float)q.inv_noise;
         q.rows_per_split = kSplitRows;
         q.nsplit = (int32_t)std::max<int64_t>(1, (P.n + kSplitRows - 1) / kSplitRows);
         q.wbase = nb.wtotal;
