@@ -181,10 +181,10 @@ def run_reference(args):
 # --------------------------------------------------------------------- GPU
 BATCH_WORKLOAD = ("64 ARD-RBF problems, n~LogU[512,16384], d~U{2..16}, l_r~LogU(0.3,3)*sqrt(d), "
                   "s^2~LogU(0.5,2), noise~LogU(1e-4,1e-1), X~N(0,I); y plus 8 Rademacher probes "
-                  "each; Nystrom m_p=min(512,max(64,n_p/8)); tol 1e-8 rel per column")
+                  "each; Nystrom m_p=min(m_max,max(64,n_p/m_div)); tol 1e-8 rel per column")
 
 
-BATCH_SHIFT = 0.25
+BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
 
 
 def run_batch(args):
@@ -206,7 +206,8 @@ def run_batch(args):
                       synthetic.inducing_subset(p.n, m, seed=300 + k)))
         B.append(np.column_stack([p.y, synthetic.rademacher(p.n, c - 1, 400 + k)]))
     opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=BATCH_SHIFT,
-                               max_iter=args.batch_max_iter, max_outer=40, profile=1)
+                               inner_tol=BATCH_INNER_TOL, max_iter=args.batch_max_iter,
+                               max_outer=40, profile=1)
     if args.inner_shift is not None:
         opt.inner_shift = args.inner_shift
     if args.inner_tol is not None:
@@ -347,9 +348,9 @@ def main():
     ap.add_argument("--inner-shift", type=float, default=None,
                     help="batch64: shift of the inner operator, in units of each noise")
     ap.add_argument("--inner-tol", type=float, default=None)
-    ap.add_argument("--batch-m-max", type=int, default=512,
+    ap.add_argument("--batch-m-max", type=int, default=1024,
                     help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
-    ap.add_argument("--batch-m-div", type=int, default=8)
+    ap.add_argument("--batch-m-div", type=int, default=4)
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
                     help="batch64: only time full batched products (kv) or preconditioner "
                          "applies (precond) and exit; a small target for profilers")
