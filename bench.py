@@ -184,6 +184,76 @@ BATCH_WORKLOAD = ("64 ARD-RBF problems, n~LogU[512,16384], d~U{2..16}, l_r~LogU(
                   "each; Nystrom m_p=min(m_max,max(64,n_p/m_div)); tol 1e-8 rel per column")
 
 
+GRAD_WORKLOAD = ("ARD-RBF n=45730 d=9, standardized Gaussian X, l_r=exp(N(0,0.5^2))*sqrt(d), s=1, "
+                 "noise=1e-3; y plus t=16 Rademacher probes solved as one block; Nystrom m=512 "
+                 "built in-step; tol 1e-8 rel per column; gradient of log p for all 11 parameters")
+
+
+def run_grad(args):
+    """One step: Nystrom set-up plus the stochastic gradient of Eq. 2 (one
+    17-column block solve and the fused derivative products)."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = synthetic.config3(seed=rank)
+    idx = synthetic.inducing_subset(p.n, 512, seed=2 + rank)
+    prec = {"auto": kpcg.KPCG_TC_IR, "tc_ir": kpcg.KPCG_TC_IR, "df64": kpcg.KPCG_DF64,
+            "fp32_ir": kpcg.KPCG_FP32_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+    opt = kpcg.default_options(precision=prec, profile=1, inner_shift=0.25, inner_tol=0.2)
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    R = torch.from_numpy(synthetic.rademacher(p.n, 16, 77 + rank)).to(dev).t().contiguous().t()
+    s = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        s.set_theta(p.log_theta, p.noise)
+        s.precond(kpcg.KPCG_PREC_NYSTROM, len(idx), idx)
+        return s.grad(y, R, tol=TOL)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+    stop_clock = sm_clock_probe()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g, _, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = stop_clock()
+    t_step = statistics.mean(times)
+    line = {
+        "metric": "time per stochastic log-likelihood gradient (17-RHS block solve + dK/dtheta.V)",
+        "value": t_step, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
+        "config": {"workload": GRAD_WORKLOAD, "precision": args.precision,
+                   "l2": "flushed between steps (256 MB write)"},
+        "solve": {"iters_total": info.iters_total, "outer_steps": info.outer_steps,
+                  "max_rel_res_fp64": info.max_rel_res, "kv_inner_ms": info.kv_inner_ms,
+                  "kv_inner_calls": info.kv_inner_calls, "kv_outer_ms": info.kv_outer_ms,
+                  "kv_outer_calls": info.kv_outer_calls, "precond_ms": info.precond_ms,
+                  "precond_calls": info.precond_calls, "step_times_s": times},
+        "grad": [float(v) for v in g],
+        "clocks": clocks,
+        "gpu_launches": int(info.launches),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+
+
 BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
 
 
@@ -341,7 +411,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
-    ap.add_argument("--workload", default="solve65k", choices=["solve65k", "batch64"],
+    ap.add_argument("--workload", default="solve65k", choices=["solve65k", "batch64", "grad45k"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -359,6 +429,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "grad45k":
+        return run_grad(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg

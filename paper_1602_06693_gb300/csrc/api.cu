@@ -250,8 +250,15 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
 static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const double* X, int64_t ldx,
                          double* R, std::vector<double>& rr, std::vector<double>& bb) {
     cudaStream_t st = h.stream;
+    // symmetric tile pairs halve the FP64 exp work but take at most two
+    // columns per pass; from three columns on, one non-symmetric pass over up
+    // to 16 columns computes each entry's exp fewer times
     h.prof.time(Profiler::KV_OUTER, st, [&] {
-        kv_f64_sym(h, X, ldx, c, B, ldb, R, h.ld, h.noise);
+        if (c >= 3 && h.dp <= 16)
+            kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, X, ldx, c, B, ldb, R, h.ld, h.kvws,
+                   st);
+        else
+            kv_f64_sym(h, X, ldx, c, B, ldb, R, h.ld, h.noise);
     });
     const int nblk = dot_blocks(h.n);
     double* partial = h.partial.need((size_t)nblk * c * 2);
@@ -486,8 +493,10 @@ static MixedOps single_ops(Ctx& h) {
     o.inner_pc = [hp](const float* R, int64_t ldr, int cc, float* Z, int64_t ldz) {
         precond_apply_f32(hp->P, R, ldr, cc, Z, ldz, hp->stream);
     };
+    // directions of the outer loop: double-float (their product error scales
+    // with the correction); true residuals stay native FP64 (residual_f64)
     o.outer_mv = [hp](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
-        kv_f64_sym(*hp, V, ldv, cc, nullptr, 0, O, ldo, hp->noise);
+        kv_df(*hp, V, ldv, cc, nullptr, 0, O, ldo, hp->noise);
     };
     o.residual = [hp](const double* B, int64_t ldb, int cc, const double* X, int64_t ldx,
                       double* R, std::vector<double>& rr, std::vector<double>& bb) {

@@ -338,6 +338,30 @@ def test_full_size_double_float_solve_sampled_rows(kpcg):
     assert np.abs(r).max() <= 1e-8 * np.linalg.norm(p.y)
 
 
+def test_full_size_gradient_block_sampled_rows(kpcg):
+    # The n = 45730, d = 9, noise 1e-3 ARD system with y and 16 probes solved as
+    # one block inside kpcg_grad (tensor-core inner PCG, FP64 flexible outer
+    # loop), as timed by `bench.py --workload grad45k`.  alpha is checked on 48
+    # sampled rows recomputed by the oracle; the solve's own FP64 residual
+    # covers all 17 columns.
+    p = synthetic.config3(seed=0)
+    idx = synthetic.inducing_subset(p.n, 512, seed=2)
+    R = synthetic.rademacher(p.n, 16, 77)
+    with _solver(kpcg, p, precision=kpcg.KPCG_TC_IR, inner_shift=0.25, inner_tol=0.2,
+                 max_iter=20000) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 512, idx)
+        g, alpha, info = s.grad(torch.from_numpy(p.y).to(DEV), _cm(R), tol=1e-8,
+                                want_alpha=True)
+    assert info.max_rel_res <= 1e-8, info.as_dict()
+    assert np.all(np.isfinite(g)) and g.shape == (p.d + 2,)
+    a = _np(alpha)
+    rows = np.sort(synthetic.rng(5).choice(p.n, 48, replace=False))
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    Krow = oracle.gram(p.X[rows], p.X, ell, s2)
+    r = p.y[rows] - (Krow @ a + p.noise * a[rows])
+    assert np.abs(r).max() <= 1e-8 * np.linalg.norm(p.y)
+
+
 # ------------------------------------------------------------- gradients
 def test_dkv_matches_oracle(kpcg):
     p = _problem(900, 6, seed=31)
