@@ -292,6 +292,7 @@ static double precond_noise(const Ctx& h) {
 
 static void build_precond(Ctx& h) {
     h.P.reset();
+    ++h.pversion;
     const double nz = precond_noise(h);
     if (h.pkind == KPCG_PREC_NYSTROM)
         nystrom_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), nz,
@@ -490,8 +491,20 @@ static MixedOps single_ops(Ctx& h) {
             kv_f32(h.xs32.p, h.n, h.dp, h.c0_32(), inner_noise, V, ldv, cc, O, ldo, h.kvws,
                    h.stream);
     };
+    // Nystrom: the batched apply for one problem (one projection pass over up to
+    // 16 columns, double-float back product); other kinds: the per-kind apply
     o.inner_pc = [hp](const float* R, int64_t ldr, int cc, float* Z, int64_t ldz) {
-        precond_apply_f32(hp->P, R, ldr, cc, Z, ldz, hp->stream);
+        Ctx& h = *hp;
+        if (h.P.kind == KPCG_PREC_NYSTROM && h.P.ready) {
+            if (h.nys1_c != cc || h.nys1_version != h.pversion) {
+                nys_batch_plan(h.nys1, {&h.P}, cc, h.stream);
+                h.nys1_c = cc;
+                h.nys1_version = h.pversion;
+            }
+            nys_batch_apply(h.nys1, R, ldr, Z, ldz, h.n, nullptr, h.stream);
+        } else {
+            precond_apply_f32(h.P, R, ldr, cc, Z, ldz, h.stream);
+        }
     };
     // directions of the outer loop: double-float (their product error scales
     // with the correction); true residuals stay native FP64 (residual_f64)

@@ -106,6 +106,12 @@ struct Ctx {
     const int* cg_active = nullptr;  // device flags of the columns the running CG iterates
     bool use_graph = false;          // replay CG iterations from a captured CUDA graph
     std::vector<char> outer_cols;    // during an outer product: columns with a nonzero direction
+    // the handle's Nystrom preconditioner as a batch of one problem (FP32 apply of
+    // the mixed solve), planned for nys1_c columns and build nys1_version
+    NysBatch nys1;
+    int nys1_c = -1;
+    long long nys1_version = -1;
+    long long pversion = 0;  // incremented by every preconditioner build
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

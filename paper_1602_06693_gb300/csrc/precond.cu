@@ -1047,7 +1047,9 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
                                        nb.u2.p);
         KPCG_LAUNCHED("nys_batch_upper_kernel");
     }
-    const unsigned blocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 256);
+    // rows per problem: at least ~16 warps per SM over the whole batch
+    const unsigned blocks =
+        (unsigned)std::min<int64_t>((nrows + 7) / 8, std::max(256, 152 * 16 / std::max(1, nb.P)));
     for (int k0 = 0; k0 < c; k0 += 16) {
         const int nc = std::min(16, c - k0);
         const dim3 g(blocks, (unsigned)nb.P);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cmath>
+#include <vector>
 
 #include "kpcg_internal.cuh"
 
@@ -53,5 +54,39 @@ void nystrom_project_solve(const PrecondState& P, const double* R, int64_t ldr, 
 void nystrom_expand(const PrecondState& P, const double* u, double* out, cudaStream_t st);
 void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
                         double noise, int64_t b, cudaStream_t st);
+
+// ------------------------------------------- batched Nystrom apply
+// Problems laid out column by column (problem p owns columns p*c .. p*c+c-1
+// of an ld x (P c) block); a single problem is the batch P = 1.
+struct NysBatchProb {
+    const float2* KXU;  // n x m, FP64 entries as FP32 pairs
+    const double* U;    // L^{-T}, m x m row-major
+    int64_t n, m;
+    int64_t wbase;      // offset of the problem in w / y (c * m doubles)
+    int64_t pbase;      // offset of the problem in the split partials
+    int32_t nsplit, rows_per_split;
+    double inv_noise;
+    float inv_noise_f;
+};
+struct NysBatch {
+    int P = 0, c = 0;
+    int64_t mmax = 0, wtotal = 0, ptotal = 0;
+    int nsplit_max = 0;
+    std::vector<NysBatchProb> hprobs;
+    DevBuf<NysBatchProb> probs;
+    DevBuf<double> part, w, y;
+    DevBuf<float2> u2;  // u = M^{-1} K_UX r as FP32 pairs for the back product
+    DevBuf<int4> itemsL, itemsU;  // (problem, column, block) items of the triangular applies
+    int nL = 0, nU = 0;
+};
+// Tables for c columns per problem from the problems' Nystrom states
+// (problems without one get m = 0 and the identity).
+void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
+                    cudaStream_t st);
+// Z = P_p^{-1} R for every problem (FP32 vectors; FP64 and double-float
+// inside), rows n_p .. nrows-1 zero; the columns of problems with no active
+// column are skipped and left unchanged.
+void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_t ldz,
+                     int64_t nrows, const int* active, cudaStream_t st);
 
 }  // namespace kpcg
