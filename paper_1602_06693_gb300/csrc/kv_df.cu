@@ -493,8 +493,49 @@ void df_launch_cb(int cb, const float4* xs, int64_t n, float c0h, float c0l, con
         case 1: df_launch<DP, 1>(xs, n, c0h, c0l, V, ldv, ncols, tab, part, s, st); break;
         case 2: df_launch<DP, 2>(xs, n, c0h, c0l, V, ldv, ncols, tab, part, s, st); break;
         case 4: df_launch<DP, 4>(xs, n, c0h, c0l, V, ldv, ncols, tab, part, s, st); break;
+        case 8:
+            if constexpr (DP <= 16) {
+                df_launch<DP, 8>(xs, n, c0h, c0l, V, ldv, ncols, tab, part, s, st);
+                break;
+            }
+            fail(KPCG_ERR_ARG, "internal: bad column block");
+        case 16:
+            if constexpr (DP <= 12) {
+                df_launch<DP, 16>(xs, n, c0h, c0l, V, ldv, ncols, tab, part, s, st);
+                break;
+            }
+            fail(KPCG_ERR_ARG, "internal: bad column block");
         default: fail(KPCG_ERR_ARG, "internal: bad column block");
     }
+}
+
+// Widest column block of the plain kernel for a padded dimension (registers).
+static int df_max_cb(int dp) { return dp <= 12 ? 16 : dp <= 16 ? 8 : 4; }
+
+// Column blocks of a product: greedy widest-first, then the smallest block
+// (of the allowed widths) that holds the remainder.
+static std::vector<int> df_blocks(int c, int maxcb) {
+    std::vector<int> out;
+    while (c > 0) {
+        int cb = maxcb;
+        while (cb > 1 && cb / 2 >= c) cb /= 2;
+        out.push_back(cb);
+        c -= std::min(cb, c);
+    }
+    return out;
+}
+
+// FP32-pipe instructions per product (the model of the benchmark): the
+// symmetric kernel evaluates n(n+1)/2 entries per pass of <= 2 columns and
+// spends 24 per entry and column (row and mirrored column), the plain one n^2
+// entries per pass and 12 per entry and column.
+static bool df_prefer_plain(int64_t n, int dp, int c) {
+    const double e = 16.0 * dp + 33.0;
+    double sym = 0.0, plain = 0.0;
+    for (int k = 0; k < c; k += 2) sym += 0.5 * (e + 24.0 * std::min(2, c - k));
+    for (int cb : df_blocks(c, df_max_cb(dp))) plain += e + 12.0 * cb;
+    (void)n;
+    return plain < sym;
 }
 
 }  // namespace
@@ -704,22 +745,23 @@ void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t
            int64_t ldo, double noise) {
     if (h.n <= 0 || c <= 0) return;
     df_prepare(h);
-    // The symmetric kernel pays off once there are several tile pairs per SM.
-    if (h.dp <= 16 && h.n >= 4 * ST && h.df_symmetric) {
+    // The symmetric kernel pays off once there are several tile pairs per SM,
+    // and while few columns are in the product.
+    if (h.dp <= 16 && h.n >= 4 * ST && h.df_symmetric && !df_prefer_plain(h.n, h.dp, c)) {
         kv_df_sym(h, V, ldv, c, B, ldb, O, ldo, noise);
         return;
     }
     cudaStream_t st = h.stream;
     const int64_t n = h.n;
     const DfSplit s = df_plan(n);
-    const int max_cb = 4;
+    const int max_cb = df_max_cb(h.dp);
     double* part = h.kvws.part64.need((size_t)s.nsplit * max_cb * s.ldp);
     const float4* xs = reinterpret_cast<const float4*>(h.xdf.p);
     const float2* tab = reinterpret_cast<const float2*>(h.df_tab.p);
-    for (int k0 = 0; k0 < c;) {
-        const int rem = c - k0;
-        const int cb = rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
-        const int ncols = std::min(cb, rem);
+    const std::vector<int> blocks = df_blocks(c, max_cb);
+    int k0 = 0;
+    for (int cb : blocks) {
+        const int ncols = std::min(cb, c - k0);
         const double* Vk = V + (int64_t)k0 * ldv;
         switch (h.dp) {
             case 4: df_launch_cb<4>(cb, xs, n, h.df_c0h, h.df_c0l, Vk, ldv, ncols, tab, part, s, st); break;

@@ -82,7 +82,8 @@ def test_matvec_f64_matches_oracle(kpcg, n, d, c):
 
 
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 6),
-                                   (700, 32, 2), (513, 12, 5), (6000, 8, 1)])
+                                   (700, 32, 2), (513, 12, 5), (6000, 8, 1), (2000, 10, 9),
+                                   (3000, 5, 17)])
 def test_matvec_double_float_matches_oracle(kpcg, n, d, c):
     # FP32-pair entries: exact grid differences, TwoSum accumulation and a
     # table-driven exp2 keep each entry within about 2^-40 of FP64, so the
