@@ -254,6 +254,66 @@ def run_grad(args):
     s.close()
 
 
+WARM_WORKLOAD = ("ARD-RBF n=131072 d=10 X~N(0,I); Adam lr 0.05 on (log l_1..10, log s^2, "
+                 "log noise) from l=1, s=1, noise=0.1; gradients with 4 fresh Rademacher probes; "
+                 "Nystrom m=512; network 12-256-256-4 on the 4 latest solutions, trained on the "
+                 "first n_train steps; each later step solved warm and cold at the same theta "
+                 "to tol 1e-8")
+
+
+def run_warm(args):
+    """A shortened hyperparameter trajectory (one bench step = the whole run):
+    per-solve iterations and device time, warm-started by the trained network
+    against cold-started PCG at the same theta."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+    from paper_1602_06693_gb300.warmstart import Trajectory
+
+    world, rank, local = dist_setup()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    n_steps, n_train = args.traj_steps, args.traj_train
+    p = synthetic.config5(seed=rank)
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=0.25, inner_tol=0.2)
+    s = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
+    pidx = synthetic.inducing_subset(p.n, 512, seed=3 + rank)
+    probes = lambda k: torch.from_numpy(synthetic.rademacher(p.n, 4, 5000 + k)).to(dev)
+    params = synthetic.mlp_init(11, p.d + 2, 256, 256, 4)
+    tr = Trajectory(s, y, pidx, probes, basis="snapshots", q=4, lr=0.05, n_train=n_train,
+                    mlp_params=params, epochs=2000, mlp_lr=1e-3, tol=TOL, compare=True)
+    z0 = np.concatenate([p.log_theta, [math.log(p.noise)]])
+    stop_clock = sm_clock_probe()
+    t0 = time.perf_counter()
+    recs = tr.run(z0, n_steps)
+    wall = time.perf_counter() - t0
+    clocks = stop_clock()
+    warm = [r for r in recs if r.warm]
+    wi = [r.iters for r in warm]
+    ci = [r.cold_iters for r in warm]
+    wt = [r.solve_ms for r in warm]
+    ct = [r.cold_ms for r in warm]
+    line = {
+        "metric": "per-solve time along the trajectory, learned warm start vs cold start",
+        "value": statistics.mean(wt) / 1e3, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f32+f64 (network: fp32 train, bf16 infer)",
+        "data": "synthetic",
+        "config": {"workload": WARM_WORKLOAD, "trajectory_steps": n_steps, "n_train": n_train,
+                   "note": "shortened trajectory: the specified one has 200 steps, 50 for training"},
+        "warm": {"iters": wi, "solve_ms": wt, "mean_ms": statistics.mean(wt)},
+        "cold": {"iters": ci, "solve_ms": ct, "mean_ms": statistics.mean(ct)},
+        "iteration_ratio": sum(wi) / max(1, sum(ci)),
+        "time_ratio": sum(wt) / max(1e-9, sum(ct)),
+        "max_rel_res": max(r.rel_res for r in recs),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+
+
 BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
 
 
@@ -411,7 +471,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
-    ap.add_argument("--workload", default="solve65k", choices=["solve65k", "batch64", "grad45k"],
+    ap.add_argument("--workload", default="solve65k",
+                    choices=["solve65k", "batch64", "grad45k", "warm131k"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -421,6 +482,8 @@ def main():
     ap.add_argument("--batch-m-max", type=int, default=1024,
                     help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
     ap.add_argument("--batch-m-div", type=int, default=4)
+    ap.add_argument("--traj-steps", type=int, default=24, help="warm131k: trajectory length")
+    ap.add_argument("--traj-train", type=int, default=12, help="warm131k: training steps")
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
                     help="batch64: only time full batched products (kv) or preconditioner "
                          "applies (precond) and exit; a small target for profilers")
@@ -431,6 +494,8 @@ def main():
         return run_batch(args)
     if args.workload == "grad45k":
         return run_grad(args)
+    if args.workload == "warm131k":
+        return run_warm(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg
