@@ -248,13 +248,17 @@ static int pcg_core(Ctx& h, int c, const T* B, int64_t ldb, T* X, int64_t ldx, b
 
 // Per-column ||B - K_y X||^2 and ||B||^2 in FP64 (host vectors).
 static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const double* X, int64_t ldx,
-                         double* R, std::vector<double>& rr, std::vector<double>& bb) {
+                         double* R, std::vector<double>& rr, std::vector<double>& bb,
+                         bool double_float = false) {
     cudaStream_t st = h.stream;
     // symmetric tile pairs halve the FP64 exp work but take at most two
     // columns per pass; from three columns on, one non-symmetric pass over up
-    // to 16 columns computes each entry's exp fewer times
+    // to 16 columns computes each entry's exp fewer times.  double_float: the
+    // double-float product instead (a residual that only steers the iteration)
     h.prof.time(Profiler::KV_OUTER, st, [&] {
-        if (c >= 3 && h.dp <= 16)
+        if (double_float)
+            kv_df(h, X, ldx, c, B, ldb, R, h.ld, h.noise);
+        else if (c >= 3 && h.dp <= 16)
             kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, X, ldx, c, B, ldb, R, h.ld, h.kvws,
                    st);
         else
@@ -357,10 +361,14 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
     };
     if (X0) {
         if (X0 != Xout) copy_cols<double>(Xout, ldx, X0, ldx, n, c, st);
+        ops.residual(B, ldb, c, Xout, ldx, R, rr, bb, false);
     } else {
+        // x0 = 0: the residual is B itself, no product needed
         fill_zero_cols(Xout, sizeof(double), ldx, n, c, st);
+        copy_cols<double>(R, ld, B, ldb, n, c, st);
+        dots(1, {{R, R}}, rr);
+        bb = rr;
     }
-    ops.residual(B, ldb, c, Xout, ldx, R, rr, bb);
     std::vector<double> pAp((size_t)W * c, 1.0), coef((size_t)c), d;
     std::vector<int> dead((size_t)c, 0);
     int nwin = 0, head = 0, stall = 0, recheck = 0;
@@ -381,7 +389,7 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
             // certify on the recomputed residual; continue from it if the
             // recursive one drifted
             if (recheck) break;
-            ops.residual(B, ldb, c, Xout, ldx, R, rr, bb);
+            ops.residual(B, ldb, c, Xout, ldx, R, rr, bb, true);
             recheck = 1;
             nwin = 0;
             --outer;
@@ -512,8 +520,8 @@ static MixedOps single_ops(Ctx& h) {
         kv_df(*hp, V, ldv, cc, nullptr, 0, O, ldo, hp->noise);
     };
     o.residual = [hp](const double* B, int64_t ldb, int cc, const double* X, int64_t ldx,
-                      double* R, std::vector<double>& rr, std::vector<double>& bb) {
-        residual_f64(*hp, B, ldb, cc, X, ldx, R, rr, bb);
+                      double* R, std::vector<double>& rr, std::vector<double>& bb, bool certify) {
+        residual_f64(*hp, B, ldb, cc, X, ldx, R, rr, bb, !certify);
     };
     if (tc) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
     return o;

@@ -333,16 +333,22 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
             }
         };
         ops.residual = [bb, c](const double* Bm, int64_t ldb, int cc, const double* Xm, int64_t ldx,
-                               double* R, std::vector<double>& rr, std::vector<double>& bn) {
+                               double* R, std::vector<double>& rr, std::vector<double>& bn,
+                               bool certify) {
             Ctx& M = bb->M;
             for (size_t p = 0; p < bb->sub.size(); ++p) {
                 Ctx& h = *bb->sub[p];
                 const int64_t off = (int64_t)p * c;
-                // native FP64: b - K x cancels terms up to ~|x|/|b| ~ 1/sigma^2
-                // larger than the result, beyond the double-float product's reach
+                // certify: native FP64 (b - K x cancels terms up to ~|x|/|b| ~
+                // 1/sigma^2 larger than the result, beyond the double-float
+                // product's reach); steering only: double-float
                 M.prof.time(Profiler::KV_OUTER, M.stream, [&] {
-                    kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, Xm + off * ldx, ldx, c,
-                           Bm + off * ldb, ldb, R + off * M.ld, M.ld, h.kvws, M.stream);
+                    if (certify)
+                        kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, Xm + off * ldx, ldx, c,
+                               Bm + off * ldb, ldb, R + off * M.ld, M.ld, h.kvws, M.stream);
+                    else
+                        kv_df(h, Xm + off * ldx, ldx, c, Bm + off * ldb, ldb, R + off * M.ld,
+                              M.ld, h.noise);
                 });
             }
             const int nblk = dot_blocks(M.n);
@@ -386,7 +392,7 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
             if (!(worst < 0.5 * prev_worst)) break;
             prev_worst = worst;
         }
-        if (status != KPCG_OK) ops.residual(Bp, L, C, Xp, L, M.R64.p, rr, bn);
+        if (status != KPCG_OK) ops.residual(Bp, L, C, Xp, L, M.R64.p, rr, bn, true);
         // exactly ld rows per column of the caller's block (ld may be below L)
         masked_copy_kernel<double, double><<<g, 256, 0, st>>>(X, ld, Xp, L, b->nrow.p, c, ld);
         KPCG_LAUNCHED("masked_copy_kernel");

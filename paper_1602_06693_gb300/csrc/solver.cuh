@@ -17,9 +17,10 @@ struct MixedOps {
     std::function<void(const float*, int64_t, int, float*, int64_t)> inner_mv, inner_pc;
     // O = K_y V with FP64-class accuracy
     std::function<void(const double*, int64_t, int, double*, int64_t)> outer_mv;
-    // R = B - K_y X (FP64-class) and the per-column ||R||^2, ||B||^2
+    // R = B - K_y X and the per-column ||R||^2, ||B||^2; certify: native FP64
+    // (the value the stop test is decided on), else FP64-class (steering only)
     std::function<void(const double*, int64_t, int, const double*, int64_t, double*,
-                       std::vector<double>&, std::vector<double>&)>
+                       std::vector<double>&, std::vector<double>&, bool certify)>
         residual;
     // true if a bounded device wait expired since the last query
     std::function<bool()> timed_out;
