@@ -24,9 +24,11 @@ struct TcBatchProb {
     float noise;        // diagonal added by the product
     int32_t pad_;
 };
-// Tiles [jt0, jt0 + nt) of row tile rt of problem prob.
+// Column tiles [jt0, jt0 + nt) against row tile rt of problem prob and, if
+// two, row tile rt + 1 as well (the epilogue then uses every value of V it
+// reads for two rows).
 struct TcBatchItem {
-    int32_t prob, rt, jt0, nt;
+    int32_t prob, rt, jt0, nt, two, pad_;
 };
 
 struct TcBatch {
@@ -35,7 +37,7 @@ struct TcBatch {
     std::vector<TcBatchProb> hprobs;
     DevBuf<TcBatchProb> probs;
     DevBuf<TcBatchItem> items;
-    DevBuf<int32_t> rt_first, rt_count;  // per (problem, row tile): its items
+    DevBuf<int32_t> rt_first, rt_count;  // per (problem, row-tile pair): its items
     DevBuf<float> Vs, part;
     DevBuf<int> err;
 };

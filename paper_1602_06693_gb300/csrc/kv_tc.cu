@@ -547,7 +547,12 @@ void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t l
 
 // ------------------------------------------------------------------------
 // Batched product over many problems of uneven size: one persistent launch
-// walks a flat work list of (problem, row tile, run of column tiles) items.
+// walks a flat work list of (problem, row-tile pair, run of column tiles)
+// items.  A pair of row tiles shares every column tile: two MMAs per column
+// tile into two TMEM accumulators (2 x 2 x 128 columns with double
+// buffering), and each epilogue thread owns row r of both tiles, so each value
+// of V read from shared memory (a broadcast read, the kernel's bound) serves
+// two rows.
 // The three roles walk the same items in the same order, so the ring and
 // accumulator phases simply continue from one item to the next; the A tile of
 // an item is reloaded once the MMAs of the previous item have finished with
@@ -561,7 +566,8 @@ constexpr int kMaxKch = 2;
 template <int CB>
 struct TcBSmem {
     static constexpr uint32_t kSub = SUB * 2;
-    static constexpr uint32_t kA = kMaxKch * kSub;
+    static constexpr uint32_t kA1 = kMaxKch * kSub;  // one row tile of A
+    static constexpr uint32_t kA = 2 * kA1;
     static constexpr uint32_t kBst = kMaxKch * kSub;
     static constexpr uint32_t kVst = CB * TN * 4;
     static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
@@ -620,7 +626,7 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 su32(tmem_slot)),
-            "r"(2 * TN));
+            "r"(4 * TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
@@ -645,8 +651,11 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                     fail = 1;
                     break;
                 }
-                mbar_expect_tx(afull, abytes);
+                mbar_expect_tx(afull, w.two ? 2 * abytes : abytes);
                 bulk_g2s(sA, pb.A + (size_t)w.rt * pb.kch * SUB, abytes, afull);
+                if (w.two)
+                    bulk_g2s(sA + S::kA1, pb.A + (size_t)(w.rt + 1) * pb.kch * SUB, abytes,
+                             afull);
                 ++u;
                 for (int j = 0; j < w.nt; ++j) {
                     const int s = (int)(t % NSTAGE);
@@ -678,6 +687,7 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                 const TcBatchItem w = items[it];
                 if (!prob_live(active, w.prob, cpp)) continue;
                 const int kch = probs[w.prob].kch;
+                const int nsub = w.two ? 2 : 1;
                 if (!mbar_wait(afull, u & 1u, deadline)) {
                     fail = 1;
                     break;
@@ -693,13 +703,17 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                     }
                     fence_after();
                     const uint32_t b0 = su32(sStage + (size_t)s * S::kStage);
-                    const uint32_t dt = tmem + (uint32_t)(b * TN);
-                    for (int kc = 0; kc < kch; ++kc)
+                    for (int sub = 0; sub < nsub; ++sub) {
+                        const uint32_t dt = tmem + (uint32_t)(b * 2 * TN + sub * TN);
+                        const uint32_t as = a0 + (uint32_t)sub * S::kA1;
+                        for (int kc = 0; kc < kch; ++kc)
 #pragma unroll
-                        for (int kk = 0; kk < KC / 16; ++kk) {
-                            const uint32_t off = (uint32_t)kc * S::kSub + (uint32_t)kk * 32;
-                            mma_bf16(dt, sdesc(a0 + off), sdesc(b0 + off), (kc | kk) ? 1u : 0u);
-                        }
+                            for (int kk = 0; kk < KC / 16; ++kk) {
+                                const uint32_t off = (uint32_t)kc * S::kSub + (uint32_t)kk * 32;
+                                mma_bf16(dt, sdesc(as + off), sdesc(b0 + off),
+                                         (kc | kk) ? 1u : 0u);
+                            }
+                    }
                     mma_commit(&tfull[b]);
                     mma_commit(&empty[s]);
                     ++t;
@@ -715,9 +729,10 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
         for (int it = blockIdx.x; it < nitems && !fail; it += gridDim.x) {
             const TcBatchItem w = items[it];
             if (!prob_live(active, w.prob, cpp)) continue;
-            float acc[CB];
+            const bool two = w.two != 0;  // uniform over the CTA
+            float acc[CB], acc2[CB];
 #pragma unroll
-            for (int k = 0; k < CB; ++k) acc[k] = 0.f;
+            for (int k = 0; k < CB; ++k) acc[k] = acc2[k] = 0.f;
             for (int j = 0; j < w.nt; ++j) {
                 const int s = (int)(t % NSTAGE), b = (int)(t & 1u);
                 const bool ok = __all_sync(
@@ -729,30 +744,58 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                 fence_after();
                 const float* vst =
                     reinterpret_cast<const float*>(sStage + (size_t)s * S::kStage + S::kBst);
+                const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
                 for (int ch = 0; ch < 4; ++ch) {
                     const int col0 = half * 64 + ch * 16;
                     uint32_t r[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + col0),
-                              r);
+                    tmem_ld16(trow + (uint32_t)(b * 2 * TN + col0), r);
                     float ev[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) ev[q] = ex2(__uint_as_float(r[q]));
                     // every accumulator runs; those past ncols read stale staging
                     // memory and are never stored (no per-column branch here)
+                    if (two) {
+                        tmem_ld16(trow + (uint32_t)(b * 2 * TN + TN + col0), r);
+                        float ev2[16];
 #pragma unroll
-                    for (int k = 0; k < CB; ++k) {
-                        const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
-                        float a = acc[k];
+                        for (int q = 0; q < 16; ++q) ev2[q] = ex2(__uint_as_float(r[q]));
 #pragma unroll
-                        for (int j4 = 0; j4 < 4; ++j4) {
-                            const float4 v = vp[j4];
-                            a = fmaf(ev[4 * j4 + 0], v.x, a);
-                            a = fmaf(ev[4 * j4 + 1], v.y, a);
-                            a = fmaf(ev[4 * j4 + 2], v.z, a);
-                            a = fmaf(ev[4 * j4 + 3], v.w, a);
+                        for (int k = 0; k < CB; ++k) {
+                            const float4* vp =
+                                reinterpret_cast<const float4*>(vst + k * TN + col0);
+                            float a = acc[k], a2 = acc2[k];
+#pragma unroll
+                            for (int j4 = 0; j4 < 4; ++j4) {
+                                const float4 v = vp[j4];
+                                a = fmaf(ev[4 * j4 + 0], v.x, a);
+                                a2 = fmaf(ev2[4 * j4 + 0], v.x, a2);
+                                a = fmaf(ev[4 * j4 + 1], v.y, a);
+                                a2 = fmaf(ev2[4 * j4 + 1], v.y, a2);
+                                a = fmaf(ev[4 * j4 + 2], v.z, a);
+                                a2 = fmaf(ev2[4 * j4 + 2], v.z, a2);
+                                a = fmaf(ev[4 * j4 + 3], v.w, a);
+                                a2 = fmaf(ev2[4 * j4 + 3], v.w, a2);
+                            }
+                            acc[k] = a;
+                            acc2[k] = a2;
                         }
-                        acc[k] = a;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < CB; ++k) {
+                            const float4* vp =
+                                reinterpret_cast<const float4*>(vst + k * TN + col0);
+                            float a = acc[k];
+#pragma unroll
+                            for (int j4 = 0; j4 < 4; ++j4) {
+                                const float4 v = vp[j4];
+                                a = fmaf(ev[4 * j4 + 0], v.x, a);
+                                a = fmaf(ev[4 * j4 + 1], v.y, a);
+                                a = fmaf(ev[4 * j4 + 2], v.z, a);
+                                a = fmaf(ev[4 * j4 + 3], v.w, a);
+                            }
+                            acc[k] = a;
+                        }
                     }
                 }
                 fence_before();
@@ -764,10 +807,15 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                 ++t;
             }
             if (fail) break;
-            const int64_t base = ((int64_t)it * 2 + half) * CB;
+            // partials [item][sub][half][column][row]
+            const int64_t base = (((int64_t)it * 2 + 0) * 2 + half) * CB;
+            const int64_t base2 = (((int64_t)it * 2 + 1) * 2 + half) * CB;
 #pragma unroll
             for (int k = 0; k < CB; ++k)
-                if (k < ncols) part[(base + k) * TM + row] = acc[k];
+                if (k < ncols) {
+                    part[(base + k) * TM + row] = acc[k];
+                    if (two) part[(base2 + k) * TM + row] = acc2[k];
+                }
         }
     }
     if (fail) atomicExch(&s_fail, 1);
@@ -778,7 +826,7 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
     if (warp == 1) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(2 * TN));
+                     "r"(4 * TN));
     }
 }
 
@@ -797,8 +845,8 @@ __global__ void tc_batch_stage_v_kernel(const TcBatchProb* __restrict__ probs,
     }
 }
 
-// O[i][p*cpp + k0 + k] = noise_p V + sum over the items of row tile i/128 in
-// order (both column halves); zero past n_p and for skipped problems.
+// O[i][p*cpp + k0 + k] = noise_p V + sum over the items of the row-tile pair
+// of i in order (both column halves); zero past n_p and for skipped problems.
 __global__ void tc_batch_reduce_kernel(const TcBatchProb* __restrict__ probs,
                                        const int32_t* __restrict__ rt_first,
                                        const int32_t* __restrict__ rt_count,
@@ -815,10 +863,11 @@ __global__ void tc_batch_reduce_kernel(const TcBatchProb* __restrict__ probs,
         float v = 0.f;
         if (live && i < pb.n) {
             const int rt = (int)(i / TM), r = (int)(i % TM);
-            const int f = rt_first[pb.rt_base + rt], cnt = rt_count[pb.rt_base + rt];
+            const int pair = rt >> 1, sub = rt & 1;
+            const int f = rt_first[pb.rt_base + pair], cnt = rt_count[pb.rt_base + pair];
             float s = pb.noise * V[col * ldv + i];
             for (int q = 0; q < cnt; ++q) {
-                const int64_t base = (int64_t)(f + q) * 2 * cb;
+                const int64_t base = (((int64_t)(f + q) * 2 + sub) * 2) * cb;
                 s += part[(base + k) * TM + r] + part[(base + cb + k) * TM + r];
             }
             v = s;
@@ -869,15 +918,16 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
         pb.kch = h.tc_kch;
         pb.rt_base = rt_base;
         pb.noise = noise[(size_t)p];
-        for (int rt = 0; rt < n_t; ++rt) {
+        for (int rt = 0; rt < n_t; rt += 2) {
+            const int two = (rt + 1 < n_t) ? 1 : 0;
             first.push_back((int32_t)items.size());
             int cnt = 0;
             for (int jt0 = 0; jt0 < n_t; jt0 += G, ++cnt)
-                items.push_back(TcBatchItem{p, rt, jt0, std::min(G, n_t - jt0)});
+                items.push_back(TcBatchItem{p, rt, jt0, std::min(G, n_t - jt0), two, 0});
             count.push_back(cnt);
         }
         voff += n_pad;
-        rt_base += n_t;
+        rt_base += (n_t + 1) / 2;
     }
     b.nv = voff;
     b.nitems = (int)items.size();
@@ -894,7 +944,7 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
     KPCG_CUDA(cudaMemcpyAsync(b.rt_count.p, count.data(), sizeof(int32_t) * count.size(),
                               cudaMemcpyHostToDevice, st));
     b.Vs.need((size_t)b.nv * 16);
-    b.part.need((size_t)b.nitems * 2 * 16 * TM);
+    b.part.need((size_t)b.nitems * 2 * 2 * 16 * TM);
     if (!b.err.p) {
         b.err.need(1);
         KPCG_CUDA(cudaMemsetAsync(b.err.p, 0, sizeof(int), st));
