@@ -905,6 +905,9 @@ __global__ void __launch_bounds__(256)
         Acc2 acc[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) acc[k] = {0.f, 0.f};
+        // unrolled for several loads of K_XU in flight per warp (occupancy is
+        // limited by the staged coefficients)
+#pragma unroll 4
         for (int64_t a = lane; a < pb.m; a += 32) {
             const float2 kv = __ldg(Ki + a);
 #pragma unroll
