@@ -277,7 +277,7 @@ def run_warm(args):
     X = torch.from_numpy(p.X).to(dev)
     y = torch.from_numpy(p.y).to(dev)
     opt = kpcg.default_options(precision=kpcg.KPCG_TC_IR, inner_shift=0.25,
-                               inner_tol=args.inner_tol if args.inner_tol else 0.2)
+                               inner_tol=args.inner_tol if args.inner_tol else 0.02)
     s = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
     pidx = synthetic.inducing_subset(p.n, 512, seed=3 + rank)
     probes = lambda k: torch.from_numpy(synthetic.rademacher(p.n, 4, 5000 + k)).to(dev)
