@@ -110,6 +110,27 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """Whole-job step time under torchrun: the slowest rank's, on every rank
+    (one process per GPU; without a process group it is the value itself)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_problem(rank, n=None):
+    """The headline workload's instance solved by one rank: replicas only, each
+    rank its own seeded system and inducing subset, no data exchanged."""
+    p = synthetic.config2(seed=rank, n=n if n else N_FULL)
+    idx = synthetic.inducing_subset(p.n, min(M_INDUCING, p.n), seed=1 + rank)
+    return p, idx
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -512,8 +533,7 @@ def main():
             "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
 
     # replicas: each rank solves its own seeded instance of the same workload
-    p = synthetic.config2(seed=rank, n=args.n)
-    idx = synthetic.inducing_subset(p.n, M_INDUCING, seed=1 + rank)
+    p, idx = replica_problem(rank, args.n)
     X = torch.from_numpy(p.X).to(dev)
     y = torch.from_numpy(p.y).to(dev)
     opt = kpcg.default_options(precision=prec, profile=1)
@@ -549,11 +569,7 @@ def main():
         times.append(e0.elapsed_time(e1) / 1e3)
         infos.append((info, st))
     clocks = stop_clock()
-    t_step = statistics.mean(times)
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(statistics.mean(times), dev)
     info, st = infos[-1]
 
     # roofline of the dominant kernel class, from the library's event timers
