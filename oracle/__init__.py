@@ -335,3 +335,20 @@ def grad_stochastic(X, log_theta, noise, y, probes, ard=True, solve=None) -> np.
     trn = np.mean(np.sum(Wt * R, axis=0)) if t else 0.0
     g[d + 1] = -0.5 * noise * trn + 0.5 * noise * (a @ a)
     return _chain_iso(g, d, ard)
+
+
+# ---------------------------------------------------------------------------
+# Predictions (Sec. 2.1: the predictive mean and variance at test inputs; the
+# variance needs one linear system per test point; Sec. 5 scores both)
+# ---------------------------------------------------------------------------
+def predict(X, ell, s2, noise, alpha, Xs, var=True):
+    """Predictive mean m_* = K(X_*, X) alpha and latent variance
+    v_* = s2 - k_*^T K_y^{-1} k_* (k_* = K(X, x_*)), by dense FP64 algebra.
+    Add the noise to v_* for the predictive variance of a noisy target."""
+    Ks = gram(Xs, X, ell, s2)  # (ns, n)
+    mean = Ks @ np.asarray(alpha, dtype=np.float64)
+    if not var:
+        return mean, None
+    W = dense_solve(X, ell, s2, noise, np.asfortranarray(Ks.T))  # K_y^{-1} k_* per column
+    v = s2 - np.einsum("ij,ji->i", Ks, W)
+    return mean, v

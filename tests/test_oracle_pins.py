@@ -361,3 +361,45 @@ def test_mlp_forward_closed_form_and_adam_first_step():
     for k in mlp.NAMES:
         np.testing.assert_allclose(P2[k] - P[k], -1e-2 * g[k] / (np.abs(g[k]) + 1e-8),
                                    rtol=1e-12, atol=1e-15)
+
+
+# ----------------------------------------------------------------- predictions
+def test_predict_single_training_point_closed_form():
+    # n = 1: K_y = s2 + noise, so m_* = s2 e^{-q} y / (s2 + noise) and
+    # v_* = s2 - s2^2 e^{-2q} / (s2 + noise) with q = |x - x_*|^2 / (2 l^2)
+    X = np.array([[0.3, -0.2]], dtype=np.float32)
+    Xs = np.array([[0.3, -0.2], [1.0, 0.5]], dtype=np.float32)
+    ell, s2, noise, y = np.array([0.7, 1.3]), 1.7, 0.05, 2.0
+    alpha = np.array([y / (s2 + noise)])
+    m, v = oracle.predict(X, ell, s2, noise, alpha, Xs)
+    d = (Xs.astype(np.float64) - X.astype(np.float64)) / ell
+    e = np.exp(-0.5 * (d ** 2).sum(1))
+    np.testing.assert_allclose(m, s2 * e * y / (s2 + noise), rtol=1e-14)
+    np.testing.assert_allclose(v, s2 - (s2 * e) ** 2 / (s2 + noise), rtol=1e-13)
+    assert v[0] == pytest.approx(s2 * noise / (s2 + noise), rel=1e-13)
+
+
+def test_predict_far_point_and_interpolation():
+    p = synthetic.make_problem(60, 3, 4, ell=0.8, noise=1e-8)
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    alpha = oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]
+    far = np.full((1, 3), 50.0, dtype=np.float32)
+    m, v = oracle.predict(p.X, ell, s2, p.noise, alpha, np.vstack([p.X[:5], far]))
+    # at training inputs with (almost) no noise the mean interpolates y and the
+    # variance vanishes; far from the data the prior returns: m = 0, v = s2
+    np.testing.assert_allclose(m[:5], p.y[:5], atol=1e-5)
+    assert np.all(np.abs(v[:5]) <= 1e-5)
+    assert abs(m[5]) <= 1e-12 and v[5] == pytest.approx(s2, rel=1e-12)
+
+
+def test_predict_variance_bounds_and_monotone_in_data():
+    p = synthetic.make_problem(80, 4, 6, ell=1.1, noise=0.05)
+    ell, s2 = oracle.split_theta(p.log_theta, 4, True)
+    Xs = synthetic.rng(7).standard_normal((40, 4)).astype(np.float32)
+    a = oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]
+    _, v = oracle.predict(p.X, ell, s2, p.noise, a, Xs)
+    assert np.all(v > 0) and np.all(v <= s2 * (1 + 1e-12))
+    # conditioning on fewer training points can only increase the variance
+    a2 = oracle.dense_solve(p.X[:40], ell, s2, p.noise, p.y[:40, None])[:, 0]
+    _, v2 = oracle.predict(p.X[:40], ell, s2, p.noise, a2, Xs)
+    assert np.all(v2 >= v - 1e-12)
