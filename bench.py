@@ -336,6 +336,58 @@ def run_warm(args):
     s.close()
 
 
+PREDICT_WORKLOAD = ("isotropic RBF n=4096 d=8 X~N(0,I), s=1, l=1, noise=1e-2, Nystrom m=256; "
+                    "1024 test inputs X_*~N(0,I); predictive mean and latent variance (one FP64 "
+                    "PCG solve per block of 16 test points, tol 1e-8)")
+
+
+def run_predict(args):
+    """One step: predictive mean and variance at 1024 test inputs."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = synthetic.config1(seed=rank)
+    idx = synthetic.inducing_subset(p.n, 256, seed=1 + rank)
+    Xs = torch.from_numpy(synthetic.rng(100 + rank).standard_normal((1024, p.d))
+                          .astype(np.float32)).to(dev)
+    s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, p.noise, ard=False,
+                    options=kpcg.default_options(precision=kpcg.KPCG_FP64))
+    s.precond(kpcg.KPCG_PREC_NYSTROM, 256, idx)
+    alpha, _, _, _ = s.solve(torch.from_numpy(p.y).to(dev), tol=TOL)
+    for _ in range(args.warmup):
+        s.predict(Xs, alpha, tol=TOL)
+    torch.cuda.synchronize(dev)
+    stop_clock = sm_clock_probe()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m, v, info = s.predict(Xs, alpha, tol=TOL)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = stop_clock()
+    line = {
+        "metric": "time for predictive mean and variance at 1024 test inputs",
+        "value": statistics.mean(times), "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": PREDICT_WORKLOAD},
+        "solve": {"iters_total": info.iters_total, "max_rel_res_fp64": info.max_rel_res,
+                  "step_times_s": times},
+        "var_range": [float(v.min()), float(v.max())],
+        "clocks": clocks, "gpu_launches": int(info.launches),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+
+
 BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
 
 
@@ -494,7 +546,7 @@ def main():
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
     ap.add_argument("--workload", default="solve65k",
-                    choices=["solve65k", "batch64", "grad45k", "warm131k"],
+                    choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -518,6 +570,8 @@ def main():
         return run_grad(args)
     if args.workload == "warm131k":
         return run_warm(args)
+    if args.workload == "predict4k":
+        return run_predict(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg

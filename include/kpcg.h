@@ -208,6 +208,20 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
 kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
                       const double* alpha0, double* grad, double* alpha, kpcg_info* info);
 
+/* Predictions at ns test inputs (Sec. 2.1: the predictive mean and variance
+ * need the kernel products of training and, for the variance, one linear
+ * system per test point; Sec. 5 scores both).
+ *   Xs: device float32, ns x d row-major (the layout of X); alpha: device, n,
+ *   alpha = K_y^{-1} y (e.g. from kpcg_solve);
+ *   mean (device, ns) = K(X_*, X) alpha, FP64 with entries rebuilt from X;
+ *   var (device, ns, nullable) = the latent variance s^2 - k_*^T K_y^{-1} k_*
+ *   with k_* = K(X, x_*): blocks of up to 16 test points are solved as
+ *   right-hand sides with the handle's precision and preconditioner to tol.
+ *   Add sigma^2 to var for the variance of a noisy target.
+ * info (nullable) sums the variance solves.  ns = 0 is a no-op. */
+kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* alpha,
+                         double* mean, double* var, double tol, kpcg_info* info);
+
 /* ---------------------------------------------------------------------------
  * Learned warm start.  Algorithm 1 takes an initial iterate x0; along a
  * hyperparameter trajectory a small network predicts coefficients c on a

@@ -28,7 +28,8 @@ SYMBOLS = (
     "kpcg_default_options", "kpcg_status_string", "kpcg_create", "kpcg_set_theta",
     "kpcg_set_options", "kpcg_precond", "kpcg_matvec_f64", "kpcg_matvec_f32",
     "kpcg_precond_apply_f64", "kpcg_solve", "kpcg_dkv", "kpcg_grad", "kpcg_destroy",
-    "kpcg_last_error", "kpcg_matvec_f64_noalloc", "kpcg_warm_basis", "kpcg_warm_fit",
+    "kpcg_last_error", "kpcg_matvec_f64_noalloc", "kpcg_predict", "kpcg_warm_basis",
+    "kpcg_warm_fit",
     "kpcg_warm_expand", "kpcg_warm_snapshots", "kpcg_warm_push", "kpcg_mlp_create",
     "kpcg_mlp_forward", "kpcg_mlp_grad", "kpcg_mlp_train",
     "kpcg_mlp_get_params", "kpcg_mlp_destroy", "kpcg_mlp_last_error", "kpcg_batch_create",
@@ -131,6 +132,7 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Info)]
         L.kpcg_dkv.argtypes = [vp, vp, i64, i32, vp, i64]
         L.kpcg_grad.argtypes = [vp, vp, vp, i32, dbl, vp, pdbl, vp, ctypes.POINTER(Info)]
+        L.kpcg_predict.argtypes = [vp, vp, i64, vp, vp, vp, dbl, ctypes.POINTER(Info)]
         L.kpcg_warm_basis.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), dbl]
         L.kpcg_warm_snapshots.argtypes = [vp, i32, dbl]
         L.kpcg_warm_push.argtypes = [vp, vp]
@@ -389,6 +391,24 @@ class Solver:
                                     _dptr(alpha, torch.float64, "alpha") if want_alpha else None,
                                     ctypes.byref(info)))
         return g, alpha, info
+
+    def predict(self, Xs, alpha, var=True, tol=1e-10):
+        """Predictive mean and latent variance at test inputs Xs (float32 CUDA,
+        ns x d): returns (mean, var | None, Info)."""
+        torch = _torch()
+        Xs = Xs.contiguous()
+        if Xs.dtype != torch.float32 or Xs.dim() != 2:
+            raise ValueError("Xs must be a float32 (ns, d) tensor")
+        ns = Xs.shape[0]
+        mean = torch.empty(ns, dtype=torch.float64, device=Xs.device)
+        v = torch.empty(ns, dtype=torch.float64, device=Xs.device) if var else None
+        info = Info()
+        self._check(lib().kpcg_predict(self._h, _dptr(Xs, torch.float32, "Xs"), ns,
+                                       _dptr(alpha, torch.float64, "alpha"),
+                                       _dptr(mean, torch.float64, "mean"),
+                                       _dptr(v, torch.float64, "var") if var else None,
+                                       float(tol), ctypes.byref(info)))
+        return mean, v, info
 
     # -- learned warm start: basis fit and expansion
     def warm_basis(self, idx, ridge=1e-6):

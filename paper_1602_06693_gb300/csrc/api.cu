@@ -527,7 +527,7 @@ static MixedOps single_ops(Ctx& h) {
     return o;
 }
 
-static kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
+kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                               const double* X0, double* Xout, int64_t ldx, int32_t* iters_host,
                               kpcg_info* info) {
     const auto t0 = std::chrono::steady_clock::now();

@@ -112,6 +112,8 @@ struct Ctx {
     int nys1_c = -1;
     long long nys1_version = -1;
     long long pversion = 0;  // incremented by every preconditioner build
+    // predictions (predict.cu): scaled test inputs, k_* blocks, their solves, partials
+    DevBuf<double> pxt, pKb, pW, ppart;
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

@@ -83,6 +83,11 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
                       std::vector<int>& iters_col, int& iters_total, int& steps,
                       std::vector<double>& rr, std::vector<double>& bb);
 bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n);
+// The solve behind kpcg_solve: K_y X = B for c columns with the handle's
+// precision and preconditioner (device blocks; iters_host, info nullable).
+kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
+                       const double* X0, double* Xout, int64_t ldx, int32_t* iters_host,
+                       kpcg_info* info);
 // (Re)build the handle's preconditioner for the noise its mode needs;
 // returns the host milliseconds spent (0 if it was current).
 double ensure_precond(Ctx& h);

@@ -423,3 +423,26 @@ def test_iteration_cap_reports_no_convergence(kpcg):
     with _solver(kpcg, p, precision=kpcg.KPCG_FP64, max_iter=3) as s:
         x, it, info, st = s.solve(_cm(p.y), tol=1e-10, raise_on_error=False)
     assert st == 6 and info.iters_total <= 3 and np.all(np.isfinite(_np(x)))
+
+
+# ------------------------------------------------------------- predictions
+@pytest.mark.parametrize("ns,precond", [(1, False), (45, False), (45, True)])
+def test_predictions_match_oracle(kpcg, ns, precond):
+    # mean: FP64 products on both sides (1e-10 relative); variance: one FP64 PCG
+    # solve per block of 16 test points to 1e-12, so v_* = s2 - k^T w carries
+    # about kappa(K_y) * 1e-12 of s2 (kappa ~ 1e4 here): 1e-7 * s2 absolute.
+    p = _problem(700, 5, seed=41, noise=0.05)
+    Xs = synthetic.rng(42).standard_normal((ns, 5)).astype(np.float32)
+    ell, s2 = oracle.split_theta(p.log_theta, 5, True)
+    alpha = oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]
+    mref, vref = oracle.predict(p.X, ell, s2, p.noise, alpha, Xs)
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
+        if precond:
+            s.precond(kpcg.KPCG_PREC_NYSTROM, 64, synthetic.inducing_subset(700, 64, seed=3))
+        m, v, info = s.predict(torch.from_numpy(Xs).to(DEV), _cm(alpha), tol=1e-12)
+        m0, v0, _ = s.predict(torch.from_numpy(Xs).to(DEV), _cm(alpha), var=False)
+    assert _rel(_np(m), mref) <= 1e-10
+    np.testing.assert_array_equal(_np(m), _np(m0))
+    assert v0 is None
+    np.testing.assert_allclose(_np(v), vref, rtol=0, atol=1e-7 * s2)
+    assert info.iters_total > 0 and info.max_rel_res <= 1e-12
