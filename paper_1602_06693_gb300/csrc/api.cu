@@ -581,6 +581,9 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                         h.prof.time(Profiler::KV_INNER, st, [&] {
                             if (dfk)
                                 kv_df(h, V, ldv, cc, nullptr, 0, O, ldo, h.noise);
+                            else if (cc >= 3 && h.dp <= 16)  // one pass over <= 16 columns
+                                kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, V, ldv, cc,
+                                       nullptr, 0, O, ldo, h.kvws, st);
                             else
                                 kv_f64_sym(h, V, ldv, cc, nullptr, 0, O, ldo, h.noise);
                         });
