@@ -583,14 +583,14 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                                 kv_df(h, V, ldv, cc, nullptr, 0, O, ldo, h.noise);
                             else if (cc >= 3 && h.dp <= 16)  // one pass over <= 16 columns
                                 kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, V, ldv, cc,
-                                       nullptr, 0, O, ldo, h.kvws, st);
+                                       nullptr, 0, O, ldo, h.kvws, h.stream);
                             else
                                 kv_f64_sym(h, V, ldv, cc, nullptr, 0, O, ldo, h.noise);
                         });
                     },
                     [&](const double* Rr, int64_t ldr, int cc, double* Z, int64_t ldz) {
                         h.prof.time(Profiler::PRECOND, st, [&] {
-                            precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, st);
+                            precond_apply_f64(h.P, Rr, ldr, cc, Z, ldz, h.stream);
                         });
                     },
                     h.c64, its, br, rr_current ? R : nullptr);
@@ -600,12 +600,12 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                     [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
                         h.prof.time(Profiler::KV_INNER, st, [&] {
                             kv_f32(h.xs32.p, n, h.dp, h.c0_32(), (float)h.noise, V, ldv, cc, O,
-                                   ldo, h.kvws, st);
+                                   ldo, h.kvws, h.stream);
                         });
                     },
                     [&](const float* Rr, int64_t ldr, int cc, float* Z, int64_t ldz) {
                         h.prof.time(Profiler::PRECOND, st, [&] {
-                            precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, st);
+                            precond_apply_f32(h.P, Rr, ldr, cc, Z, ldz, h.stream);
                         });
                     },
                     h.c32, its, br);
@@ -869,6 +869,7 @@ kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_
         kpcg::check_dev_ptr(X, "X");
         if (((uintptr_t)X) % 4) fail(KPCG_ERR_ARG, "X must be 4-byte aligned");
         h = new kpcg_ctx();
+        h->use_graph = true;  // replay CG chunks from graphs whenever profiling is off
         KPCG_CUDA(cudaGetDevice(&h->device));
         h->stream = (cudaStream_t)stream;
         h->n = n;

@@ -30,6 +30,17 @@
 #include "precond.cuh"
 
 namespace kpcg {
+
+// Raise a kernel's dynamic shared-memory limit once per size (the first
+// call runs outside any graph capture; later ones find it raised).
+static void raise_smem_limit(const void* kern, size_t smem) {
+    static std::map<const void*, size_t> done;
+    size_t& have = done[kern];
+    if (smem <= have) return;
+    KPCG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    have = smem;
+}
+
 namespace {
 
 constexpr int NB = 32;  // panel width of the blocked Cholesky
@@ -626,9 +637,7 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     KPCG_LAUNCHED("tri_upper_apply_kernel");
     const size_t smem = sizeof(double) * (size_t)m * c;
     if (smem > 200 * 1024) fail(KPCG_ERR_ARG, "Nystrom apply: m * c too large");
-    if (smem > 48 * 1024)
-        KPCG_CUDA(cudaFuncSetAttribute(nys_back_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) raise_smem_limit((const void*)nys_back_kernel<T>, smem);
     int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 16);
     nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, w, c, R, ldr, Z, ldz,
                                                   1.0 / P.noise);
@@ -691,9 +700,7 @@ static void bj_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z
                      cudaStream_t st) {
     const int64_t nb = (P.n + P.b - 1) / P.b;
     const size_t smem = sizeof(double) * 2 * (size_t)P.b;
-    if (smem > 48 * 1024)
-        KPCG_CUDA(cudaFuncSetAttribute(bj_apply_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) raise_smem_limit((const void*)bj_apply_kernel<T>, smem);
     bj_apply_kernel<T><<<dim3((unsigned)nb, c), 256, smem, st>>>(P.U.p, P.n, P.b, R, ldr, Z, ldz);
     KPCG_LAUNCHED("bj_apply_kernel");
 }
@@ -949,15 +956,6 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-// Raise a kernel's dynamic shared-memory limit once per size (the first
-// apply runs outside any graph capture; later ones find it raised).
-static void raise_smem_limit(const void* kern, size_t smem) {
-    static std::map<const void*, size_t> done;
-    size_t& have = done[kern];
-    if (smem <= have) return;
-    KPCG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    have = smem;
-}
 
 void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, int c,
                     cudaStream_t st) {
