@@ -389,6 +389,77 @@ def run_predict(args):
     s.close()
 
 
+FIG1_LOG_ELL = (-1.0, -0.5, 0.0, 0.5, 1.0)
+FIG1_LOG_NOISE = (-4.0, -3.0, -2.0, -1.0, 0.0)
+FIG1_SHAPES = {"concrete": (1030, 8), "power": (9568, 4)}
+
+
+def fig1_problem(shape, seed=0):
+    """Synthetic stand-in of a dataset shape for the preconditioner comparison
+    of Sec. 4: standardized Gaussian X, y = sum sin(x) + noise, isotropic kernel."""
+    n, d = FIG1_SHAPES[shape]
+    return synthetic.make_problem(n, d, seed, dist="standardized", ard=False, ell=1.0,
+                                  name=f"{shape}-shaped n={n} d={d}")
+
+
+def fig1_cell(kpcg, torch, dev, p, log_ell, log_noise, kind):
+    """Iterations of (P)CG on one grid cell (Sec. 4): isotropic RBF with s^2 = 1,
+    l = 10^log_ell, noise 10^log_noise, stop at ||r||^2 < n 1e-10, cap 100 000;
+    Nystrom with m = sqrt(n) inducing points, block-Jacobi with blocks of sqrt(n)."""
+    m = int(math.ceil(math.sqrt(p.n)))
+    lt = np.array([log_ell * math.log(10.0), 0.0])
+    opt = kpcg.default_options(precision=kpcg.KPCG_FP64, tol_mode=1, max_iter=100000)
+    with kpcg.Solver(torch.from_numpy(p.X).to(dev), lt, 10.0 ** log_noise, ard=False,
+                     options=opt) as s:
+        if kind == "nystrom":
+            s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=5))
+        elif kind == "block_jacobi":
+            s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, m)
+        _, it, info, st = s.solve(torch.from_numpy(p.y).to(dev), tol=1e-10,
+                                  raise_on_error=False)
+    return int(it[0]), int(st)
+
+
+def run_fig1(args):
+    """The preconditioner comparison of Sec. 4 on synthetic data of the Concrete
+    shape (and, with --fig1-power, the Power-plant shape): iteration counts over
+    the (log10 l, log10 noise) grid and the gain log10(#PCG / #CG)."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    shapes = ["concrete"] + (["power"] if args.fig1_power else [])
+    out = {}
+    t0 = time.perf_counter()
+    for shape in shapes:
+        p = fig1_problem(shape)
+        grid = []
+        for le in FIG1_LOG_ELL:
+            for ln in FIG1_LOG_NOISE:
+                row = {"log10_ell": le, "log10_noise": ln}
+                for kind in ("none", "nystrom", "block_jacobi"):
+                    it, st = fig1_cell(kpcg, torch, dev, p, le, ln, kind)
+                    row[kind] = it
+                    row[kind + "_status"] = st
+                for kind in ("nystrom", "block_jacobi"):
+                    row[kind + "_gain_log10"] = (math.log10(max(row[kind], 1) / max(row["none"], 1)))
+                grid.append(row)
+        out[shape] = grid
+    wall = time.perf_counter() - t0
+    line = {"metric": "PCG iterations over the (l, noise) grid, Sec. 4 comparison",
+            "value": wall, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "isotropic RBF, s^2=1, stop ||r||^2 < n 1e-10, cap 1e5; "
+                                   "Nystrom m=sqrt(n), block-Jacobi b=sqrt(n); synthetic X of "
+                                   "the dataset shapes", "shapes": shapes},
+            "grid": out}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
 
 
@@ -547,7 +618,7 @@ def main():
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
     ap.add_argument("--workload", default="solve65k",
-                    choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k"],
+                    choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k", "fig1"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -557,6 +628,7 @@ def main():
     ap.add_argument("--batch-m-max", type=int, default=1024,
                     help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
     ap.add_argument("--batch-m-div", type=int, default=4)
+    ap.add_argument("--fig1-power", action="store_true", help="fig1: add the Power-plant shape")
     ap.add_argument("--traj-steps", type=int, default=24, help="warm131k: trajectory length")
     ap.add_argument("--traj-train", type=int, default=12, help="warm131k: training steps")
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
@@ -573,6 +645,8 @@ def main():
         return run_warm(args)
     if args.workload == "predict4k":
         return run_predict(args)
+    if args.workload == "fig1":
+        return run_fig1(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg

@@ -446,3 +446,28 @@ def test_predictions_match_oracle(kpcg, ns, precond):
     assert v0 is None
     np.testing.assert_allclose(_np(v), vref, rtol=0, atol=1e-7 * s2)
     assert info.iters_total > 0 and info.max_rel_res <= 1e-12
+
+
+# --------------------------------------------- preconditioner comparison grid
+@pytest.mark.parametrize("log_ell,log_noise", [(0.0, -1.0), (0.5, -2.0), (-0.5, -1.0)])
+@pytest.mark.parametrize("kind", ["none", "nystrom", "block_jacobi"])
+def test_comparison_grid_iterations_match_oracle(kpcg, log_ell, log_noise, kind):
+    # Cells of the Sec. 4 comparison (Concrete shape, isotropic, s^2 = 1, stop at
+    # ||r||^2 < n 1e-10): FP64 PCG on both sides, so the iteration counts agree up
+    # to rounding-order effects (2 iterations or 5%).
+    import math
+    import bench
+    p = bench.fig1_problem("concrete")
+    it_gpu, st = bench.fig1_cell(kpcg, torch, DEV, p, log_ell, log_noise, kind)
+    assert st == 0
+    m = int(math.ceil(math.sqrt(p.n)))
+    ell = np.full(p.d, 10.0 ** log_ell)
+    noise = 10.0 ** log_noise
+    pc = None
+    if kind == "nystrom":
+        pc = oracle.Nystrom(p.X, ell, 1.0, noise, synthetic.inducing_subset(p.n, m, seed=5))
+    elif kind == "block_jacobi":
+        pc = oracle.BlockJacobi(p.X, ell, 1.0, noise, m)
+    _, it, _, rc = oracle.pcg(p.X, ell, 1.0, noise, p.y, precond=pc, tol=1e-10, tol_mode=1)
+    assert rc == 0
+    assert abs(it_gpu - int(it[0])) <= max(2, 0.05 * int(it[0])), (it_gpu, int(it[0]))
