@@ -352,3 +352,59 @@ def predict(X, ell, s2, noise, alpha, Xs, var=True):
     W = dense_solve(X, ell, s2, noise, np.asfortranarray(Ks.T))  # K_y^{-1} k_* per column
     v = s2 - np.einsum("ij,ji->i", Ks, W)
     return mean, v
+
+
+# ---------------------------------------------------------------------------
+# FITC preconditioner (Sec. 3.1): P = Q + diag(K - Q) + noise I, Q = K_XU K_UU^{-1} K_UX
+# ---------------------------------------------------------------------------
+class FITC:
+    """Dense FP64 construction of the FITC approximation of K_y (small n)."""
+
+    kind = 3
+
+    def __init__(self, X, ell, s2, noise, idx):
+        X = _f64c(X)
+        self.idx = np.ascontiguousarray(idx, dtype=np.int64)
+        U = X[self.idx]
+        KXU = gram(X, U, ell, s2)
+        KUU = gram(U, U, ell, s2)
+        Q = KXU @ chol_solve(cholesky(KUU), np.asfortranarray(KXU.T))
+        diagK = np.full(X.shape[0], float(s2))  # K_ii = s2 (Eq. 1)
+        self.P = Q - np.diag(np.diag(Q)) + np.diag(diagK + float(noise))
+        self.L = cholesky(self.P)
+        self.n = X.shape[0]
+
+    def apply(self, R) -> np.ndarray:
+        return chol_solve(self.L, R)
+
+
+def pcg_dense(A, b, apply_pinv, tol=1e-8, tol_mode=0, max_iter=100000):
+    """Textbook preconditioned CG (Algorithm 1 as read by the C oracle: when the
+    recursive residual passes, the true one is recomputed and CG restarts from
+    x, at most 5 times) on a dense SPD A, one right-hand side; returns
+    (x, iterations).  Used with preconditioners the C oracle does not have."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    x = np.zeros(n)
+    thr = n * tol if tol_mode == 1 else tol * tol * (b @ b)
+    it = 0
+    for _restart in range(7):
+        r = b - A @ x
+        if r @ r <= thr or it >= max_iter or _restart == 6:
+            break
+        z = apply_pinv(r)
+        p = z.copy()
+        rho = r @ z
+        while it < max_iter:
+            q = A @ p
+            a = rho / (p @ q)
+            it += 1
+            x += a * p
+            r -= a * q
+            if r @ r <= thr:
+                break
+            z = apply_pinv(r)
+            rho_new = r @ z
+            p = z + (rho_new / rho) * p
+            rho = rho_new
+    return x, it

@@ -403,3 +403,45 @@ def test_predict_variance_bounds_and_monotone_in_data():
     a2 = oracle.dense_solve(p.X[:40], ell, s2, p.noise, p.y[:40, None])[:, 0]
     _, v2 = oracle.predict(p.X[:40], ell, s2, p.noise, a2, Xs)
     assert np.all(v2 >= v - 1e-12)
+
+
+# -------------------------------------------------------------------- FITC
+def test_fitc_diagonal_matches_k_y_and_is_spd():
+    # FITC keeps the diagonal of K_y exactly (the correction diag(K - Q) puts
+    # it back) and P - noise I = Q + diag(K - Q) is positive semi-definite
+    p = synthetic.make_problem(120, 3, 9, ell=0.9, noise=0.02)
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    idx = synthetic.inducing_subset(120, 15, seed=2)
+    F = oracle.FITC(p.X, ell, s2, p.noise, idx)
+    np.testing.assert_allclose(np.diag(F.P), s2 + p.noise, rtol=1e-14)
+    w = np.linalg.eigvalsh(F.P - p.noise * np.eye(120))
+    assert w.min() >= -1e-10 * w.max()
+    # off the diagonal it is the Nystrom approximation, not K
+    K = oracle.gram(p.X, p.X, ell, s2)
+    assert np.abs(F.P - K - p.noise * np.eye(120)).max() > 1e-3
+
+
+def test_fitc_with_all_points_is_k_y():
+    # m = n: Q = K, diag(K - Q) = 0, P = K + noise I; PCG then converges at once
+    p = synthetic.make_problem(50, 2, 3, ell=1.0, noise=0.1)
+    ell, s2 = oracle.split_theta(p.log_theta, 2, True)
+    F = oracle.FITC(p.X, ell, s2, p.noise, np.arange(50))
+    Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
+    np.testing.assert_allclose(F.P, Ky, atol=1e-8 * np.abs(Ky).max())
+    _, it = oracle.pcg_dense(Ky, p.y, F.apply, tol=1e-10)
+    assert it == 1
+
+
+def test_pcg_dense_matches_c_oracle_iterations():
+    # the NumPy PCG used with FITC follows the same recurrence as the C oracle
+    p = synthetic.make_problem(200, 4, 12, ell=1.3, noise=0.01)
+    ell, s2 = oracle.split_theta(p.log_theta, 4, True)
+    Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
+    idx = synthetic.inducing_subset(200, 20, seed=4)
+    N = oracle.Nystrom(p.X, ell, s2, p.noise, idx)
+    for pc in (None, N):
+        _, it_c, _, _ = oracle.pcg(p.X, ell, s2, p.noise, p.y, precond=pc, tol=1e-9)
+        x, it_d = oracle.pcg_dense(Ky, p.y, (pc.apply if pc else (lambda r: r)), tol=1e-9)
+        # same recurrence and restart rule; rounding order differs (dense product)
+        assert abs(int(it_c[0]) - it_d) <= max(2, 0.05 * int(it_c[0])), (int(it_c[0]), it_d)
+        assert np.linalg.norm(Ky @ x - p.y) <= 1e-9 * np.linalg.norm(p.y)
