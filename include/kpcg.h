@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
     KPCG_PREC_NONE = 0,          /* P = I: plain CG                              */
     KPCG_PREC_NYSTROM = 1,       /* P = K_XU K_UU^-1 K_UX + sigma^2 I (Sec. 3.1)  */
-    KPCG_PREC_BLOCK_JACOBI = 2   /* P = bldiag(K_y) (Sec. 3.3.1)                  */
+    KPCG_PREC_BLOCK_JACOBI = 2,  /* P = bldiag(K_y) (Sec. 3.3.1)                  */
+    KPCG_PREC_FITC = 3           /* P = Q + diag(K - Q) + sigma^2 I, Q the Nystrom
+                                    approximation K_XU K_UU^-1 K_UX (Sec. 3.1)   */
 } kpcg_precond_kind;
 
 typedef enum {
@@ -152,6 +154,10 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt);
  *     1e-12*tr/m*10^k (k = 0..6) is added to its diagonal.
  *   KPCG_PREC_BLOCK_JACOBI: size = b, idx ignored; contiguous blocks of b rows,
  *     the last one shorter, P = bldiag(K_y) (Sec. 3.3.1).
+ *   KPCG_PREC_FITC: size = m, idx as for Nystrom; P = Q + diag(K - Q) + sigma^2 I
+ *     (Sec. 3.1).  With D = diag(K - Q) + sigma^2 the inversion lemma gives
+ *     P^-1 = D^-1/2 [I - K~ (K_UU + K~^T K~)^-1 K~^T] D^-1/2, K~ = D^-1/2 K_XU;
+ *     K_UU and the inner matrix are factored with the same jitter rule.
  *   KPCG_PREC_NONE: removes the preconditioner.
  * In the mixed modes the preconditioner approximates the inner operator, so
  * it is built with noise sigma^2 (1 + inner_shift); it is rebuilt when the

@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     KPCG_FP32_IR,
     KPCG_FP64,
     KPCG_PREC_BLOCK_JACOBI,
+    KPCG_PREC_FITC,
     KPCG_PREC_NONE,
     KPCG_PREC_NYSTROM,
     KPCG_TC_IR,

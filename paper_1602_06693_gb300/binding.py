@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
-KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI = 0, 1, 2
+KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI, KPCG_PREC_FITC = 0, 1, 2, 3
 KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64 = 0, 1, 2, 3, 4
 
 _STATUS = {

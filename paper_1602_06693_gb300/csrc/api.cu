@@ -304,6 +304,9 @@ static void build_precond(Ctx& h) {
     else if (h.pkind == KPCG_PREC_BLOCK_JACOBI)
         block_jacobi_setup(h.P, h.xs64.p, h.n, h.dp, h.c0_64(), nz,
                            std::min<int64_t>(h.psize, h.n), h.stream);
+    else if (h.pkind == KPCG_PREC_FITC)
+        fitc_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), h.s2, nz,
+                   h.pidx.data(), h.psize, h.stream);
     h.P.n = h.n;
     h.P.noise = nz;
     KPCG_CUDA(cudaStreamSynchronize(h.stream));
@@ -933,10 +936,10 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt) {
 kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx) {
     if (!h) return KPCG_ERR_ARG;
     KPCG_GUARD(h, {
-        if (kind == KPCG_PREC_NYSTROM) {
+        if (kind == KPCG_PREC_NYSTROM || kind == KPCG_PREC_FITC) {
             if (size < 1 || size > h->n || size > 4096)
-                fail(KPCG_ERR_ARG, "Nystrom m must be in [1, min(n, 4096)]");
-            if (!idx) fail(KPCG_ERR_ARG, "Nystrom needs the inducing indices");
+                fail(KPCG_ERR_ARG, "inducing-point count m must be in [1, min(n, 4096)]");
+            if (!idx) fail(KPCG_ERR_ARG, "Nystrom and FITC need the inducing indices");
             for (int64_t a = 0; a < size; ++a) {
                 if (idx[a] < 0 || idx[a] >= h->n) fail(KPCG_ERR_ARG, "inducing index out of range");
                 if (a && idx[a] <= idx[a - 1])

@@ -522,13 +522,14 @@ static int factor_and_invert(double* A, double* U, int64_t b, int64_t n_total, i
     return 0;
 }
 
-void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
-                   float c0_32, double c0_64, double noise, const int64_t* idx_host, int64_t m,
-                   cudaStream_t st) {
-    P.kind = KPCG_PREC_NYSTROM;
+// Inducing rows and K_XU (FP64 entries, direct differences, stored as exact
+// FP32 pairs: at small noise the preconditioner needs FP64-accurate entries;
+// an FP32 rounding of K_XU alone raised the PCG iteration count by 10-50%).
+static void nys_gather_kxu(PrecondState& P, const float* xs32, const double* xs64, int64_t n,
+                           int dp, double c0_64, const int64_t* idx_host, int64_t m,
+                           cudaStream_t st) {
     P.n = n;
     P.m = m;
-    P.noise = noise;
     int64_t* idx = P.idx.need((size_t)m);
     KPCG_CUDA(cudaMemcpyAsync(idx, idx_host, sizeof(int64_t) * m, cudaMemcpyHostToDevice, st));
     float* us32 = P.us32.need((size_t)m * dp);
@@ -538,27 +539,19 @@ void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64
     KPCG_LAUNCHED("gather_rows_f32");
     gather_rows_f64<<<g, 256, 0, st>>>(xs64, idx, m, dp, us64);
     KPCG_LAUNCHED("gather_rows_f64");
-    // K_XU in FP64 entries (direct differences), stored as exact FP32 pairs: at
-    // small noise the preconditioner needs FP64-accurate entries (an FP32
-    // rounding of K_XU alone raised the PCG iteration count by 10-50%).
     float2* KXU = P.KXU.need((size_t)n * m);
     kxu_pair_f64(xs64, n, us64, m, dp, c0_64, KXU, st);
-    // M0 = sigma^2 K_UU + K_UX K_XU
-    double* M0 = P.M0.need((size_t)m * m);
-    kuu_f64(us64, m, dp, c0_64, noise, 0.0, M0, st);
-    const int64_t tiles = (m + ST - 1) / ST;
-    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 4095) / 4096));
-    const int64_t rps = ((n + nsplit - 1) / nsplit + SR - 1) / SR * SR;
-    nsplit = (int)((n + rps - 1) / rps);
-    double* part = P.scratch.need((size_t)nsplit * m * m);
-    dim3 gs((unsigned)tiles, (unsigned)tiles, (unsigned)nsplit);
-    syrk_kxu_kernel<<<gs, 256, 0, st>>>(KXU, n, m, rps, part);
-    KPCG_LAUNCHED("syrk_kxu_kernel");
-    syrk_reduce_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, nsplit, m, M0);
-    KPCG_LAUNCHED("syrk_reduce_kernel");
-    // trace for the jitter ladder
+}
+
+// Factor A (m x m, from A0 plus jitter) into P.M = L and P.U = L^{-T} with the
+// deterministic acceptance rule (the paper is silent): every pivot must exceed
+// 3e-12 * max diag(A0), else the jitter 1e-12 tr(A0)/m 10^k, k = 0..6, is added;
+// a nearly singular matrix otherwise "factors" or not depending on rounding,
+// and pivots near zero make a useless preconditioner.  Returns the jitter.
+static double factor_with_rule(PrecondState& P, const double* A0, int64_t m, cudaStream_t st,
+                               const char* what) {
     std::vector<double> diag((size_t)m);
-    KPCG_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), M0, sizeof(double) * (m + 1),
+    KPCG_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), A0, sizeof(double) * (m + 1),
                                 sizeof(double), (size_t)m, cudaMemcpyDeviceToHost, st));
     KPCG_CUDA(cudaStreamSynchronize(st));
     double tr = 0.0, dmax = 0.0;
@@ -566,26 +559,125 @@ void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64
         tr += v;
         dmax = std::max(dmax, v);
     }
-    // Deterministic acceptance (the paper is silent): every pivot must exceed
-    // kPivotTol * max diag(M); a nearly singular M otherwise "factors" or not
-    // depending on rounding details, and a factor with pivots near zero makes
-    // a useless preconditioner.
     const double kPivotTol = 3e-12;
     double* M = P.M.need((size_t)m * m);
     double* U = P.U.need((size_t)m * m);
     int* status = P.status.need(1);
     int rc = 1;
-    P.jitter = 0.0;
+    double jitter = 0.0;
     for (int k = -1; k <= 6 && rc; ++k) {
-        P.jitter = (k < 0) ? 0.0 : 1e-12 * tr / (double)m * std::pow(10.0, (double)k);
-        KPCG_CUDA(cudaMemcpyAsync(M, M0, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
-        if (P.jitter > 0.0) {
-            add_diag_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(M, m, P.jitter);
+        jitter = (k < 0) ? 0.0 : 1e-12 * tr / (double)m * std::pow(10.0, (double)k);
+        KPCG_CUDA(cudaMemcpyAsync(M, A0, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+        if (jitter > 0.0) {
+            add_diag_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(M, m, jitter);
             KPCG_LAUNCHED("add_diag_kernel");
         }
         rc = factor_and_invert(M, U, m, m, 1, status, st, kPivotTol * dmax);
     }
-    if (rc) fail(KPCG_ERR_NOT_SPD, "Nystrom inner matrix is not positive definite after jitter");
+    if (rc) fail(KPCG_ERR_NOT_SPD, std::string(what) + " is not positive definite after jitter");
+    return jitter;
+}
+
+// M0 = noise K_UU + K_UX K_XU (FP64 SYRK over the pairs), factored by the rule.
+static void nys_inner(PrecondState& P, int64_t n, int64_t m, int dp, double c0_64, double noise,
+                      cudaStream_t st) {
+    double* M0 = P.M0.need((size_t)m * m);
+    kuu_f64(P.us64.p, m, dp, c0_64, noise, 0.0, M0, st);
+    const int64_t tiles = (m + ST - 1) / ST;
+    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 4095) / 4096));
+    const int64_t rps = ((n + nsplit - 1) / nsplit + SR - 1) / SR * SR;
+    nsplit = (int)((n + rps - 1) / rps);
+    double* part = P.scratch.need((size_t)nsplit * m * m);
+    dim3 gs((unsigned)tiles, (unsigned)tiles, (unsigned)nsplit);
+    syrk_kxu_kernel<<<gs, 256, 0, st>>>(P.KXU.p, n, m, rps, part);
+    KPCG_LAUNCHED("syrk_kxu_kernel");
+    syrk_reduce_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, nsplit, m, M0);
+    KPCG_LAUNCHED("syrk_reduce_kernel");
+    P.jitter = factor_with_rule(P, M0, m, st, "Nystrom inner matrix");
+}
+
+void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                   float c0_32, double c0_64, double noise, const int64_t* idx_host, int64_t m,
+                   cudaStream_t st) {
+    (void)c0_32;
+    P.kind = KPCG_PREC_NYSTROM;
+    P.noise = noise;
+    P.apply_noise = noise;
+    nys_gather_kxu(P, xs32, xs64, n, dp, c0_64, idx_host, m, st);
+    nys_inner(P, n, m, dp, c0_64, noise, st);
+    P.ready = true;
+}
+
+namespace {
+
+// dq[i] = |L^{-1} k_i|^2 = k_i^T K_UU^{-1} k_i with U = L^{-T} row-major:
+// (L^{-1} k)_a = sum_{b <= a} U[b][a] k_b.  One CTA per row, FP64.
+__global__ void fitc_diag_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
+                                 const double* __restrict__ U, double* __restrict__ dq) {
+    extern __shared__ double sk[];
+    __shared__ double red[8];
+    const int64_t i = blockIdx.x;
+    for (int64_t a = threadIdx.x; a < m; a += blockDim.x) {
+        const float2 kv = KXU[i * m + a];
+        sk[a] = (double)kv.x + (double)kv.y;
+    }
+    __syncthreads();
+    double s = 0.0;
+    for (int64_t a = threadIdx.x; a < m; a += blockDim.x) {
+        double v = 0.0;
+        for (int64_t b = 0; b <= a; ++b) v = fma(U[b * m + a], sk[b], v);
+        s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        dq[i] = t;
+    }
+}
+
+// D_i = s2 + noise - dq_i (at least noise: diag(K - Q) >= 0), dscale_i = D_i^{-1/2},
+// and row i of K_XU scaled by dscale_i (re-split into an exact FP32 pair).
+__global__ void fitc_scale_kernel(float2* __restrict__ KXU, int64_t n, int64_t m,
+                                  const double* __restrict__ dq, double s2, double noise,
+                                  double* __restrict__ dscale) {
+    const int64_t i = blockIdx.x;
+    const double D = fmax(s2 + noise - dq[i], noise);
+    const double sc = 1.0 / sqrt(D);
+    if (threadIdx.x == 0) dscale[i] = sc;
+    for (int64_t a = threadIdx.x; a < m; a += blockDim.x) {
+        const float2 kv = KXU[i * m + a];
+        const double v = ((double)kv.x + (double)kv.y) * sc;
+        const float hi = (float)v;
+        KXU[i * m + a] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+}  // namespace
+
+void fitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                float c0_32, double c0_64, double s2, double noise, const int64_t* idx_host,
+                int64_t m, cudaStream_t st) {
+    (void)c0_32;
+    P.kind = KPCG_PREC_FITC;
+    P.noise = noise;
+    P.apply_noise = 1.0;
+    nys_gather_kxu(P, xs32, xs64, n, dp, c0_64, idx_host, m, st);
+    // K_UU and its factor (the same acceptance rule), then diag(Q)
+    double* Kuu = P.M0.need((size_t)m * m);
+    kuu_f64(P.us64.p, m, dp, c0_64, 1.0, 0.0, Kuu, st);
+    (void)factor_with_rule(P, Kuu, m, st, "K_UU");
+    double* dq = P.w.need((size_t)n);
+    fitc_diag_kernel<<<(unsigned)n, 256, sizeof(double) * (size_t)m, st>>>(P.KXU.p, n, m, P.U.p,
+                                                                           dq);
+    KPCG_LAUNCHED("fitc_diag_kernel");
+    double* dsc = P.dscale.need((size_t)n);
+    fitc_scale_kernel<<<(unsigned)n, 256, 0, st>>>(P.KXU.p, n, m, dq, s2, noise, dsc);
+    KPCG_LAUNCHED("fitc_scale_kernel");
+    // inner matrix K_UU + K~^T K~ (unit noise) and its factor
+    nys_inner(P, n, m, dp, c0_64, 1.0, st);
     P.ready = true;
 }
 
@@ -640,7 +732,7 @@ static void nystrom_apply(const PrecondState& P, const T* R, int64_t ldr, int c,
     if (smem > 48 * 1024) raise_smem_limit((const void*)nys_back_kernel<T>, smem);
     int blocks = (int)std::min<int64_t>((n + 7) / 8, 152 * 16);
     nys_back_kernel<T><<<blocks, 256, smem, st>>>(P.KXU.p, n, m, w, c, R, ldr, Z, ldz,
-                                                  1.0 / P.noise);
+                                                  1.0 / P.apply_noise);
     KPCG_LAUNCHED("nys_back_kernel");
 }
 
@@ -706,10 +798,46 @@ static void bj_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z
 }
 
 template <typename T>
+__global__ void scale_rows_kernel(T* __restrict__ dst, int64_t ldd, const T* __restrict__ src,
+                                  int64_t lds, const double* __restrict__ sc, int64_t n) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i + (int64_t)k * ldd] = (T)((double)src[i + (int64_t)k * lds] * sc[i]);
+}
+
+template <typename T>
+static T* fitc_tmp(const PrecondState& P, size_t count);
+template <>
+double* fitc_tmp<double>(const PrecondState& P, size_t count) {
+    return const_cast<PrecondState&>(P).tmp64.need(count);
+}
+template <>
+float* fitc_tmp<float>(const PrecondState& P, size_t count) {
+    return const_cast<PrecondState&>(P).tmp32.need(count);
+}
+
+// FITC: z = D^{-1/2} Nys(D^{-1/2} r) with the unit-noise apply on the scaled K_XU.
+template <typename T>
+static void fitc_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
+                       cudaStream_t st) {
+    const int64_t n = P.n;
+    T* tmp = fitc_tmp<T>(P, (size_t)n * c);
+    const dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)c);
+    scale_rows_kernel<T><<<g, 256, 0, st>>>(tmp, n, R, ldr, P.dscale.p, n);
+    KPCG_LAUNCHED("scale_rows_kernel");
+    nystrom_apply<T>(P, tmp, n, c, Z, ldz, st);
+    scale_rows_kernel<T><<<g, 256, 0, st>>>(Z, ldz, Z, ldz, P.dscale.p, n);
+    KPCG_LAUNCHED("scale_rows_kernel");
+}
+
+template <typename T>
 static void apply_any(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
                       cudaStream_t st) {
     if (P.kind == KPCG_PREC_NYSTROM && P.ready)
         nystrom_apply<T>(P, R, ldr, c, Z, ldz, st);
+    else if (P.kind == KPCG_PREC_FITC && P.ready)
+        fitc_apply<T>(P, R, ldr, c, Z, ldz, st);
     else if (P.kind == KPCG_PREC_BLOCK_JACOBI && P.ready)
         bj_apply<T>(P, R, ldr, c, Z, ldz, st);
     else

@@ -24,6 +24,10 @@ struct PrecondState {
     DevBuf<double> scratch;  // split partials of the set-up products
     DevBuf<double> wpart, w, y;
     DevBuf<int> status;
+    double apply_noise = 0.0;  // divisor of the Nystrom apply (1 for FITC's scaled form)
+    DevBuf<double> dscale;     // FITC: D^{-1/2}, D = diag(K - Q) + sigma^2
+    DevBuf<double> tmp64;      // FITC: scaled right-hand sides
+    DevBuf<float> tmp32;
 
     void reset() {
         kind = KPCG_PREC_NONE;
@@ -40,6 +44,10 @@ struct PrecondState {
         w.release();
         y.release();
         status.release();
+        apply_noise = 0.0;
+        dscale.release();
+        tmp64.release();
+        tmp32.release();
     }
 };
 
@@ -54,6 +62,14 @@ void nystrom_project_solve(const PrecondState& P, const double* R, int64_t ldr, 
 void nystrom_expand(const PrecondState& P, const double* u, double* out, cudaStream_t st);
 void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
                         double noise, int64_t b, cudaStream_t st);
+// FITC (Sec. 3.1): P = Q + diag(K - Q) + sigma^2 I, Q = K_XU K_UU^{-1} K_UX.  With
+// D = diag(K - Q) + sigma^2 and K~ = D^{-1/2} K_XU the inversion lemma gives
+// P^{-1} = D^{-1/2} [I - K~ (K_UU + K~^T K~)^{-1} K~^T] D^{-1/2}: the Nystrom
+// apply with unit noise on the row-scaled K_XU, between two diagonal scalings.
+// s2: the amplitude (K_ii = s2).
+void fitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                float c0_32, double c0_64, double s2, double noise, const int64_t* idx_host,
+                int64_t m, cudaStream_t st);
 
 // ------------------------------------------- batched Nystrom apply
 // Problems laid out column by column (problem p owns columns p*c .. p*c+c-1

@@ -471,3 +471,42 @@ def test_comparison_grid_iterations_match_oracle(kpcg, log_ell, log_noise, kind)
     _, it, _, rc = oracle.pcg(p.X, ell, 1.0, noise, p.y, precond=pc, tol=1e-10, tol_mode=1)
     assert rc == 0
     assert abs(it_gpu - int(it[0])) <= max(2, 0.05 * int(it[0])), (it_gpu, int(it[0]))
+
+
+# ------------------------------------------------------------------ FITC
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_fitc_apply_and_solve_match_oracle(kpcg, precision):
+    # apply: FP64 on both sides (the GPU applies the inversion lemma, the oracle
+    # a dense Cholesky of P), 1e-9; solve: the same iterates as textbook PCG with
+    # the oracle's FITC (2 iterations or 5%), solution as the dense solve
+    p = _problem(900, 5, seed=51, noise=0.02)
+    idx = synthetic.inducing_subset(900, 40, seed=7)
+    ell, s2 = oracle.split_theta(p.log_theta, 5, True)
+    F = oracle.FITC(p.X, ell, s2, p.noise, idx)
+    R = synthetic.rng(8).standard_normal((900, 3))
+    prec = kpcg.KPCG_FP64 if precision == "fp64" else kpcg.KPCG_DF64
+    with _solver(kpcg, p, precision=prec) as s:
+        s.precond(kpcg.KPCG_PREC_FITC, 40, idx)
+        Z = _np(s.precond_apply(_cm(R)))
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-10)
+    assert st == 0
+    for k in range(3):
+        assert _rel(Z[:, k], F.apply(R[:, k])) <= 1e-9, k
+    Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
+    xref, it_ref = oracle.pcg_dense(Ky, p.y, F.apply, tol=1e-10)
+    assert _rel(_np(x), oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]) <= 1e-7
+    assert abs(int(it[0]) - it_ref) <= max(2, 0.05 * it_ref), (int(it[0]), it_ref)
+
+
+def test_fitc_in_the_mixed_solver(kpcg):
+    # FITC as the inner preconditioner of the tensor-core mixed solve (FP32 apply)
+    p = _problem(2000, 6, seed=53, noise=0.01)
+    idx = synthetic.inducing_subset(2000, 100, seed=9)
+    with _solver(kpcg, p, precision=kpcg.KPCG_TC_IR, inner_shift=0.25, inner_tol=0.1) as s:
+        s.precond(kpcg.KPCG_PREC_FITC, 100, idx)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+    assert st == 0 and info.max_rel_res <= 1e-8
+    ell, s2 = oracle.split_theta(p.log_theta, 6, True)
+    rows = np.arange(0, 2000, 97)
+    r = p.y[rows] - (oracle.gram(p.X[rows], p.X, ell, s2) @ _np(x) + p.noise * _np(x)[rows])
+    assert np.abs(r).max() <= 1e-8 * np.linalg.norm(p.y)
