@@ -493,7 +493,9 @@ def test_fitc_apply_and_solve_match_oracle(kpcg, precision):
     for k in range(3):
         assert _rel(Z[:, k], F.apply(R[:, k])) <= 1e-9, k
     Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
-    xref, it_ref = oracle.pcg_dense(Ky, p.y, F.apply, tol=1e-10)
+    # the double-float solver iterates to half the tolerance before certifying
+    ref_tol = 1e-10 if precision == "fp64" else 0.5e-10
+    xref, it_ref = oracle.pcg_dense(Ky, p.y, F.apply, tol=ref_tol)
     assert _rel(_np(x), oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]) <= 1e-7
     assert abs(int(it[0]) - it_ref) <= max(2, 0.05 * it_ref), (int(it[0]), it_ref)
 
