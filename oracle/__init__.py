@@ -408,3 +408,96 @@ def pcg_dense(A, b, apply_pinv, tol=1e-8, tol_mode=0, max_iter=100000):
             p = z + (rho_new / rho) * p
             rho = rho_new
     return x, it
+
+
+# ---------------------------------------------------------------------------
+# Spectral preconditioner (Sec. 3.2, random Fourier features)
+# ---------------------------------------------------------------------------
+class Spectral:
+    """P = Phi Phi^T + noise I with the random-feature approximation of Sec. 3.2:
+    K^_ij = (s2/m) sum_r cos(2 pi s_r^T (x_i - x_j)), written as Phi Phi^T with
+    Phi_i = sqrt(s2/m) [cos(2 pi s_r^T x_i), sin(2 pi s_r^T x_i)]_{r=1..m} (the
+    cosine of a difference is cos cos + sin sin).  The frequencies are drawn from
+    N(0, Lambda / (4 pi^2)), Lambda = diag(1/l_r^2); they enter as standard-normal
+    draws omega (m x d), s_r = omega_r / (2 pi l).  Dense FP64 (small n): P is
+    formed and factored."""
+
+    kind = 4
+
+    def __init__(self, X, ell, s2, noise, omega):
+        X = _f64c(X)
+        n, d = X.shape
+        omega = np.asarray(omega, dtype=np.float64).reshape(-1, d)
+        m = omega.shape[0]
+        ell = np.broadcast_to(np.asarray(ell, dtype=np.float64), (d,))
+        S = omega / (2.0 * np.pi * ell[None, :])  # spectral points s_r (rows)
+        ph = 2.0 * np.pi * (X @ S.T)              # n x m phases
+        self.Phi = np.sqrt(float(s2) / m) * np.concatenate([np.cos(ph), np.sin(ph)], axis=1)
+        self.Khat = self.Phi @ self.Phi.T
+        self.P = self.Khat + float(noise) * np.eye(n)
+        self.L = cholesky(self.P)
+        self.n, self.m, self.noise = n, m, float(noise)
+
+    def apply(self, R) -> np.ndarray:
+        return chol_solve(self.L, R)
+
+
+# ---------------------------------------------------------------------------
+# GP classification: Laplace approximation with the probit likelihood
+# (Sec. 2.2 and Appendix B)
+# ---------------------------------------------------------------------------
+def probit_terms(y, f):
+    """Per point: log p(y_i|f_i) = log Phi(y_i f_i) (the probit likelihood of
+    Appendix B), its first derivative g_i and W_ii = -(second derivative).
+    With z = y f and r = N(z)/Phi(z): g = y r, W = r^2 + z r (y = +-1).  The
+    ratio is taken through the log CDF so that it stays finite for z << 0."""
+    from scipy.special import log_ndtr
+
+    y = np.asarray(y, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    z = y * f
+    lp = log_ndtr(z)
+    r = np.exp(-0.5 * z * z - 0.5 * np.log(2.0 * np.pi) - lp)
+    return lp, y * r, r * r + z * r
+
+
+def laplace_probit(X, ell, s2, y, tol=1e-12, max_newton=100):
+    """The Newton iteration for the posterior mode f^ of the Laplace
+    approximation (Appendix B, Algorithm "Laplace approximation for GPs"), dense
+    FP64 for small n.  Each step: W and g at f; b = W f + g; v = W^1/2 K b;
+    solve B z = v with B = I + W^1/2 K W^1/2 (Cholesky here, PCG on the GPU);
+    a = b - W^1/2 z; f = K a.  The paper only says "until convergence": the
+    loop stops once the objective Psi(f) = log p(y|f) - 1/2 f^T K^{-1} f
+    (= log p(y|f) - 1/2 a^T f) changes by at most tol * max(1, |Psi|), or after
+    max_newton steps.  Returns f^, a, the step count, Psi and the approximate
+    log marginal likelihood log q = -1/2 log|B| - 1/2 a^T f^ + log p(y|f^)
+    (Sec. 2.2), with B taken at f^."""
+    X = _f64c(X)
+    y = np.asarray(y, dtype=np.float64)
+    n = X.shape[0]
+    K = gram(X, X, ell, s2)
+    f = np.zeros(n)
+    a = np.zeros(n)
+    psi_old = float(probit_terms(y, f)[0].sum())
+    psi = psi_old
+    steps = 0
+    while steps < max_newton:
+        steps += 1
+        _lp, g, W = probit_terms(y, f)
+        sW = np.sqrt(W)
+        b = W * f + g
+        v = sW * (K @ b)
+        B = np.eye(n) + sW[:, None] * K * sW[None, :]
+        z = chol_solve(cholesky(B), v)
+        a = b - sW * z
+        f = K @ a
+        psi = float(probit_terms(y, f)[0].sum() - 0.5 * a @ f)
+        done = abs(psi - psi_old) <= tol * max(1.0, abs(psi))
+        psi_old = psi
+        if done:
+            break
+    lp, _g, W = probit_terms(y, f)
+    sW = np.sqrt(W)
+    LB = cholesky(np.eye(n) + sW[:, None] * K * sW[None, :])
+    logq = float(-np.sum(np.log(np.diag(LB))) - 0.5 * a @ f + lp.sum())
+    return {"f": f, "a": a, "steps": steps, "psi": psi, "logq": logq}

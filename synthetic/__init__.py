@@ -42,6 +42,10 @@ __all__ = [
     "rademacher",
     "inducing_subset",
     "mlp_init",
+    "spectral_draws",
+    "classification_problem",
+    "eeg_shape",
+    "credit_shape",
 ]
 
 
@@ -200,3 +204,40 @@ def mlp_init(seed: int, n_in: int, h1: int, h2: int, n_out: int) -> dict:
 
     return {"W1": xavier(h1, n_in), "b1": np.zeros(h1), "W2": xavier(h2, h1),
             "b2": np.zeros(h2), "W3": xavier(n_out, h2), "b3": np.zeros(n_out)}
+
+
+def spectral_draws(m: int, d: int, seed: int) -> np.ndarray:
+    """m x d standard-normal draws (float64, row-major): the random part of the
+    spectral points of the random-feature preconditioner (Sec. 3.2), which both
+    sides scale by 1 / (2 pi l) themselves."""
+    return np.ascontiguousarray(rng(seed).standard_normal((m, d)))
+
+
+def classification_problem(n: int, d: int, seed: int, *, ell=None, s2: float = 4.0,
+                           flip: float = 0.05, name: str = "") -> GPProblem:
+    """Binary labels y = +-1 for probit GP classification (Sec. 2.2, App. B):
+    X ~ N(0, I_d) standardized per column, y = sign(sum_j sin(x_j)), each label
+    flipped with probability ``flip``; ``noise`` is unused by the classifier
+    (set to 1).  ``ell`` defaults to sqrt(d), ARD."""
+    g = rng(seed)
+    X = g.standard_normal((n, d))
+    X = (X - X.mean(axis=0)) / X.std(axis=0)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    s = np.sin(X.astype(np.float64)).sum(axis=1)
+    y = np.where(s >= 0.0, 1.0, -1.0)
+    y = np.where(g.random(n) < flip, -y, y)
+    ls = np.full(d, math.sqrt(d)) if ell is None else \
+        np.broadcast_to(np.asarray(ell, dtype=np.float64), (d,)).copy()
+    log_theta = np.concatenate([np.log(ls), [math.log(s2)]])
+    return GPProblem(X=X, y=y, log_theta=log_theta.astype(np.float64), noise=1.0, ard=True,
+                     name=name)
+
+
+def eeg_shape(seed: int = 0) -> GPProblem:
+    """Stand-in of the EEG classification set's shape (n=14979, d=14, Sec. 5)."""
+    return classification_problem(14979, 14, seed, name="probit n=14979 d=14 (EEG shape)")
+
+
+def credit_shape(seed: int = 0) -> GPProblem:
+    """Stand-in of the Credit classification set's shape (n=1000, d=24, App. C)."""
+    return classification_problem(1000, 24, seed, name="probit n=1000 d=24 (Credit shape)")

@@ -445,3 +445,145 @@ def test_pcg_dense_matches_c_oracle_iterations():
         # same recurrence and restart rule; rounding order differs (dense product)
         assert abs(int(it_c[0]) - it_d) <= max(2, 0.05 * int(it_c[0])), (int(it_c[0]), it_d)
         assert np.linalg.norm(Ky @ x - p.y) <= 1e-9 * np.linalg.norm(p.y)
+
+
+# ------------------------------------------------- Sec. 3.2 spectral features
+def test_spectral_diagonal_rank_and_shift_invariance():
+    # cos^2 + sin^2 = 1 puts s2 on the diagonal for any draws; the features
+    # depend on x_i - x_j only; Phi has 2m columns, so rank(K^) <= 2m
+    X, ls, s2, noise, _ = _small(30, 3, seed=4)
+    om = synthetic.spectral_draws(25, 3, seed=5)
+    S = oracle.Spectral(X, ls, s2, noise, om)
+    np.testing.assert_allclose(np.diag(S.Khat), s2, rtol=1e-13)
+    S2 = oracle.Spectral(X + np.array([0.7, -1.9, 3.1]), ls, s2, noise, om)
+    np.testing.assert_allclose(S2.Khat, S.Khat, atol=1e-12 * s2)
+    S3 = oracle.Spectral(X, ls, s2, noise, om[:5])
+    w = np.linalg.eigvalsh(S3.Khat)
+    assert (w > 1e-10 * w.max()).sum() <= 10
+
+
+def test_spectral_converges_to_the_rbf_kernel():
+    # E cos(w^T (x - x') / l) = exp(-|(x - x') / l|^2 / 2) for w ~ N(0, I), the
+    # spectral density of Eq. 1: with m draws each entry has a standard error of
+    # at most s2 / sqrt(2m); a slip in the 2 pi or 1/l scaling is off by O(1)
+    X, ls, s2, noise, _ = _small(25, 3, seed=6)
+    m = 40000
+    S = oracle.Spectral(X, ls, s2, noise, synthetic.spectral_draws(m, 3, seed=7))
+    K = _lib_gram(X, X, ls, s2)
+    assert np.abs(S.Khat - K).max() <= 6.0 * s2 / math.sqrt(2 * m)
+
+
+def test_spectral_inversion_lemma_carries_the_noise():
+    # (Phi Phi^T + lam I)^{-1} v = lam^{-1} [v - Phi (lam I + Phi^T Phi)^{-1} Phi^T v]
+    # (the inversion lemma); the printed (I + Phi^T Phi) holds only for lam = 1
+    X, ls, s2, _, _ = _small(40, 3, seed=8)
+    lam = 0.05
+    S = oracle.Spectral(X, ls, s2, lam, synthetic.spectral_draws(12, 3, seed=9))
+    v = synthetic.rng(10).standard_normal(40)
+    F = S.Phi
+    I2 = np.eye(F.shape[1])
+    lemma = (v - F @ np.linalg.solve(lam * I2 + F.T @ F, F.T @ v)) / lam
+    np.testing.assert_allclose(S.apply(v), lemma, rtol=1e-9, atol=1e-9 * np.abs(lemma).max())
+    printed = (v - F @ np.linalg.solve(I2 + F.T @ F, F.T @ v)) / lam
+    assert np.linalg.norm(printed - lemma) > 1e-3 * np.linalg.norm(lemma)
+
+
+# ------------------------------------- App. B: probit likelihood and Laplace
+def test_probit_terms_closed_form_and_finite_differences():
+    from scipy.stats import norm
+
+    y = np.array([1.0, -1.0, 1.0, -1.0])
+    lp, g, W = oracle.probit_terms(y, np.zeros(4))
+    np.testing.assert_allclose(lp, -math.log(2.0), rtol=1e-15)
+    np.testing.assert_allclose(g, y * math.sqrt(2.0 / math.pi), rtol=1e-14)
+    np.testing.assert_allclose(W, 2.0 / math.pi, rtol=1e-14)
+    # derivatives of log Phi(y f) by central differences of SciPy's log CDF
+    y = np.array([1.0, -1.0, 1.0, -1.0, 1.0, -1.0])
+    f = np.array([-7.0, -0.3, 0.4, 6.5, -25.0, 2.2])
+    lp, g, W = oracle.probit_terms(y, f)
+    L = lambda ff: norm.logcdf(y * ff)  # noqa: E731
+    np.testing.assert_allclose(lp, L(f), rtol=1e-13)
+    h = 1e-5
+    np.testing.assert_allclose(g, (L(f + h) - L(f - h)) / (2 * h), rtol=1e-7)
+    h = 1e-3
+    np.testing.assert_allclose(W, -(L(f + h) - 2 * L(f) + L(f - h)) / h**2, rtol=1e-5)
+    assert np.all((W > 0.0) & (W < 1.0))
+
+
+def _laplace_small(n, d, seed, s2=2.0, ell=0.9):
+    p = synthetic.classification_problem(n, d, seed, s2=s2, ell=ell)
+    ls, s2 = oracle.split_theta(p.log_theta, d, True)
+    return p, ls, s2
+
+
+def test_laplace_mode_is_stationary():
+    # at the mode grad Psi = g(f^) - K^{-1} f^ = 0, so f^ = K g(f^) and a = K^{-1} f^
+    # = g(f^); Newton on the concave Psi converges in a handful of steps
+    p, ls, s2 = _laplace_small(80, 3, seed=3)
+    r = oracle.laplace_probit(p.X, ls, s2, p.y)
+    K = _lib_gram(p.X, p.X, ls, s2)
+    _, g, _ = oracle.probit_terms(p.y, r["f"])
+    assert np.linalg.norm(K @ g - r["f"]) <= 1e-8 * np.linalg.norm(r["f"])
+    assert np.linalg.norm(r["a"] - g) <= 1e-6 * np.linalg.norm(g)
+    assert 3 <= r["steps"] <= 12
+    # the labels are explained: sign(f^) agrees with most of them
+    assert np.mean(np.sign(r["f"]) == p.y) > 0.8
+
+
+def test_laplace_mode_matches_a_generic_optimiser():
+    # maximise Psi(f) = sum log Phi(y f) - 1/2 f^T K^{-1} f with SciPy's BFGS in
+    # the whitened variable f = L u (L L^T = K + tiny jitter), log CDF from SciPy
+    from scipy.optimize import minimize
+    from scipy.stats import norm
+
+    p, ls, s2 = _laplace_small(14, 2, seed=5)
+    K = _lib_gram(p.X, p.X, ls, s2)
+    Lk = np.linalg.cholesky(K + 1e-10 * np.eye(14))
+    y = p.y
+
+    def negpsi(u):
+        f = Lk @ u
+        z = y * f
+        ratio = np.exp(norm.logpdf(z) - norm.logcdf(z))
+        return -(norm.logcdf(z).sum() - 0.5 * u @ u), -(Lk.T @ (y * ratio) - u)
+
+    res = minimize(negpsi, np.zeros(14), jac=True, method="BFGS",
+                   options={"gtol": 1e-11, "maxiter": 10000})
+    f_ref = Lk @ res.x
+    r = oracle.laplace_probit(p.X, ls, s2, y)
+    np.testing.assert_allclose(r["f"], f_ref, rtol=1e-5, atol=1e-6 * np.abs(f_ref).max())
+
+
+def test_laplace_log_marginal_is_the_gaussian_integral_form():
+    # the Laplace approximation of log int p(y|f) N(f|0,K) df is
+    # log p(y|f^) + log N(f^|0,K) + n/2 log 2 pi - 1/2 log|K^{-1} + W|; Sec. 2.2's
+    # -1/2 log|B| - 1/2 f^T K^{-1} f + log p(y|f^) must equal it
+    p, ls, s2 = _laplace_small(30, 3, seed=7, ell=0.6)
+    r = oracle.laplace_probit(p.X, ls, s2, p.y)
+    K = _lib_gram(p.X, p.X, ls, s2)
+    f = r["f"]
+    lp, _, W = oracle.probit_terms(p.y, f)
+    Kinv = np.linalg.inv(K)
+    n = 30
+    lognorm = -0.5 * f @ Kinv @ f - 0.5 * np.linalg.slogdet(K)[1] - 0.5 * n * math.log(2 * math.pi)
+    ref = lp.sum() + lognorm + 0.5 * n * math.log(2 * math.pi) \
+        - 0.5 * np.linalg.slogdet(Kinv + np.diag(W))[1]
+    assert r["logq"] == pytest.approx(ref, rel=1e-7)
+
+
+def test_laplace_one_point_closed_form():
+    # n = 1, K = s2: the mode is the root of f - s2 g(f) = 0, and
+    # log q = log Phi(y f) - f^2 / (2 s2) - 1/2 log(1 + s2 W)
+    from scipy.optimize import brentq
+    from scipy.stats import norm
+
+    for y, s2 in ((1.0, 3.0), (-1.0, 0.4)):
+        gfun = lambda f: y * norm.pdf(f) / norm.cdf(y * f)  # noqa: E731
+        f = brentq(lambda f: f - s2 * gfun(f), -10.0, 10.0, xtol=1e-15)
+        z = y * f
+        rr = norm.pdf(z) / norm.cdf(z)
+        Wv = rr * rr + z * rr
+        ref = math.log(norm.cdf(z)) - f * f / (2 * s2) - 0.5 * math.log(1 + s2 * Wv)
+        r = oracle.laplace_probit(np.zeros((1, 1), np.float32), np.ones(1), s2, np.array([y]))
+        assert r["f"][0] == pytest.approx(f, rel=1e-10)
+        assert r["logq"] == pytest.approx(ref, rel=1e-10)
