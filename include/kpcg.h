@@ -56,8 +56,10 @@ typedef enum {
     KPCG_PREC_NONE = 0,          /* P = I: plain CG                              */
     KPCG_PREC_NYSTROM = 1,       /* P = K_XU K_UU^-1 K_UX + sigma^2 I (Sec. 3.1)  */
     KPCG_PREC_BLOCK_JACOBI = 2,  /* P = bldiag(K_y) (Sec. 3.3.1)                  */
-    KPCG_PREC_FITC = 3           /* P = Q + diag(K - Q) + sigma^2 I, Q the Nystrom
+    KPCG_PREC_FITC = 3,          /* P = Q + diag(K - Q) + sigma^2 I, Q the Nystrom
                                     approximation K_XU K_UU^-1 K_UX (Sec. 3.1)   */
+    KPCG_PREC_SPECTRAL = 4       /* P = Phi Phi^T + sigma^2 I, random Fourier
+                                    features (Sec. 3.2); kpcg_precond_spectral   */
 } kpcg_precond_kind;
 
 typedef enum {
@@ -165,6 +167,20 @@ kpcg_status kpcg_set_options(kpcg_t h, const kpcg_options* opt);
  * fails (the handle is then left without a preconditioner). */
 kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* idx);
 
+/* Build the random-feature preconditioner of Sec. 3.2 (KPCG_PREC_SPECTRAL).
+ * K is approximated by K^_ij = (s^2/m) sum_r cos(2 pi s_r^T (x_i - x_j)) =
+ * (Phi Phi^T)_ij, Phi_i = sqrt(s^2/m) [cos(2 pi s_r^T x_i), sin(2 pi s_r^T x_i)]_r
+ * (n x 2m), with spectral points s_r ~ N(0, Lambda / (4 pi^2)), Lambda =
+ * diag(1/l_r^2).  The random draws are an input: omega (host, m x d row-major,
+ * float64) holds standard-normal values and s_r = omega_r / (2 pi l), so the
+ * same draws serve every theta (the preconditioner is rebuilt from them after
+ * kpcg_set_theta).  P^-1 = sigma^-2 [I - Phi (sigma^2 I + Phi^T Phi)^-1 Phi^T]
+ * (the inversion lemma; the printed (I + Phi^T Phi) holds only for unit noise),
+ * the inner 2m x 2m matrix factored with the jitter rule of kpcg_precond.
+ * m in [1, 2048]; values must be finite.  In the mixed modes it is built for
+ * the shifted inner noise, like the other kinds. */
+kpcg_status kpcg_precond_spectral(kpcg_t h, int64_t m, const double* omega);
+
 /* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
  * matrix-free product of Sec. 2.1.  impl 0: entries and sums in native FP64;
  * impl 1: the double-float kernel of KPCG_DF64 (FP32-pair arithmetic, about
@@ -227,6 +243,41 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
  * info (nullable) sums the variance solves.  ns = 0 is a no-op. */
 kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* alpha,
                          double* mean, double* var, double tol, kpcg_info* info);
+
+/* ---------------------------------------------------------------------------
+ * GP classification with the probit likelihood p(y_i|f_i) = Phi(y_i f_i): the
+ * Laplace approximation (Sec. 2.2; Appendix B, Algorithm "Laplace
+ * approximation for GPs").  From f = 0, each Newton step computes
+ * W = -d^2/df^2 log p(y|f) (diagonal) and g = d/df log p(y|f) at f,
+ * b = W f + g, v = W^1/2 K b, solves B z = v with B = I + W^1/2 K W^1/2 by
+ * PCG, and sets a = b - W^1/2 z, f = K a.  The loop stops when the objective
+ * Psi(f) = log p(y|f) - 1/2 a^T f changes by at most newton_tol*max(1,|Psi|)
+ * (the paper only says "until convergence").
+ *   K: the handle's kernel (amplitude s^2, lengthscales); sigma^2 is unused.
+ *   Products with K: the double-float kernel (KPCG_DF64's), whatever the
+ *   handle's precision; the per-point terms are FP64.
+ *   Preconditioner of B: with a Nystrom request on the handle (kpcg_precond,
+ *   KPCG_PREC_NYSTROM) P_B = I + W^1/2 K_XU K_UU^-1 K_UX W^1/2 on the same
+ *   inducing points, rebuilt every Newton step (W changes); with none, P_B = I;
+ *   other kinds are rejected (KPCG_ERR_ARG).
+ *   y: device, n labels, each +1 or -1 (checked).  f (device, n): the mode f^;
+ *   a (device, n, nullable): a = K^-1 f^ (Appendix B), needed by predictions.
+ *   newton_tol > 0, max_newton >= 1, cg_tol in (0, 1): each B-solve stops at
+ *   ||v - B z|| <= cg_tol ||v|| (recomputed, at most 4 restarts).
+ * Returns KPCG_ERR_NO_CONVERGENCE when max_newton steps end before the stop
+ * test or a B-solve misses cg_tol (f and a then hold the last iterate). */
+typedef struct {
+    int32_t newton_steps;   /* Newton steps taken                                   */
+    int32_t cg_iters_total; /* CG iterations over all B-solves                      */
+    double psi;             /* Psi at the returned f                                */
+    double max_rel_res;     /* worst recomputed ||v - B z|| / ||v|| of the B-solves */
+    double time_ms;         /* wall time of the call on the host                    */
+    double setup_ms;        /* part of time_ms spent building P_B                   */
+    int32_t launches;       /* CUDA kernels this call launched                      */
+} kpcg_laplace_info;
+
+kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t max_newton,
+                         double cg_tol, double* f, double* a, kpcg_laplace_info* info);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  Algorithm 1 takes an initial iterate x0; along a

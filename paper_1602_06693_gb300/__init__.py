@@ -14,9 +14,11 @@ from .binding import (  # noqa: F401
     KPCG_PREC_FITC,
     KPCG_PREC_NONE,
     KPCG_PREC_NYSTROM,
+    KPCG_PREC_SPECTRAL,
     KPCG_TC_IR,
     Batch,
     KpcgError,
+    LaplaceInfo,
     MLP,
     Options,
     Problem,

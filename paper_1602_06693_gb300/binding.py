@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
 KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI, KPCG_PREC_FITC = 0, 1, 2, 3
+KPCG_PREC_SPECTRAL = 4
 KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64 = 0, 1, 2, 3, 4
 
 _STATUS = {
@@ -36,7 +37,7 @@ SYMBOLS = (
     "kpcg_batch_solve", "kpcg_batch_matvec_f32", "kpcg_batch_precond_apply_f32",
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
     "kpcg_batch_destroy",
-    "kpcg_batch_last_error",
+    "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace",
 )
 
 _NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
@@ -78,6 +79,18 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LaplaceInfo(ctypes.Structure):
+    _fields_ = [
+        ("newton_steps", ctypes.c_int32),
+        ("cg_iters_total", ctypes.c_int32),
+        ("psi", ctypes.c_double),
+        ("max_rel_res", ctypes.c_double),
+        ("time_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("launches", ctypes.c_int32),
+    ]
 
 
 class Problem(ctypes.Structure):
@@ -125,6 +138,8 @@ def lib():
         L.kpcg_set_theta.argtypes = [vp, pdbl, dbl]
         L.kpcg_set_options.argtypes = [vp, ctypes.POINTER(Options)]
         L.kpcg_precond.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.kpcg_precond_spectral.argtypes = [vp, i64, pdbl]
+        L.kpcg_laplace.argtypes = [vp, vp, dbl, i32, dbl, vp, vp, ctypes.POINTER(LaplaceInfo)]
         L.kpcg_matvec_f64.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_matvec_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_precond_apply_f64.argtypes = [vp, vp, i64, i32, vp, i64]
@@ -313,6 +328,29 @@ class Solver:
             idx = np.ascontiguousarray(idx, dtype=np.int64)
             p = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         self._check(lib().kpcg_precond(self._h, int(kind), int(size), p))
+
+    def precond_spectral(self, omega):
+        """Random-feature preconditioner (Sec. 3.2) from m x d standard-normal draws."""
+        om = np.ascontiguousarray(omega, dtype=np.float64).reshape(-1, self.d)
+        self._check(lib().kpcg_precond_spectral(
+            self._h, int(om.shape[0]), om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def laplace(self, y, newton_tol=1e-12, max_newton=50, cg_tol=1e-10, want_a=True):
+        """Probit Laplace mode (Sec. 2.2, Appendix B): returns (f, a, info, status);
+        y is a float64 CUDA vector of +-1 labels."""
+        torch = _torch()
+        if y.dtype != torch.float64 or not y.is_cuda or y.dim() != 1 or not y.is_contiguous():
+            raise TypeError("y must be a contiguous float64 CUDA vector")
+        f = torch.empty(self.n, dtype=torch.float64, device=y.device)
+        a = torch.empty(self.n, dtype=torch.float64, device=y.device) if want_a else None
+        info = LaplaceInfo()
+        st = lib().kpcg_laplace(self._h, ctypes.c_void_p(y.data_ptr()), float(newton_tol),
+                                int(max_newton), float(cg_tol), ctypes.c_void_p(f.data_ptr()),
+                                ctypes.c_void_p(a.data_ptr()) if a is not None else None,
+                                ctypes.byref(info))
+        if st not in (0, 6):
+            self._check(st)
+        return f, a, info, st
 
     def matvec_f64(self, V, impl=0, out=None):
         torch = _torch()

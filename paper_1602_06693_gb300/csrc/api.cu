@@ -281,6 +281,13 @@ static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const doub
         }
 }
 
+int pcg_f64(Ctx& h, int c, const double* B, int64_t ldb, double* X, int64_t ldx, bool x0_zero,
+            double tol, int max_iter, const VecOp& matvec, const VecOp& precond,
+            CgBufs<double>& bufs, std::vector<int>& iters, int& broken) {
+    return pcg_core<double>(h, c, B, ldb, X, ldx, x0_zero, tol, 0, max_iter, matvec, precond,
+                            bufs, iters, broken);
+}
+
 bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
     if (bb == 0.0) return true;
     return tol_mode == 1 ? rr < (double)n * tol : rr <= tol * tol * bb;
@@ -307,6 +314,9 @@ static void build_precond(Ctx& h) {
     else if (h.pkind == KPCG_PREC_FITC)
         fitc_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), h.s2, nz,
                    h.pidx.data(), h.psize, h.stream);
+    else if (h.pkind == KPCG_PREC_SPECTRAL)
+        spectral_setup(h.P, h.xs64.p, h.n, h.dp, h.s2, nz, h.pomega.data(), h.d, h.psize,
+                       h.stream);
     h.P.n = h.n;
     h.P.noise = nz;
     KPCG_CUDA(cudaStreamSynchronize(h.stream));
@@ -506,7 +516,7 @@ static MixedOps single_ops(Ctx& h) {
     // 16 columns, double-float back product); other kinds: the per-kind apply
     o.inner_pc = [hp](const float* R, int64_t ldr, int cc, float* Z, int64_t ldz) {
         Ctx& h = *hp;
-        if (h.P.kind == KPCG_PREC_NYSTROM && h.P.ready) {
+        if ((h.P.kind == KPCG_PREC_NYSTROM || h.P.kind == KPCG_PREC_SPECTRAL) && h.P.ready) {
             if (h.nys1_c != cc || h.nys1_version != h.pversion) {
                 nys_batch_plan(h.nys1, {&h.P}, cc, h.stream);
                 h.nys1_c = cc;
@@ -951,6 +961,8 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
             h->pidx.clear();
         } else if (kind == KPCG_PREC_NONE) {
             h->pidx.clear();
+        } else if (kind == KPCG_PREC_SPECTRAL) {
+            fail(KPCG_ERR_ARG, "the random-feature preconditioner is built by kpcg_precond_spectral");
         } else {
             fail(KPCG_ERR_ARG, "unknown preconditioner kind");
         }
@@ -966,6 +978,31 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
                 h->P.reset();
                 throw;
             }
+        }
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_precond_spectral(kpcg_t h, int64_t m, const double* omega) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (m < 1 || m > 2048) fail(KPCG_ERR_ARG, "feature count m must be in [1, 2048]");
+        if (!omega) fail(KPCG_ERR_ARG, "omega (host, m x d) is required");
+        const size_t cnt = (size_t)m * (size_t)h->d;
+        for (size_t e = 0; e < cnt; ++e)
+            if (!std::isfinite(omega[e])) fail(KPCG_ERR_ARG, "omega has a non-finite value");
+        h->pkind = KPCG_PREC_NONE;
+        h->P.reset();
+        h->pidx.clear();
+        h->pomega.assign(omega, omega + cnt);
+        h->pkind = KPCG_PREC_SPECTRAL;
+        h->psize = m;
+        try {
+            kpcg::build_precond(*h);
+        } catch (...) {
+            h->pkind = KPCG_PREC_NONE;
+            h->P.reset();
+            throw;
         }
     });
     return KPCG_OK;

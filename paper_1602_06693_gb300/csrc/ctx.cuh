@@ -90,6 +90,7 @@ struct Ctx {
     int pkind = KPCG_PREC_NONE;
     int64_t psize = 0;
     std::vector<int64_t> pidx;
+    std::vector<double> pomega;  // spectral draws (m x d) of KPCG_PREC_SPECTRAL
     // warm-start basis (Nystrom-type fit), rebuilt lazily when theta changes
     PrecondState Wb;
     std::vector<int64_t> widx;
@@ -114,6 +115,11 @@ struct Ctx {
     long long pversion = 0;  // incremented by every preconditioner build
     // predictions (predict.cu): scaled test inputs, k_* blocks, their solves, partials
     DevBuf<double> pxt, pKb, pW, ppart;
+    // Laplace approximation (laplace.cu): P_B, the unscaled K_XU, vectors, CG state
+    PrecondState LP;
+    DevBuf<float2> lkxu0;
+    DevBuf<double> lap;
+    CgBufs<double> lcg;
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

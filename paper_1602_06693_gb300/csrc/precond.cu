@@ -578,11 +578,11 @@ static double factor_with_rule(PrecondState& P, const double* A0, int64_t m, cud
     return jitter;
 }
 
-// M0 = noise K_UU + K_UX K_XU (FP64 SYRK over the pairs), factored by the rule.
-static void nys_inner(PrecondState& P, int64_t n, int64_t m, int dp, double c0_64, double noise,
-                      cudaStream_t st) {
-    double* M0 = P.M0.need((size_t)m * m);
-    kuu_f64(P.us64.p, m, dp, c0_64, noise, 0.0, M0, st);
+// M0 += K_UX K_XU (FP64 SYRK over the pairs of P.KXU, n x m), then M0 is
+// factored by the rule.
+static void nys_syrk_factor(PrecondState& P, int64_t n, int64_t m, cudaStream_t st,
+                            const char* what) {
+    double* M0 = P.M0.p;
     const int64_t tiles = (m + ST - 1) / ST;
     int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 4095) / 4096));
     const int64_t rps = ((n + nsplit - 1) / nsplit + SR - 1) / SR * SR;
@@ -593,7 +593,15 @@ static void nys_inner(PrecondState& P, int64_t n, int64_t m, int dp, double c0_6
     KPCG_LAUNCHED("syrk_kxu_kernel");
     syrk_reduce_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(part, nsplit, m, M0);
     KPCG_LAUNCHED("syrk_reduce_kernel");
-    P.jitter = factor_with_rule(P, M0, m, st, "Nystrom inner matrix");
+    P.jitter = factor_with_rule(P, M0, m, st, what);
+}
+
+// M0 = noise K_UU + K_UX K_XU, factored by the rule.
+static void nys_inner(PrecondState& P, int64_t n, int64_t m, int dp, double c0_64, double noise,
+                      cudaStream_t st) {
+    double* M0 = P.M0.need((size_t)m * m);
+    kuu_f64(P.us64.p, m, dp, c0_64, noise, 0.0, M0, st);
+    nys_syrk_factor(P, n, m, st, "Nystrom inner matrix");
 }
 
 void nystrom_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
@@ -677,6 +685,94 @@ void fitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t 
     fitc_scale_kernel<<<(unsigned)n, 256, 0, st>>>(P.KXU.p, n, m, dq, s2, noise, dsc);
     KPCG_LAUNCHED("fitc_scale_kernel");
     // inner matrix K_UU + K~^T K~ (unit noise) and its factor
+    nys_inner(P, n, m, dp, c0_64, 1.0, st);
+    P.ready = true;
+}
+
+namespace {
+
+// Row i of Phi: amp [cos(w_r . x~_i) | sin(w_r . x~_i)], r = 0..m-1 (cosines in
+// columns 0..m-1, sines in m..2m-1), FP64 phases and values stored as exact
+// FP32 pairs.  With x~ = (x - mu) / l, w_r . x~_i = 2 pi s_r . x_i - 2 pi s_r . mu
+// for s_r = w_r / (2 pi l): the constant phase cancels in Phi Phi^T.  xs holds
+// x~ sqrt(1/2) (the FP64 kernels' scaling), so om carries w sqrt(2).  One
+// thread per (i, r).
+__global__ void rff_kernel(const double* __restrict__ xs, int64_t n, int dp,
+                           const double* __restrict__ om, int64_t m, double amp,
+                           float2* __restrict__ Phi) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    const int64_t i = e / m, r = e - i * m;
+    double ph = 0.0;
+    for (int k = 0; k < dp; ++k) ph = fma(om[r * dp + k], xs[i * dp + k], ph);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    cs *= amp;
+    sn *= amp;
+    const float ch = (float)cs, sh = (float)sn;
+    Phi[i * 2 * m + r] = make_float2(ch, (float)(cs - (double)ch));
+    Phi[i * 2 * m + m + r] = make_float2(sh, (float)(sn - (double)sh));
+}
+
+// dst[i][a] = sc[i] src[i][a] for n x m pairs, re-split into exact FP32 pairs.
+__global__ void scale_pairs_kernel(const float2* __restrict__ src, int64_t n, int64_t m,
+                                   const double* __restrict__ sc, float2* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    const float2 kv = src[e];
+    const double v = ((double)kv.x + (double)kv.y) * sc[e / m];
+    const float hi = (float)v;
+    dst[e] = make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace
+
+void spectral_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double s2,
+                    double noise, const double* omega_host, int d, int64_t m, cudaStream_t st) {
+    P.kind = KPCG_PREC_SPECTRAL;
+    P.n = n;
+    P.m = 2 * m;
+    P.noise = noise;
+    P.apply_noise = noise;
+    std::vector<double> om((size_t)m * dp, 0.0);
+    for (int64_t r = 0; r < m; ++r)
+        for (int k = 0; k < d; ++k)
+            om[(size_t)(r * dp + k)] = omega_host[r * d + k] * 1.4142135623730950488;
+    double* omd = P.us64.need((size_t)m * dp);
+    KPCG_CUDA(cudaMemcpyAsync(omd, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice,
+                              st));
+    float2* Phi = P.KXU.need((size_t)n * 2 * m);
+    rff_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, st>>>(xs64, n, dp, omd, m,
+                                                                std::sqrt(s2 / (double)m), Phi);
+    KPCG_LAUNCHED("rff_kernel");
+    // inner matrix noise I + Phi^T Phi
+    const int64_t q = 2 * m;
+    double* M0 = P.M0.need((size_t)q * q);
+    KPCG_CUDA(cudaMemsetAsync(M0, 0, sizeof(double) * q * q, st));
+    add_diag_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(M0, q, noise);
+    KPCG_LAUNCHED("add_diag_kernel");
+    nys_syrk_factor(P, n, q, st, "random-feature inner matrix");
+    P.ready = true;
+}
+
+void laplace_precond_setup(PrecondState& P, DevBuf<float2>& kxu0, bool first, const float* xs32,
+                           const double* xs64, int64_t n, int dp, double c0_64,
+                           const double* sW, const int64_t* idx_host, int64_t m,
+                           cudaStream_t st) {
+    if (first || !kxu0.p) {
+        nys_gather_kxu(P, xs32, xs64, n, dp, c0_64, idx_host, m, st);
+        float2* k0 = kxu0.need((size_t)n * m);
+        KPCG_CUDA(cudaMemcpyAsync(k0, P.KXU.p, sizeof(float2) * n * m, cudaMemcpyDeviceToDevice,
+                                  st));
+    }
+    P.kind = KPCG_PREC_NYSTROM;
+    P.n = n;
+    P.m = m;
+    P.noise = 1.0;
+    P.apply_noise = 1.0;
+    scale_pairs_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, st>>>(kxu0.p, n, m, sW,
+                                                                        P.KXU.p);
+    KPCG_LAUNCHED("scale_pairs_kernel");
     nys_inner(P, n, m, dp, c0_64, 1.0, st);
     P.ready = true;
 }
@@ -834,7 +930,7 @@ static void fitc_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T*
 template <typename T>
 static void apply_any(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
                       cudaStream_t st) {
-    if (P.kind == KPCG_PREC_NYSTROM && P.ready)
+    if ((P.kind == KPCG_PREC_NYSTROM || P.kind == KPCG_PREC_SPECTRAL) && P.ready)
         nystrom_apply<T>(P, R, ldr, c, Z, ldz, st);
     else if (P.kind == KPCG_PREC_FITC && P.ready)
         fitc_apply<T>(P, R, ldr, c, Z, ldz, st);
@@ -1098,11 +1194,12 @@ void nys_batch_plan(NysBatch& nb, const std::vector<const PrecondState*>& Ps, in
         const PrecondState& P = *Ps[(size_t)p];
         NysBatchProb& q = nb.hprobs[(size_t)p];
         q.n = P.n;
-        const bool on = P.ready && P.kind == KPCG_PREC_NYSTROM;
+        const bool on =
+            P.ready && (P.kind == KPCG_PREC_NYSTROM || P.kind == KPCG_PREC_SPECTRAL);
         q.m = on ? P.m : 0;
         q.KXU = on ? P.KXU.p : nullptr;
         q.U = on ? P.U.p : nullptr;
-        q.inv_noise = on ? 1.0 / P.noise : 1.0;
+        q.inv_noise = on ? 1.0 / P.apply_noise : 1.0;
         q.inv_noise_f = (float)q.inv_noise;
         q.rows_per_split = kSplitRows;
         q.nsplit = (int32_t)std::max<int64_t>(1, (P.n + kSplitRows - 1) / kSplitRows);

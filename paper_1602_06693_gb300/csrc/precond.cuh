@@ -60,6 +60,23 @@ void nystrom_project_solve(const PrecondState& P, const double* R, int64_t ldr, 
                            cudaStream_t st);
 // out = K_XU u for one column (FP64).
 void nystrom_expand(const PrecondState& P, const double* u, double* out, cudaStream_t st);
+// Random-feature preconditioner (Sec. 3.2): P = Phi Phi^T + noise I with
+// Phi_i = sqrt(s2/m) [cos(w_r . x~_i), sin(w_r . x~_i)]_r (n x 2m, stored in KXU),
+// applied as the Nystrom form with K_UU = I:
+// P^{-1} = noise^{-1} [I - Phi (noise I + Phi^T Phi)^{-1} Phi^T].  omega_host:
+// m x d standard-normal draws (row-major); in the scaled inputs x~ = (x - mu)/l
+// the spectral points s_r = w_r / (2 pi l) act through w_r . x~.
+void spectral_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double s2,
+                    double noise, const double* omega_host, int d, int64_t m, cudaStream_t st);
+// Preconditioner of B = I + W^1/2 K W^1/2 (the Laplace step, Sec. 2.2):
+// P_B = I + W^1/2 Q W^1/2 with Q = K_XU K_UU^{-1} K_UX, so
+// P_B^{-1} = I - K~ (K_UU + K~^T K~)^{-1} K~^T with K~ = W^1/2 K_XU: the Nystrom
+// apply with unit noise on the row-scaled K_XU.  kxu0 keeps the unscaled K_XU
+// between Newton steps (computed when `first`); sW = W^1/2 (device, n).
+void laplace_precond_setup(PrecondState& P, DevBuf<float2>& kxu0, bool first, const float* xs32,
+                           const double* xs64, int64_t n, int dp, double c0_64,
+                           const double* sW, const int64_t* idx_host, int64_t m,
+                           cudaStream_t st);
 void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
                         double noise, int64_t b, cudaStream_t st);
 // FITC (Sec. 3.1): P = Q + diag(K - Q) + sigma^2 I, Q = K_XU K_UU^{-1} K_UX.  With

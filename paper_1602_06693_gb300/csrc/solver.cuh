@@ -83,6 +83,14 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
                       std::vector<int>& iters_col, int& iters_total, int& steps,
                       std::vector<double>& rr, std::vector<double>& bb);
 bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n);
+// O = A V for c columns (ld-strided, column-major); must launch on h.stream
+using VecOp = std::function<void(const double*, int64_t, int, double*, int64_t)>;
+// Column-wise PCG (Algorithm 1) in FP64 on an operator and preconditioner of
+// the caller's (relative stop test ||r|| <= tol ||b|| per column, on the
+// recursive residual); X holds x0 unless x0_zero.  Returns the iterations run.
+int pcg_f64(Ctx& h, int c, const double* B, int64_t ldb, double* X, int64_t ldx, bool x0_zero,
+            double tol, int max_iter, const VecOp& matvec, const VecOp& precond,
+            CgBufs<double>& bufs, std::vector<int>& iters, int& broken);
 // The solve behind kpcg_solve: K_y X = B for c columns with the handle's
 // precision and preconditioner (device blocks; iters_host, info nullable).
 kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
