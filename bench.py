@@ -392,6 +392,7 @@ def run_predict(args):
 FIG1_LOG_ELL = (-1.0, -0.5, 0.0, 0.5, 1.0)
 FIG1_LOG_NOISE = (-4.0, -3.0, -2.0, -1.0, 0.0)
 FIG1_SHAPES = {"concrete": (1030, 8), "power": (9568, 4)}
+FIG1_KINDS = ("none", "nystrom", "fitc", "spectral", "block_jacobi")
 
 
 def fig1_problem(shape, seed=0):
@@ -405,7 +406,8 @@ def fig1_problem(shape, seed=0):
 def fig1_cell(kpcg, torch, dev, p, log_ell, log_noise, kind):
     """Iterations of (P)CG on one grid cell (Sec. 4): isotropic RBF with s^2 = 1,
     l = 10^log_ell, noise 10^log_noise, stop at ||r||^2 < n 1e-10, cap 100 000;
-    Nystrom with m = sqrt(n) inducing points, block-Jacobi with blocks of sqrt(n)."""
+    Nystrom and FITC with m = sqrt(n) inducing points, the random-feature
+    preconditioner with m = sqrt(n) frequencies, block-Jacobi with blocks of sqrt(n)."""
     m = int(math.ceil(math.sqrt(p.n)))
     lt = np.array([log_ell * math.log(10.0), 0.0])
     opt = kpcg.default_options(precision=kpcg.KPCG_FP64, tol_mode=1, max_iter=100000)
@@ -413,6 +415,10 @@ def fig1_cell(kpcg, torch, dev, p, log_ell, log_noise, kind):
                      options=opt) as s:
         if kind == "nystrom":
             s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=5))
+        elif kind == "fitc":
+            s.precond(kpcg.KPCG_PREC_FITC, m, synthetic.inducing_subset(p.n, m, seed=5))
+        elif kind == "spectral":
+            s.precond_spectral(synthetic.spectral_draws(m, p.d, seed=5))
         elif kind == "block_jacobi":
             s.precond(kpcg.KPCG_PREC_BLOCK_JACOBI, m)
         _, it, info, st = s.solve(torch.from_numpy(p.y).to(dev), tol=1e-10,
@@ -439,11 +445,11 @@ def run_fig1(args):
         for le in FIG1_LOG_ELL:
             for ln in FIG1_LOG_NOISE:
                 row = {"log10_ell": le, "log10_noise": ln}
-                for kind in ("none", "nystrom", "block_jacobi"):
+                for kind in FIG1_KINDS:
                     it, st = fig1_cell(kpcg, torch, dev, p, le, ln, kind)
                     row[kind] = it
                     row[kind + "_status"] = st
-                for kind in ("nystrom", "block_jacobi"):
+                for kind in FIG1_KINDS[1:]:
                     row[kind + "_gain_log10"] = (math.log10(max(row[kind], 1) / max(row["none"], 1)))
                 grid.append(row)
         out[shape] = grid
@@ -453,11 +459,143 @@ def run_fig1(args):
             "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "isotropic RBF, s^2=1, stop ||r||^2 < n 1e-10, cap 1e5; "
-                                   "Nystrom m=sqrt(n), block-Jacobi b=sqrt(n); synthetic X of "
-                                   "the dataset shapes", "shapes": shapes},
+                                   "Nystrom and FITC m=sqrt(n), random features m=sqrt(n), "
+                                   "block-Jacobi b=sqrt(n); synthetic X of the dataset shapes",
+                       "shapes": shapes},
             "grid": out}
     if rank == 0:
         print(json.dumps(line))
+
+
+LAPLACE_M = 512
+LAPLACE_WORKLOAD = ("probit GP classification, EEG shape n=14979 d=14 (X~N(0,I) standardized, "
+                    "y=sign(sum sin x) with 5% flipped), ARD l=sqrt(14), s^2=4; Laplace mode by "
+                    "Newton from f=0 (stop |dPsi| <= 1e-12 |Psi|), each B = I + W^1/2 K W^1/2 "
+                    "solve by PCG to 1e-10 with the Nystrom form of B (m=512, rebuilt per step), "
+                    "double-float K.V")
+
+
+def laplace_oracle_sample(n_sample=2500):
+    """The dense FP64 oracle on the first n_sample rows of the same workload
+    (its cost is the O(n^3) Cholesky of B per Newton step), scaled to the full
+    n by (n / n_sample)^3."""
+    import oracle
+    p = synthetic.eeg_shape(seed=0)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
+    t0 = time.perf_counter()
+    r = oracle.laplace_probit(p.X[:n_sample], ell, s2, p.y[:n_sample], tol=1e-12)
+    t = time.perf_counter() - t0
+    scale = (p.n / n_sample) ** 3
+    return {"value": t * scale, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"dense FP64 oracle Newton on the first {n_sample} rows "
+                       f"({r['steps']} steps, {t:.1f} s), scaled by (n/{n_sample})^3")}
+
+
+def run_laplace(args):
+    """One step: the Laplace mode of the EEG-shaped probit classifier."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = synthetic.eeg_shape(seed=rank)
+    idx = synthetic.inducing_subset(p.n, LAPLACE_M, seed=12 + rank)
+    opt = kpcg.default_options(precision=kpcg.KPCG_DF64)
+    s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, 1.0, ard=True, options=opt)
+    s.precond(kpcg.KPCG_PREC_NYSTROM, LAPLACE_M, idx)
+    y = torch.from_numpy(p.y).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        s.laplace(y)
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+    stop_clock = sm_clock_probe()
+    times, info = [], None
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, a, info, st = s.laplace(y)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = stop_clock()
+    t_step = max_over_ranks(statistics.mean(times), dev)
+    # the dominant kernel: the double-float K.V of one column (every CG
+    # iteration of a B-solve and two per Newton step), timed alone
+    v = torch.from_numpy(synthetic.rng(3).standard_normal(p.n)).to(dev)
+    for _ in range(3):
+        s.matvec_f64(v, impl=1)
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.matvec_f64(v, impl=1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    kv_ms = e0.elapsed_time(e1) / reps
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ops = df_ops_per_product(p.n, p.d, 1)
+    peak = 152 * 128 * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "kernel": "kv_df_sym_kernel (double-float K.V, 1 column)",
+            "achieved": ops / (kv_ms / 1e3) / 1e12, "peak": peak, "unit": "Top/s",
+            "frac": ops / (kv_ms / 1e3) / 1e12 / peak, "traffic": None,
+            "peak_source": (f"FP32 pipe issue rate: 152 SMs x 128 lanes x {sm_max:.0f} MHz "
+                            "(unit counts and max clock)"),
+            "avg_ms": kv_ms, "ops_per_call": ops,
+            "timing": f"{reps} back-to-back products, CUDA events on the launching stream"}
+    # end to end: labels from pinned host memory, f back to the host
+    yh = torch.from_numpy(p.y).pin_memory()
+    fh = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(3.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        yd = yh.to(dev, non_blocking=True)
+        fd, _, _, _ = s.laplace(yd, want_a=False)
+        fh.copy_(fd, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_t.append(time.perf_counter() - t0)
+    extra = {}
+    if rank == 0 and world == 1 and not args.skip_baselines:
+        try:
+            extra["cpu_baseline"] = laplace_oracle_sample()
+        except Exception as e:
+            extra["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    line = {
+        "metric": "time to the Laplace mode of a probit GP classifier (EEG shape)",
+        "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": LAPLACE_WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "laplace": {"status": st, "newton_steps": info.newton_steps,
+                    "cg_iters_total": info.cg_iters_total, "psi": info.psi,
+                    "max_rel_res": info.max_rel_res, "setup_ms": info.setup_ms,
+                    "step_times_s": times,
+                    "train_accuracy": float((torch.sign(f) == y).double().mean())},
+        "roofline": roof, "clocks": clocks,
+        "e2e": {"value": statistics.mean(e2e_t), "unit": "s",
+                "h2d_bytes_per_step": int(yh.numel() * 8),
+                "d2h_bytes_per_step": int(fh.numel() * 8)},
+        "gpu_launches": int(info.launches),
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
 
 
 BATCH_SHIFT, BATCH_INNER_TOL = 0.25, 0.2
@@ -618,7 +756,8 @@ def main():
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
     ap.add_argument("--workload", default="solve65k",
-                    choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k", "fig1"],
+                    choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k", "fig1",
+                             "laplace15k"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -647,6 +786,8 @@ def main():
         return run_predict(args)
     if args.workload == "fig1":
         return run_fig1(args)
+    if args.workload == "laplace15k":
+        return run_laplace(args)
 
     import torch
     import paper_1602_06693_gb300 as kpcg
