@@ -501,3 +501,25 @@ def laplace_probit(X, ell, s2, y, tol=1e-12, max_newton=100):
     LB = cholesky(np.eye(n) + sW[:, None] * K * sW[None, :])
     logq = float(-np.sum(np.log(np.diag(LB))) - 0.5 * a @ f + lp.sum())
     return {"f": f, "a": a, "steps": steps, "psi": psi, "logq": logq}
+
+
+def laplace_predict(X, ell, s2, y, f, a, Xs):
+    """Predictions of the probit classifier at test inputs Xs (Sec. 2.2 and
+    Appendix B, "Prediction"): latent mean m_* = k_*^T a, latent variance
+    v_* = s2 - k_*^T W^1/2 B^{-1} W^1/2 k_* (one B-solve per test point, B and W
+    at the mode f), and the predictive probability Phi(m_* / sqrt(1 + v_*)),
+    the exact Gaussian integral of the probit likelihood.  Dense FP64."""
+    from scipy.special import ndtr
+
+    X = _f64c(X)
+    Ks = gram(Xs, X, ell, s2)  # (ns, n)
+    mean = Ks @ np.asarray(a, dtype=np.float64)
+    _lp, _g, W = probit_terms(y, f)
+    sW = np.sqrt(W)
+    K = gram(X, X, ell, s2)
+    n = X.shape[0]
+    LB = cholesky(np.eye(n) + sW[:, None] * K * sW[None, :])
+    R = np.asfortranarray(sW[:, None] * Ks.T)
+    V = chol_solve(LB, R)
+    var = float(s2) - np.einsum("ij,ij->j", R, V)
+    return mean, var, ndtr(mean / np.sqrt(1.0 + var))

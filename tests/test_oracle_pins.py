@@ -587,3 +587,49 @@ def test_laplace_one_point_closed_form():
         r = oracle.laplace_probit(np.zeros((1, 1), np.float32), np.ones(1), s2, np.array([y]))
         assert r["f"][0] == pytest.approx(f, rel=1e-10)
         assert r["logq"] == pytest.approx(ref, rel=1e-10)
+
+
+def test_laplace_predictive_variance_is_the_posterior_form():
+    # s2 - k^T W^1/2 B^{-1} W^1/2 k = s2 - k^T (K + W^{-1})^{-1} k (the inversion
+    # lemma; the Gaussian posterior of the latent at x_*), computed with NumPy
+    p, ls, s2 = _laplace_small(40, 3, seed=9, ell=0.8)
+    r = oracle.laplace_probit(p.X, ls, s2, p.y)
+    Xs = synthetic.rng(3).standard_normal((7, 3))
+    m, v, pr = oracle.laplace_predict(p.X, ls, s2, p.y, r["f"], r["a"], Xs)
+    K = _lib_gram(p.X, p.X, ls, s2)
+    ks = _lib_gram(p.X, Xs, ls, s2)  # (n, ns)
+    _, g, W = oracle.probit_terms(p.y, r["f"])
+    v_ref = s2 - np.einsum("ij,ij->j", ks, np.linalg.solve(K + np.diag(1.0 / W), ks))
+    np.testing.assert_allclose(v, v_ref, rtol=1e-8)
+    np.testing.assert_allclose(m, ks.T @ g, rtol=1e-6, atol=1e-9)
+    assert np.all((v > 0) & (v <= s2)) and np.all((pr > 0) & (pr < 1))
+
+
+def test_laplace_predictive_probability_is_the_gaussian_integral():
+    # Phi(m / sqrt(1 + v)) = int Phi(t) N(t | m, v) dt, checked by quadrature; far
+    # from the data the prediction falls back to the prior (m = 0, v = s2, 1/2)
+    from scipy.integrate import quad
+    from scipy.stats import norm
+
+    p, ls, s2 = _laplace_small(30, 2, seed=11, ell=0.7)
+    r = oracle.laplace_probit(p.X, ls, s2, p.y)
+    Xs = np.array([[0.3, -0.2], [1.1, 0.4], [60.0, -80.0]])
+    m, v, pr = oracle.laplace_predict(p.X, ls, s2, p.y, r["f"], r["a"], Xs)
+    for k in range(2):
+        ref, _ = quad(lambda t: norm.cdf(t) * norm.pdf(t, m[k], math.sqrt(v[k])),
+                      m[k] - 12 * math.sqrt(v[k]), m[k] + 12 * math.sqrt(v[k]),
+                      epsabs=1e-13, epsrel=1e-12)
+        assert pr[k] == pytest.approx(ref, rel=1e-9)
+    assert abs(m[2]) < 1e-12 and v[2] == pytest.approx(s2, rel=1e-12)
+    assert pr[2] == pytest.approx(0.5, abs=1e-12)
+
+
+def test_laplace_prediction_one_point_closed_form():
+    # n = 1, x_* = x_1: m = s2 a, v = s2 - s2^2 W / (1 + s2 W) = s2 / (1 + s2 W)
+    X = np.zeros((1, 2), np.float32)
+    for y, s2 in ((1.0, 2.5), (-1.0, 0.7)):
+        r = oracle.laplace_probit(X, np.ones(2), s2, np.array([y]))
+        _, _, W = oracle.probit_terms(np.array([y]), r["f"])
+        m, v, _ = oracle.laplace_predict(X, np.ones(2), s2, np.array([y]), r["f"], r["a"], X)
+        assert m[0] == pytest.approx(s2 * r["a"][0], rel=1e-13)
+        assert v[0] == pytest.approx(s2 / (1 + s2 * W[0]), rel=1e-12)
