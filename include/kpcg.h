@@ -279,6 +279,22 @@ typedef struct {
 kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t max_newton,
                          double cg_tol, double* f, double* a, kpcg_laplace_info* info);
 
+/* Predictions of the probit classifier at ns test inputs (Sec. 2.2; Appendix B,
+ * "Prediction"), from the mode f and a = K^-1 f of kpcg_laplace on the same
+ * handle and labels:
+ *   mean (device, ns) = k_*^T a, the latent mean (FP64, entries rebuilt);
+ *   var (device, ns, nullable) = s^2 - k_*^T W^1/2 B^-1 W^1/2 k_*, W and B at f:
+ *   blocks of up to 16 test points are solved as right-hand sides of B by PCG to
+ *   cg_tol (certified, preconditioned as in kpcg_laplace);
+ *   prob (device, ns, nullable) = Phi(mean / sqrt(1 + var)), the predictive
+ *   probability of y_* = +1 (the Gaussian integral of the probit likelihood).
+ * Xs: device float32, ns x d row-major.  info (nullable): cg_iters_total sums
+ * the blocks' iteration counts (the most any column took), max_rel_res is the
+ * worst certified residual; newton_steps and psi are 0.  ns = 0 is a no-op. */
+kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, const double* a,
+                                 const float* Xs, int64_t ns, double* mean, double* var,
+                                 double* prob, double cg_tol, kpcg_laplace_info* info);
+
 /* ---------------------------------------------------------------------------
  * Learned warm start.  Algorithm 1 takes an initial iterate x0; along a
  * hyperparameter trajectory a small network predicts coefficients c on a

@@ -37,7 +37,7 @@ SYMBOLS = (
     "kpcg_batch_solve", "kpcg_batch_matvec_f32", "kpcg_batch_precond_apply_f32",
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
     "kpcg_batch_destroy",
-    "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace",
+    "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace", "kpcg_laplace_predict",
 )
 
 _NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
@@ -140,6 +140,8 @@ def lib():
         L.kpcg_precond.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int64)]
         L.kpcg_precond_spectral.argtypes = [vp, i64, pdbl]
         L.kpcg_laplace.argtypes = [vp, vp, dbl, i32, dbl, vp, vp, ctypes.POINTER(LaplaceInfo)]
+        L.kpcg_laplace_predict.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, dbl,
+                                           ctypes.POINTER(LaplaceInfo)]
         L.kpcg_matvec_f64.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_matvec_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32]
         L.kpcg_precond_apply_f64.argtypes = [vp, vp, i64, i32, vp, i64]
@@ -351,6 +353,30 @@ class Solver:
         if st not in (0, 6):
             self._check(st)
         return f, a, info, st
+
+    def laplace_predict(self, y, f, a, Xs, var=True, prob=True, cg_tol=1e-10):
+        """Probit predictions at Xs (float32 CUDA, ns x d) from the mode (f, a):
+        returns (mean, var or None, prob or None, LaplaceInfo)."""
+        torch = _torch()
+        if Xs.dtype != torch.float32 or not Xs.is_cuda or not Xs.is_contiguous():
+            raise TypeError("Xs must be a contiguous float32 CUDA tensor (ns x d row-major)")
+        ns = int(Xs.shape[0])
+        mk = lambda: torch.empty(ns, dtype=torch.float64, device=Xs.device)  # noqa: E731
+        mean = mk()
+        v = mk() if var else None
+        p = mk() if prob else None
+        info = LaplaceInfo()
+        f64 = torch.float64
+        for t, nm in ((y, "y"), (f, "f"), (a, "a")):
+            if t.dim() != 1 or t.shape[0] != self.n or not t.is_contiguous():
+                raise TypeError(f"{nm} must be a contiguous vector of length n")
+        self._check(lib().kpcg_laplace_predict(
+            self._h, _dptr(y, f64, "y"), _dptr(f, f64, "f"), _dptr(a, f64, "a"),
+            ctypes.c_void_p(Xs.data_ptr()), ns, _dptr(mean, f64, "mean"),
+            _dptr(v, f64, "var") if v is not None else None,
+            _dptr(p, f64, "prob") if p is not None else None, float(cg_tol),
+            ctypes.byref(info)))
+        return mean, v, p, info
 
     def matvec_f64(self, V, impl=0, out=None):
         torch = _torch()

@@ -120,6 +120,7 @@ struct Ctx {
     DevBuf<float2> lkxu0;
     DevBuf<double> lap;
     CgBufs<double> lcg;
+    DevBuf<double> lpw, lpv;  // Laplace predictions: blocks of right-hand sides, variances
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

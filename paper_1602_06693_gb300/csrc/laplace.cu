@@ -69,12 +69,20 @@ __global__ void lap_bfinish_kernel(double* out, int64_t ldo, const double* __res
         out[i + k * ldo] = fma(s[i], u[i + k * ldu], p[i + k * ldp]);
 }
 
-// r = v - w
+// r = v - w, c columns of leading dimension ld
 __global__ void lap_sub_kernel(double* __restrict__ r, const double* __restrict__ v,
-                               const double* __restrict__ w, int64_t n) {
+                               const double* __restrict__ w, int64_t n, int64_t ld) {
+    const int64_t o = (int64_t)blockIdx.y * ld;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        r[i] = v[i] - w[i];
+        r[o + i] = v[o + i] - w[o + i];
+}
+
+// p_* = Phi(m_* / sqrt(1 + v_*)), the probit predictive probability
+__global__ void lap_prob_kernel(const double* __restrict__ m, const double* __restrict__ v,
+                                int64_t ns, double* __restrict__ prob) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ns) prob[i] = normcdf(m[i] / sqrt(1.0 + v[i]));
 }
 
 // a = b - s * z
@@ -135,6 +143,82 @@ double lap_psi(Ctx& h, const double* y, const double* f, const double* a, double
     return l - 0.5 * q;
 }
 
+// B P = P + sW (K (sW P)) for up to the scratch width of columns: w = sW P,
+// u = K w (double-float), then the sum.  Launches on H.stream at call time
+// (graph capture swaps it).
+VecOp make_bop(Ctx* hp, const double* sW, double* u, double* w) {
+    return [hp, sW, u, w](const double* P, int64_t ldp, int cc, double* Q, int64_t ldq) {
+        Ctx& H = *hp;
+        const dim3 gg(lap_grid(H.n), (unsigned)cc);
+        lap_scale_kernel<<<gg, 256, 0, H.stream>>>(w, H.ld, P, ldp, sW, H.n);
+        KPCG_LAUNCHED("lap_scale_kernel");
+        kv_df(H, w, H.ld, cc, nullptr, 0, u, H.ld, 0.0);
+        lap_bfinish_kernel<<<gg, 256, 0, H.stream>>>(Q, ldq, P, ldp, u, H.ld, sW, H.n);
+        KPCG_LAUNCHED("lap_bfinish_kernel");
+    };
+}
+
+// The preconditioner of B: the Nystrom form in H.LP, or the identity.
+VecOp make_bpc(Ctx* hp, bool pre) {
+    return [hp, pre](const double* R, int64_t ldr, int cc, double* Z, int64_t ldz) {
+        Ctx& H = *hp;
+        if (pre)
+            precond_apply_f64(H.LP, R, ldr, cc, Z, ldz, H.stream);
+        else
+            copy_cols<double>(Z, ldz, R, ldr, H.n, cc, H.stream);
+    };
+}
+
+// B Z = R for nb columns (ld-strided): PCG from zero, then each column's
+// residual is recomputed with a fresh product and CG restarts from Z while
+// one misses tol (at most 4 restarts).  t, r: scratch of nb columns.  Adds
+// the iterations (the most any column took) to cg_total; returns the worst
+// certified relative residual.
+double bsolve(Ctx& c, const VecOp& mvB, const VecOp& pcB, const double* R, int nb, double* Z,
+              double tol, double* t, double* r, int& cg_total) {
+    const int64_t n = c.n, ld = c.ld;
+    const int nblk = dot_blocks(n);
+    std::vector<int> iters;
+    double worst = 0.0;
+    for (int attempt = 0; attempt < 5; ++attempt) {
+        int broken = 0;
+        pcg_f64(c, nb, R, ld, Z, ld, attempt == 0, tol, c.opt.max_iter, mvB, pcB, c.lcg, iters,
+                broken);
+        cg_total += iters.empty() ? 0 : *std::max_element(iters.begin(), iters.end());
+        if (broken) fail(KPCG_ERR_BREAKDOWN, "breakdown in a B-solve");
+        mvB(Z, ld, nb, t, ld);
+        lap_sub_kernel<<<dim3(lap_grid(n), (unsigned)nb), 256, 0, c.stream>>>(r, R, t, n, ld);
+        KPCG_LAUNCHED("lap_sub_kernel");
+        double* pp = c.partial.need((size_t)nblk * nb * 2);
+        dot_cols<double>(r, ld, r, ld, n, nb, pp, nblk, c.stream);
+        dot_cols<double>(R, ld, R, ld, n, nb, pp + (size_t)nblk * nb, nblk, c.stream);
+        std::vector<double> hq((size_t)nblk * nb * 2);
+        KPCG_CUDA(cudaMemcpyAsync(hq.data(), pp, sizeof(double) * hq.size(),
+                                  cudaMemcpyDeviceToHost, c.stream));
+        KPCG_CUDA(cudaStreamSynchronize(c.stream));
+        worst = 0.0;
+        for (int k = 0; k < nb; ++k) {
+            double rr = 0.0, vv = 0.0;
+            for (int q = 0; q < nblk; ++q) {
+                rr += hq[(size_t)k * nblk + q];
+                vv += hq[(size_t)(nb + k) * nblk + q];
+            }
+            worst = std::max(worst, vv > 0.0 ? std::sqrt(rr / vv) : 0.0);
+        }
+        if (worst <= tol) break;
+    }
+    return worst;
+}
+
+void check_labels(Ctx& c, const double* y) {
+    std::vector<double> hy((size_t)c.n);
+    KPCG_CUDA(cudaMemcpyAsync(hy.data(), y, sizeof(double) * c.n, cudaMemcpyDeviceToHost,
+                              c.stream));
+    KPCG_CUDA(cudaStreamSynchronize(c.stream));
+    for (double v : hy)
+        if (v != 1.0 && v != -1.0) fail(KPCG_ERR_ARG, "labels must be +1 or -1");
+}
+
 }  // namespace
 }  // namespace kpcg
 
@@ -158,16 +242,9 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
             fail(KPCG_ERR_ARG, "the Laplace B-solve takes a Nystrom preconditioner or none");
         const int64_t n = c.n, ld = c.ld;
         cudaStream_t st = c.stream;
-        {
-            std::vector<double> hy((size_t)n);
-            KPCG_CUDA(cudaMemcpyAsync(hy.data(), y, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                                      st));
-            KPCG_CUDA(cudaStreamSynchronize(st));
-            for (double v : hy)
-                if (v != 1.0 && v != -1.0) fail(KPCG_ERR_ARG, "labels must be +1 or -1");
-        }
-        // vectors f, a, sW = W^1/2, b, v, z; u and w are scratch of the B product
-        double* base = c.lap.need((size_t)ld * 8 + 2 * 152 * 8);
+        check_labels(c, y);
+        // vectors f, a, sW = W^1/2, b, v, z; u, w, t, r are scratch of the B-solve
+        double* base = c.lap.need((size_t)ld * 10 + 2 * 152 * 8);
         double* f = base;
         double* a = base + ld;
         double* sW = base + 2 * ld;
@@ -176,38 +253,20 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         double* z = base + 5 * ld;
         double* u = base + 6 * ld;
         double* w = base + 7 * ld;
-        double* part = base + 8 * ld;
+        double* t = base + 8 * ld;
+        double* r = base + 9 * ld;
+        double* part = base + 10 * ld;
         KPCG_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * ld, st));
         KPCG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * ld, st));
         const unsigned g = lap_grid(n);
         const bool pre = c.pkind == KPCG_PREC_NYSTROM;
-
-        // B p = p + sW (K (sW p)), on h.stream at call time (graph capture swaps it)
-        Ctx* hp = &c;
-        const VecOp mvB = [hp, sW, u, w](const double* P, int64_t ldp, int cc, double* Q,
-                                         int64_t ldq) {
-            Ctx& H = *hp;
-            const dim3 gg(lap_grid(H.n), (unsigned)cc);
-            lap_scale_kernel<<<gg, 256, 0, H.stream>>>(w, H.ld, P, ldp, sW, H.n);
-            KPCG_LAUNCHED("lap_scale_kernel");
-            kv_df(H, w, H.ld, cc, nullptr, 0, u, H.ld, 0.0);
-            lap_bfinish_kernel<<<gg, 256, 0, H.stream>>>(Q, ldq, P, ldp, u, H.ld, sW, H.n);
-            KPCG_LAUNCHED("lap_bfinish_kernel");
-        };
-        const VecOp pcB = [hp, pre](const double* R, int64_t ldr, int cc, double* Z, int64_t ldz) {
-            Ctx& H = *hp;
-            if (pre)
-                precond_apply_f64(H.LP, R, ldr, cc, Z, ldz, H.stream);
-            else
-                copy_cols<double>(Z, ldz, R, ldr, H.n, cc, H.stream);
-        };
+        const VecOp mvB = make_bop(&c, sW, u, w);
+        const VecOp pcB = make_bpc(&c, pre);
 
         double psi_old = lap_psi(c, y, f, a, part);  // n log(1/2) at f = 0
         double psi = psi_old, setup_ms = 0.0, worst = 0.0;
         int steps = 0, cg_total = 0;
         bool converged = false, solved = true;
-        std::vector<int> iters;
-        const int nblk = dot_blocks(n);
         while (steps < max_newton) {
             ++steps;
             lap_terms_kernel<<<g, 256, 0, st>>>(y, f, n, sW, b);
@@ -225,34 +284,7 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
             kv_df(c, b, ld, 1, nullptr, 0, u, ld, 0.0);
             lap_scale_kernel<<<dim3(g, 1), 256, 0, st>>>(v, ld, u, ld, sW, n);
             KPCG_LAUNCHED("lap_scale_kernel");
-            // B z = v: PCG from zero; the recursive residual is re-certified with
-            // a fresh product and CG restarts from z while it misses cg_tol
-            double rel = 0.0;
-            for (int attempt = 0; attempt < 5; ++attempt) {
-                int broken = 0;
-                pcg_f64(c, 1, v, ld, z, ld, attempt == 0, cg_tol, c.opt.max_iter, mvB, pcB,
-                        c.lcg, iters, broken);
-                cg_total += iters.empty() ? 0 : iters[0];
-                if (broken) fail(KPCG_ERR_BREAKDOWN, "breakdown in the B-solve");
-                // r = v - B z (w = B z; u, w are mvB's scratch, w written last)
-                mvB(z, ld, 1, w, ld);
-                lap_sub_kernel<<<g, 256, 0, st>>>(u, v, w, n);
-                KPCG_LAUNCHED("lap_sub_kernel");
-                double* pp = c.partial.need((size_t)nblk * 2);
-                dot_cols<double>(u, ld, u, ld, n, 1, pp, nblk, st);
-                dot_cols<double>(v, ld, v, ld, n, 1, pp + nblk, nblk, st);
-                std::vector<double> hq((size_t)nblk * 2);
-                KPCG_CUDA(cudaMemcpyAsync(hq.data(), pp, sizeof(double) * hq.size(),
-                                          cudaMemcpyDeviceToHost, st));
-                KPCG_CUDA(cudaStreamSynchronize(st));
-                double rr = 0.0, vv = 0.0;
-                for (int t = 0; t < nblk; ++t) {
-                    rr += hq[(size_t)t];
-                    vv += hq[(size_t)(nblk + t)];
-                }
-                rel = vv > 0.0 ? std::sqrt(rr / vv) : 0.0;
-                if (rel <= cg_tol) break;
-            }
+            const double rel = bsolve(c, mvB, pcB, v, 1, z, cg_tol, t, r, cg_total);
             worst = std::max(worst, rel);
             if (rel > cg_tol) solved = false;
             // a = b - sW z;  f = K a
@@ -284,6 +316,112 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
             info->launches = (int)(launch_count() - launches0);
         }
         if (!converged) fail(KPCG_ERR_NO_CONVERGENCE, "Newton steps exhausted before the stop test");
+        if (!solved) fail(KPCG_ERR_NO_CONVERGENCE, "a B-solve missed cg_tol");
+        return KPCG_OK;
+    } catch (const kpcg::Error& e) {
+        h->err = e.msg;
+        return e.status;
+    } catch (const std::exception& e) {
+        h->err = e.what();
+        return KPCG_ERR_ARG;
+    }
+}
+
+kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, const double* a,
+                                 const float* Xs, int64_t ns, double* mean, double* var,
+                                 double* prob, double cg_tol, kpcg_laplace_info* info) {
+    if (!h) return KPCG_ERR_ARG;
+    try {
+        using namespace kpcg;
+        Ctx& c = *h;
+        const auto t0 = std::chrono::steady_clock::now();
+        const long long launches0 = launch_count();
+        if (ns < 0) fail(KPCG_ERR_ARG, "ns must be >= 0");
+        if (ns == 0) return KPCG_OK;
+        if (!y || !f || !a || !Xs || !mean) fail(KPCG_ERR_ARG, "NULL argument");
+        const bool want_var = var || prob;
+        if (want_var && !(cg_tol > 0.0 && cg_tol < 1.0))
+            fail(KPCG_ERR_ARG, "cg_tol must be in (0, 1)");
+        if (c.pkind != KPCG_PREC_NONE && c.pkind != KPCG_PREC_NYSTROM)
+            fail(KPCG_ERR_ARG, "the Laplace B-solve takes a Nystrom preconditioner or none");
+        cudaStream_t st = c.stream;
+        check_labels(c, y);
+        // latent mean m_* = K(X_*, X) a
+        const double* xt = predict_mean(c, Xs, ns, a, mean);
+        int cg_total = 0;
+        double worst = 0.0, setup_ms = 0.0;
+        bool solved = true;
+        if (want_var) {
+            constexpr int PB = 16;  // test points per block of right-hand sides
+            const int64_t n = c.n, ld = c.ld;
+            double* base = c.lpw.need((size_t)ld * (2 + 7 * PB));
+            double* sW = base;
+            double* bb = base + ld;
+            double* Kb = base + 2 * ld;
+            double* R = Kb + PB * ld;
+            double* Z = R + PB * ld;
+            double* u = Z + PB * ld;
+            double* w = u + PB * ld;
+            double* t = w + PB * ld;
+            double* r = t + PB * ld;
+            const unsigned g = lap_grid(n);
+            lap_terms_kernel<<<g, 256, 0, st>>>(y, f, n, sW, bb);  // W at the mode
+            KPCG_LAUNCHED("lap_terms_kernel");
+            const bool pre = c.pkind == KPCG_PREC_NYSTROM;
+            if (pre) {
+                const auto s0 = std::chrono::steady_clock::now();
+                laplace_precond_setup(c.LP, c.lkxu0, true, c.xs32.p, c.xs64.p, n, c.dp,
+                                      c.c0_64(), sW, c.pidx.data(), c.psize, st);
+                KPCG_CUDA(cudaStreamSynchronize(st));
+                setup_ms = std::chrono::duration<double, std::milli>(
+                               std::chrono::steady_clock::now() - s0)
+                               .count();
+            }
+            const VecOp mvB = make_bop(&c, sW, u, w);
+            const VecOp pcB = make_bpc(&c, pre);
+            const int nblk = dot_blocks(n);
+            std::vector<double> hv((size_t)ns);
+            for (int64_t b0 = 0; b0 < ns; b0 += PB) {
+                const int nb = (int)std::min<int64_t>(PB, ns - b0);
+                // R = W^1/2 k_*, Z = B^{-1} R, v_* = s^2 - R^T Z
+                predict_kblock(c, xt + b0 * c.dp, nb, Kb, ld);
+                lap_scale_kernel<<<dim3(g, (unsigned)nb), 256, 0, st>>>(R, ld, Kb, ld, sW, n);
+                KPCG_LAUNCHED("lap_scale_kernel");
+                const double rel = bsolve(c, mvB, pcB, R, nb, Z, cg_tol, t, r, cg_total);
+                worst = std::max(worst, rel);
+                if (rel > cg_tol) solved = false;
+                double* pp = c.partial.need((size_t)nblk * nb);
+                dot_cols<double>(R, ld, Z, ld, n, nb, pp, nblk, st);
+                std::vector<double> hp((size_t)nblk * nb);
+                KPCG_CUDA(cudaMemcpyAsync(hp.data(), pp, sizeof(double) * hp.size(),
+                                          cudaMemcpyDeviceToHost, st));
+                KPCG_CUDA(cudaStreamSynchronize(st));
+                for (int k = 0; k < nb; ++k) {
+                    double q = 0.0;
+                    for (int e = 0; e < nblk; ++e) q += hp[(size_t)k * nblk + e];
+                    hv[(size_t)(b0 + k)] = c.s2 - q;
+                }
+            }
+            double* vd = var ? var : c.lpv.need((size_t)ns);
+            KPCG_CUDA(cudaMemcpyAsync(vd, hv.data(), sizeof(double) * ns, cudaMemcpyHostToDevice,
+                                      st));
+            if (prob) {
+                lap_prob_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(mean, vd, ns, prob);
+                KPCG_LAUNCHED("lap_prob_kernel");
+            }
+        }
+        KPCG_CUDA(cudaStreamSynchronize(st));
+        if (info) {
+            info->newton_steps = 0;
+            info->cg_iters_total = cg_total;
+            info->psi = 0.0;
+            info->max_rel_res = worst;
+            info->setup_ms = setup_ms;
+            info->time_ms = std::chrono::duration<double, std::milli>(
+                                std::chrono::steady_clock::now() - t0)
+                                .count();
+            info->launches = (int)(launch_count() - launches0);
+        }
         if (!solved) fail(KPCG_ERR_NO_CONVERGENCE, "a B-solve missed cg_tol");
         return KPCG_OK;
     } catch (const kpcg::Error& e) {

@@ -106,6 +106,43 @@ void launch_mean(const double* xt, int64_t ns, const double* xs, int64_t n, doub
 }
 
 }  // namespace
+
+const double* predict_mean(Ctx& c, const float* Xs, int64_t ns, const double* alpha,
+                           double* mean) {
+    cudaStream_t st = c.stream;
+    const int dp = c.dp;
+    const double c0 = c.c0_64();
+    double* xt = c.pxt.need((size_t)ns * dp);
+    pred_prescale_kernel<<<(unsigned)((ns * dp + 255) / 256), 256, 0, st>>>(
+        Xs, ns, c.d, dp, c.mu.p, c.inv_ell.p, xt);
+    KPCG_LAUNCHED("pred_prescale_kernel");
+    // column ranges split over about eight CTAs per SM, added in order
+    const int64_t nrb = (ns + PT - 1) / PT;
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + nrb - 1) / nrb,
+                                                            (c.n + PJ - 1) / PJ));
+    int64_t cps = ((c.n + nsplit - 1) / nsplit + PJ - 1) / PJ * PJ;
+    nsplit = (c.n + cps - 1) / cps;
+    double* part = c.ppart.need((size_t)nsplit * ns);
+    switch (dp) {
+        case 4: launch_mean<4>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
+        case 8: launch_mean<8>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
+        case 12: launch_mean<12>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
+        case 16: launch_mean<16>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
+        case 32: launch_mean<32>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
+        default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+    }
+    pred_mean_reduce_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(part, (int)nsplit, ns,
+                                                                          mean);
+    KPCG_LAUNCHED("pred_mean_reduce_kernel");
+    return xt;
+}
+
+void predict_kblock(Ctx& c, const double* xt, int nb, double* Kb, int64_t ldk) {
+    pred_kblock_kernel<<<dim3((unsigned)std::min<int64_t>((c.n + 255) / 256, 512), (unsigned)nb),
+                         256, 0, c.stream>>>(c.xs64.p, c.n, c.dp, xt, c.c0_64(), Kb, ldk);
+    KPCG_LAUNCHED("pred_kblock_kernel");
+}
+
 }  // namespace kpcg
 
 using kpcg::fail;
@@ -124,29 +161,7 @@ kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* al
         Ctx& c = *h;
         cudaStream_t st = c.stream;
         const int dp = c.dp;
-        const double c0 = c.c0_64();
-        double* xt = c.pxt.need((size_t)ns * dp);
-        pred_prescale_kernel<<<(unsigned)((ns * dp + 255) / 256), 256, 0, st>>>(
-            Xs, ns, c.d, dp, c.mu.p, c.inv_ell.p, xt);
-        KPCG_LAUNCHED("pred_prescale_kernel");
-        // mean: column ranges split over about eight CTAs per SM, added in order
-        const int64_t nrb = (ns + PT - 1) / PT;
-        int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + nrb - 1) / nrb,
-                                                                (c.n + PJ - 1) / PJ));
-        int64_t cps = ((c.n + nsplit - 1) / nsplit + PJ - 1) / PJ * PJ;
-        nsplit = (c.n + cps - 1) / cps;
-        double* part = c.ppart.need((size_t)nsplit * ns);
-        switch (dp) {
-            case 4: launch_mean<4>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
-            case 8: launch_mean<8>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
-            case 12: launch_mean<12>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
-            case 16: launch_mean<16>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
-            case 32: launch_mean<32>(xt, ns, c.xs64.p, c.n, c0, alpha, cps, (int)nsplit, part, st); break;
-            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
-        }
-        pred_mean_reduce_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(part, (int)nsplit,
-                                                                              ns, mean);
-        KPCG_LAUNCHED("pred_mean_reduce_kernel");
+        const double* xt = predict_mean(c, Xs, ns, alpha, mean);
         kpcg_info tot{};
         double max_rel = 0.0;
         if (var) {
@@ -158,10 +173,7 @@ kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* al
             const int nblk = dot_blocks(c.n);
             for (int64_t b0 = 0; b0 < ns; b0 += PB) {
                 const int nb = (int)std::min<int64_t>(PB, ns - b0);
-                pred_kblock_kernel<<<dim3((unsigned)std::min<int64_t>((c.n + 255) / 256, 512),
-                                          (unsigned)nb),
-                                     256, 0, st>>>(c.xs64.p, c.n, dp, xt + b0 * dp, c0, Kb, ld);
-                KPCG_LAUNCHED("pred_kblock_kernel");
+                predict_kblock(c, xt + b0 * dp, nb, Kb, ld);
                 kpcg_info bi{};
                 const kpcg_status s = solve_impl(c, Kb, ld, nb, tol, nullptr, W, ld, nullptr, &bi);
                 if (s != KPCG_OK) fail(s, "variance solve: " + c.err);

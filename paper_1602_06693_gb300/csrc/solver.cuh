@@ -96,6 +96,12 @@ int pcg_f64(Ctx& h, int c, const double* B, int64_t ldb, double* X, int64_t ldx,
 kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
                        const double* X0, double* Xout, int64_t ldx, int32_t* iters_host,
                        kpcg_info* info);
+// Predictions (predict.cu): scale Xs (ns x d row-major, float32) into the
+// handle's coordinates (kept in c.pxt, returned) and write mean = K(X_*, X) alpha
+// (FP64); and the block K(X, X_*) of nb scaled test points into Kb (ld ldk).
+const double* predict_mean(Ctx& c, const float* Xs, int64_t ns, const double* alpha,
+                           double* mean);
+void predict_kblock(Ctx& c, const double* xt, int nb, double* Kb, int64_t ldk);
 // (Re)build the handle's preconditioner for the noise its mode needs;
 // returns the host milliseconds spent (0 if it was current).
 double ensure_precond(Ctx& h);

@@ -192,3 +192,47 @@ def test_laplace_argument_errors(kpcg):
         s.precond(kpcg.KPCG_PREC_NONE)
         f, a, info, st = s.laplace(_cm(p.y), max_newton=1)
         assert st == 6 and info.newton_steps == 1  # stopped before the test was met
+
+
+# ---------------------------------------- probit predictions (Sec. 2.2, App. B)
+@pytest.mark.parametrize("m", [0, 90])
+def test_laplace_predictions_match_oracle(kpcg, m):
+    # mean from a (FP64 on both sides), variance through one B-solve per test
+    # point (blocks of 16; 37 points leave a ragged block of 5), probability
+    p = synthetic.classification_problem(1200, 5, seed=41, s2=3.0, ell=1.4)
+    ell, s2 = oracle.split_theta(p.log_theta, 5, True)
+    ref = oracle.laplace_probit(p.X, ell, s2, p.y, tol=1e-12)
+    Xs = synthetic.rng(42).standard_normal((37, 5)).astype(np.float32)
+    Xs[3] = p.X[10]  # a training input
+    Xs[4] = 40.0     # far from the data: the prior
+    mr, vr, pr = oracle.laplace_predict(p.X, ell, s2, p.y, ref["f"], ref["a"], Xs)
+    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+        if m:
+            s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=13))
+        y = _cm(p.y)
+        f, a, info, st = s.laplace(y, newton_tol=1e-12, cg_tol=1e-10)
+        assert st == 0
+        mean, var, prob, pinfo = s.laplace_predict(y, f, a, torch.from_numpy(Xs).to(DEV))
+    mean, var, prob = _np(mean), _np(var), _np(prob)
+    # the GPU's own mode agrees with the oracle's to ~1e-7 (the B-solves are
+    # certified at 1e-10); predictions inherit that, with one more B-solve each
+    assert np.abs(mean - mr).max() <= 1e-6 * max(1.0, np.abs(mr).max())
+    assert np.abs(var - vr).max() <= 1e-6 * s2
+    assert np.abs(prob - pr).max() <= 1e-6
+    assert abs(mean[4]) < 1e-12 and var[4] == pytest.approx(s2, rel=1e-12)
+    assert pinfo.max_rel_res <= 1e-10 and pinfo.cg_iters_total > 0
+
+
+def test_laplace_predict_mean_only_and_empty(kpcg):
+    p = synthetic.classification_problem(500, 3, seed=43)
+    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+        y = _cm(p.y)
+        f, a, info, st = s.laplace(y)
+        Xs = torch.from_numpy(synthetic.rng(44).standard_normal((3, 3)).astype(np.float32)).to(DEV)
+        mean, var, prob, pinfo = s.laplace_predict(y, f, a, Xs, var=False, prob=False)
+        assert var is None and prob is None and pinfo.cg_iters_total == 0
+        mean0, _, _, _ = s.laplace_predict(y, f, a, Xs[:0])
+        assert mean0.numel() == 0
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    ref = oracle.gram(_np(Xs), p.X, ell, s2) @ _np(a)
+    assert _rel(_np(mean), ref) <= 1e-12
