@@ -568,6 +568,21 @@ def run_laplace(args):
         fh.copy_(fd, non_blocking=True)
         torch.cuda.synchronize(dev)
         e2e_t.append(time.perf_counter() - t0)
+    # predictions at 1024 test inputs from the mode (mean, variance, probability)
+    Xs = torch.from_numpy(synthetic.rng(200 + rank).standard_normal((1024, p.d))
+                          .astype(np.float32)).to(dev)
+    s.laplace_predict(y, f, a, Xs)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, pv, pp, pinfo = s.laplace_predict(y, f, a, Xs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    pred = {"test_points": 1024, "time_s": e0.elapsed_time(e1) / 1e3,
+            "cg_iters_total": pinfo.cg_iters_total, "max_rel_res": pinfo.max_rel_res,
+            "var_range": [float(pv.min()), float(pv.max())],
+            "prob_range": [float(pp.min()), float(pp.max())]}
     extra = {}
     if rank == 0 and world == 1 and not args.skip_baselines:
         try:
@@ -585,7 +600,8 @@ def run_laplace(args):
                     "cg_iters_total": info.cg_iters_total, "psi": info.psi,
                     "max_rel_res": info.max_rel_res, "setup_ms": info.setup_ms,
                     "step_times_s": times,
-                    "train_accuracy": float((torch.sign(f) == y).double().mean())},
+                    "train_accuracy": float((torch.sign(f) == y).double().mean()),
+                    "predict": pred},
         "roofline": roof, "clocks": clocks,
         "e2e": {"value": statistics.mean(e2e_t), "unit": "s",
                 "h2d_bytes_per_step": int(yh.numel() * 8),
