@@ -471,7 +471,8 @@ LAPLACE_M = 512
 LAPLACE_WORKLOAD = ("probit GP classification, EEG shape n=14979 d=14 (X~N(0,I) standardized, "
                     "y=sign(sum sin x) with 5% flipped), ARD l=sqrt(14), s^2=4; Laplace mode by "
                     "Newton from f=0 (stop |dPsi| <= 1e-12 |Psi|), each B = I + W^1/2 K W^1/2 "
-                    "solve by PCG to 1e-10 with the Nystrom form of B (m=512, rebuilt per step), "
+                    "solve by PCG to 1e-10 from the previous step's z with the Nystrom form of B (m=512, "
+                    "rebuilt when W^1/2 drifts by >10%), "
                     "double-float K.V")
 
 
@@ -598,6 +599,7 @@ def run_laplace(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "laplace": {"status": st, "newton_steps": info.newton_steps,
                     "cg_iters_total": info.cg_iters_total, "psi": info.psi,
+                    "precond_builds": info.precond_builds,
                     "max_rel_res": info.max_rel_res, "setup_ms": info.setup_ms,
                     "step_times_s": times,
                     "train_accuracy": float((torch.sign(f) == y).double().mean()),

@@ -258,8 +258,10 @@ kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* al
  *   handle's precision; the per-point terms are FP64.
  *   Preconditioner of B: with a Nystrom request on the handle (kpcg_precond,
  *   KPCG_PREC_NYSTROM) P_B = I + W^1/2 K_XU K_UU^-1 K_UX W^1/2 on the same
- *   inducing points, rebuilt every Newton step (W changes); with none, P_B = I;
- *   other kinds are rejected (KPCG_ERR_ARG).
+ *   inducing points, built at the first Newton step and rebuilt when W^1/2 has
+ *   moved by more than 10% on some point since (a stale P_B is still SPD); with
+ *   none, P_B = I; other kinds are rejected (KPCG_ERR_ARG).  From the second
+ *   step on, each B-solve starts from the previous step's z.
  *   y: device, n labels, each +1 or -1 (checked).  f (device, n): the mode f^;
  *   a (device, n, nullable): a = K^-1 f^ (Appendix B), needed by predictions.
  *   newton_tol > 0, max_newton >= 1, cg_tol in (0, 1): each B-solve stops at
@@ -274,6 +276,7 @@ typedef struct {
     double time_ms;         /* wall time of the call on the host                    */
     double setup_ms;        /* part of time_ms spent building P_B                   */
     int32_t launches;       /* CUDA kernels this call launched                      */
+    int32_t precond_builds; /* builds of P_B during the call                        */
 } kpcg_laplace_info;
 
 kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t max_newton,

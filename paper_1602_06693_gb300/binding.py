@@ -90,6 +90,7 @@ class LaplaceInfo(ctypes.Structure):
         ("time_ms", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
         ("launches", ctypes.c_int32),
+        ("precond_builds", ctypes.c_int32),
     ]
 
 

@@ -20,6 +20,7 @@ namespace {
 
 constexpr double kSqrt2OverPi = 0.79788456080286535588;  // sqrt(2 / pi)
 constexpr double kSqrtHalf = 0.70710678118654752440;
+constexpr double kRebuildDrift = 0.1;  // relative drift of W^1/2 that rebuilds P_B
 
 // N(z) / Phi(z) for the standard normal density and CDF.  With
 // Phi(z) = erfc(-z/sqrt2)/2 = erfcx(-z/sqrt2) exp(-z^2/2)/2 the exponentials
@@ -122,6 +123,25 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// part[blk] = max_i |sW_i / sWb_i - 1| over the block's rows (the drift of W^1/2
+// since the preconditioner of B was built on sWb)
+__global__ void __launch_bounds__(256)
+    lap_drift_kernel(const double* __restrict__ sW, const double* __restrict__ sWb, int64_t n,
+                     double* __restrict__ part) {
+    __shared__ double sm[256];
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, fabs(sW[i] / sWb[i] - 1.0));
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
 unsigned lap_grid(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
 }
@@ -169,21 +189,21 @@ VecOp make_bpc(Ctx* hp, bool pre) {
     };
 }
 
-// B Z = R for nb columns (ld-strided): PCG from zero, then each column's
+// B Z = R for nb columns (ld-strided): PCG from zero (from Z if z_given), then each column's
 // residual is recomputed with a fresh product and CG restarts from Z while
 // one misses tol (at most 4 restarts).  t, r: scratch of nb columns.  Adds
 // the iterations (the most any column took) to cg_total; returns the worst
 // certified relative residual.
 double bsolve(Ctx& c, const VecOp& mvB, const VecOp& pcB, const double* R, int nb, double* Z,
-              double tol, double* t, double* r, int& cg_total) {
+              double tol, double* t, double* r, int& cg_total, bool z_given = false) {
     const int64_t n = c.n, ld = c.ld;
     const int nblk = dot_blocks(n);
     std::vector<int> iters;
     double worst = 0.0;
     for (int attempt = 0; attempt < 5; ++attempt) {
         int broken = 0;
-        pcg_f64(c, nb, R, ld, Z, ld, attempt == 0, tol, c.opt.max_iter, mvB, pcB, c.lcg, iters,
-                broken);
+        pcg_f64(c, nb, R, ld, Z, ld, attempt == 0 && !z_given, tol, c.opt.max_iter, mvB, pcB,
+                c.lcg, iters, broken);
         cg_total += iters.empty() ? 0 : *std::max_element(iters.begin(), iters.end());
         if (broken) fail(KPCG_ERR_BREAKDOWN, "breakdown in a B-solve");
         mvB(Z, ld, nb, t, ld);
@@ -243,8 +263,9 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         const int64_t n = c.n, ld = c.ld;
         cudaStream_t st = c.stream;
         check_labels(c, y);
-        // vectors f, a, sW = W^1/2, b, v, z; u, w, t, r are scratch of the B-solve
-        double* base = c.lap.need((size_t)ld * 10 + 2 * 152 * 8);
+        // vectors f, a, sW = W^1/2, b, v, z, sWb (sW of the last P_B build); u, w,
+        // t, r are scratch of the B-solve
+        double* base = c.lap.need((size_t)ld * 11 + 2 * 152 * 8);
         double* f = base;
         double* a = base + ld;
         double* sW = base + 2 * ld;
@@ -255,7 +276,8 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         double* w = base + 7 * ld;
         double* t = base + 8 * ld;
         double* r = base + 9 * ld;
-        double* part = base + 10 * ld;
+        double* sWb = base + 10 * ld;
+        double* part = base + 11 * ld;
         KPCG_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * ld, st));
         KPCG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * ld, st));
         const unsigned g = lap_grid(n);
@@ -265,15 +287,30 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
 
         double psi_old = lap_psi(c, y, f, a, part);  // n log(1/2) at f = 0
         double psi = psi_old, setup_ms = 0.0, worst = 0.0;
-        int steps = 0, cg_total = 0;
+        int steps = 0, cg_total = 0, builds = 0;
         bool converged = false, solved = true;
         while (steps < max_newton) {
             ++steps;
             lap_terms_kernel<<<g, 256, 0, st>>>(y, f, n, sW, b);
             KPCG_LAUNCHED("lap_terms_kernel");
-            if (pre) {
+            // P_B is rebuilt when W^1/2 moved by more than 10% on some row since
+            // the last build; a stale P_B is still SPD, so PCG stays correct
+            bool rebuild = pre && builds == 0;
+            if (pre && builds > 0) {
+                lap_drift_kernel<<<g, 256, 0, st>>>(sW, sWb, n, part);
+                KPCG_LAUNCHED("lap_drift_kernel");
+                std::vector<double> hd(g);
+                KPCG_CUDA(cudaMemcpyAsync(hd.data(), part, sizeof(double) * g,
+                                          cudaMemcpyDeviceToHost, st));
+                KPCG_CUDA(cudaStreamSynchronize(st));
+                rebuild = *std::max_element(hd.begin(), hd.end()) > kRebuildDrift;
+            }
+            if (rebuild) {
+                ++builds;
+                KPCG_CUDA(cudaMemcpyAsync(sWb, sW, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                          st));
                 const auto s0 = std::chrono::steady_clock::now();
-                laplace_precond_setup(c.LP, c.lkxu0, steps == 1, c.xs32.p, c.xs64.p, n, c.dp,
+                laplace_precond_setup(c.LP, c.lkxu0, builds == 1, c.xs32.p, c.xs64.p, n, c.dp,
                                       c.c0_64(), sW, c.pidx.data(), c.psize, st);
                 KPCG_CUDA(cudaStreamSynchronize(st));
                 setup_ms += std::chrono::duration<double, std::milli>(
@@ -284,7 +321,8 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
             kv_df(c, b, ld, 1, nullptr, 0, u, ld, 0.0);
             lap_scale_kernel<<<dim3(g, 1), 256, 0, st>>>(v, ld, u, ld, sW, n);
             KPCG_LAUNCHED("lap_scale_kernel");
-            const double rel = bsolve(c, mvB, pcB, v, 1, z, cg_tol, t, r, cg_total);
+            // from the previous step's z: B and v change little near the mode
+            const double rel = bsolve(c, mvB, pcB, v, 1, z, cg_tol, t, r, cg_total, steps > 1);
             worst = std::max(worst, rel);
             if (rel > cg_tol) solved = false;
             // a = b - sW z;  f = K a
@@ -306,6 +344,7 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         KPCG_CUDA(cudaStreamSynchronize(st));
         if (info) {
             info->newton_steps = steps;
+            info->precond_builds = builds;
             info->cg_iters_total = cg_total;
             info->psi = psi;
             info->max_rel_res = worst;
@@ -348,7 +387,7 @@ kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, con
         check_labels(c, y);
         // latent mean m_* = K(X_*, X) a
         const double* xt = predict_mean(c, Xs, ns, a, mean);
-        int cg_total = 0;
+        int cg_total = 0, pre_built = 0;
         double worst = 0.0, setup_ms = 0.0;
         bool solved = true;
         if (want_var) {
@@ -372,6 +411,7 @@ kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, con
                 const auto s0 = std::chrono::steady_clock::now();
                 laplace_precond_setup(c.LP, c.lkxu0, true, c.xs32.p, c.xs64.p, n, c.dp,
                                       c.c0_64(), sW, c.pidx.data(), c.psize, st);
+                pre_built = 1;
                 KPCG_CUDA(cudaStreamSynchronize(st));
                 setup_ms = std::chrono::duration<double, std::milli>(
                                std::chrono::steady_clock::now() - s0)
@@ -413,6 +453,7 @@ kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, con
         KPCG_CUDA(cudaStreamSynchronize(st));
         if (info) {
             info->newton_steps = 0;
+            info->precond_builds = pre_built;
             info->cg_iters_total = cg_total;
             info->psi = 0.0;
             info->max_rel_res = worst;
