@@ -236,3 +236,41 @@ def test_laplace_predict_mean_only_and_empty(kpcg):
     ell, s2 = oracle.split_theta(p.log_theta, 3, True)
     ref = oracle.gram(_np(Xs), p.X, ell, s2) @ _np(a)
     assert _rel(_np(mean), ref) <= 1e-12
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("n", [1, 2, 129])
+def test_laplace_small_and_ragged_sizes(kpcg, n):
+    # n = 1 (one label, the scalar Newton of the one-point closed form), n = 2,
+    # and one row past a 128-row tile; predictions at 1 and 16 test points
+    p = synthetic.classification_problem(max(n, 2), 3, seed=50 + n, s2=2.0, ell=1.0)
+    X, y = p.X[:n], p.y[:n]
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    ref = oracle.laplace_probit(X, ell, s2, y, tol=1e-12)
+    opt = kpcg.default_options(precision=kpcg.KPCG_DF64)
+    with kpcg.Solver(torch.from_numpy(np.ascontiguousarray(X)).to(DEV), p.log_theta, 1.0,
+                     ard=True, options=opt) as s:
+        yd = _cm(y)
+        f, a, info, st = s.laplace(yd, newton_tol=1e-12, cg_tol=1e-10)
+        assert st == 0 and abs(info.newton_steps - ref["steps"]) <= 1
+        assert _rel(_np(f), ref["f"]) <= 1e-7
+        for ns in (1, 16):
+            Xs = synthetic.rng(60 + ns).standard_normal((ns, 3)).astype(np.float32)
+            mean, var, prob, _ = s.laplace_predict(yd, f, a, torch.from_numpy(Xs).to(DEV))
+            mr, vr, pr = oracle.laplace_predict(X, ell, s2, y, ref["f"], ref["a"], Xs)
+            assert np.abs(_np(var) - vr).max() <= 1e-6 * s2
+            assert np.abs(_np(prob) - pr).max() <= 1e-6
+
+
+def test_spectral_single_frequency(kpcg):
+    # m = 1: Phi has two columns (one cosine, one sine)
+    p = synthetic.make_problem(300, 2, seed=61, ell=0.8, noise=0.1)
+    ell, s2 = oracle.split_theta(p.log_theta, 2, True)
+    om = synthetic.spectral_draws(1, 2, seed=62)
+    S = oracle.Spectral(p.X, ell, s2, p.noise, om)
+    R = synthetic.rng(63).standard_normal((300, 2))
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
+        s.precond_spectral(om)
+        Z = _np(s.precond_apply(_cm(R)))
+    for k in range(2):
+        assert _rel(Z[:, k], S.apply(R[:, k])) <= 1e-9
