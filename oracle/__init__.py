@@ -523,3 +523,36 @@ def laplace_predict(X, ell, s2, y, f, a, Xs):
     V = chol_solve(LB, R)
     var = float(s2) - np.einsum("ij,ij->j", R, V)
     return mean, var, ndtr(mean / np.sqrt(1.0 + var))
+
+
+# ---------------------------------------------------------------------------
+# PITC preconditioner (Sec. 3.1): P = Q + bldiag(K - Q) + noise I
+# ---------------------------------------------------------------------------
+class PITC:
+    """Dense FP64 construction of the PITC approximation of K_y (small n): the
+    Nystrom Q = K_XU K_UU^{-1} K_UX off the diagonal blocks, K_y itself on the
+    diagonal blocks (contiguous blocks of b rows in input order, the last one
+    shorter), factored by Cholesky."""
+
+    kind = 5
+
+    def __init__(self, X, ell, s2, noise, idx, b):
+        X = _f64c(X)
+        n = X.shape[0]
+        self.idx = np.ascontiguousarray(idx, dtype=np.int64)
+        U = X[self.idx]
+        KXU = gram(X, U, ell, s2)
+        KUU = gram(U, U, ell, s2)
+        Q = KXU @ chol_solve(cholesky(KUU), np.asfortranarray(KXU.T))
+        K = gram(X, X, ell, s2)
+        P = Q.copy()
+        for r0 in range(0, n, int(b)):
+            r1 = min(n, r0 + int(b))
+            P[r0:r1, r0:r1] = K[r0:r1, r0:r1]
+        P[np.diag_indices(n)] += float(noise)
+        self.P = P
+        self.L = cholesky(P)
+        self.n, self.b = n, int(b)
+
+    def apply(self, R) -> np.ndarray:
+        return chol_solve(self.L, R)

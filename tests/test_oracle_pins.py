@@ -633,3 +633,26 @@ def test_laplace_prediction_one_point_closed_form():
         m, v, _ = oracle.laplace_predict(X, np.ones(2), s2, np.array([y]), r["f"], r["a"], X)
         assert m[0] == pytest.approx(s2 * r["a"][0], rel=1e-13)
         assert v[0] == pytest.approx(s2 / (1 + s2 * W[0]), rel=1e-12)
+
+
+# ------------------------------------------------------------- Sec. 3.1 PITC
+def test_pitc_blocks_limits_and_structure():
+    # diagonal blocks are those of K_y, entries off them are the Nystrom Q;
+    # blocks of one row give FITC, one block of all rows gives K_y
+    p = synthetic.make_problem(90, 3, 14, ell=0.9, noise=0.03)
+    ell, s2 = oracle.split_theta(p.log_theta, 3, True)
+    idx = synthetic.inducing_subset(90, 12, seed=3)
+    Pt = oracle.PITC(p.X, ell, s2, p.noise, idx, 25)  # blocks 25, 25, 25, 15
+    Ky = _lib_gram(p.X, p.X, ell, s2) + p.noise * np.eye(90)
+    KXU = _lib_gram(p.X, p.X[idx], ell, s2)
+    Q = KXU @ np.linalg.solve(_lib_gram(p.X[idx], p.X[idx], ell, s2), KXU.T)
+    for r0 in (0, 25, 50, 75):
+        r1 = min(90, r0 + 25)
+        np.testing.assert_allclose(Pt.P[r0:r1, r0:r1], Ky[r0:r1, r0:r1], atol=1e-12)
+    np.testing.assert_allclose(Pt.P[:25, 25:], Q[:25, 25:], atol=1e-8)
+    np.testing.assert_allclose(Pt.P[75:, :75], Q[75:, :75], atol=1e-8)
+    F = oracle.FITC(p.X, ell, s2, p.noise, idx)
+    np.testing.assert_allclose(oracle.PITC(p.X, ell, s2, p.noise, idx, 1).P, F.P, atol=1e-12)
+    np.testing.assert_allclose(oracle.PITC(p.X, ell, s2, p.noise, idx, 90).P, Ky, atol=1e-12)
+    v = synthetic.rng(4).standard_normal(90)
+    np.testing.assert_allclose(Pt.P @ Pt.apply(v), v, atol=1e-9 * np.abs(v).max())
