@@ -392,7 +392,7 @@ def run_predict(args):
 FIG1_LOG_ELL = (-1.0, -0.5, 0.0, 0.5, 1.0)
 FIG1_LOG_NOISE = (-4.0, -3.0, -2.0, -1.0, 0.0)
 FIG1_SHAPES = {"concrete": (1030, 8), "power": (9568, 4)}
-FIG1_KINDS = ("none", "nystrom", "fitc", "spectral", "block_jacobi")
+FIG1_KINDS = ("none", "nystrom", "fitc", "pitc", "spectral", "block_jacobi")
 
 
 def fig1_problem(shape, seed=0):
@@ -406,8 +406,9 @@ def fig1_problem(shape, seed=0):
 def fig1_cell(kpcg, torch, dev, p, log_ell, log_noise, kind):
     """Iterations of (P)CG on one grid cell (Sec. 4): isotropic RBF with s^2 = 1,
     l = 10^log_ell, noise 10^log_noise, stop at ||r||^2 < n 1e-10, cap 100 000;
-    Nystrom and FITC with m = sqrt(n) inducing points, the random-feature
-    preconditioner with m = sqrt(n) frequencies, block-Jacobi with blocks of sqrt(n)."""
+    Nystrom, FITC and PITC with m = sqrt(n) inducing points (PITC blocks of sqrt(n)
+    rows), the random-feature preconditioner with m = sqrt(n) frequencies,
+    block-Jacobi with blocks of sqrt(n)."""
     m = int(math.ceil(math.sqrt(p.n)))
     lt = np.array([log_ell * math.log(10.0), 0.0])
     opt = kpcg.default_options(precision=kpcg.KPCG_FP64, tol_mode=1, max_iter=100000)
@@ -417,6 +418,8 @@ def fig1_cell(kpcg, torch, dev, p, log_ell, log_noise, kind):
             s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=5))
         elif kind == "fitc":
             s.precond(kpcg.KPCG_PREC_FITC, m, synthetic.inducing_subset(p.n, m, seed=5))
+        elif kind == "pitc":
+            s.precond_pitc(m, synthetic.inducing_subset(p.n, m, seed=5), m)
         elif kind == "spectral":
             s.precond_spectral(synthetic.spectral_draws(m, p.d, seed=5))
         elif kind == "block_jacobi":
@@ -459,7 +462,7 @@ def run_fig1(args):
             "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "isotropic RBF, s^2=1, stop ||r||^2 < n 1e-10, cap 1e5; "
-                                   "Nystrom and FITC m=sqrt(n), random features m=sqrt(n), "
+                                   "Nystrom, FITC, PITC m=sqrt(n) (PITC blocks sqrt(n)), random features m=sqrt(n), "
                                    "block-Jacobi b=sqrt(n); synthetic X of the dataset shapes",
                        "shapes": shapes},
             "grid": out}

@@ -58,8 +58,10 @@ typedef enum {
     KPCG_PREC_BLOCK_JACOBI = 2,  /* P = bldiag(K_y) (Sec. 3.3.1)                  */
     KPCG_PREC_FITC = 3,          /* P = Q + diag(K - Q) + sigma^2 I, Q the Nystrom
                                     approximation K_XU K_UU^-1 K_UX (Sec. 3.1)   */
-    KPCG_PREC_SPECTRAL = 4       /* P = Phi Phi^T + sigma^2 I, random Fourier
+    KPCG_PREC_SPECTRAL = 4,      /* P = Phi Phi^T + sigma^2 I, random Fourier
                                     features (Sec. 3.2); kpcg_precond_spectral   */
+    KPCG_PREC_PITC = 5           /* P = Q + bldiag(K - Q) + sigma^2 I (Sec. 3.1);
+                                    kpcg_precond_pitc                             */
 } kpcg_precond_kind;
 
 typedef enum {
@@ -180,6 +182,18 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
  * m in [1, 2048]; values must be finite.  In the mixed modes it is built for
  * the shifted inner noise, like the other kinds. */
 kpcg_status kpcg_precond_spectral(kpcg_t h, int64_t m, const double* omega);
+
+/* Build the PITC preconditioner of Sec. 3.1 (KPCG_PREC_PITC):
+ * P = Q + bldiag(K - Q) + sigma^2 I, Q = K_XU K_UU^-1 K_UX on the m inducing
+ * points idx (host, sorted, distinct, as for Nystrom), blocks of b contiguous
+ * rows in input order (the last one shorter).  As the paper says, the block
+ * diagonal D = bldiag(K - Q) + sigma^2 I takes the place of sigma^2 I in the
+ * inversion lemma: with D = L_D L_D^T (block Cholesky, FP64) and
+ * K~ = L_D^-1 K_XU, P^-1 = L_D^-T [I - K~ (K_UU + K~^T K~)^-1 K~^T] L_D^-1.
+ * K_UU and the inner matrix use the jitter rule of kpcg_precond; a block of D
+ * that does not factor returns KPCG_ERR_NOT_SPD.  m in [1, min(n, 4096)],
+ * b in [1, 4096].  Set-up costs O(n m^2 + n b m); b = 1 is FITC. */
+kpcg_status kpcg_precond_pitc(kpcg_t h, int64_t m, const int64_t* idx, int64_t b);
 
 /* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
  * matrix-free product of Sec. 2.1.  impl 0: entries and sums in native FP64;

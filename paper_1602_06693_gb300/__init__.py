@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     KPCG_PREC_FITC,
     KPCG_PREC_NONE,
     KPCG_PREC_NYSTROM,
+    KPCG_PREC_PITC,
     KPCG_PREC_SPECTRAL,
     KPCG_TC_IR,
     Batch,

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
 KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI, KPCG_PREC_FITC = 0, 1, 2, 3
-KPCG_PREC_SPECTRAL = 4
+KPCG_PREC_SPECTRAL, KPCG_PREC_PITC = 4, 5
 KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64 = 0, 1, 2, 3, 4
 
 _STATUS = {
@@ -38,6 +38,7 @@ SYMBOLS = (
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
     "kpcg_batch_destroy",
     "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace", "kpcg_laplace_predict",
+    "kpcg_precond_pitc",
 )
 
 _NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
@@ -140,6 +141,7 @@ def lib():
         L.kpcg_set_options.argtypes = [vp, ctypes.POINTER(Options)]
         L.kpcg_precond.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int64)]
         L.kpcg_precond_spectral.argtypes = [vp, i64, pdbl]
+        L.kpcg_precond_pitc.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), i64]
         L.kpcg_laplace.argtypes = [vp, vp, dbl, i32, dbl, vp, vp, ctypes.POINTER(LaplaceInfo)]
         L.kpcg_laplace_predict.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, dbl,
                                            ctypes.POINTER(LaplaceInfo)]
@@ -331,6 +333,13 @@ class Solver:
             idx = np.ascontiguousarray(idx, dtype=np.int64)
             p = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         self._check(lib().kpcg_precond(self._h, int(kind), int(size), p))
+
+    def precond_pitc(self, m, idx, b):
+        """PITC preconditioner (Sec. 3.1): m inducing rows idx, blocks of b rows."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        self._check(lib().kpcg_precond_pitc(self._h, int(m),
+                                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                            int(b)))
 
     def precond_spectral(self, omega):
         """Random-feature preconditioner (Sec. 3.2) from m x d standard-normal draws."""

@@ -314,6 +314,9 @@ static void build_precond(Ctx& h) {
     else if (h.pkind == KPCG_PREC_FITC)
         fitc_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_32(), h.c0_64(), h.s2, nz,
                    h.pidx.data(), h.psize, h.stream);
+    else if (h.pkind == KPCG_PREC_PITC)
+        pitc_setup(h.P, h.xs32.p, h.xs64.p, h.n, h.dp, h.c0_64(), nz, h.pidx.data(), h.psize,
+                   std::min<int64_t>(h.pblock, h.n), h.stream);
     else if (h.pkind == KPCG_PREC_SPECTRAL)
         spectral_setup(h.P, h.xs64.p, h.n, h.dp, h.s2, nz, h.pomega.data(), h.d, h.psize,
                        h.stream);
@@ -963,6 +966,8 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
             h->pidx.clear();
         } else if (kind == KPCG_PREC_SPECTRAL) {
             fail(KPCG_ERR_ARG, "the random-feature preconditioner is built by kpcg_precond_spectral");
+        } else if (kind == KPCG_PREC_PITC) {
+            fail(KPCG_ERR_ARG, "PITC is built by kpcg_precond_pitc");
         } else {
             fail(KPCG_ERR_ARG, "unknown preconditioner kind");
         }
@@ -978,6 +983,35 @@ kpcg_status kpcg_precond(kpcg_t h, int32_t kind, int64_t size, const int64_t* id
                 h->P.reset();
                 throw;
             }
+        }
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_precond_pitc(kpcg_t h, int64_t m, const int64_t* idx, int64_t b) {
+    if (!h) return KPCG_ERR_ARG;
+    KPCG_GUARD(h, {
+        if (m < 1 || m > h->n || m > 4096)
+            fail(KPCG_ERR_ARG, "inducing-point count m must be in [1, min(n, 4096)]");
+        if (b < 1 || b > 4096) fail(KPCG_ERR_ARG, "block size must be in [1, 4096]");
+        if (!idx) fail(KPCG_ERR_ARG, "PITC needs the inducing indices");
+        for (int64_t a = 0; a < m; ++a) {
+            if (idx[a] < 0 || idx[a] >= h->n) fail(KPCG_ERR_ARG, "inducing index out of range");
+            if (a && idx[a] <= idx[a - 1])
+                fail(KPCG_ERR_ARG, "inducing indices must be sorted and distinct");
+        }
+        h->pkind = KPCG_PREC_NONE;
+        h->P.reset();
+        h->pidx.assign(idx, idx + m);
+        h->pkind = KPCG_PREC_PITC;
+        h->psize = m;
+        h->pblock = b;
+        try {
+            kpcg::build_precond(*h);
+        } catch (...) {
+            h->pkind = KPCG_PREC_NONE;
+            h->P.reset();
+            throw;
         }
     });
     return KPCG_OK;

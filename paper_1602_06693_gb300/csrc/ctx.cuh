@@ -91,6 +91,7 @@ struct Ctx {
     int64_t psize = 0;
     std::vector<int64_t> pidx;
     std::vector<double> pomega;  // spectral draws (m x d) of KPCG_PREC_SPECTRAL
+    int64_t pblock = 0;          // block size of KPCG_PREC_PITC
     // warm-start basis (Nystrom-type fit), rebuilt lazily when theta changes
     PrecondState Wb;
     std::vector<int64_t> widx;

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "kpcg_internal.cuh"
@@ -777,6 +778,138 @@ void laplace_precond_setup(PrecondState& P, DevBuf<float2>& kxu0, bool first, co
     P.ready = true;
 }
 
+namespace {
+
+// V[i][a] = (L^{-1} k_i)_a = sum_{b <= a} U[b][a] k_ib, U = L^{-T} of K_UU
+// (row-major); one CTA per row, FP64.
+__global__ void pitc_v_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
+                              const double* __restrict__ U, double* __restrict__ V) {
+    extern __shared__ double sk[];
+    const int64_t i = blockIdx.x;
+    for (int64_t a = threadIdx.x; a < m; a += blockDim.x) {
+        const float2 kv = KXU[i * m + a];
+        sk[a] = (double)kv.x + (double)kv.y;
+    }
+    __syncthreads();
+    for (int64_t a = threadIdx.x; a < m; a += blockDim.x) {
+        double v = 0.0;
+        for (int64_t b = 0; b <= a; ++b) v = fma(U[b * m + a], sk[b], v);
+        V[i * m + a] = v;
+    }
+}
+
+// Block q of D = bldiag(K - Q) + noise I (row-major with its own size bq, the
+// block-Jacobi layout): entry (r, c) = K(x_r, x_c) - v_r . v_c + noise [r = c],
+// FP64, K from direct differences.  16 x 16 output tiles, V staged 32 columns
+// at a time.
+__global__ void __launch_bounds__(256)
+    pitc_fill_kernel(const double* __restrict__ xs, int64_t n, int dp, double c0, double noise,
+                     const double* __restrict__ V, int64_t m, int64_t b, double* __restrict__ A) {
+    __shared__ double Vr[16][33];
+    __shared__ double Vc[16][33];
+    // blockIdx.x = (q * tiles + tile row) * tiles + tile column
+    const int64_t tiles = (b + 15) / 16;
+    const int64_t q = (int64_t)blockIdx.x / (tiles * tiles);
+    const int64_t tt = (int64_t)blockIdx.x - q * tiles * tiles;
+    const int64_t bq = bsize(q, b, n);
+    const int64_t r0 = (tt / tiles) * 16, k0 = (tt % tiles) * 16;
+    if (r0 >= bq || k0 >= bq) return;  // uniform over the CTA
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t base = q * b;
+    double acc = 0.0;
+    for (int64_t a0 = 0; a0 < m; a0 += 32) {
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            const int rr = e >> 5, aa = e & 31;
+            const int64_t a = a0 + aa;
+            Vr[rr][aa] = (r0 + rr < bq && a < m) ? V[(base + r0 + rr) * m + a] : 0.0;
+            Vc[rr][aa] = (k0 + rr < bq && a < m) ? V[(base + k0 + rr) * m + a] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) acc = fma(Vr[ty][u], Vc[tx][u], acc);
+        __syncthreads();
+    }
+    const int64_t r = r0 + ty, c = k0 + tx;
+    if (r < bq && c < bq) {
+        const double* xr = xs + (base + r) * dp;
+        const double* xc = xs + (base + c) * dp;
+        double e = c0;
+        for (int t = 0; t < dp; ++t) {
+            const double d = xr[t] - xc[t];
+            e = fma(-d, d, e);
+        }
+        A[q * b * b + r * bq + c] = exp(e) - acc + (r == c ? noise : 0.0);
+    }
+}
+
+// Y = L_D^{-1} K_XU block by block: Y[i][a] = sum_{j <= i in i's block}
+// U_D[j][i] K_XU[j][a] (U_D = L_D^{-T} per block, row-major), written as exact
+// FP32 pairs.  Threads run along a (coalesced); blockIdx.x is the row i.
+__global__ void pitc_y_kernel(const float2* __restrict__ KXU, int64_t n, int64_t m,
+                              const double* __restrict__ UD, int64_t b,
+                              float2* __restrict__ Y) {
+    const int64_t i = blockIdx.x;
+    const int64_t a = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    const int64_t q = i / b;
+    const int64_t bq = bsize(q, b, n);
+    const int64_t r0 = q * b, ii = i - r0;
+    const double* U = UD + q * b * b;
+    double acc = 0.0;
+    for (int64_t j = 0; j <= ii; ++j) {
+        const float2 kv = KXU[(r0 + j) * m + a];
+        acc = fma(U[j * bq + ii], (double)kv.x + (double)kv.y, acc);
+    }
+    const float hi = (float)acc;
+    Y[i * m + a] = make_float2(hi, (float)(acc - (double)hi));
+}
+
+}  // namespace
+
+void pitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                double c0_64, double noise, const int64_t* idx_host, int64_t m, int64_t b,
+                cudaStream_t st) {
+    P.kind = KPCG_PREC_PITC;
+    P.noise = noise;
+    P.apply_noise = 1.0;
+    P.b = b;
+    nys_gather_kxu(P, xs32, xs64, n, dp, c0_64, idx_host, m, st);
+    // K_UU = L L^T (the jitter rule), V = L^{-1} K_UX, Q = V^T V
+    double* Kuu = P.M0.need((size_t)m * m);
+    kuu_f64(P.us64.p, m, dp, c0_64, 1.0, 0.0, Kuu, st);
+    (void)factor_with_rule(P, Kuu, m, st, "K_UU");
+    double* V = P.tmp64.need((size_t)n * m);
+    const size_t smem = sizeof(double) * (size_t)m;
+    if (smem > 48 * 1024) raise_smem_limit((const void*)pitc_v_kernel, smem);
+    pitc_v_kernel<<<(unsigned)n, 256, smem, st>>>(P.KXU.p, n, m, P.U.p, V);
+    KPCG_LAUNCHED("pitc_v_kernel");
+    // D = bldiag(K - Q) + noise I and its block factors L_D, U_D = L_D^{-T}
+    const int64_t nb = (n + b - 1) / b;
+    double* A = P.dblk.need((size_t)nb * b * b);
+    double* UD = P.dinv.need((size_t)nb * b * b);
+    const int64_t tiles = (b + 15) / 16;
+    pitc_fill_kernel<<<(unsigned)(nb * tiles * tiles), 256, 0, st>>>(xs64, n, dp, c0_64, noise,
+                                                                     V, m, b, A);
+    KPCG_LAUNCHED("pitc_fill_kernel");
+    int* status = P.status.need((size_t)std::max<int64_t>(nb, 1));
+    const int rc = factor_and_invert(A, UD, b, n, nb, status, st);
+    if (rc)
+        fail(KPCG_ERR_NOT_SPD,
+             "PITC diagonal block not positive definite near row " + std::to_string(rc - 1));
+    // K~ = L_D^{-1} K_XU as pairs; it replaces K_XU for the inner matrix and the apply
+    DevBuf<float2> Y;
+    Y.need((size_t)n * m);
+    pitc_y_kernel<<<dim3((unsigned)n, (unsigned)((m + 255) / 256)), 256, 0, st>>>(P.KXU.p, n, m, UD,
+                                                                                  b, Y.p);
+    KPCG_LAUNCHED("pitc_y_kernel");
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    std::swap(P.KXU.p, Y.p);
+    std::swap(P.KXU.count, Y.count);
+    // inner matrix K_UU + K~^T K~ (unit noise) and its factor
+    nys_inner(P, n, m, dp, c0_64, 1.0, st);
+    P.ready = true;
+}
+
 void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, double c0_64,
                         double noise, int64_t b, cudaStream_t st) {
     P.kind = KPCG_PREC_BLOCK_JACOBI;
@@ -927,6 +1060,64 @@ static void fitc_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T*
     KPCG_LAUNCHED("scale_rows_kernel");
 }
 
+namespace {
+
+// One triangular factor of D^{-1} per block and column (one CTA each), U = L^{-T}
+// per block: forward out_i = (L^{-1} in)_i = sum_{j <= i} U[j][i] in_j; backward
+// out_j = (L^{-T} in)_j = sum_{i >= j} U[j][i] in_i.  The block is staged in
+// shared memory first, so out may alias in.
+template <typename T, bool FORWARD>
+__global__ void pitc_tri_kernel(const double* __restrict__ Ub, int64_t n, int64_t b, const T* in,
+                                int64_t ldi, T* out, int64_t ldo) {
+    extern __shared__ double sv[];  // b
+    const int64_t q = blockIdx.x;
+    const int k = blockIdx.y;
+    const int64_t bq = bsize(q, b, n);
+    const int64_t r0 = q * b;
+    const double* U = Ub + q * b * b;
+    for (int64_t i = threadIdx.x; i < bq; i += blockDim.x)
+        sv[i] = (double)in[r0 + i + (int64_t)k * ldi];
+    __syncthreads();
+    if (FORWARD) {
+        for (int64_t i = threadIdx.x; i < bq; i += blockDim.x) {
+            double s = 0.0;
+            for (int64_t j = 0; j <= i; ++j) s = fma(U[j * bq + i], sv[j], s);
+            out[r0 + i + (int64_t)k * ldo] = (T)s;
+        }
+    } else {
+        const int lane = threadIdx.x & 31;
+        const int nw = blockDim.x >> 5;
+        for (int64_t j = threadIdx.x >> 5; j < bq; j += nw) {
+            const double* Uj = U + j * bq;
+            double s = 0.0;
+            for (int64_t i = j + lane; i < bq; i += 32) s = fma(Uj[i], sv[i], s);
+            s = warp_sum(s);
+            if (lane == 0) out[r0 + j + (int64_t)k * ldo] = (T)s;
+        }
+    }
+}
+
+}  // namespace
+
+// PITC: z = L_D^{-T} Nys(L_D^{-1} r) with the unit-noise apply on K~ = L_D^{-1} K_XU
+// (D^{-1} = L_D^{-T} L_D^{-1}; the inversion lemma with D in place of noise I).
+template <typename T>
+static void pitc_apply(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
+                       cudaStream_t st) {
+    const int64_t n = P.n, b = P.b;
+    const int64_t nb = (n + b - 1) / b;
+    T* tmp = fitc_tmp<T>(P, (size_t)n * c);
+    const size_t smem = sizeof(double) * (size_t)b;
+    if (smem > 48 * 1024) fail(KPCG_ERR_ARG, "PITC block too large");
+    pitc_tri_kernel<T, true><<<dim3((unsigned)nb, (unsigned)c), 256, smem, st>>>(P.dinv.p, n, b,
+                                                                               R, ldr, tmp, n);
+    KPCG_LAUNCHED("pitc_tri_kernel");
+    nystrom_apply<T>(P, tmp, n, c, Z, ldz, st);
+    pitc_tri_kernel<T, false><<<dim3((unsigned)nb, (unsigned)c), 256, smem, st>>>(P.dinv.p, n, b,
+                                                                                Z, ldz, Z, ldz);
+    KPCG_LAUNCHED("pitc_tri_kernel");
+}
+
 template <typename T>
 static void apply_any(const PrecondState& P, const T* R, int64_t ldr, int c, T* Z, int64_t ldz,
                       cudaStream_t st) {
@@ -934,6 +1125,8 @@ static void apply_any(const PrecondState& P, const T* R, int64_t ldr, int c, T* 
         nystrom_apply<T>(P, R, ldr, c, Z, ldz, st);
     else if (P.kind == KPCG_PREC_FITC && P.ready)
         fitc_apply<T>(P, R, ldr, c, Z, ldz, st);
+    else if (P.kind == KPCG_PREC_PITC && P.ready)
+        pitc_apply<T>(P, R, ldr, c, Z, ldz, st);
     else if (P.kind == KPCG_PREC_BLOCK_JACOBI && P.ready)
         bj_apply<T>(P, R, ldr, c, Z, ldz, st);
     else

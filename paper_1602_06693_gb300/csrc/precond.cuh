@@ -28,6 +28,7 @@ struct PrecondState {
     DevBuf<double> dscale;     // FITC: D^{-1/2}, D = diag(K - Q) + sigma^2
     DevBuf<double> tmp64;      // FITC: scaled right-hand sides
     DevBuf<float> tmp32;
+    DevBuf<double> dblk, dinv;  // PITC: block factors L_D of D and U_D = L_D^{-T}
 
     void reset() {
         kind = KPCG_PREC_NONE;
@@ -48,6 +49,8 @@ struct PrecondState {
         dscale.release();
         tmp64.release();
         tmp32.release();
+        dblk.release();
+        dinv.release();
     }
 };
 
@@ -87,6 +90,14 @@ void block_jacobi_setup(PrecondState& P, const double* xs64, int64_t n, int dp, 
 void fitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
                 float c0_32, double c0_64, double s2, double noise, const int64_t* idx_host,
                 int64_t m, cudaStream_t st);
+// PITC (Sec. 3.1): P = Q + bldiag(K - Q) + sigma^2 I with contiguous blocks of b
+// rows.  With D = bldiag(K - Q) + sigma^2 I = L_D L_D^T (block Cholesky) and
+// K~ = L_D^{-1} K_XU the inversion lemma gives
+// P^{-1} = L_D^{-T} [I - K~ (K_UU + K~^T K~)^{-1} K~^T] L_D^{-1}: the Nystrom apply
+// with unit noise between two block-triangular factors.
+void pitc_setup(PrecondState& P, const float* xs32, const double* xs64, int64_t n, int dp,
+                double c0_64, double noise, const int64_t* idx_host, int64_t m, int64_t b,
+                cudaStream_t st);
 
 // ------------------------------------------- batched Nystrom apply
 // Problems laid out column by column (problem p owns columns p*c .. p*c+c-1

@@ -274,3 +274,50 @@ def test_spectral_single_frequency(kpcg):
         Z = _np(s.precond_apply(_cm(R)))
     for k in range(2):
         assert _rel(Z[:, k], S.apply(R[:, k])) <= 1e-9
+
+
+# -------------------------------------------------------------- PITC (Sec. 3.1)
+@pytest.mark.parametrize("n,d,m,b", [(1000, 4, 50, 64), (700, 6, 30, 1), (513, 3, 40, 513)])
+def test_pitc_apply_matches_oracle(kpcg, n, d, m, b):
+    # 15 blocks of 64 and a ragged one of 40; b = 1 (FITC); one block (K_y itself)
+    p = synthetic.make_problem(n, d, seed=n + b, ell=1.1, noise=0.03)
+    ell, s2 = oracle.split_theta(p.log_theta, d, True)
+    idx = synthetic.inducing_subset(n, m, seed=8)
+    Pt = oracle.PITC(p.X, ell, s2, p.noise, idx, b)
+    R = synthetic.rng(9).standard_normal((n, 3))
+    with _solver(kpcg, p, precision=kpcg.KPCG_FP64) as s:
+        s.precond_pitc(m, idx, b)
+        Z = _np(s.precond_apply(_cm(R)))
+    for k in range(3):
+        assert _rel(Z[:, k], Pt.apply(R[:, k])) <= 1e-9, k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_pitc_solve_matches_oracle(kpcg, precision):
+    p = synthetic.make_problem(1100, 5, seed=71, ell="loguniform", noise=0.01)
+    ell, s2 = oracle.split_theta(p.log_theta, 5, True)
+    idx = synthetic.inducing_subset(1100, 60, seed=10)
+    Pt = oracle.PITC(p.X, ell, s2, p.noise, idx, 100)
+    prec = kpcg.KPCG_FP64 if precision == "fp64" else kpcg.KPCG_DF64
+    with _solver(kpcg, p, precision=prec) as s:
+        s.precond_pitc(60, idx, 100)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-10)
+    assert st == 0
+    Ky = oracle.dense_ky(p.X, ell, s2, p.noise)
+    ref_tol = 1e-10 if precision == "fp64" else 0.5e-10
+    _, it_ref = oracle.pcg_dense(Ky, p.y, Pt.apply, tol=ref_tol)
+    assert _rel(_np(x), oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]) <= 1e-7
+    assert abs(int(it[0]) - it_ref) <= max(2, 0.05 * it_ref), (int(it[0]), it_ref)
+
+
+def test_pitc_in_the_mixed_solver_and_errors(kpcg):
+    p = synthetic.make_problem(2000, 6, seed=73, noise=0.01)
+    idx = synthetic.inducing_subset(2000, 100, seed=11)
+    with _solver(kpcg, p, precision=kpcg.KPCG_TC_IR, inner_shift=0.25, inner_tol=0.1) as s:
+        s.precond_pitc(100, idx, 45)
+        x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
+        assert st == 0 and info.max_rel_res <= 1e-8
+        with pytest.raises(kpcg.KpcgError):
+            s.precond(kpcg.KPCG_PREC_PITC, 100, idx)
+        with pytest.raises(kpcg.KpcgError):
+            s.precond_pitc(100, idx, 0)
