@@ -7,6 +7,10 @@ FP64, OpenMP over rows); this module loads it with ctypes and assembles the
 gradient of the log marginal likelihood (Eq. 2 with the stochastic trace of
 Sec. 2.1) from its products.
 
+It also restates, densely in NumPy for small n, the FITC, PITC and random-feature
+preconditioners (Sec. 3.1, 3.2), the predictive mean and variance (Sec. 2.1), and the
+probit Laplace approximation with its predictions (Sec. 2.2, Appendix B).
+
 Every function cites the passage of the paper it restates.  Parameters are
 taken in log space: ``log_theta = [log l_1..log l_d, log s^2]`` (ARD) or
 ``[log l, log s^2]`` (isotropic), noise sigma^2 separate.  Gradients are
