@@ -470,13 +470,14 @@ def run_fig1(args):
         print(json.dumps(line))
 
 
-LAPLACE_M = 512
+LAPLACE_M, LAPLACE_INNER_TOL = 128, 1e-4
 LAPLACE_WORKLOAD = ("probit GP classification, EEG shape n=14979 d=14 (X~N(0,I) standardized, "
                     "y=sign(sum sin x) with 5% flipped), ARD l=sqrt(14), s^2=4; Laplace mode by "
                     "Newton from f=0 (stop |dPsi| <= 1e-12 |Psi|), each B = I + W^1/2 K W^1/2 "
-                    "solve by PCG to 1e-10 from the previous step's z with the Nystrom form of B (m=512, "
-                    "rebuilt when W^1/2 drifts by >10%), "
-                    "double-float K.V")
+                    "solve to 1e-10 from the previous step's z, preconditioned by the Nystrom "
+                    "form of B (default m=128, rebuilt when W^1/2 drifts by >10%); default B-solve: "
+                    "flexible CG around tensor-core inner PCG (inner_tol 1e-4); double-float K.V "
+                    "for b, a, the outer directions and the certified residuals")
 
 
 def laplace_oracle_sample(n_sample=2500):
@@ -508,10 +509,15 @@ def run_laplace(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     p = synthetic.eeg_shape(seed=rank)
-    idx = synthetic.inducing_subset(p.n, LAPLACE_M, seed=12 + rank)
-    opt = kpcg.default_options(precision=kpcg.KPCG_DF64)
+    lm = args.laplace_m
+    idx = synthetic.inducing_subset(p.n, lm, seed=12 + rank) if lm > 0 else None
+    prec = {"auto": kpcg.KPCG_TC_IR, "df64": kpcg.KPCG_DF64, "fp32_ir": kpcg.KPCG_FP32_IR,
+            "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+    opt = kpcg.default_options(precision=prec)
+    opt.inner_tol = args.inner_tol if args.inner_tol is not None else LAPLACE_INNER_TOL
     s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, 1.0, ard=True, options=opt)
-    s.precond(kpcg.KPCG_PREC_NYSTROM, LAPLACE_M, idx)
+    if lm > 0:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, lm, idx)
     y = torch.from_numpy(p.y).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -573,20 +579,22 @@ def run_laplace(args):
         torch.cuda.synchronize(dev)
         e2e_t.append(time.perf_counter() - t0)
     # predictions at 1024 test inputs from the mode (mean, variance, probability)
-    Xs = torch.from_numpy(synthetic.rng(200 + rank).standard_normal((1024, p.d))
-                          .astype(np.float32)).to(dev)
-    s.laplace_predict(y, f, a, Xs)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    _, pv, pp, pinfo = s.laplace_predict(y, f, a, Xs)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    pred = {"test_points": 1024, "time_s": e0.elapsed_time(e1) / 1e3,
-            "cg_iters_total": pinfo.cg_iters_total, "max_rel_res": pinfo.max_rel_res,
-            "var_range": [float(pv.min()), float(pv.max())],
-            "prob_range": [float(pp.min()), float(pp.max())]}
+    pred = None
+    if not args.no_predict:
+        Xs = torch.from_numpy(synthetic.rng(200 + rank).standard_normal((1024, p.d))
+                              .astype(np.float32)).to(dev)
+        s.laplace_predict(y, f, a, Xs)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, pv, pp, pinfo = s.laplace_predict(y, f, a, Xs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pred = {"test_points": 1024, "time_s": e0.elapsed_time(e1) / 1e3,
+                "cg_iters_total": pinfo.cg_iters_total, "max_rel_res": pinfo.max_rel_res,
+                "var_range": [float(pv.min()), float(pv.max())],
+                "prob_range": [float(pp.min()), float(pp.max())]}
     extra = {}
     if rank == 0 and world == 1 and not args.skip_baselines:
         try:
@@ -598,8 +606,12 @@ def run_laplace(args):
         "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": LAPLACE_WORKLOAD, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": {"workload": LAPLACE_WORKLOAD, "m_b": lm, "inner_tol": opt.inner_tol,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "b_solves": ("double-float PCG" if prec in (kpcg.KPCG_DF64, kpcg.KPCG_FP64)
+                                else "flexible CG around FP32/tensor-core inner PCG, "
+                                     "double-float outer")},
         "laplace": {"status": st, "newton_steps": info.newton_steps,
                     "cg_iters_total": info.cg_iters_total, "psi": info.psi,
                     "precond_builds": info.precond_builds,
@@ -789,6 +801,10 @@ def main():
                     help="batch64: inducing points m_p = min(m_max, max(64, n_p / m_div))")
     ap.add_argument("--batch-m-div", type=int, default=4)
     ap.add_argument("--fig1-power", action="store_true", help="fig1: add the Power-plant shape")
+    ap.add_argument("--laplace-m", type=int, default=LAPLACE_M,
+                    help="laplace15k: inducing points of the preconditioner of B (0: none)")
+    ap.add_argument("--no-predict", action="store_true",
+                    help="laplace15k: skip the predictions (a short target for profilers)")
     ap.add_argument("--traj-steps", type=int, default=24, help="warm131k: trajectory length")
     ap.add_argument("--traj-train", type=int, default=12, help="warm131k: training steps")
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],

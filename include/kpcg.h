@@ -268,8 +268,13 @@ kpcg_status kpcg_predict(kpcg_t h, const float* Xs, int64_t ns, const double* al
  * Psi(f) = log p(y|f) - 1/2 a^T f changes by at most newton_tol*max(1,|Psi|)
  * (the paper only says "until convergence").
  *   K: the handle's kernel (amplitude s^2, lengthscales); sigma^2 is unused.
- *   Products with K: the double-float kernel (KPCG_DF64's), whatever the
- *   handle's precision; the per-point terms are FP64.
+ *   Products with K: the double-float kernel (KPCG_DF64's) for b, a and every
+ *   certified residual; the per-point terms are FP64.  With the handle's
+ *   precision KPCG_TC_IR or KPCG_FP32_IR each B-solve is the flexible-CG
+ *   mixed solve of kpcg_solve (inner PCG on B in FP32 with the tensor-core or
+ *   FP32 K.V, to opt.inner_tol; outer products and residuals double-float):
+ *   B >= I, so reduced-precision products barely perturb it.  Otherwise PCG
+ *   runs on the double-float B throughout.
  *   Preconditioner of B: with a Nystrom request on the handle (kpcg_precond,
  *   KPCG_PREC_NYSTROM) P_B = I + W^1/2 K_XU K_UU^-1 K_UX W^1/2 on the same
  *   inducing points, built at the first Newton step and rebuilt when W^1/2 has

@@ -122,6 +122,7 @@ struct Ctx {
     DevBuf<double> lap;
     CgBufs<double> lcg;
     DevBuf<double> lpw, lpv;  // Laplace predictions: blocks of right-hand sides, variances
+    DevBuf<float> lpw32;      // Laplace mixed-precision B-solves: FP32 W^1/2 and scratch
     Profiler prof;
     // tensor-core operands (bf16 bits, pre-swizzled), rebuilt when theta changes
     int theta_version = 0, tc_version = -1, tc_kch = 0;

@@ -50,10 +50,10 @@ __global__ void lap_terms_kernel(const double* __restrict__ y, const double* __r
     }
 }
 
-// dst = s * src (element-wise, FP64), c columns.
-__global__ void lap_scale_kernel(double* __restrict__ dst, int64_t ldd,
-                                 const double* __restrict__ src, int64_t lds,
-                                 const double* __restrict__ s, int64_t n) {
+// dst = s * src (element-wise in T), c columns.
+template <typename T>
+__global__ void lap_scale_kernel(T* __restrict__ dst, int64_t ldd, const T* __restrict__ src,
+                                 int64_t lds, const T* __restrict__ s, int64_t n) {
     const int k = blockIdx.y;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -61,13 +61,21 @@ __global__ void lap_scale_kernel(double* __restrict__ dst, int64_t ldd,
 }
 
 // out = p + s * u (the last step of the B product), c columns.
-__global__ void lap_bfinish_kernel(double* out, int64_t ldo, const double* __restrict__ p,
-                                   int64_t ldp, const double* u, int64_t ldu,
-                                   const double* __restrict__ s, int64_t n) {
+template <typename T>
+__global__ void lap_bfinish_kernel(T* out, int64_t ldo, const T* __restrict__ p, int64_t ldp,
+                                   const T* u, int64_t ldu, const T* __restrict__ s, int64_t n) {
     const int k = blockIdx.y;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i + k * ldo] = fma(s[i], u[i + k * ldu], p[i + k * ldp]);
+}
+
+// s32 = (float) s
+__global__ void lap_to_f32_kernel(float* __restrict__ d, const double* __restrict__ s,
+                                  int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = (float)s[i];
 }
 
 // r = v - w, c columns of leading dimension ld
@@ -170,10 +178,10 @@ VecOp make_bop(Ctx* hp, const double* sW, double* u, double* w) {
     return [hp, sW, u, w](const double* P, int64_t ldp, int cc, double* Q, int64_t ldq) {
         Ctx& H = *hp;
         const dim3 gg(lap_grid(H.n), (unsigned)cc);
-        lap_scale_kernel<<<gg, 256, 0, H.stream>>>(w, H.ld, P, ldp, sW, H.n);
+        lap_scale_kernel<double><<<gg, 256, 0, H.stream>>>(w, H.ld, P, ldp, sW, H.n);
         KPCG_LAUNCHED("lap_scale_kernel");
         kv_df(H, w, H.ld, cc, nullptr, 0, u, H.ld, 0.0);
-        lap_bfinish_kernel<<<gg, 256, 0, H.stream>>>(Q, ldq, P, ldp, u, H.ld, sW, H.n);
+        lap_bfinish_kernel<double><<<gg, 256, 0, H.stream>>>(Q, ldq, P, ldp, u, H.ld, sW, H.n);
         KPCG_LAUNCHED("lap_bfinish_kernel");
     };
 }
@@ -227,6 +235,99 @@ double bsolve(Ctx& c, const VecOp& mvB, const VecOp& pcB, const double* R, int n
         }
         if (worst <= tol) break;
     }
+    return worst;
+}
+
+// Scratch of the mixed-precision B-solve: FP32 W^1/2 and two FP32 blocks.
+struct LapMixed {
+    const float* sW32;
+    float *w32, *u32;
+};
+
+// The B operators for the flexible-CG solve of fcg_solve: inner FP32 products
+// B v = v + sW (K (sW v)) with the tensor-core (tc) or FP32 K.V and the FP32
+// apply of P_B; outer products and every residual with the double-float B
+// product (B >= I, so a residual of FP64 class certifies it).  r is scratch.
+MixedOps lap_mixed_ops(Ctx* hp, const VecOp& mvB, const LapMixed& m, bool tc, bool pre,
+                       double* r) {
+    MixedOps o;
+    o.inner_mv = [hp, m, tc](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+        Ctx& H = *hp;
+        const dim3 gg(lap_grid(H.n), (unsigned)cc);
+        lap_scale_kernel<float><<<gg, 256, 0, H.stream>>>(m.w32, H.ld, V, ldv, m.sW32, H.n);
+        KPCG_LAUNCHED("lap_scale_kernel");
+        if (tc)
+            kv_tc_apply(H, m.w32, H.ld, cc, m.u32, H.ld, 0.f);
+        else
+            kv_f32(H.xs32.p, H.n, H.dp, H.c0_32(), 0.f, m.w32, H.ld, cc, m.u32, H.ld, H.kvws,
+                   H.stream);
+        lap_bfinish_kernel<float><<<gg, 256, 0, H.stream>>>(O, ldo, V, ldv, m.u32, H.ld, m.sW32,
+                                                            H.n);
+        KPCG_LAUNCHED("lap_bfinish_kernel");
+    };
+    o.inner_pc = [hp, pre](const float* R, int64_t ldr, int cc, float* Z, int64_t ldz) {
+        Ctx& H = *hp;
+        if (pre)
+            precond_apply_f32(H.LP, R, ldr, cc, Z, ldz, H.stream);
+        else
+            copy_cols<float>(Z, ldz, R, ldr, H.n, cc, H.stream);
+    };
+    o.outer_mv = mvB;
+    o.residual = [hp, mvB, r](const double* B, int64_t ldb, int cc, const double* X, int64_t ldx,
+                              double* R, std::vector<double>& rr, std::vector<double>& bb,
+                              bool) {
+        Ctx& H = *hp;
+        if (ldb != H.ld) fail(KPCG_ERR_ARG, "B-solve right-hand sides must have leading dim ld");
+        mvB(X, ldx, cc, r, H.ld);
+        lap_sub_kernel<<<dim3(lap_grid(H.n), (unsigned)cc), 256, 0, H.stream>>>(R, B, r, H.n,
+                                                                                 H.ld);
+        KPCG_LAUNCHED("lap_sub_kernel");
+        const int nblk = dot_blocks(H.n);
+        double* pp = H.partial.need((size_t)nblk * cc * 2);
+        dot_cols<double>(R, H.ld, R, H.ld, H.n, cc, pp, nblk, H.stream);
+        dot_cols<double>(B, ldb, B, ldb, H.n, cc, pp + (size_t)nblk * cc, nblk, H.stream);
+        std::vector<double> hq((size_t)nblk * cc * 2);
+        KPCG_CUDA(cudaMemcpyAsync(hq.data(), pp, sizeof(double) * hq.size(),
+                                  cudaMemcpyDeviceToHost, H.stream));
+        KPCG_CUDA(cudaStreamSynchronize(H.stream));
+        rr.assign((size_t)cc, 0.0);
+        bb.assign((size_t)cc, 0.0);
+        for (int k = 0; k < cc; ++k)
+            for (int q = 0; q < nblk; ++q) {
+                rr[(size_t)k] += hq[(size_t)k * nblk + q];
+                bb[(size_t)k] += hq[(size_t)(cc + k) * nblk + q];
+            }
+    };
+    if (tc) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
+    return o;
+}
+
+// B Z = R (nb columns, leading dimension ld): with a mixed operator set, the
+// flexible-CG solve (from Z if z_given; tol_mode forced to the relative test),
+// else bsolve.  Returns the worst certified relative residual.
+double solve_b(Ctx& c, const VecOp& mvB, const VecOp& pcB, const MixedOps* mixed,
+               const double* R, int nb, double* Z, double tol, double* t, double* r,
+               int& cg_total, bool z_given) {
+    if (!mixed) return bsolve(c, mvB, pcB, R, nb, Z, tol, t, r, cg_total, z_given);
+    std::vector<int> iters_col((size_t)nb, 0);
+    int iters_total = 0, steps = 0;
+    std::vector<double> rr, bb;
+    const int saved_mode = c.opt.tol_mode;
+    c.opt.tol_mode = 0;
+    kpcg_status stt;
+    try {
+        stt = fcg_solve(c, *mixed, R, c.ld, nb, tol, z_given ? Z : nullptr, Z, c.ld, iters_col,
+                        iters_total, steps, rr, bb);
+    } catch (...) {
+        c.opt.tol_mode = saved_mode;
+        throw;
+    }
+    c.opt.tol_mode = saved_mode;
+    cg_total += iters_total;
+    if (stt == KPCG_ERR_BREAKDOWN) fail(KPCG_ERR_BREAKDOWN, "breakdown in a B-solve");
+    double worst = 0.0;
+    for (int k = 0; k < nb && k < (int)rr.size(); ++k)
+        if (bb[(size_t)k] > 0.0) worst = std::max(worst, std::sqrt(rr[(size_t)k] / bb[(size_t)k]));
     return worst;
 }
 
@@ -284,6 +385,16 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         const bool pre = c.pkind == KPCG_PREC_NYSTROM;
         const VecOp mvB = make_bop(&c, sW, u, w);
         const VecOp pcB = make_bpc(&c, pre);
+        // mixed precision (KPCG_TC_IR / KPCG_FP32_IR): FP32 W^1/2 and scratch
+        const bool tc = c.opt.precision == KPCG_TC_IR;
+        const bool use_mixed = tc || c.opt.precision == KPCG_FP32_IR;
+        if (tc && !kv_tc_supported(c.dp))
+            fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+        float* f32 = c.lpw32.need((size_t)ld * 3);
+        const LapMixed lm{f32, f32 + ld, f32 + 2 * ld};
+        MixedOps mops;
+        if (use_mixed) mops = lap_mixed_ops(&c, mvB, lm, tc, pre, t);
+        const MixedOps* mixed = use_mixed ? &mops : nullptr;
 
         double psi_old = lap_psi(c, y, f, a, part);  // n log(1/2) at f = 0
         double psi = psi_old, setup_ms = 0.0, worst = 0.0;
@@ -319,10 +430,15 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
             }
             // v = sW (K b)
             kv_df(c, b, ld, 1, nullptr, 0, u, ld, 0.0);
-            lap_scale_kernel<<<dim3(g, 1), 256, 0, st>>>(v, ld, u, ld, sW, n);
+            lap_scale_kernel<double><<<dim3(g, 1), 256, 0, st>>>(v, ld, u, ld, sW, n);
             KPCG_LAUNCHED("lap_scale_kernel");
             // from the previous step's z: B and v change little near the mode
-            const double rel = bsolve(c, mvB, pcB, v, 1, z, cg_tol, t, r, cg_total, steps > 1);
+            if (use_mixed) {
+                lap_to_f32_kernel<<<g, 256, 0, st>>>(f32, sW, n);
+                KPCG_LAUNCHED("lap_to_f32_kernel");
+            }
+            const double rel =
+                solve_b(c, mvB, pcB, mixed, v, 1, z, cg_tol, t, r, cg_total, steps > 1);
             worst = std::max(worst, rel);
             if (rel > cg_tol) solved = false;
             // a = b - sW z;  f = K a
@@ -419,15 +535,30 @@ kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, con
             }
             const VecOp mvB = make_bop(&c, sW, u, w);
             const VecOp pcB = make_bpc(&c, pre);
+            const bool tc = c.opt.precision == KPCG_TC_IR;
+            const bool use_mixed = tc || c.opt.precision == KPCG_FP32_IR;
+            if (tc && !kv_tc_supported(c.dp))
+                fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+            float* f32 = c.lpw32.need((size_t)ld * (1 + 2 * PB));
+            const LapMixed lm{f32, f32 + ld, f32 + (1 + PB) * ld};
+            MixedOps mops;
+            if (use_mixed) {
+                lap_to_f32_kernel<<<g, 256, 0, st>>>(f32, sW, n);
+                KPCG_LAUNCHED("lap_to_f32_kernel");
+                mops = lap_mixed_ops(&c, mvB, lm, tc, pre, t);
+            }
+            const MixedOps* mixed = use_mixed ? &mops : nullptr;
             const int nblk = dot_blocks(n);
             std::vector<double> hv((size_t)ns);
             for (int64_t b0 = 0; b0 < ns; b0 += PB) {
                 const int nb = (int)std::min<int64_t>(PB, ns - b0);
                 // R = W^1/2 k_*, Z = B^{-1} R, v_* = s^2 - R^T Z
                 predict_kblock(c, xt + b0 * c.dp, nb, Kb, ld);
-                lap_scale_kernel<<<dim3(g, (unsigned)nb), 256, 0, st>>>(R, ld, Kb, ld, sW, n);
+                lap_scale_kernel<double><<<dim3(g, (unsigned)nb), 256, 0, st>>>(R, ld, Kb, ld, sW,
+                                                                                n);
                 KPCG_LAUNCHED("lap_scale_kernel");
-                const double rel = bsolve(c, mvB, pcB, R, nb, Z, cg_tol, t, r, cg_total);
+                const double rel =
+                    solve_b(c, mvB, pcB, mixed, R, nb, Z, cg_tol, t, r, cg_total, false);
                 worst = std::max(worst, rel);
                 if (rel > cg_tol) solved = false;
                 double* pp = c.partial.need((size_t)nblk * nb);

@@ -128,10 +128,11 @@ def test_spectral_argument_errors(kpcg):
 
 
 # ----------------------------------------------- Laplace (Sec. 2.2, Appendix B)
-def _laplace_parity(kpcg, p, m):
+def _laplace_parity(kpcg, p, m, precision=None):
     ell, s2 = oracle.split_theta(p.log_theta, p.d, True)
     ref = oracle.laplace_probit(p.X, ell, s2, p.y, tol=1e-12)
-    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+    prec = kpcg.KPCG_DF64 if precision is None else precision
+    with _solver(kpcg, p, precision=prec) as s:
         if m:
             s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=11))
         f, a, info, st = s.laplace(_cm(p.y), newton_tol=1e-12, cg_tol=1e-10)
@@ -151,6 +152,16 @@ def test_laplace_matches_oracle_with_and_without_preconditioner(kpcg):
     # the Nystrom form of B needs fewer CG iterations over the Newton loop
     assert nys.cg_iters_total < plain.cg_iters_total, (nys.cg_iters_total,
                                                         plain.cg_iters_total)
+
+
+@pytest.mark.parametrize("mode", ["tc_ir", "fp32_ir"])
+@pytest.mark.parametrize("m", [0, 120])
+def test_laplace_mixed_precision_b_solves_match_oracle(kpcg, mode, m):
+    # the B-solves as flexible CG around FP32 / tensor-core inner solves: same
+    # mode, same Newton steps, certified residuals at 1e-10
+    p = synthetic.classification_problem(1500, 6, seed=31, s2=4.0, ell=1.5)
+    prec = kpcg.KPCG_TC_IR if mode == "tc_ir" else kpcg.KPCG_FP32_IR
+    _laplace_parity(kpcg, p, m, precision=prec)
 
 
 def test_laplace_credit_shape_matches_oracle(kpcg):
@@ -195,8 +206,8 @@ def test_laplace_argument_errors(kpcg):
 
 
 # ---------------------------------------- probit predictions (Sec. 2.2, App. B)
-@pytest.mark.parametrize("m", [0, 90])
-def test_laplace_predictions_match_oracle(kpcg, m):
+@pytest.mark.parametrize("m,mode", [(0, "df64"), (90, "df64"), (90, "tc_ir")])
+def test_laplace_predictions_match_oracle(kpcg, m, mode):
     # mean from a (FP64 on both sides), variance through one B-solve per test
     # point (blocks of 16; 37 points leave a ragged block of 5), probability
     p = synthetic.classification_problem(1200, 5, seed=41, s2=3.0, ell=1.4)
@@ -206,7 +217,8 @@ def test_laplace_predictions_match_oracle(kpcg, m):
     Xs[3] = p.X[10]  # a training input
     Xs[4] = 40.0     # far from the data: the prior
     mr, vr, pr = oracle.laplace_predict(p.X, ell, s2, p.y, ref["f"], ref["a"], Xs)
-    with _solver(kpcg, p, precision=kpcg.KPCG_DF64) as s:
+    prec = kpcg.KPCG_TC_IR if mode == "tc_ir" else kpcg.KPCG_DF64
+    with _solver(kpcg, p, precision=prec) as s:
         if m:
             s.precond(kpcg.KPCG_PREC_NYSTROM, m, synthetic.inducing_subset(p.n, m, seed=13))
         y = _cm(p.y)
