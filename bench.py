@@ -565,6 +565,30 @@ def run_laplace(args):
                             "(unit counts and max clock)"),
             "avg_ms": kv_ms, "ops_per_call": ops,
             "timing": f"{reps} back-to-back products, CUDA events on the launching stream"}
+    # the inner product of the mixed B-solves: tensor-core K.V of one column
+    roof_inner = None
+    if prec == kpcg.KPCG_TC_IR:
+        v32 = v.float()
+        for _ in range(3):
+            s.matvec_f32(v32, impl=1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            s.matvec_f32(v32, impl=1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tc_ms = e0.elapsed_time(e1) / reps
+        # the exponent comes from the tensor cores; each of the n^2 entries then
+        # takes one ex2 on the special-function units (16 per SM per clock)
+        tc_ops = float(p.n) * p.n
+        mufu = 152 * 16 * sm_max * 1e6 / 1e12
+        roof_inner = {"bound": "alu", "kernel": "kv_tc_kernel (tcgen05, 1 column)",
+                      "achieved": tc_ops / (tc_ms / 1e3) / 1e12, "peak": mufu, "unit": "Tex2/s",
+                      "frac": tc_ops / (tc_ms / 1e3) / 1e12 / mufu, "avg_ms": tc_ms,
+                      "ops_per_call": tc_ops, "timing": roof["timing"],
+                      "peak_source": (f"ex2 issue: 152 SMs x 16 per clock x {sm_max:.0f} MHz "
+                                      "(unit counts and max clock)")}
     # end to end: labels from pinned host memory, f back to the host
     yh = torch.from_numpy(p.y).pin_memory()
     fh = torch.empty(p.n, dtype=torch.float64).pin_memory()
@@ -619,7 +643,7 @@ def run_laplace(args):
                     "step_times_s": times,
                     "train_accuracy": float((torch.sign(f) == y).double().mean()),
                     "predict": pred},
-        "roofline": roof, "clocks": clocks,
+        "roofline": roof, "roofline_inner": roof_inner, "clocks": clocks,
         "e2e": {"value": statistics.mean(e2e_t), "unit": "s",
                 "h2d_bytes_per_step": int(yh.numel() * 8),
                 "d2h_bytes_per_step": int(fh.numel() * 8)},
