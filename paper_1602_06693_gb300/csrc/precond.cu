@@ -585,7 +585,13 @@ static void nys_syrk_factor(PrecondState& P, int64_t n, int64_t m, cudaStream_t 
                             const char* what) {
     double* M0 = P.M0.p;
     const int64_t tiles = (m + ST - 1) / ST;
-    int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 4095) / 4096));
+    // row splits: one per 4096 rows (at most 64), and enough for about four
+    // CTAs per SM over the lower tiles when m is small, with >= 4 SR rows each
+    const int64_t lower = tiles * (tiles + 1) / 2;
+    int64_t ns = std::max<int64_t>(std::min<int64_t>(64, (n + 4095) / 4096),
+                                   (152 * 4 + lower - 1) / lower);
+    ns = std::min<int64_t>(ns, std::max<int64_t>(1, n / (4 * SR)));
+    int nsplit = (int)std::max<int64_t>(1, ns);
     const int64_t rps = ((n + nsplit - 1) / nsplit + SR - 1) / SR * SR;
     nsplit = (int)((n + rps - 1) / rps);
     double* part = P.scratch.need((size_t)nsplit * m * m);
