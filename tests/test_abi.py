@@ -79,3 +79,35 @@ def test_oracle_and_library_share_no_code():
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f == "__init__.py", f
     otxt = open(os.path.join(ROOT, "oracle", "kpcg_oracle.c")).read()
     assert "kpcg.h" not in otxt and "csrc" not in otxt
+
+
+def test_null_handle_is_an_argument_error(built):
+    # every handle call checks its handle before touching the device
+    import ctypes
+    import paper_1602_06693_gb300 as kpcg
+    L = kpcg.lib()
+    nul = ctypes.c_void_p()
+    assert L.kpcg_precond_spectral(nul, 4, None) == 1
+    assert L.kpcg_precond_pitc(nul, 4, None, 8) == 1
+    assert L.kpcg_laplace(nul, None, 1e-12, 10, 1e-10, None, None, None) == 1
+    assert L.kpcg_laplace_predict(nul, None, None, None, None, 3, None, None, None, 1e-10,
+                                  None) == 1
+    assert kpcg.KPCG_PREC_SPECTRAL == 4 and kpcg.KPCG_PREC_PITC == 5
+    assert ctypes.sizeof(kpcg.LaplaceInfo) == 4 + 4 + 8 * 4 + 4 + 4
+
+
+def test_classification_and_spectral_inputs():
+    # seeded, +-1 labels of both signs, standardized columns, standard-normal draws
+    import numpy as np
+    import synthetic
+    p = synthetic.classification_problem(500, 6, seed=3)
+    assert p.X.dtype == np.float32 and p.X.shape == (500, 6) and p.ard
+    assert set(np.unique(p.y)) == {-1.0, 1.0} and 0.3 < (p.y > 0).mean() < 0.7
+    np.testing.assert_allclose(p.X.mean(axis=0), 0.0, atol=1e-6)
+    q = synthetic.classification_problem(500, 6, seed=3)
+    assert np.array_equal(p.X, q.X) and np.array_equal(p.y, q.y)
+    om = synthetic.spectral_draws(2000, 3, seed=1)
+    assert om.shape == (2000, 3) and om.flags.c_contiguous
+    assert abs(om.mean()) < 0.05 and abs(om.std() - 1.0) < 0.05
+    e = synthetic.eeg_shape()
+    assert e.X.shape == (14979, 14)
