@@ -5,10 +5,13 @@
  *
  * The library solves (K(X,X|theta) + sigma^2 I) alpha = B for a block of
  * right-hand sides (Sec. 2.1, Algorithm 1) with the RBF/ARD kernel of Eq. 1,
- * preconditioned by the Nystrom (Sec. 3.1) or block-Jacobi (Sec. 3.3.1)
- * approximation, and estimates the gradient of the log marginal likelihood
- * (Eq. 2) with Rademacher probes (Sec. 2.1).  K is never stored: its entries
- * are rebuilt from X inside every product.
+ * preconditioned by the Nystrom, FITC or PITC (Sec. 3.1), random-feature
+ * (Sec. 3.2) or block-Jacobi (Sec. 3.3.1) approximation, estimates the
+ * gradient of the log marginal likelihood (Eq. 2) with Rademacher probes
+ * (Sec. 2.1), predicts at test inputs, solves many uneven problems in one
+ * batch, and finds the Laplace approximation of probit GP classification
+ * (Sec. 2.2, Appendix B) with its predictions.  K is never stored: its
+ * entries are rebuilt from X inside every product.
  *
  * Notation: amplitude s^2 (the paper's sigma^2 in Eq. 1), noise sigma^2 (the
  * paper's lambda), lengthscales l_r.  Parameters are passed in log space:
