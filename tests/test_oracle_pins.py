@@ -656,3 +656,35 @@ def test_pitc_blocks_limits_and_structure():
     np.testing.assert_allclose(oracle.PITC(p.X, ell, s2, p.noise, idx, 90).P, Ky, atol=1e-12)
     v = synthetic.rng(4).standard_normal(90)
     np.testing.assert_allclose(Pt.P @ Pt.apply(v), v, atol=1e-9 * np.abs(v).max())
+
+
+# ------------------------------------- Sec. 4 qualitative claims (soft checks)
+def test_sec4_low_rank_preconditioners_gain_most_at_long_lengthscales():
+    # Sec. 4: Nystrom, FITC and PITC cut iterations most when the lengthscale is
+    # long (not at short ones), and block-Jacobi on unordered inputs does not
+    # help on a dense K.  A soft check of the paper's claims on synthetic data
+    # (isotropic, s2 = 1, noise 1e-4, stop at ||r||^2 < n 1e-10, m = sqrt(n)),
+    # not a parity pin: per preconditioner, the best gain over the longer
+    # lengthscales 10^0 and 10^0.5 beats the gain at 10^-0.5 and is a real cut.
+    n, d = 324, 4
+    p = synthetic.make_problem(n, d, 21, dist="standardized", ard=False, ell=1.0)
+    m = 18
+    idx = synthetic.inducing_subset(n, m, seed=5)
+    noise = 1e-4
+    gains = {}
+    for le in (-0.5, 0.0, 0.5):
+        ell = np.full(d, 10.0 ** le)
+        Ky = oracle.dense_ky(p.X, ell, 1.0, noise)
+        tol = float(np.sqrt(n * 1e-10) / np.linalg.norm(p.y))
+        _, it_cg = oracle.pcg_dense(Ky, p.y, lambda r: r, tol=tol)
+        pcs = {"nystrom": oracle.Nystrom(p.X, ell, 1.0, noise, idx),
+               "fitc": oracle.FITC(p.X, ell, 1.0, noise, idx),
+               "pitc": oracle.PITC(p.X, ell, 1.0, noise, idx, m),
+               "block_jacobi": oracle.BlockJacobi(p.X, ell, 1.0, noise, m)}
+        for k, P in pcs.items():
+            _, it = oracle.pcg_dense(Ky, p.y, P.apply, tol=tol)
+            gains[(k, le)] = math.log10(max(it, 1) / max(it_cg, 1))
+    for k in ("nystrom", "fitc", "pitc"):
+        best_long = min(gains[(k, 0.0)], gains[(k, 0.5)])
+        assert best_long < gains[(k, -0.5)] and best_long < -0.1, (k, gains)
+    assert min(gains[("block_jacobi", 0.0)], gains[("block_jacobi", 0.5)]) > -0.05, gains
