@@ -78,10 +78,15 @@ typedef enum {
                           tcgen05 BF16 MMAs on a three-way split of the scaled
                           inputs form the exponent in FP32 (TMEM), exp2 on the
                           MUFU; requires d <= 16                                 */
-    KPCG_DF64 = 4      /* FP64 vectors and scalars; iterations use the
+    KPCG_DF64 = 4,     /* FP64 vectors and scalars; iterations use the
                           double-float K.V (FP32-pair arithmetic on the FP32
                           pipe, about 44 bits); stop and restart decisions use
                           the native FP64 residual                               */
+    KPCG_FP32X_IR = 5  /* as KPCG_FP32_IR, the inner K.V in FP32 on exact
+                          pairwise differences: the scaled inputs stay split
+                          into FP32 pairs (no per-point rounding), each entry
+                          rounds once in FP32, row and column sums are
+                          compensated; requires d <= 16                          */
 } kpcg_precision;
 
 typedef struct {
@@ -210,7 +215,11 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
  * impl 1: the tensor-core kernel KPCG_TC_IR iterates with (tcgen05 BF16x3
  *         split exponent, FP32 accumulate, exp2 and contraction in FP32);
  *         d <= 16, else KPCG_ERR_ARG.  A bounded wait that expires inside
- *         the kernel returns KPCG_ERR_TIMEOUT. */
+ *         the kernel returns KPCG_ERR_TIMEOUT;
+ * impl 2: the KPCG_FP32X_IR inner kernel (exact differences of the split
+ *         inputs, compensated sums) with exp2 on the MUFU (ex2.approx);
+ * impl 3: the same with a polynomial exp2 on the FMA pipe (the one the
+ *         solver uses); impl 2 and 3 need d <= 16. */
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 
@@ -387,17 +396,37 @@ const char* kpcg_mlp_last_error(kpcg_mlp_t m);
  * partial sums) is one static device array of 16 MiB that every GPU loading
  * the library holds until exit.  Sizes needing more are rejected with
  * KPCG_ERR_ARG and a message; on a 152-SM GPU every n below 74 880 fits for
- * d <= 8 (131 064 for d <= 4, 43 680 for d <= 16, 24 960 for d <= 32).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) while the
- * device is current; make that first call before any stream capture.  Every
- * call shares the array and leaves its contents behind, so calls that overlap
- * on the GPU (other streams, other host threads) race: serialise them.  The
- * call returns after the stream has finished its work.  On error the message
- * is available from kpcg_last_error(NULL). */
+ * d <= 8 (131 064 for d <= 4, 43 680 for d <= 16, 24 960 for d <= 32); n above
+ * 2^31 is rejected the same way.  X, V and O must be device (or managed)
+ * pointers, X 4-byte and V, O 8-byte aligned (else KPCG_ERR_ARG).  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * while the device is current and keeps it for the life of the process; if
+ * you capture streams, make that first call before a capture begins, and do
+ * not call it again on a device after cudaDeviceReset (the kept address would
+ * be stale).  Every call shares the array and leaves its contents behind, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  The call synchronises the stream before it returns.  On
+ * error the message is available from kpcg_last_error(NULL). */
 kpcg_status kpcg_matvec_f64_noalloc(const float* X, int64_t n, int32_t d,
                                     const double* log_theta, int32_t ard, double noise_var,
                                     const double* V, int64_t ldv, int32_t c, double* O,
                                     int64_t ldo, void* stream);
+
+/* Measured issue rates of the pipes that bound the kernel products (Sec. 2.1
+ * products rebuild K's entries, so they are limited by arithmetic, not by
+ * memory): out (host, 7 doubles) receives
+ *   [0] FP32 FMA lane-instructions per second,
+ *   [1] MUFU ex2.approx.ftz.f32 lane-instructions per second,
+ *   [2] FP64 FMA lane-instructions per second,
+ *   [3..5] the SM clock in MHz seen inside each of the three probes (clock64
+ *          cycles over %globaltimer nanoseconds on one CTA),
+ *   [6] the number of SMs.
+ * Each probe runs about 20 ms on the current device (stream: cudaStream_t,
+ * NULL = legacy default), dependent chains of one instruction kind on every
+ * SM.  The paper has no counterpart: this is a measurement tool for the
+ * rooflines of the library's kernels.  On error the message is available
+ * from kpcg_last_error(NULL). */
+kpcg_status kpcg_probe_rates(void* stream, double* out);
 
 /* ---- Many independent systems of uneven size, solved together ----------
  * Each problem is an independent system (K_p + sigma_p^2 I) x = b of Eq. 1

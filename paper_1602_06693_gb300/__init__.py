@@ -9,6 +9,7 @@ from .binding import (  # noqa: F401
     KPCG_FP32,
     KPCG_DF64,
     KPCG_FP32_IR,
+    KPCG_FP32X_IR,
     KPCG_FP64,
     KPCG_PREC_BLOCK_JACOBI,
     KPCG_PREC_FITC,
@@ -31,4 +32,5 @@ from .binding import (  # noqa: F401
     lib,
     library_path,
     matvec_f64_noalloc,
+    probe_rates,
 )

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
 KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI, KPCG_PREC_FITC = 0, 1, 2, 3
 KPCG_PREC_SPECTRAL, KPCG_PREC_PITC = 4, 5
-KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64 = 0, 1, 2, 3, 4
+KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64, KPCG_FP32X_IR = 0, 1, 2, 3, 4, 5
 
 _STATUS = {
     0: "KPCG_OK", 1: "KPCG_ERR_ARG", 2: "KPCG_ERR_CUDA", 3: "KPCG_ERR_OOM",
@@ -38,7 +38,7 @@ SYMBOLS = (
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
     "kpcg_batch_destroy",
     "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace", "kpcg_laplace_predict",
-    "kpcg_precond_pitc",
+    "kpcg_precond_pitc", "kpcg_probe_rates",
 )
 
 _NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
@@ -170,6 +170,7 @@ def lib():
         L.kpcg_mlp_last_error.restype = ctypes.c_char_p
         L.kpcg_matvec_f64_noalloc.argtypes = [vp, i64, i32, pdbl, i32, dbl, vp, i64, i32, vp,
                                               i64, vp]
+        L.kpcg_probe_rates.argtypes = [vp, pdbl]
         L.kpcg_batch_create.argtypes = [i32, ctypes.POINTER(Problem), ctypes.POINTER(Options), vp,
                                         ctypes.POINTER(vp)]
         L.kpcg_batch_solve.argtypes = [vp, vp, i64, i32, dbl, vp, ctypes.POINTER(ctypes.c_int32),
@@ -213,7 +214,11 @@ def matvec_f64_noalloc(X, log_theta, noise, V, ard=True, out=None, stream=None):
     V, ldv, c = _colmajor(V, "V")
     O = out if out is not None else (torch.empty_like(V) if V.dim() == 1 else
                                      fortran_empty(n, c, torch.float64, V.device))
-    O_, ldo, _ = _colmajor(O, "out")
+    O_, ldo, co = _colmajor(O, "out")
+    if tuple(O.shape) != tuple(V.shape) or O.device != V.device:
+        raise ValueError("out must have V's shape and device")
+    if co != c:
+        raise ValueError("out must have as many columns as V")
     lt = np.ascontiguousarray(log_theta, dtype=np.float64)
     st = stream if stream is not None else torch.cuda.current_stream(X.device)
     L = lib()
@@ -225,6 +230,22 @@ def matvec_f64_noalloc(X, log_theta, noise, V, ard=True, out=None, stream=None):
     if rc != 0:
         raise KpcgError(rc, L.kpcg_last_error(None).decode())
     return O
+
+
+def probe_rates(stream=None):
+    """kpcg_probe_rates: measured FP32 FMA, MUFU ex2 and FP64 FMA lane-instruction
+    rates (per second) of the current device, the SM clock (MHz) inside each
+    probe, and the SM count."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = (ctypes.c_double * 7)()
+    L = lib()
+    rc = L.kpcg_probe_rates(ctypes.c_void_p(st.cuda_stream), out)
+    if rc != 0:
+        raise KpcgError(rc, L.kpcg_last_error(None).decode())
+    v = list(out)
+    return {"fp32_fma_per_s": v[0], "ex2_per_s": v[1], "fp64_fma_per_s": v[2],
+            "sm_mhz_fp32": v[3], "sm_mhz_ex2": v[4], "sm_mhz_fp64": v[5], "sms": int(v[6])}
 
 
 def default_options(**kw) -> Options:

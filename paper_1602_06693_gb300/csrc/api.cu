@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -29,6 +31,13 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
 static thread_local long long g_launches = 0;
 void note_launch() { ++g_launches; }
 void note_launches(long long k) { g_launches += k; }
+bool trace_on() {
+    static const int on = [] {
+        const char* e = std::getenv("KPCG_TRACE");
+        return (e && e[0] && e[0] != '0') ? 1 : 0;
+    }();
+    return on != 0;
+}
 long long launch_count() { return g_launches; }
 
 int padded_dim(int d) {
@@ -120,7 +129,7 @@ static void check_theta(const double* log_theta, int n_theta, double noise) {
     if (!(noise > 0.0) || !std::isfinite(noise)) fail(KPCG_ERR_ARG, "noise_var must be > 0");
 }
 
-static void check_dev_ptr(const void* p, const char* name) {
+void check_dev_ptr(const void* p, const char* name) {
     if (!p) fail(KPCG_ERR_ARG, std::string(name) + " is NULL");
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -297,7 +306,8 @@ bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
 // Noise of the system the preconditioner approximates: sigma^2 for the
 // single-precision solvers, the shifted inner noise for the mixed ones.
 static double precond_noise(const Ctx& h) {
-    const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TC_IR;
+    const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TC_IR ||
+                       h.opt.precision == KPCG_FP32X_IR;
     return mixed ? h.noise * (1.0 + h.opt.inner_shift) : h.noise;
 }
 
@@ -401,6 +411,9 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
             if (bb[k] > 0 && !dead[k]) worst = std::max(worst, std::sqrt(rr[k] / bb[k]));
         }
         steps = outer;
+        if (trace_on())
+            std::fprintf(stderr, "kpcg fcg outer %d worst_rel_res %.3e inner_iters %d%s\n", outer,
+                         worst, iters_total, recheck ? " (recomputed)" : "");
         if (all) {
             // certify on the recomputed residual; continue from it if the
             // recursive one drifted
@@ -505,12 +518,16 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
 static MixedOps single_ops(Ctx& h) {
     MixedOps o;
     const bool tc = (h.opt.precision == KPCG_TC_IR);
+    const bool xf = (h.opt.precision == KPCG_FP32X_IR);
     const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
     Ctx* hp = &h;
-    o.inner_mv = [hp, tc, inner_noise](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+    o.inner_mv = [hp, tc, xf, inner_noise](const float* V, int64_t ldv, int cc, float* O,
+                                           int64_t ldo) {
         Ctx& h = *hp;
         if (tc)
             kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
+        else if (xf)
+            kv_xf(h, V, ldv, cc, O, ldo, inner_noise, 1);
         else
             kv_f32(h.xs32.p, h.n, h.dp, h.c0_32(), inner_noise, V, ldv, cc, O, ldo, h.kvws,
                    h.stream);
@@ -555,6 +572,8 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
     const int prec = h.opt.precision;
     if (prec == KPCG_TC_IR && !kv_tc_supported(h.dp))
         fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+    if (prec == KPCG_FP32X_IR && !kv_xf_supported(h))
+        fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
     std::vector<int> iters_col((size_t)c, 0);
     int iters_total = 0, steps = 0, broken = 0;
     kpcg_status status = KPCG_OK;
@@ -663,6 +682,13 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
             }
             for (int k = 0; k < c; ++k)
                 all = all && col_converged(rr[k], bb[k], tol, h.opt.tol_mode, n);
+            if (trace_on()) {
+                double w = 0.0;
+                for (int k = 0; k < c; ++k)
+                    if (bb[k] > 0) w = std::max(w, std::sqrt(rr[k] / bb[k]));
+                std::fprintf(stderr, "kpcg pass %d iters %d worst_rel_res %.3e%s\n", pass,
+                             iters_total, w, br ? " (breakdown)" : "");
+            }
             steps = pass;
             if (all || ran == 0) break;
         }
@@ -862,7 +888,7 @@ const char* kpcg_status_string(kpcg_status s) {
 static void check_opts(const kpcg_options* o) {
     if (o->max_iter < 0 || o->max_outer < 0 || o->check_every < 1 || o->max_restarts < 0)
         fail(KPCG_ERR_ARG, "invalid options");
-    if (o->precision < KPCG_FP64 || o->precision > KPCG_DF64)
+    if (o->precision < KPCG_FP64 || o->precision > KPCG_FP32X_IR)
         fail(KPCG_ERR_ARG, "invalid precision");
     if (o->tol_mode != 0 && o->tol_mode != 1) fail(KPCG_ERR_ARG, "invalid tol_mode");
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) fail(KPCG_ERR_ARG, "inner_tol not in (0,1)");
@@ -1078,6 +1104,10 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
             if (kpcg::kv_tc_error(*h))
                 fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
+        } else if (impl == 2 || impl == 3) {
+            if (!kpcg::kv_xf_supported(*h))
+                fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
+            kpcg::kv_xf(*h, V, ldv, c, O, ldo, (float)h->noise, impl - 2);
         } else {
             fail(KPCG_ERR_ARG, "unknown impl");
         }

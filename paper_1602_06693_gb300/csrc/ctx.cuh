@@ -133,6 +133,7 @@ struct Ctx {
     int df_version = -1;
     float df_c0h = 0.f, df_c0l = 0.f;
     DevBuf<float> xdf;
+    DevBuf<float> xf2;  // (hi, lo) pairs of x' for the exact-difference FP32 kernel
     DevBuf<float2> df_tab;
     DevBuf<double> df_grid;
     bool df_symmetric = true;  // symmetric tile-pair kernel (cleared by tests of the other)
@@ -156,6 +157,12 @@ void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t
 // row-split kernel for small n or d > 16.  Same arguments as kv_df.
 void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb,
                 double* O, int64_t ldo, double noise);
+// O = (K + noise I) V in FP32 with exact pairwise differences of the split
+// inputs and compensated sums (kv_df.cu; d <= 16).  expp 0: MUFU exp2,
+// 1: polynomial exp2 on the FMA pipe.
+void kv_xf(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise,
+           int expp);
+bool kv_xf_supported(const Ctx& h);
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);

@@ -26,6 +26,11 @@ void note_launch();
 // count k kernel launches made by replaying a captured graph
 void note_launches(long long k);
 long long launch_count();
+// KPCG_TRACE=1 in the environment: the solvers print one line per outer step
+// (worst relative residual, iterations so far) to stderr.
+bool trace_on();
+// KPCG_ERR_ARG unless p is a non-NULL device (or managed) pointer.
+void check_dev_ptr(const void* p, const char* name);
 #define KPCG_LAUNCHED(name) \
     (::kpcg::note_launch(), ::kpcg::cuda_check(cudaGetLastError(), name, __FILE__, __LINE__))
 

@@ -400,6 +400,162 @@ __global__ void __launch_bounds__(ST)
     for (int k = 0; k < CB; ++k) prow[(((size_t)I * nchunk + wk.w) * CB + k) * ST + t] = S[k];
 }
 
+
+// ---------------------------------------------------------------------------
+// Exact-difference FP32 product (the inner operator of KPCG_FP32X_IR).
+//
+// Rounding the scaled inputs x' to FP32 perturbs every point by ~2^-24: a
+// perturbation that moves whole rows and columns of K together, so it acts on
+// smooth vectors with the size of K's largest eigenvalue, and K_y^{-1} then
+// multiplies it by up to 1/sigma^2 -- at n = 65536 and sigma^2 = 1e-4 the
+// product of the two is ~8, and an FP32 inner solve cannot precondition the
+// system.  Rounding errors that are independent per entry act like a random
+// matrix instead, of norm ~ eps rms(K) sqrt(n), far below sigma^2.
+// So this kernel keeps every per-point quantity exact and lets only the
+// per-entry arithmetic round:
+//  * x' arrives as the double-float pair (hi, lo) of kv_df_kernel (hi on a
+//    per-dimension grid, so hi_i - hi_j is exact; lo carries the next 24 bits);
+//    the difference is D + E rounded once, the squared distance sums in FP32;
+//  * exp2 of the exponent: MUFU ex2.approx (EXPP = 0) or a degree-7 Taylor
+//    polynomial of 2^f = e^(f ln 2), |f| <= 1/2, on the FMA pipe (EXPP = 1,
+//    about one FP32 ulp);
+//  * row sums with V are compensated (TwoSum into an FP32 pair), so the
+//    accumulation adds no per-row error; the mirrored column sums of an
+//    off-diagonal tile pair go through the shared-memory transpose of the
+//    symmetric double-float kernel and are compensated the same way.
+// V and O are FP32 (the inner PCG's vectors); partial sums leave as FP64.
+template <int EXPP>
+__device__ __forceinline__ float xf_exp2(float a) {
+    if (EXPP == 0) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+        return y;
+    } else {
+        a = fmaxf(a, -125.f);
+        const float big = a + 12582912.f;                  // 1.5 * 2^23: round to integer
+        const int ki = __float_as_int(big) - 0x4B400000;
+        const float f = a - (big - 12582912.f);           // exact, |f| <= 1/2
+        // (ln 2)^k / k!, k = 7 .. 1
+        float p = fmaf(f, 1.5252733804059840e-05f, 1.5403530393381608e-04f);
+        p = fmaf(p, f, 1.3333558146428443e-03f);
+        p = fmaf(p, f, 9.6181291076284772e-03f);
+        p = fmaf(p, f, 5.5504108664821580e-02f);
+        p = fmaf(p, f, 2.4022650695910071e-01f);
+        p = fmaf(p, f, 6.9314718055994531e-01f);
+        p = fmaf(p, f, 1.f);
+        return __int_as_float(__float_as_int(p) + (ki << 23));
+    }
+}
+
+__device__ __forceinline__ void xf_acc(float& S, float& C, float P) {
+    const float s = S + P;
+    const float bp = s - S;
+    const float err = (S - (s - bp)) + (P - bp);
+    S = s;
+    C += err;
+}
+
+template <int DP, int CB, int EXPP>
+__global__ void __launch_bounds__(ST)
+    kv_xf_sym_kernel(const float2* __restrict__ xs, int64_t n, int nt, float c0,
+                     const float* __restrict__ V, int64_t ldv, int ncols,
+                     const int4* __restrict__ work, int G, int nchunk,
+                     double* __restrict__ prow, double* __restrict__ pcol) {
+    extern __shared__ float2 xfsm[];
+    float2* sx = xfsm;                                                 // ST * DP
+    float* sv = reinterpret_cast<float*>(sx + ST * DP);                // ST * CB
+    float (*W)[ST][SCW + 1] = reinterpret_cast<float (*)[ST][SCW + 1]>(sv + ST * CB);
+    float2 (*red)[4][SCW] = reinterpret_cast<float2 (*)[4][SCW]>(&W[CB][0][0]);
+    const int4 wk = work[blockIdx.x];  // (I, J0, J1, chunk)
+    const int I = wk.x;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int64_t i = (int64_t)I * ST + t;
+    float2 xi[DP];
+#pragma unroll
+    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : make_float2(0.f, 0.f);
+    float vi[CB], S[CB], C[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        vi[k] = (i < n && k < ncols) ? V[i + (int64_t)k * ldv] : 0.f;
+        S[k] = C[k] = 0.f;
+    }
+    for (int J = wk.y; J < wk.z; ++J) {
+        __syncthreads();
+        for (int e = t; e < ST * DP; e += ST) {
+            const int jj = e / DP;
+            const int64_t j = (int64_t)J * ST + jj;
+            sx[e] = (j < n) ? xs[j * DP + (e - jj * DP)] : make_float2(0.f, 0.f);
+        }
+        for (int e = t; e < ST * CB; e += ST) {
+            const int k = e / ST, jj = e - k * ST;
+            const int64_t j = (int64_t)J * ST + jj;
+            sv[jj * CB + k] = (j < n && k < ncols) ? V[j + (int64_t)k * ldv] : 0.f;
+        }
+        __syncthreads();
+        const bool mirror = (J != I);
+        for (int cst = 0; cst < ST; cst += SCW) {
+            for (int jj = 0; jj < SCW; ++jj) {
+                const int jc = cst + jj;
+                float a = c0;
+#pragma unroll
+                for (int q = 0; q < DP; ++q) {
+                    const float2 xj = sx[jc * DP + q];
+                    const float dl = (xi[q].x - xj.x) + (xi[q].y - xj.y);
+                    a = fmaf(-dl, dl, a);
+                }
+                const float e = xf_exp2<EXPP>(a);
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    xf_acc(S[k], C[k], e * sv[jc * CB + k]);
+                    if (mirror) W[k][t][jj] = e * vi[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CB; ++k) df_renorm(S[k], C[k]);
+            if (mirror) {
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    float cs = 0.f, cc = 0.f;
+                    for (int r = 0; r < 32; ++r) xf_acc(cs, cc, W[k][warp * 32 + r][lane]);
+                    red[k][warp][lane] = make_float2(cs, cc);
+                }
+                __syncthreads();
+                if (warp == 0) {
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            s += (double)red[k][w][lane].x + (double)red[k][w][lane].y;
+                        pcol[(((size_t)J * nt + I) * CB + k) * ST + cst + lane] = s;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k)
+        prow[(((size_t)I * nchunk + wk.w) * CB + k) * ST + t] = (double)S[k] + (double)C[k];
+}
+
+// O = noise V + the partial sums of kv_xf_sym_kernel, in FP64, rounded to FP32.
+__global__ void kv_xf_sym_reduce_kernel(const double* __restrict__ prow,
+                                        const double* __restrict__ pcol, int nt, int G,
+                                        int nchunk, int cb, int ncols,
+                                        const float* __restrict__ V, int64_t ldv, float noise,
+                                        float* __restrict__ O, int64_t ldo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n || k >= ncols) return;
+    const int T = (int)(i / ST), r = (int)(i % ST);
+    double s = (double)noise * (double)V[i + (int64_t)k * ldv];
+    for (int ch = T / G; ch < nchunk; ++ch) s += prow[(((size_t)T * nchunk + ch) * cb + k) * ST + r];
+    for (int I = 0; I < T; ++I) s += pcol[(((size_t)T * nt + I) * cb + k) * ST + r];
+    O[i + (int64_t)k * ldo] = (float)s;
+}
+
 __global__ void kv_df_sym_reduce_kernel(const double* __restrict__ prow,
                                         const double* __restrict__ pcol, int nt, int G,
                                         int nchunk, int cb, int ncols,
@@ -445,8 +601,10 @@ __global__ void colmax_kernel(const double* __restrict__ xs64, int64_t n, int dp
 }
 
 // hi = x' rounded to the grid 2^(k_r - 23), lo = fl(x' - hi), lo2 = x' - hi - lo.
+// The (hi, lo) pairs alone feed the exact-difference FP32 kernel.
 __global__ void df_prep_kernel(const double* __restrict__ xs64, int64_t n, int dp, double scale,
-                               const double* __restrict__ grid, float4* __restrict__ out) {
+                               const double* __restrict__ grid, float4* __restrict__ out,
+                               float2* __restrict__ out2) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * dp) return;
     const int q = (int)(e % dp);
@@ -456,6 +614,7 @@ __global__ void df_prep_kernel(const double* __restrict__ xs64, int64_t n, int d
     const float lo = (float)(x - hi);
     const float lo2 = (float)(x - hi - (double)lo);
     out[e] = make_float4((float)hi, lo, lo2, 0.f);
+    out2[e] = make_float2((float)hi, lo);
 }
 
 struct DfSplit {
@@ -573,8 +732,9 @@ static void df_prepare(Ctx& h) {
     KPCG_CUDA(cudaMemcpyAsync(mx + h.dp, grid.data(), sizeof(double) * h.dp,
                               cudaMemcpyHostToDevice, st));
     float4* xdf = reinterpret_cast<float4*>(h.xdf.need((size_t)n * h.dp * 4));
+    float2* xf2 = reinterpret_cast<float2*>(h.xf2.need((size_t)n * h.dp * 2));
     df_prep_kernel<<<(unsigned)((n * h.dp + 255) / 256), 256, 0, st>>>(h.xs64.p, n, h.dp, scale,
-                                                                       mx + h.dp, xdf);
+                                                                       mx + h.dp, xdf, xf2);
     KPCG_LAUNCHED("df_prep_kernel");
     const double c0 = std::log2(h.s2);
     h.df_c0h = (float)c0;
@@ -776,6 +936,75 @@ void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t
             ldb, O + (int64_t)k0 * ldo, ldo, n);
         KPCG_LAUNCHED("kv_df_reduce_kernel");
         k0 += ncols;
+    }
+}
+
+template <int DP, int CB, int EXPP>
+static void xf_sym_launch1(const float2* xs, int64_t n, int nt, float c0, const float* V,
+                           int64_t ldv, int ncols, const int4* work, int nwork, int G, int nchunk,
+                           double* prow, double* pcol, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * ST * DP + sizeof(float) * ST * CB +
+                        sizeof(float) * CB * ST * (SCW + 1) + sizeof(float2) * CB * 4 * SCW;
+    static bool attr = false;
+    if (!attr) {
+        KPCG_CUDA(cudaFuncSetAttribute(kv_xf_sym_kernel<DP, CB, EXPP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    kv_xf_sym_kernel<DP, CB, EXPP><<<nwork, ST, smem, st>>>(xs, n, nt, c0, V, ldv, ncols, work, G,
+                                                            nchunk, prow, pcol);
+    KPCG_LAUNCHED("kv_xf_sym_kernel");
+}
+
+template <int DP>
+static void xf_sym_launch(int cb, int expp, const float2* xs, int64_t n, int nt, float c0,
+                          const float* V, int64_t ldv, int ncols, const int4* work, int nwork,
+                          int G, int nchunk, double* prow, double* pcol, cudaStream_t st) {
+    if (expp == 0) {
+        if (cb == 1)
+            xf_sym_launch1<DP, 1, 0>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+        else
+            xf_sym_launch1<DP, 2, 0>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+    } else {
+        if (cb == 1)
+            xf_sym_launch1<DP, 1, 1>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+        else
+            xf_sym_launch1<DP, 2, 1>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+    }
+}
+
+bool kv_xf_supported(const Ctx& h) { return h.dp <= 16 && h.n >= 1; }
+
+void kv_xf(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise,
+           int expp) {
+    if (h.n <= 0 || c <= 0) return;
+    if (!kv_xf_supported(h)) fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
+    df_prepare(h);
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int nt = (int)((n + ST - 1) / ST);
+    const int G = ensure_sym_work(h, nt);
+    const int nchunk = (nt + G - 1) / G;
+    const int max_cb = 2;
+    double* prow = h.df_prow.need((size_t)nt * nchunk * max_cb * ST);
+    double* pcol = h.df_pcol.need((size_t)nt * nt * max_cb * ST);
+    const float2* xs = reinterpret_cast<const float2*>(h.xf2.p);
+    const int4* work = reinterpret_cast<const int4*>(h.df_work.p);
+    const float c0 = h.df_c0h;
+    for (int k0 = 0; k0 < c;) {
+        const int cb = (c - k0 >= 2) ? 2 : 1;
+        const float* Vk = V + (int64_t)k0 * ldv;
+        switch (h.dp) {
+            case 4: xf_sym_launch<4>(cb, expp, xs, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 8: xf_sym_launch<8>(cb, expp, xs, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 12: xf_sym_launch<12>(cb, expp, xs, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 16: xf_sym_launch<16>(cb, expp, xs, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+        kv_xf_sym_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)cb), 256, 0, st>>>(
+            prow, pcol, nt, G, nchunk, cb, cb, Vk, ldv, noise, O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("kv_xf_sym_reduce_kernel");
+        k0 += cb;
     }
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -81,6 +82,16 @@ extern "C" kpcg_status kpcg_matvec_f64_noalloc(const float* X, int64_t n, int32_
     try {
         if (!X || !log_theta || !V || !O) fail(KPCG_ERR_ARG, "NULL argument");
         if (n < 1 || c < 0 || ldv < n || ldo < n) fail(KPCG_ERR_ARG, "bad sizes");
+        // n is capped before any size arithmetic, so the scratch plan below
+        // cannot wrap around
+        if (n > ((int64_t)1 << 31)) fail(KPCG_ERR_ARG, "n too large");
+        check_dev_ptr(X, "X");
+        check_dev_ptr(V, "V");
+        check_dev_ptr(O, "O");
+        if ((reinterpret_cast<uintptr_t>(X) & 3u) != 0)
+            fail(KPCG_ERR_ARG, "X must be 4-byte aligned");
+        if ((reinterpret_cast<uintptr_t>(V) & 7u) != 0 || (reinterpret_cast<uintptr_t>(O) & 7u) != 0)
+            fail(KPCG_ERR_ARG, "V and O must be 8-byte aligned");
         const int dp = padded_dim(d);
         if (d < 1 || dp < 0) fail(KPCG_ERR_ARG, "d must be in [1, 32]");
         if (!(noise_var > 0.0) || !std::isfinite(noise_var))

@@ -68,6 +68,25 @@ def test_create_rejects_host_pointer_without_gpu(built):
     assert L.kpcg_last_error(None)
 
 
+def test_noalloc_rejects_host_pointers_without_gpu(built):
+    # The allocation-free product validates X, V and O before any launch: host
+    # memory is refused with KPCG_ERR_ARG (here no driver or device exists).
+    import ctypes
+    import numpy as np
+    import paper_1602_06693_gb300 as kpcg
+    L = kpcg.lib()
+    X = np.zeros((4, 2), dtype=np.float32)
+    V = np.zeros(4)
+    O = np.zeros(4)
+    lt = np.zeros(3)
+    st = L.kpcg_matvec_f64_noalloc(ctypes.c_void_p(X.ctypes.data), 4, 2,
+                                   lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, 0.1,
+                                   ctypes.c_void_p(V.ctypes.data), 4, 1,
+                                   ctypes.c_void_p(O.ctypes.data), 4, None)
+    assert st == 1, st  # KPCG_ERR_ARG
+    assert b"pointer" in L.kpcg_last_error(None)
+
+
 def test_oracle_and_library_share_no_code():
     # The oracle is plain C in oracle/, the CUDA path lives in the package:
     # neither includes or imports the other.

@@ -128,6 +128,52 @@ def test_matvec_tensor_core_matches_oracle(kpcg, n, d, c):
         assert _rel(out[:, k], ref[:, k]) <= 2e-5, k
 
 
+@pytest.mark.parametrize("impl", [2, 3])
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 2),
+                                   (513, 12, 5), (6000, 8, 1), (129, 4, 2)])
+def test_matvec_exact_difference_fp32_matches_oracle(kpcg, impl, n, d, c):
+    # Exact pairwise differences of the split inputs, one FP32 rounding per
+    # entry (ex2.approx: ~2^-22; the polynomial exp2: ~2^-23), compensated row
+    # and column sums: the product is within a few FP32 roundings of FP64 and
+    # its errors are independent per entry.
+    p = _problem(n, d, seed=17 * n + d)
+    V = synthetic.rng(4).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=impl))
+        again = _np(s.matvec_f32(_cm(V, torch.float32), impl=impl))
+    np.testing.assert_array_equal(out, again)  # deterministic
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= (2e-6 if impl == 3 else 5e-6), k
+
+
+def _rough_part(err, u):
+    """err minus its projection on u: a uniform relative bias of the entries
+    (e.g. of exp2) changes K V along K V itself and is harmless to CG; the
+    rest of the error is what a preconditioned solve has to absorb."""
+    return err - (err @ u) / (u @ u) * u
+
+
+def test_exact_difference_fp32_has_no_per_point_error(kpcg):
+    # On the ill-conditioned uniform-cube workload (n = 8192, noise 1e-4) the
+    # product with a smooth vector exposes per-point rounding of the inputs:
+    # it shifts whole rows of K together, so K 1 comes back with a rough error
+    # of size ~2^-24 |K 1|.  The exact-difference kernels keep that rough part
+    # at the level of independent per-entry roundings.
+    p = synthetic.config2(seed=0, n=8192)
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    one = np.ones(p.n)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, one)
+    with _solver(kpcg, p) as s:
+        e = {impl: np.linalg.norm(_rough_part(_np(s.matvec_f32(_cm(one, torch.float32),
+                                                                impl=impl)) - ref, ref))
+             for impl in (0, 2, 3)}
+    assert e[2] <= 0.05 * e[0] and e[3] <= 0.05 * e[0], e
+    # per unit vector, far below the noise sigma^2 = 1e-4
+    assert max(e[2], e[3]) / np.sqrt(p.n) <= 0.02 * p.noise, e
+
+
 def test_tensor_core_follows_theta_changes(kpcg):
     p = _problem(777, 6, seed=3)
     V = synthetic.rng(8).standard_normal(777)
@@ -245,13 +291,14 @@ def test_config1_other_precisions(kpcg, config1_ref, precision):
     assert _rel(_np(x), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("prec", ["FP32_IR", "FP32X_IR"])
 @pytest.mark.parametrize("kind", ["nystrom", "bj", "none"])
-def test_ill_conditioned_mixed_precision_solve(kpcg, kind):
+def test_ill_conditioned_mixed_precision_solve(kpcg, kind, prec):
     # The uniform-cube ARD workload with noise 1e-4, scaled down to n = 2048.
     p = synthetic.config2(seed=0, n=2048)
     ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
     ref = oracle.dense_solve(p.X, ell, s2, p.noise, p.y)
-    with _solver(kpcg, p, precision=kpcg.KPCG_FP32_IR) as s:
+    with _solver(kpcg, p, precision=getattr(kpcg, "KPCG_" + prec)) as s:
         if kind == "nystrom":
             s.precond(kpcg.KPCG_PREC_NYSTROM, 512, synthetic.inducing_subset(p.n, 512, seed=1))
         elif kind == "bj":

@@ -8,6 +8,7 @@ tolerance of the parity tests; this file is collected last on purpose.
 import numpy as np
 import pytest
 
+import oracle
 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,29 @@ def test_noalloc_matches_handle_product_on_two_calls(kpcg):
         torch.cuda.synchronize()
         assert got.shape == ref.shape
         assert _rel(got, ref) <= 1e-12
+
+
+def test_noalloc_matches_oracle_on_a_side_stream(kpcg):
+    # More than four columns (two passes of the column-block loop over the
+    # shared scratch), padded dimensions 12 and 16, an explicit non-default
+    # stream; compared with the FP64 oracle directly and with impl 0.
+    side = torch.cuda.Stream()
+    for n, d, c in ((2100, 12, 6), (1500, 16, 5)):
+        p = synthetic.make_problem(n, d, 10 + d, dist="normal", ell="loguniform", noise=1e-3)
+        Vn = synthetic.rng(11).standard_normal((n, c))
+        ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+        ref = oracle.kyv(p.X, ell, s2, p.noise, Vn)
+        X = torch.from_numpy(p.X).to("cuda:0")
+        V = _cm(Vn)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            got = kpcg.matvec_f64_noalloc(X, p.log_theta, p.noise, V, ard=p.ard, stream=side)
+        side.synchronize()
+        got_np = got.cpu().numpy()
+        assert np.linalg.norm(got_np - ref) / np.linalg.norm(ref) <= 1e-12
+        with kpcg.Solver(X, p.log_theta, p.noise, ard=p.ard) as s:
+            h = s.matvec_f64(V, impl=0)
+        assert _rel(got, h) <= 1e-12
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(kpcg):
