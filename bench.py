@@ -4,16 +4,21 @@
 Workload (one "step"): the ARD-RBF system (K + sigma^2 I) alpha = y with
 n = 65536, d = 8, X ~ U[0,1]^8, l_r ~ LogUniform(0.3, 3), s = 1, sigma^2 = 1e-4
 (seeded, synthetic), Nystrom preconditioner with m = 1024 random inducing
-points built inside the step, solved to ||y - K_y alpha|| <= 1e-8 ||y|| by the
-mixed-precision solver (outer flexible CG in FP64, inner FP32 PCG).  Inputs are
-resident in HBM when the timed region starts; L2 is flushed between steps.
+points built inside the step, solved to ||y - K_y alpha|| <= 1e-8 ||y||
+(recomputed in native FP64) by the mixed-precision solver: flexible CG in FP64
+(double-float direction products, FP64 certified residuals) around an inner
+FP32 PCG with the tensor-core K.V (--precision selects another mode).  Inputs
+are resident in HBM when the timed region starts; L2 is flushed between steps.
 
-Printed: one JSON line with the time per solve (seconds, lower is better), the
-end-to-end time through the C ABI from host buffers, the roofline of the
-dominant kernel, the FP64 CPU oracle's time on a bounded sample of the same
-workload, and the plain-FP32 PCG comparison on the same GPU.
+Printed: one JSON line with the time per solve (seconds, lower is better) on
+the production path, the end-to-end time through the C ABI from host buffers,
+the roofline of every kernel class (algorithmic work over the pipe rates
+measured on this GPU by kpcg_probe_rates), the FP64 CPU oracle's time on a
+bounded sample of the same workload, and the same-GPU comparisons (plain FP32
+PCG's floor and time to 1e-6, block-Jacobi, the double-float solver).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kpcg|reference]
+        [--workload solve65k|batch64|grad45k|warm131k|predict4k|fig1|laplace15k]
 """
 from __future__ import annotations
 
@@ -38,20 +43,104 @@ N_FULL, D, M_INDUCING, TOL = 65536, 8, 1024, 1e-8
 METRIC = "PCG time-to-rel-res 1e-8 at n=65k vs plain FP32; K.V TFLOP/s vs roofline"
 WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum sin(x)+N(0,0.01); "
             "Nystrom m=1024 built in-step; tol 1e-8 rel; 1 RHS")
-# Algorithmic work of one double-float K.V, in FP32-pipe instructions.  K is
-# symmetric, so each of the n(n+1)/2 distinct entries is evaluated once: per
-# dimension 16 (exact difference, three-part low difference, TwoProduct, two
-# FMAs, TwoSum into the exponent) plus 33 for the table-driven exp2 of a
-# double-float; every (i, j) then costs 12 per right-hand side (split product
-# and TwoSum accumulation).
-def df_ops_per_product(n, d, c):
-    return n * (n + 1) / 2 * (16 * d + 33) + float(n) * n * 12 * c
+# The headline solver: flexible CG in FP64 (double-float outer directions,
+# native-FP64 certified residuals) around an inner FP32 PCG whose K.V runs on
+# the tensor cores, on the operator shifted by inner_shift * sigma^2.  The
+# shift and inner tolerance were picked by the sweep recorded in
+# profiles/precision_n65536.md.
+HEADLINE_PREC = "tc_ir"
+MODE_OPTS = {
+    "tc_ir": dict(inner_shift=4.0, inner_tol=0.1),
+    "fp32_ir": dict(inner_shift=4.0, inner_tol=0.1),
+    "xf_ir": dict(inner_shift=0.25, inner_tol=0.3),
+    "df64": {},
+    "fp64": {},
+}
 
 
-# Native-FP64 kernel: d subtractions and d FMAs for the distance, the FP64 exp
-# (counted as one operation) and c FMAs.
-def fp64_ops_per_entry(d, c):
-    return 2 * d + 1 + c
+def mode_id(kpcg, name):
+    return {"tc_ir": kpcg.KPCG_TC_IR, "fp32_ir": kpcg.KPCG_FP32_IR, "xf_ir": kpcg.KPCG_FP32X_IR,
+            "df64": kpcg.KPCG_DF64, "fp64": kpcg.KPCG_FP64}[name]
+
+
+def kv_algorithmic(n, d, c):
+    """Algorithmic work of one product (K + sigma^2 I) V on n points with c
+    columns.  K is symmetric: its n(n+1)/2 distinct entries each need one
+    exp2, 2d flops for the squared distance (a difference and an FMA per
+    dimension) and, with V, 2c FMAs (row i and, mirrored, column j)."""
+    ent = n * (n + 1) / 2.0
+    return {"distinct_entries": ent, "ex2": ent, "distance_flops": 2.0 * d * ent,
+            "contraction_flops": 2.0 * n * n * c, "fp32_slots": ent * (2 * d + 2 * c)}
+
+
+def alu_roofline(kernel, n, d, c, ms, rates, fp64=False, tensor_tflops=None):
+    """Roofline of one K.V launch of `ms` milliseconds.  frac: the
+    tensor/MUFU bound (the exps on the MUFU, the distance and contraction
+    flops on the tensor cores at the measured BF16 rate) over the measured
+    time, for the n(n+1)/2 distinct entries; frac_simt: the bound with the
+    distance and contraction on the FP32 pipe instead (2d + 2c issue slots per
+    distinct entry); frac_evaluated: the tensor/MUFU bound for all n^2 entries
+    (what a kernel that does not use the symmetry must evaluate).  fp64: the
+    native-FP64 residual kernel against the measured FP64 FMA rate (distance,
+    contraction and the exp counted as one operation each)."""
+    w = kv_algorithmic(n, d, c)
+    t = ms / 1e3
+    if fp64:
+        ops = w["fp32_slots"] + w["ex2"]
+        r = rates["fp64_fma_per_s"]
+        return {"bound": "alu", "pipe": "fp64", "kernel": kernel, "achieved": ops / t / 1e12,
+                "peak": r / 1e12, "unit": "Top/s", "frac": ops / r / t, "avg_ms": ms,
+                "algorithmic": w}
+    return roofline_from_work(kernel, w, ms, rates, tensor_tflops)
+
+
+def roofline_from_work(kernel, w, ms, rates, tensor_tflops=None):
+    """The tensor/MUFU roofline of alu_roofline for a summed work record w."""
+    t = ms / 1e3
+    tens = (tensor_tflops or rates.get("bf16_tflops") or 1934.6) * 1e12
+    t_ex2 = w["ex2"] / rates["ex2_per_s"]
+    t_ten = (w["distance_flops"] + w["contraction_flops"]) / tens
+    t_fma = w["fp32_slots"] / rates["fp32_fma_per_s"]
+    if t_ex2 >= t_ten:
+        pipe, work, r, unit = "mufu_ex2", w["ex2"], rates["ex2_per_s"], "Tex2/s"
+    else:
+        pipe, work, r, unit = "tensor", w["distance_flops"] + w["contraction_flops"], tens, \
+            "TFLOP/s"
+    t_b = max(t_ex2, t_ten)
+    return {"bound": "alu" if pipe == "mufu_ex2" else "tensor", "pipe": pipe, "kernel": kernel,
+            "achieved": work / t / 1e12, "peak": r / 1e12, "unit": unit, "frac": t_b / t,
+            "frac_simt": max(t_fma, t_ex2) / t, "frac_evaluated": 2.0 * t_b / t,
+            "avg_ms": ms, "algorithmic": w}
+
+
+PEAK_SOURCE = ("kpcg_probe_rates on this GPU in this process (dependent chains of one "
+               "instruction kind on every SM, CUDA events): of measured")
+_RATES = {}
+
+
+def probed_rates(kpcg):
+    """Measured FP32 FMA, MUFU ex2 and FP64 FMA rates of this GPU, once per process."""
+    if not _RATES:
+        _RATES.update(kpcg.probe_rates())
+    return dict(_RATES)
+
+
+def df_issue_efficiency(n, d, c, ms, rates):
+    """How fully the double-float kernel issues its own instructions: its
+    instruction model (per distinct entry: 16 per dimension for the exact
+    difference, TwoProduct and TwoSum, 33 for the table-driven exp2, 12 per
+    column for each of the row and the mirrored column) over the FP32 rate."""
+    ops = n * (n + 1) / 2.0 * (16 * d + 33 + 24 * c)
+    return ops / (ms / 1e3) / rates["fp32_fma_per_s"]
+
+
+def nystrom_roofline(n, m, c, ms, hbm_gbs):
+    """The Nystrom apply streams K_XU (n x m FP32 pairs) twice and reads and
+    writes the n x c block: HBM-bound."""
+    b = 2 * 8.0 * n * m + 3 * 8.0 * n * c
+    t = ms / 1e3
+    return {"bound": "hbm", "kernel": "Nystrom apply", "achieved": b / t / 1e9, "peak": hbm_gbs,
+            "unit": "GB/s", "frac": b / t / 1e9 / hbm_gbs, "avg_ms": ms, "bytes": b}
 
 
 def sm_clock_probe():
@@ -140,39 +229,53 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(n=N_FULL, iters=2):
-    """Time the FP64 CPU oracle on a bounded sample of the workload: its Nystrom
-    set-up plus `iters` PCG iterations at full size.  Scaled to a whole solve
-    with the iteration count the oracle's own complete run recorded."""
+def oracle_sample(n=N_FULL, state=None):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the
+    workload and scale it to one whole solve.  Sample: the oracle's Nystrom
+    set-up (m = 1024) on the first n/2 rows (its cost is linear in the rows
+    once K_XU is far larger than the caches), doubled; one full-size product
+    K_y v; one preconditioner apply on the n/2-row set-up, doubled.  Whole
+    solve = set-up + (iterations + 2) x (product + apply), with the iteration
+    count of the oracle's own complete run at this n.  `state` (a dict) keeps
+    the set-up and its time between calls, so repeated samples time only the
+    product and the apply."""
     import oracle
+    if state is None:
+        state = {}
     p = synthetic.config2(seed=0, n=n)
     ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
-    idx = synthetic.inducing_subset(n, M_INDUCING, seed=1)
+    half = n // 2
+    if "P" not in state:
+        idx = synthetic.inducing_subset(half, M_INDUCING, seed=1)
+        t0 = time.perf_counter()
+        state["P"] = oracle.Nystrom(p.X[:half], ell, s2, p.noise, idx)
+        state["setup_half_s"] = time.perf_counter() - t0
+    setup = state["setup_half_s"] * n / half
     t0 = time.perf_counter()
-    P = oracle.Nystrom(p.X, ell, s2, p.noise, idx)
-    t_setup = time.perf_counter() - t0
+    oracle.kyv(p.X, ell, s2, p.noise, p.y)
+    t_kv = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.pcg(p.X, ell, s2, p.noise, p.y, precond=P, tol=1e-30, max_iter=iters)
-    t_iters = time.perf_counter() - t0
-    # or_pcg also spends one K_y x for r0 and one for the final residual: iters + 2 products
-    per_iter = t_iters / (iters + 2)
+    state["P"].apply(p.y[:half])
+    t_ap = time.perf_counter() - t0
+    per_iter = t_kv + t_ap * n / half
     rec_path = os.path.join(ROOT, "tests", "golden", f"oracle_pcg_n{n}.json")
     n_iter, src = None, None
     if os.path.exists(rec_path):
         with open(rec_path) as f:
             rec = json.load(f)
         n_iter, src = int(rec["iterations"]), os.path.relpath(rec_path, ROOT)
-    est = t_setup + per_iter * (n_iter + 2) if n_iter else None
+    est = setup + per_iter * (n_iter + 2) if n_iter else None
     return {
         "value": est,
         "unit": "s",
         "cores": oracle.num_threads(),
         "kind": "oracle",
-        "sample": (f"FP64 oracle Nystrom set-up + {iters} PCG iterations at n={n} "
-                   f"({t_setup:.1f} s + {t_iters:.1f} s); whole solve = set-up + "
-                   f"{n_iter} iterations x {per_iter:.2f} s"
+        "sample": (f"FP64 oracle: Nystrom set-up (m={M_INDUCING}) on the first {half} rows "
+                   f"({state['setup_half_s']:.1f} s, doubled), one full-size K_y v "
+                   f"({t_kv:.2f} s) and one apply on the half set-up ({t_ap:.3f} s, doubled) "
+                   f"at n={n}; whole solve = set-up + ({n_iter} + 2) x (product + apply)"
                    + (f" (iteration count from {src})" if src else " (no recorded count)")),
-        "setup_s": t_setup,
+        "setup_s": setup,
         "s_per_iteration": per_iter,
     }
 
@@ -183,8 +286,9 @@ def run_reference(args):
         return
     vals = []
     base = None
+    state = {}  # the set-up sample is timed once; every step times a product and an apply
     for s in range(args.warmup + args.steps):
-        base = oracle_sample(iters=1)
+        base = oracle_sample(state=state)
         if s >= args.warmup:
             vals.append(base["value"])
     v = statistics.mean(vals) if vals and None not in vals else None
@@ -222,8 +326,7 @@ def run_grad(args):
     stream = torch.cuda.current_stream(dev)
     p = synthetic.config3(seed=rank)
     idx = synthetic.inducing_subset(p.n, 512, seed=2 + rank)
-    prec = {"auto": kpcg.KPCG_TC_IR, "tc_ir": kpcg.KPCG_TC_IR, "df64": kpcg.KPCG_DF64,
-            "fp32_ir": kpcg.KPCG_FP32_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+    prec = kpcg.KPCG_TC_IR if args.precision == "auto" else mode_id(kpcg, args.precision)
     opt = kpcg.default_options(precision=prec, profile=1, inner_shift=0.25, inner_tol=0.2)
     X = torch.from_numpy(p.X).to(dev)
     y = torch.from_numpy(p.y).to(dev)
@@ -511,8 +614,7 @@ def run_laplace(args):
     p = synthetic.eeg_shape(seed=rank)
     lm = args.laplace_m
     idx = synthetic.inducing_subset(p.n, lm, seed=12 + rank) if lm > 0 else None
-    prec = {"auto": kpcg.KPCG_TC_IR, "df64": kpcg.KPCG_DF64, "fp32_ir": kpcg.KPCG_FP32_IR,
-            "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
+    prec = kpcg.KPCG_TC_IR if args.precision == "auto" else mode_id(kpcg, args.precision)
     opt = kpcg.default_options(precision=prec)
     opt.inner_tol = args.inner_tol if args.inner_tol is not None else LAPLACE_INNER_TOL
     s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, 1.0, ard=True, options=opt)
@@ -554,17 +656,12 @@ def run_laplace(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     kv_ms = e0.elapsed_time(e1) / reps
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ops = df_ops_per_product(p.n, p.d, 1)
-    peak = 152 * 128 * sm_max * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": "kv_df_sym_kernel (double-float K.V, 1 column)",
-            "achieved": ops / (kv_ms / 1e3) / 1e12, "peak": peak, "unit": "Top/s",
-            "frac": ops / (kv_ms / 1e3) / 1e12 / peak, "traffic": None,
-            "peak_source": (f"FP32 pipe issue rate: 152 SMs x 128 lanes x {sm_max:.0f} MHz "
-                            "(unit counts and max clock)"),
-            "avg_ms": kv_ms, "ops_per_call": ops,
-            "timing": f"{reps} back-to-back products, CUDA events on the launching stream"}
+    rates = probed_rates(kpcg)
+    roof = alu_roofline("kv_df_sym_kernel (double-float K.V, 1 column)", p.n, p.d, 1, kv_ms,
+                        rates)
+    roof.update({"traffic": None, "peak_source": PEAK_SOURCE,
+                 "timing": f"{reps} back-to-back products, CUDA events on the launching stream",
+                 "issue_efficiency": df_issue_efficiency(p.n, p.d, 1, kv_ms, rates)})
     # the inner product of the mixed B-solves: tensor-core K.V of one column
     roof_inner = None
     if prec == kpcg.KPCG_TC_IR:
@@ -579,16 +676,8 @@ def run_laplace(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         tc_ms = e0.elapsed_time(e1) / reps
-        # the exponent comes from the tensor cores; each of the n^2 entries then
-        # takes one ex2 on the special-function units (16 per SM per clock)
-        tc_ops = float(p.n) * p.n
-        mufu = 152 * 16 * sm_max * 1e6 / 1e12
-        roof_inner = {"bound": "alu", "kernel": "kv_tc_kernel (tcgen05, 1 column)",
-                      "achieved": tc_ops / (tc_ms / 1e3) / 1e12, "peak": mufu, "unit": "Tex2/s",
-                      "frac": tc_ops / (tc_ms / 1e3) / 1e12 / mufu, "avg_ms": tc_ms,
-                      "ops_per_call": tc_ops, "timing": roof["timing"],
-                      "peak_source": (f"ex2 issue: 152 SMs x 16 per clock x {sm_max:.0f} MHz "
-                                      "(unit counts and max clock)")}
+        roof_inner = alu_roofline("kv_tc_kernel (tcgen05, 1 column)", p.n, p.d, 1, tc_ms, rates)
+        roof_inner.update({"timing": roof["timing"], "peak_source": PEAK_SOURCE})
     # end to end: labels from pinned host memory, f back to the host
     yh = torch.from_numpy(p.y).pin_memory()
     fh = torch.empty(p.n, dtype=torch.float64).pin_memory()
@@ -734,7 +823,6 @@ def run_batch(args):
     # call does less than a full product; time one full product instead (all
     # problems, the tuned tiling; staging and reduction included).
     entries = float(sum(p.n ** 2 for p in problems))
-    ops = entries * (c + 1)
     Vf = b.empty(c, torch.float32)
     Vf.normal_()
     for _ in range(2):
@@ -754,9 +842,10 @@ def run_batch(args):
     ef1.record(stream)
     torch.cuda.synchronize(dev)
     precond_full_ms = ef0.elapsed_time(ef1) / 5
-    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * sm_max * 1e6 / 1e12
-    achieved = ops / (avg_ms / 1e3) / 1e12
+    rates = probed_rates(kpcg)
+    rates["bf16_tflops"] = float(measured_peaks().get("bf16_tflops", 1934.6))
+    works = [kv_algorithmic(q.n, q.d, c) for q in problems]
+    wsum = {k: sum(w[k] for w in works) for k in works[0]}
     # end to end from pinned host buffers through the public API
     Bh = Bb.cpu().pin_memory()
     Xh = torch.empty_like(Bh).pin_memory()
@@ -787,11 +876,9 @@ def run_batch(args):
                                      "kv_outer_calls": pinfo.kv_outer_calls,
                                      "precond_ms": pinfo.precond_ms,
                                      "precond_calls": pinfo.precond_calls}},
-        "roofline": {"bound": "alu", "kernel": "kv_tc_batch_kernel (+stage, reduce), full product",
-                     "achieved": achieved, "peak": peak, "unit": "Top/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"FP32 pipe issue rate 152 x 128 x {sm_max:.0f} MHz (unit counts)",
-                     "ops_per_call": ops, "avg_ms": avg_ms},
+        "roofline": roofline_from_work("kv_tc_batch_kernel (+stage, reduce), full product",
+                                       wsum, avg_ms, rates)
+        | {"traffic": None, "peak_source": PEAK_SOURCE, "evaluated_entries": entries},
         "clocks": clocks,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(Bh.numel() * 8),
                 "d2h_bytes_per_step": int(Xh.numel() * 8)},
@@ -802,19 +889,331 @@ def run_batch(args):
     b.close()
 
 
+def solve_options(kpcg, mode, **kw):
+    o = dict(MODE_OPTS[mode])
+    o.update(kw)
+    return kpcg.default_options(precision=mode_id(kpcg, mode), **o)
+
+
+def timed(stream, fn):
+    """(result, ms) of fn() between two CUDA events on `stream`."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return r, e0.elapsed_time(e1)
+
+
+def solve_once(kpcg, X, y, p, idx, opt, stream, kind="nystrom", size=M_INDUCING, tol=TOL):
+    """Build the preconditioner and solve from scratch; returns (info, status,
+    set-up ms, total ms)."""
+    s = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
+    try:
+        k = kpcg.KPCG_PREC_NYSTROM if kind == "nystrom" else kpcg.KPCG_PREC_BLOCK_JACOBI
+        _, set_ms = timed(stream, lambda: s.precond(k, size, idx if kind == "nystrom" else None))
+        (x, _, info, st), sol_ms = timed(stream, lambda: s.solve(y, tol=tol, raise_on_error=False))
+        return info, st, set_ms, set_ms + sol_ms
+    finally:
+        s.close()
+
+
+DTYPES = {"tc_ir": "bf16x3 exponent, f32 inner, f64 outer (double-float directions, fp64 "
+                   "certified residual)",
+          "fp32_ir": "f32 inner, f64 outer", "xf_ir": "f32 inner (exact differences), f64 outer",
+          "df64": "double-float iterations, fp64 certified residual", "fp64": "f64"}
+KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
+            "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
+            "df64": "kv_df_sym_kernel (double-float)", "fp64": "kv_f64_sym_kernel (FP64)"}
+# DRAM bytes per launch from ncu captures (profiles/), by kernel name; a
+# kernel changed since its capture has no entry.
+KNOWN_TRAFFIC = {}
+
+
+def run_solve(args):
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = HEADLINE_PREC if args.precision == "auto" else args.precision
+    extra_opts = {}
+    if args.inner_shift is not None:
+        extra_opts["inner_shift"] = args.inner_shift
+    if args.inner_tol is not None:
+        extra_opts["inner_tol"] = args.inner_tol
+    rates = probed_rates(kpcg)
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    rates["bf16_tflops"] = float(measured_peaks().get("bf16_tflops", 1934.6))
+
+    # replicas: each rank solves its own seeded instance of the same workload
+    p, idx = replica_problem(rank, args.n)
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    opt = solve_options(kpcg, mode, profile=0, **extra_opts)
+    solver = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    set_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step():
+        solver.set_theta(p.log_theta, p.noise)  # drop the preconditioner: rebuilt in-step
+        set_ev[0].record(stream)
+        solver.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
+        set_ev[1].record(stream)
+        return solver.solve(y, tol=TOL, raise_on_error=False)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+
+    stop_clock = sm_clock_probe()
+    times, setups, infos = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, it, info, st = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        setups.append(set_ev[0].elapsed_time(set_ev[1]))
+        infos.append((info, st))
+    clocks = stop_clock()
+    t_step = max_over_ranks(statistics.mean(times), dev)
+    info, st = infos[-1]
+
+    # The same step with the library's profiler on: CUDA events on the
+    # handle's stream around every product and apply (kernel by kernel, no
+    # graph replay), run right after the timed region on the same inputs.
+    popt = solve_options(kpcg, mode, profile=1, **extra_opts)
+    flush.fill_(3.0)
+    pinfo, pst, pset_ms, ptot_ms = solve_once(kpcg, X, y, p, idx, popt, stream)
+    cats = {}
+    if pinfo.kv_inner_calls:
+        ms = pinfo.kv_inner_ms / pinfo.kv_inner_calls
+        cats["kv_inner"] = alu_roofline(KV_NAMES[mode], p.n, D, 1, ms, rates,
+                                        fp64=(mode == "fp64"))
+        cats["kv_inner"].update(calls=pinfo.kv_inner_calls, total_ms=pinfo.kv_inner_ms)
+        if mode == "df64":
+            cats["kv_inner"]["issue_efficiency"] = df_issue_efficiency(p.n, D, 1, ms, rates)
+    if pinfo.kv_outer_calls:
+        ms = pinfo.kv_outer_ms / pinfo.kv_outer_calls
+        cats["kv_outer"] = alu_roofline("kv_df_sym_kernel (double-float outer directions)",
+                                        p.n, D, 1, ms, rates)
+        cats["kv_outer"].update(calls=pinfo.kv_outer_calls, total_ms=pinfo.kv_outer_ms,
+                                issue_efficiency=df_issue_efficiency(p.n, D, 1, ms, rates))
+    if pinfo.resid_calls:
+        ms = pinfo.resid_ms / pinfo.resid_calls
+        cats["resid"] = alu_roofline("kv_f64_sym_kernel (native FP64 certified residual)",
+                                     p.n, D, 1, ms, rates, fp64=True)
+        cats["resid"].update(calls=pinfo.resid_calls, total_ms=pinfo.resid_ms)
+    if pinfo.precond_calls:
+        ms = pinfo.precond_ms / pinfo.precond_calls
+        cats["precond"] = nystrom_roofline(p.n, M_INDUCING, 1, ms, hbm)
+        cats["precond"].update(calls=pinfo.precond_calls, total_ms=pinfo.precond_ms)
+    dom = max(cats, key=lambda k: cats[k]["total_ms"]) if cats else None
+    roof = dict(cats[dom]) if dom else {}
+    if roof:
+        roof["peak_source"] = (PEAK_SOURCE if roof["bound"] == "alu" else
+                               "MEASURED_PEAKS.json hbm_gbs (of measured)")
+        roof["timing"] = ("average launch of this class from CUDA events on the handle's stream "
+                          "in a profiled run of the same step right after the timed region")
+        roof["traffic"] = KNOWN_TRAFFIC.get(roof["kernel"].split(" ")[0])
+
+    # end to end through the C ABI from host buffers
+    Xh = torch.from_numpy(p.X).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(3.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Xd = Xh.to(dev, non_blocking=True)
+        yd = yh.to(dev, non_blocking=True)
+        s2 = kpcg.Solver(Xd, p.log_theta, p.noise, ard=True, options=opt)
+        s2.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
+        xs, _, _, _ = s2.solve(yd, tol=TOL, raise_on_error=False)
+        xh.copy_(xs, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(time.perf_counter() - t0)
+        s2.close()
+    e2e = {"value": statistics.mean(e2e_times), "unit": "s",
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + idx.nbytes),
+           "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.skip_baselines:
+        extra["comparisons"] = comparisons(kpcg, X, y, p, idx, stream, mode, extra_opts, args)
+        try:
+            extra["cpu_baseline"] = oracle_sample()
+        except Exception as e:  # the baseline never blocks the GPU line
+            extra["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+
+    launches_per_step = int(info.launches)  # counted by the library inside the solve
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[mode], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "solver": mode, "inner_shift": opt.inner_shift, "inner_tol": opt.inner_tol,
+                   "path": "production (CUDA-graph replay of CG chunks, profiling off)"},
+        "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
+                  "max_rel_res_fp64": info.max_rel_res,
+                  "setup_ms": statistics.mean(setups), "step_times_s": times,
+                  "profiled": {"status": pst, "total_ms": ptot_ms, "setup_ms": pset_ms,
+                               "kv_inner_ms": pinfo.kv_inner_ms,
+                               "kv_inner_calls": pinfo.kv_inner_calls,
+                               "kv_outer_ms": pinfo.kv_outer_ms,
+                               "kv_outer_calls": pinfo.kv_outer_calls,
+                               "resid_ms": pinfo.resid_ms, "resid_calls": pinfo.resid_calls,
+                               "precond_ms": pinfo.precond_ms,
+                               "precond_calls": pinfo.precond_calls}},
+        "roofline": roof,
+        "kernels": cats,
+        "peaks": {"probe": rates, "hbm_gbs": hbm,
+                  "bf16_tflops": measured_peaks().get("bf16_tflops")},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def comparisons(kpcg, X, y, p, idx, stream, mode, extra_opts, args):
+    """The same-GPU comparisons of the measurement plan: plain FP32 PCG (its
+    floor and time to 1e-6), the headline solver's time to 1e-6, the
+    block-Jacobi arm (b = 512) and the double-float solver, each from scratch
+    (preconditioner set-up included)."""
+    out = {}
+    # plain FP32 PCG, same Nystrom preconditioner, no restarts: one solve per
+    # tolerance; the floor is the best FP64-recomputed residual any of them left
+    fp32 = []
+    for tol in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+        o32 = kpcg.default_options(precision=kpcg.KPCG_FP32, max_iter=args.fp32_max_iter,
+                                   max_restarts=0)
+        info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, idx, o32, stream, tol=tol)
+        fp32.append({"tol": tol, "status": st, "iters": info.iters_total,
+                     "rel_res_fp64": info.max_rel_res, "time_s": tot_ms / 1e3})
+    floor = min(r["rel_res_fp64"] for r in fp32)
+    t6 = [r["time_s"] for r in fp32 if r["tol"] == 1e-6 and r["rel_res_fp64"] <= 1e-6]
+    out["fp32_pcg"] = {"floor_rel_res_fp64": floor, "time_to_1e-6_s": t6[0] if t6 else None,
+                       "reached_1e-8": any(r["rel_res_fp64"] <= 1e-8 for r in fp32),
+                       "runs": fp32,
+                       "note": f"plain FP32 PCG, Nystrom m={M_INDUCING}, capped at "
+                               f"{args.fp32_max_iter} iterations, no restarts"}
+    o = solve_options(kpcg, mode, profile=0, **extra_opts)
+    info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, idx, o, stream, tol=1e-6)
+    out["kpcg_time_to_1e-6_s"] = tot_ms / 1e3
+    out["kpcg_to_1e-6"] = {"status": st, "iters": info.iters_total,
+                           "rel_res_fp64": info.max_rel_res}
+    ob = solve_options(kpcg, mode, profile=0, max_iter=args.bj_max_iter, **extra_opts)
+    info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, None, ob, stream, kind="block_jacobi",
+                                          size=512)
+    out["block_jacobi_512"] = {"status": st, "time_s": tot_ms / 1e3, "setup_ms": set_ms,
+                               "iters": info.iters_total, "outer_steps": info.outer_steps,
+                               "rel_res_fp64": info.max_rel_res,
+                               "note": f"same solver, block-Jacobi blocks of 512, at most "
+                                       f"{args.bj_max_iter} iterations"}
+    if mode != "df64":
+        od = solve_options(kpcg, "df64", profile=0)
+        info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, idx, od, stream)
+        out["df64"] = {"status": st, "time_s": tot_ms / 1e3, "iters": info.iters_total,
+                       "rel_res_fp64": info.max_rel_res}
+    return out
+
+
+KV_IMPLS = {"f64": ("f64", 0, "kv_f64_sym_kernel (native FP64)"),
+            "df": ("f64", 1, "kv_df_sym_kernel (double-float)"),
+            "f32": ("f32", 0, "kv_simt_kernel<float>"),
+            "tc": ("f32", 1, "kv_tc_kernel (tcgen05, BF16x3 exponent)"),
+            "xf": ("f32", 3, "kv_xf_sym_kernel (exact differences)"),
+            "tcx": ("f32", 4, "kv_tcx_kernel (tcgen05, sliced per-point-exact exponent)")}
+
+
+def run_kv(args):
+    """One K.V kernel alone on the benchmark's input distribution at --n
+    points and --kv-cols columns: --warmup untimed then --steps timed
+    products with CUDA events on the launching stream (inputs larger than L2
+    at n >= 16384); a small target for profilers too."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = synthetic.config2(seed=0, n=args.n)
+    kind, impl, kname = KV_IMPLS[args.kv_impl]
+    s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, p.noise, ard=True)
+    c = args.kv_cols
+    V = torch.from_numpy(synthetic.rng(4).standard_normal((c, p.n))).to(dev).t()
+    if kind == "f32":
+        V = V.float()
+    mv = (lambda: s.matvec_f64(V, impl=impl)) if kind == "f64" else \
+        (lambda: s.matvec_f32(V, impl=impl))
+    for _ in range(args.warmup):
+        mv()
+    torch.cuda.synchronize(dev)
+    stop_clock = sm_clock_probe()
+    _, ms = timed(stream, lambda: [mv() for _ in range(args.steps)])
+    clocks = stop_clock()
+    ms /= args.steps
+    rates = probed_rates(kpcg)
+    rates["bf16_tflops"] = float(measured_peaks().get("bf16_tflops", 1934.6))
+    roof = alu_roofline(kname, p.n, p.d, c, ms, rates, fp64=(args.kv_impl == "f64"))
+    roof.update({"peak_source": PEAK_SOURCE, "traffic": KNOWN_TRAFFIC.get(kname.split(" ")[0]),
+                 "timing": f"{args.steps} back-to-back products, CUDA events on the stream"})
+    if args.kv_impl == "df":
+        roof["issue_efficiency"] = df_issue_efficiency(p.n, p.d, c, ms, rates)
+    print(json.dumps({"metric": f"time per K.V product ({args.kv_impl}, c={c})", "value": ms / 1e3,
+                      "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                      "vs_baseline": None, "data": "synthetic",
+                      "config": {"workload": f"K.V of the n={p.n} uniform-cube ARD system"},
+                      "roofline": roof, "peaks": rates, "clocks": clocks}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kpcg", choices=["kpcg", "reference"])
-    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "tc_ir", "fp32_ir", "xf_ir", "df64", "fp64"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)
+    ap.add_argument("--bj-max-iter", type=int, default=6000,
+                    help="block-Jacobi comparison: iteration cap")
+    ap.add_argument("--kv-impl", default="tcx", choices=sorted(KV_IMPLS),
+                    help="kv: the kernel timed")
+    ap.add_argument("--kv-cols", type=int, default=1, help="kv: columns of V")
     ap.add_argument("--workload", default="solve65k",
                     choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k", "fig1",
-                             "laplace15k"],
+                             "laplace15k", "kv"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -849,172 +1248,9 @@ def main():
         return run_fig1(args)
     if args.workload == "laplace15k":
         return run_laplace(args)
-
-    import torch
-    import paper_1602_06693_gb300 as kpcg
-
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    prec = {"auto": kpcg.KPCG_DF64, "df64": kpcg.KPCG_DF64, "fp32_ir": kpcg.KPCG_FP32_IR,
-            "tc_ir": kpcg.KPCG_TC_IR, "fp64": kpcg.KPCG_FP64}[args.precision]
-
-    # replicas: each rank solves its own seeded instance of the same workload
-    p, idx = replica_problem(rank, args.n)
-    X = torch.from_numpy(p.X).to(dev)
-    y = torch.from_numpy(p.y).to(dev)
-    opt = kpcg.default_options(precision=prec, profile=1)
-    solver = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=opt)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-
-    def step():
-        solver.set_theta(p.log_theta, p.noise)  # drop the preconditioner: rebuilt in-step
-        solver.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
-        x, it, info, st = solver.solve(y, tol=TOL, raise_on_error=False)
-        return x, it, info, st
-
-    for _ in range(args.warmup):
-        step()
-        flush.fill_(1.0)
-    torch.cuda.synchronize(dev)
-
-    stop_clock = sm_clock_probe()
-    times, infos = [], []
-    for _ in range(args.steps):
-        flush.fill_(2.0)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        x, it, info, st = step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        infos.append((info, st))
-    clocks = stop_clock()
-    t_step = max_over_ranks(statistics.mean(times), dev)
-    info, st = infos[-1]
-
-    # roofline of the dominant kernel class, from the library's event timers
-    cats = {"kv_inner": (info.kv_inner_ms, info.kv_inner_calls),
-            "kv_outer_fp64": (info.kv_outer_ms, info.kv_outer_calls),
-            "precond_apply": (info.precond_ms, info.precond_calls)}
-    dom = max(cats, key=lambda k: cats[k][0])
-    ms, calls = cats[dom]
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if dom.startswith("kv"):
-        entries = float(p.n) ** 2
-        if dom == "kv_inner" and prec == kpcg.KPCG_DF64:
-            ops = df_ops_per_product(p.n, D, 1)
-            peak = 152 * 128 * sm_max * 1e6 / 1e12
-            peak_src = (f"FP32 pipe issue rate: 152 SMs x 128 lanes x {sm_max:.0f} MHz "
-                        "(unit counts and max clock; no measured FP32 figure)")
-            kname = "kv_df_sym_kernel (double-float K.V, symmetric tile pairs)"
-        else:
-            ops = fp64_ops_per_entry(D, 1) * entries
-            peak = 1.25 / 2  # 1.25 TFLOP/s nominal FP64 = 0.625 T FMA-class op/s
-            peak_src = "nominal GB300 FP64 rate, 1.25 TFLOP/s = 0.625 Top/s"
-            kname = "kv_simt_kernel<double> (native FP64 K.V)"
-        achieved = ops / (ms / calls / 1e3) / 1e12
-        traffic, tsrc = None, None
-        if dom == "kv_inner" and prec == kpcg.KPCG_DF64:
-            # ncu capture at n = 16384 (profiles/kv_df_sym_kernel_n16384.md): 2.29 MB of
-            # DRAM reads, 0 writes; the kernel re-reads nothing from DRAM, so its traffic
-            # is its inputs and grows like n, not n^2
-            traffic = 2.29e6 * p.n / 16384
-            tsrc = "dram read+write per launch, ncu at n=16384 scaled by n (inputs only)"
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "Top/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": tsrc, "peak_source": peak_src, "calls": calls,
-                "avg_ms": ms / calls, "ops_per_call": ops}
-    else:
-        # Nystrom apply streams K_XU (n x m FP32) twice and reads/writes n-vectors
-        bytes_ = 2 * 4.0 * p.n * M_INDUCING + 3 * 8.0 * p.n
-        achieved = bytes_ / (ms / calls / 1e3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": "Nystrom apply", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "calls": calls,
-                "avg_ms": ms / calls}
-
-    # end to end through the C ABI from host buffers
-    Xh = torch.from_numpy(p.X).pin_memory()
-    yh = torch.from_numpy(p.y).pin_memory()
-    xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize(dev)
-    e2e_times = []
-    for _ in range(max(1, min(args.steps, 2))):
-        flush.fill_(3.0)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        Xd = Xh.to(dev, non_blocking=True)
-        yd = yh.to(dev, non_blocking=True)
-        s2 = kpcg.Solver(Xd, p.log_theta, p.noise, ard=True, options=opt)
-        s2.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
-        xs, _, _, _ = s2.solve(yd, tol=TOL, raise_on_error=False)
-        xh.copy_(xs, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        e2e_times.append(time.perf_counter() - t0)
-        s2.close()
-    e2e = {"value": statistics.mean(e2e_times), "unit": "s",
-           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + idx.nbytes),
-           "d2h_bytes_per_step": int(xh.numel() * 8)}
-
-    extra = {}
-    if rank == 0 and world == 1 and not args.skip_baselines:
-        # plain FP32 PCG on the same GPU, same preconditioner
-        o32 = kpcg.default_options(precision=kpcg.KPCG_FP32, max_iter=args.fp32_max_iter,
-                                   max_restarts=0)
-        s32 = kpcg.Solver(X, p.log_theta, p.noise, ard=True, options=o32)
-        t0 = time.perf_counter()
-        s32.precond(kpcg.KPCG_PREC_NYSTROM, M_INDUCING, idx)
-        x32, it32, inf32, st32 = s32.solve(y, tol=TOL, raise_on_error=False)
-        torch.cuda.synchronize(dev)
-        t32 = time.perf_counter() - t0
-        extra["fp32_pcg"] = {"status": st32, "time_s": t32, "iters": int(inf32.iters_total),
-                             "final_rel_res_fp64": inf32.max_rel_res,
-                             "reached_tol": bool(st32 == 0),
-                             "note": f"plain FP32 PCG, capped at {args.fp32_max_iter} iterations"}
-        s32.close()
-        try:
-            extra["cpu_baseline"] = oracle_sample()
-        except Exception as e:  # the baseline never blocks the GPU line
-            extra["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
-
-    launches_per_step = int(info.launches)  # counted by the library inside the solve
-    line = {
-        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "precision": args.precision},
-        "solve": {"status": st, "iters_total": info.iters_total, "outer_steps": info.outer_steps,
-                  "max_rel_res_fp64": info.max_rel_res, "setup_ms": info.setup_ms,
-                  "kv_inner_ms": info.kv_inner_ms, "kv_inner_calls": info.kv_inner_calls,
-                  "kv_outer_ms": info.kv_outer_ms, "kv_outer_calls": info.kv_outer_calls,
-                  "precond_ms": info.precond_ms, "precond_calls": info.precond_calls,
-                  "step_times_s": times},
-        "roofline": roof,
-        "clocks": clocks,
-        "e2e": e2e,
-        "gpu_launches": launches_per_step,
-    }
-    line.update(extra)
-    if rank == 0:
-        print(json.dumps(line))
-    solver.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    if args.workload == "kv":
+        return run_kv(args)
+    return run_solve(args)
 
 
 if __name__ == "__main__":

@@ -82,11 +82,16 @@ typedef enum {
                           double-float K.V (FP32-pair arithmetic on the FP32
                           pipe, about 44 bits); stop and restart decisions use
                           the native FP64 residual                               */
-    KPCG_FP32X_IR = 5  /* as KPCG_FP32_IR, the inner K.V in FP32 on exact
+    KPCG_FP32X_IR = 5, /* as KPCG_FP32_IR, the inner K.V in FP32 on exact
                           pairwise differences: the scaled inputs stay split
                           into FP32 pairs (no per-point rounding), each entry
                           rounds once in FP32, row and column sums are
                           compensated; requires d <= 16                          */
+    KPCG_TCX_IR = 6    /* as KPCG_TC_IR, the inner K.V on per-point-exact
+                          tensor-core operands: the scaled inputs cut into five
+                          8-bit BF16 slices, the exponent summed level by level
+                          (FP32 roundings relative to the exponent itself),
+                          exp2 on the MUFU, compensated row sums; d <= 10       */
 } kpcg_precision;
 
 typedef struct {
@@ -111,6 +116,15 @@ typedef struct {
     int32_t profile;      /* 1: time every K.V and preconditioner call with CUDA
                              events on the handle's stream and report the sums
                              in kpcg_info; default 0                           */
+    int32_t wait_stall;   /* test hook of the bounded waits: 1 makes the MMA
+                             thread of the single-problem tensor-core kernels
+                             first wait on a barrier nothing arrives at, so the
+                             wait expires and the call returns KPCG_ERR_TIMEOUT;
+                             default 0                                          */
+    int64_t wait_limit_ns; /* limit of each wait inside the tensor-core kernels
+                             (ns); 0 = the default, 2 s; a wait that expires
+                             records an error, lets the kernel's own bulk copies
+                             land, frees its tensor memory and returns          */
 } kpcg_options;
 
 typedef struct {
@@ -125,12 +139,17 @@ typedef struct {
                              working-precision K.V calls (single modes)        */
     int32_t kv_inner_calls;
     int32_t kv_outer_calls;
-    double kv_outer_ms;   /* FP64 K.V calls of the outer loop and residuals    */
+    double kv_outer_ms;   /* double-float K.V calls of the outer loop's
+                             directions (mixed modes)                          */
     double precond_ms;    /* preconditioner applications                       */
     int32_t precond_calls;
     int32_t launches;     /* CUDA kernels this call launched (always filled)   */
     double precond_jitter; /* diagonal jitter the Nystrom inner matrix needed
                              (0 when it factored as built)                    */
+    double resid_ms;      /* (profile = 1) true-residual products: the native
+                             FP64 certifications and double-float steering
+                             residuals                                         */
+    int32_t resid_calls;
 } kpcg_info;
 
 /* Fill *opt with the defaults documented in kpcg_options. */
@@ -219,7 +238,10 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
  * impl 2: the KPCG_FP32X_IR inner kernel (exact differences of the split
  *         inputs, compensated sums) with exp2 on the MUFU (ex2.approx);
  * impl 3: the same with a polynomial exp2 on the FMA pipe (the one the
- *         solver uses); impl 2 and 3 need d <= 16. */
+ *         solver uses); impl 2 and 3 need d <= 16;
+ * impl 4: the KPCG_TCX_IR inner kernel (tcgen05 on sliced per-point-exact
+ *         operands, compensated row sums); d <= 10, a bounded wait that
+ *         expires returns KPCG_ERR_TIMEOUT. */
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 

@@ -18,6 +18,7 @@ from .binding import (  # noqa: F401
     KPCG_PREC_PITC,
     KPCG_PREC_SPECTRAL,
     KPCG_TC_IR,
+    KPCG_TCX_IR,
     Batch,
     KpcgError,
     LaplaceInfo,

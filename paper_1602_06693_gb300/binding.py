@@ -17,7 +17,8 @@ _LIB_PATH = os.path.join(HERE, "libkpcg.so")
 
 KPCG_PREC_NONE, KPCG_PREC_NYSTROM, KPCG_PREC_BLOCK_JACOBI, KPCG_PREC_FITC = 0, 1, 2, 3
 KPCG_PREC_SPECTRAL, KPCG_PREC_PITC = 4, 5
-KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64, KPCG_FP32X_IR = 0, 1, 2, 3, 4, 5
+KPCG_FP64, KPCG_FP32, KPCG_FP32_IR, KPCG_TC_IR, KPCG_DF64, KPCG_FP32X_IR, KPCG_TCX_IR = (
+    0, 1, 2, 3, 4, 5, 6)
 
 _STATUS = {
     0: "KPCG_OK", 1: "KPCG_ERR_ARG", 2: "KPCG_ERR_CUDA", 3: "KPCG_ERR_OOM",
@@ -58,6 +59,8 @@ class Options(ctypes.Structure):
         ("inner_max_iter", ctypes.c_int32),
         ("fcg_window", ctypes.c_int32),
         ("profile", ctypes.c_int32),
+        ("wait_stall", ctypes.c_int32),
+        ("wait_limit_ns", ctypes.c_int64),
     ]
 
 
@@ -76,6 +79,8 @@ class Info(ctypes.Structure):
         ("precond_calls", ctypes.c_int32),
         ("launches", ctypes.c_int32),
         ("precond_jitter", ctypes.c_double),
+        ("resid_ms", ctypes.c_double),
+        ("resid_calls", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -264,7 +264,7 @@ static void residual_f64(Ctx& h, const double* B, int64_t ldb, int c, const doub
     // columns per pass; from three columns on, one non-symmetric pass over up
     // to 16 columns computes each entry's exp fewer times.  double_float: the
     // double-float product instead (a residual that only steers the iteration)
-    h.prof.time(Profiler::KV_OUTER, st, [&] {
+    h.prof.time(Profiler::RESID, st, [&] {
         if (double_float)
             kv_df(h, X, ldx, c, B, ldb, R, h.ld, h.noise);
         else if (c >= 3 && h.dp <= 16)
@@ -307,7 +307,7 @@ bool col_converged(double rr, double bb, double tol, int tol_mode, int64_t n) {
 // single-precision solvers, the shifted inner noise for the mixed ones.
 static double precond_noise(const Ctx& h) {
     const bool mixed = h.opt.precision == KPCG_FP32_IR || h.opt.precision == KPCG_TC_IR ||
-                       h.opt.precision == KPCG_FP32X_IR;
+                       h.opt.precision == KPCG_FP32X_IR || h.opt.precision == KPCG_TCX_IR;
     return mixed ? h.noise * (1.0 + h.opt.inner_shift) : h.noise;
 }
 
@@ -453,6 +453,9 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
             },
             h.c32, its, br);
         iters_total += ran;
+        // a bounded wait that expired inside the inner products ends the solve
+        if (ops.timed_out && ops.timed_out())
+            fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         for (int k = 0; k < c; ++k) iters_col[k] += (its[k] < 0 ? -1 - its[k] : its[k]);
         convert_scale_cols<double, float>(Z, ld, d32, ld, n, c, cs, 0, st);
         // p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j over the window
@@ -519,12 +522,15 @@ static MixedOps single_ops(Ctx& h) {
     MixedOps o;
     const bool tc = (h.opt.precision == KPCG_TC_IR);
     const bool xf = (h.opt.precision == KPCG_FP32X_IR);
+    const bool tcx = (h.opt.precision == KPCG_TCX_IR);
     const float inner_noise = (float)(h.noise * (1.0 + h.opt.inner_shift));
     Ctx* hp = &h;
-    o.inner_mv = [hp, tc, xf, inner_noise](const float* V, int64_t ldv, int cc, float* O,
-                                           int64_t ldo) {
+    o.inner_mv = [hp, tc, xf, tcx, inner_noise](const float* V, int64_t ldv, int cc, float* O,
+                                                int64_t ldo) {
         Ctx& h = *hp;
-        if (tc)
+        if (tcx)
+            kv_tcx_apply(h, V, ldv, cc, O, ldo, inner_noise);
+        else if (tc)
             kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
         else if (xf)
             kv_xf(h, V, ldv, cc, O, ldo, inner_noise, 1);
@@ -556,7 +562,7 @@ static MixedOps single_ops(Ctx& h) {
                       double* R, std::vector<double>& rr, std::vector<double>& bb, bool certify) {
         residual_f64(*hp, B, ldb, cc, X, ldx, R, rr, bb, !certify);
     };
-    if (tc) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
+    if (tc || tcx) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
     return o;
 }
 
@@ -574,6 +580,8 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
         fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
     if (prec == KPCG_FP32X_IR && !kv_xf_supported(h))
         fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
+    if (prec == KPCG_TCX_IR && !kv_tcx_supported(h.d))
+        fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
     std::vector<int> iters_col((size_t)c, 0);
     int iters_total = 0, steps = 0, broken = 0;
     kpcg_status status = KPCG_OK;
@@ -728,6 +736,8 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
         info->kv_outer_calls = calls[Profiler::KV_OUTER];
         info->precond_ms = ms[Profiler::PRECOND];
         info->precond_calls = calls[Profiler::PRECOND];
+        info->resid_ms = ms[Profiler::RESID];
+        info->resid_calls = calls[Profiler::RESID];
         info->launches = (int)(launch_count() - launches0);
         info->precond_jitter = h.P.ready ? h.P.jitter : 0.0;
     } else {
@@ -868,6 +878,8 @@ void kpcg_default_options(kpcg_options* opt) {
     opt->inner_max_iter = 2000;
     opt->fcg_window = 16;
     opt->profile = 0;
+    opt->wait_stall = 0;
+    opt->wait_limit_ns = 0;
 }
 
 const char* kpcg_status_string(kpcg_status s) {
@@ -888,7 +900,7 @@ const char* kpcg_status_string(kpcg_status s) {
 static void check_opts(const kpcg_options* o) {
     if (o->max_iter < 0 || o->max_outer < 0 || o->check_every < 1 || o->max_restarts < 0)
         fail(KPCG_ERR_ARG, "invalid options");
-    if (o->precision < KPCG_FP64 || o->precision > KPCG_FP32X_IR)
+    if (o->precision < KPCG_FP64 || o->precision > KPCG_TCX_IR)
         fail(KPCG_ERR_ARG, "invalid precision");
     if (o->tol_mode != 0 && o->tol_mode != 1) fail(KPCG_ERR_ARG, "invalid tol_mode");
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) fail(KPCG_ERR_ARG, "inner_tol not in (0,1)");
@@ -896,6 +908,9 @@ static void check_opts(const kpcg_options* o) {
         fail(KPCG_ERR_ARG, "inner_shift must be >= 0");
     if (o->inner_max_iter < 1 || o->fcg_window < 1 || o->fcg_window > 64)
         fail(KPCG_ERR_ARG, "inner_max_iter >= 1 and fcg_window in [1, 64] required");
+    if (o->wait_stall != 0 && o->wait_stall != 1) fail(KPCG_ERR_ARG, "wait_stall must be 0 or 1");
+    if (o->wait_limit_ns < 0 || o->wait_limit_ns > (int64_t)60000000000)
+        fail(KPCG_ERR_ARG, "wait_limit_ns must be in [0, 60 s]");
 }
 
 kpcg_status kpcg_create(const float* X, int64_t n, int32_t d, const double* log_theta, int32_t ard,
@@ -1108,6 +1123,12 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             if (!kpcg::kv_xf_supported(*h))
                 fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
             kpcg::kv_xf(*h, V, ldv, c, O, ldo, (float)h->noise, impl - 2);
+        } else if (impl == 4) {
+            if (!kpcg::kv_tcx_supported(h->d))
+                fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
+            kpcg::kv_tcx_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         } else {
             fail(KPCG_ERR_ARG, "unknown impl");
         }

@@ -342,7 +342,7 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
                 // certify: native FP64 (b - K x cancels terms up to ~|x|/|b| ~
                 // 1/sigma^2 larger than the result, beyond the double-float
                 // product's reach); steering only: double-float
-                M.prof.time(Profiler::KV_OUTER, M.stream, [&] {
+                M.prof.time(Profiler::RESID, M.stream, [&] {
                     if (certify)
                         kv_f64(h.xs64.p, h.n, h.dp, h.c0_64(), h.noise, Xm + off * ldx, ldx, c,
                                Bm + off * ldb, ldb, R + off * M.ld, M.ld, h.kvws, M.stream);
@@ -421,6 +421,8 @@ kpcg_status kpcg_batch_solve(kpcg_batch_t b, const double* B, int64_t ld, int32_
             info->kv_outer_calls = calls[Profiler::KV_OUTER];
             info->precond_ms = ms[Profiler::PRECOND];
             info->precond_calls = calls[Profiler::PRECOND];
+            info->resid_ms = ms[Profiler::RESID];
+            info->resid_calls = calls[Profiler::RESID];
             info->launches = (int)(launch_count() - launches0);
             double jit = 0.0;
             for (auto* h : b->sub) jit = std::max(jit, h->P.ready ? h->P.jitter : 0.0);

@@ -19,7 +19,10 @@ struct CgBufs {
 // Device-time accounting of the hot calls (opt.profile): CUDA events around
 // each call on the handle's stream, summed when the call returns.
 struct Profiler {
-    enum { KV_INNER = 0, KV_OUTER = 1, PRECOND = 2, NCAT = 3 };
+    // KV_INNER: reduced-precision products (mixed modes) or the working-precision
+    // products (single modes); KV_OUTER: outer direction products; RESID: true
+    // residuals (FP64 certification, double-float steering); PRECOND: applies
+    enum { KV_INNER = 0, KV_OUTER = 1, PRECOND = 2, RESID = 3, NCAT = 4 };
     bool on = false;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[NCAT];
@@ -129,6 +132,11 @@ struct Ctx {
     DevBuf<uint16_t> tcA, tcB;
     DevBuf<float> tcV, tcPart;
     DevBuf<int> tc_err;
+    // per-point-exact tensor-core operands (kv_tcx_apply), rebuilt when theta changes
+    int tcx_version = -1, tcx_kch = 0, tcx_nmma = 0;
+    float tcx_escale = 1.f;
+    DevBuf<uint16_t> tcxA, tcxB;
+    DevBuf<double> tcxPart, tcx_max;
     // double-float operands (kv_df.cu), rebuilt when theta changes
     int df_version = -1;
     float df_c0h = 0.f, df_c0l = 0.f;
@@ -163,6 +171,12 @@ void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, in
 void kv_xf(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise,
            int expp);
 bool kv_xf_supported(const Ctx& h);
+// Tensor-core K.V on per-point-exact sliced operands (kv_tc.cu; d <= 10):
+// FP32 in and out, FP32 exponent rounding relative to the exponent itself,
+// compensated row sums.
+void kv_tcx_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                  float noise);
+bool kv_tcx_supported(int d);
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);

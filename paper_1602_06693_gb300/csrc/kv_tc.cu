@@ -152,6 +152,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// 32 columns without the wait (tmem_wait_ld() completes them).
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ float ex2(float a) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
@@ -235,6 +252,142 @@ __global__ void tc_prep_kernel(const double* __restrict__ xs64, int64_t n, int64
     put(bbase, 6 * d + 5, one);
 }
 
+// ---------------------------------------------------------------------------
+// Per-point-exact operands (kv_tcx_apply).  The BF16 x3 split above rounds
+// every scaled input to ~2^-24: a per-point perturbation, which moves whole
+// rows of K together and, against a small noise term, is amplified by
+// K_y^{-1} like ||K|| / sigma^2.  Here each x'/S (S a power of two >= max|x'|)
+// is cut into TCX_S slices of 8 bits, x'/S = sum_a s_a 2^(-7-8a) with integer
+// s_a in [-128, 128] (exact in BF16), and the exponent, in units of
+// 2^-14 S^2,
+//     a_ij 2^14 / S^2 = qh_i + qh_j + 2 sum_{a+b<TCX_L} s_a(i).s_b(j) 2^(-8(a+b)),
+//     qh_i = (log2(s^2)/2 - |x'_i|^2) 2^14 / S^2,
+// is one MMA chain ordered by level k = a + b, each level's terms pre-scaled
+// by 2^(-8k) (exact in BF16).  Every level-0 product is an integer below 2^15
+// and their sum stays below 2^24, so level 0 accumulates exactly; it already
+// holds a_ij to about 2^-8 of |x'|^2, so the later, smaller levels are added
+// to an accumulator of the size of a_ij itself, and the FP32 roundings are
+// relative to a_ij, independent per entry.  qh_i enters as three BF16 parts
+// of its integer part at level 0 (paired with a column of ones) and one
+// 8-bit part of its fraction per later level.  The dropped levels (a + b >=
+// TCX_L) pair two pseudo-random low slices, an error independent per entry of
+// order 2^-40 |x'|^2.
+constexpr int TCX_S = 5;  // slices of x'/S
+constexpr int TCX_L = 5;  // levels kept
+struct TcxLayout {
+    int off[TCX_L + 1];  // first column of each level; off[TCX_L] = K
+    int d;
+};
+
+TcxLayout tcx_layout(int d) {
+    TcxLayout L;
+    L.d = d;
+    int o = 0;
+    for (int k = 0; k < TCX_L; ++k) {
+        L.off[k] = o;
+        const int cols = (k == 0) ? d + 6 : (k + 1) * d + 2;
+        o += (cols + 15) / 16 * 16;
+    }
+    L.off[TCX_L] = o;
+    return L;
+}
+
+__global__ void tcx_absmax_kernel(const double* __restrict__ xs64, int64_t cnt,
+                                  double* __restrict__ out) {
+    __shared__ double sh[1024];
+    double m = 0.0;
+    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(xs64[e]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void tcx_prep_kernel(const double* __restrict__ xs64, int64_t n, int64_t n_pad, int dp,
+                                int kch, double scale, double c0, double invS, double qscale,
+                                TcxLayout L, __nv_bfloat16* __restrict__ Aop,
+                                __nv_bfloat16* __restrict__ Bop) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const int d = L.d;
+    const int kdim = kch * KC;
+    const int64_t tile = i / TM;
+    const int r = (int)(i % TM);
+    uint8_t* abase = reinterpret_cast<uint8_t*>(Aop) + (size_t)tile * kch * SUB * 2;
+    uint8_t* bbase = reinterpret_cast<uint8_t*>(Bop) + (size_t)tile * kch * SUB * 2;
+    auto put = [&](uint8_t* base, int k, double v) {
+        const int kc = k / KC, kk = k % KC;
+        *reinterpret_cast<__nv_bfloat16*>(base + (size_t)kc * SUB * 2 + swz_off(r, kk)) =
+            __double2bfloat16(v);
+    };
+    for (int k = 0; k < kdim; ++k) {
+        put(abase, k, 0.0);
+        put(bbase, k, 0.0);
+    }
+    if (i >= n) {  // padding column of K: exp2(-huge) = 0
+        put(bbase, d + 3, -1e30);
+        return;
+    }
+    double sl[TCX_S][10];
+    double nrm = 0.0;
+    for (int q = 0; q < d; ++q) {
+        const double x = xs64[i * dp + q] * scale;
+        nrm += x * x;
+        double t = x * invS * 128.0;
+        for (int a = 0; a < TCX_S; ++a) {
+            const double v = rint(t);
+            sl[a][q] = v;
+            t = (t - v) * 256.0;
+        }
+    }
+    const double qh = (0.5 * c0 - nrm) * qscale;
+    const double I = rint(qh);
+    double f = qh - I;
+    const double I2 = rint(I / 65536.0);
+    const double rem = I - I2 * 65536.0;
+    const double I1 = rint(rem / 256.0);
+    const double I0 = rem - I1 * 256.0;
+    double fr[TCX_L];
+    fr[0] = 0.0;
+    for (int k = 1; k < TCX_L; ++k) {
+        const double t = f * 256.0;
+        fr[k] = rint(t);
+        f = t - fr[k];
+    }
+    // level 0
+    for (int q = 0; q < d; ++q) {
+        put(abase, q, sl[0][q]);
+        put(bbase, q, 2.0 * sl[0][q]);
+    }
+    const double parts[3] = {I2 * 65536.0, I1 * 256.0, I0};
+    for (int u = 0; u < 3; ++u) {
+        put(abase, d + u, parts[u]);
+        put(bbase, d + u, 1.0);
+        put(abase, d + 3 + u, 1.0);
+        put(bbase, d + 3 + u, parts[u]);
+    }
+    // levels 1 .. TCX_L-1, pre-scaled by 2^(-8k)
+    for (int k = 1; k < TCX_L; ++k) {
+        const int base = L.off[k];
+        const double sc = ldexp(1.0, -8 * k);
+        for (int a = 0; a <= k; ++a) {
+            const int b = k - a;
+            for (int q = 0; q < d; ++q) {
+                put(abase, base + a * d + q, sl[a][q] * sc);
+                put(bbase, base + a * d + q, 2.0 * sl[b][q]);
+            }
+        }
+        const int e1 = base + (k + 1) * d;
+        put(abase, e1, fr[k] * sc);
+        put(bbase, e1, 1.0);
+        put(abase, e1 + 1, sc);
+        put(bbase, e1 + 1, fr[k]);
+    }
+}
+
 __global__ void tc_stage_v_kernel(const float* __restrict__ V, int64_t ldv, int64_t n,
                                   int64_t n_pad, float* __restrict__ Vs) {
     const int k = blockIdx.y;
@@ -245,35 +398,45 @@ __global__ void tc_stage_v_kernel(const float* __restrict__ V, int64_t ldv, int6
 
 template <int KCH, int CB>
 struct TcSmem {
+    static constexpr int kNst = KCH >= 3 ? 3 : NSTAGE;          // ring depth (smem budget)
     static constexpr uint32_t kSub = SUB * 2;                    // 16 KB
     static constexpr uint32_t kA = KCH * kSub;                   // A tile
     static constexpr uint32_t kBst = KCH * kSub;                 // B part of a stage
     static constexpr uint32_t kVst = CB * TN * 4;                // V part of a stage
     static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
     static constexpr uint32_t kBars = 1024;
-    static constexpr uint32_t kTotal = 1024 /*align slack*/ + kA + NSTAGE * kStage + kBars;
+    static constexpr uint32_t kTotal = 1024 /*align slack*/ + kA + kNst * kStage + kBars;
 };
 
-template <int KCH, int CB>
+// EXACT = 0: the operands of tc_prep_kernel, FP32 contraction, FP32 partials.
+// EXACT = 1: the per-point-exact operands of tcx_prep_kernel (nmma MMAs of
+// K = 16 per tile, the accumulator times escale is the exp2 argument), row
+// sums compensated (TwoSum into an FP32 pair), FP64 partials in part64.
+template <int KCH, int CB, int EXACT>
 __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
     kv_tc_kernel(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
                  const float* __restrict__ Vs, int64_t n, int64_t n_pad, int ncols,
-                 int tiles_per_split, float* __restrict__ part, int* __restrict__ err) {
+                 int tiles_per_split, float* __restrict__ part, int* __restrict__ err,
+                 int nmma, float escale, double* __restrict__ part64, uint64_t wait_ns,
+                 int stall) {
     using S = TcSmem<KCH, CB>;
+    constexpr int NST = S::kNst;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sStage = smem + S::kA;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kA + NSTAGE * S::kStage);
-    uint64_t* full = bars;                  // [NSTAGE] bulk copies landed
-    uint64_t* empty = bars + NSTAGE;        // [NSTAGE] MMA done + epilogue done with V
-    uint64_t* tfull = bars + 2 * NSTAGE;    // [2] accumulator ready
-    uint64_t* tempty = bars + 2 * NSTAGE + 2;  // [2] accumulator drained
-    uint64_t* afull = bars + 2 * NSTAGE + 4;
-    uint64_t* done = bars + 2 * NSTAGE + 5;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 6);
-    float* comb = reinterpret_cast<float*>(sStage);  // reused after the loop: [CB][TM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kA + NST * S::kStage);
+    uint64_t* full = bars;                  // [NST] bulk copies landed
+    uint64_t* empty = bars + NST;           // [NST] MMA done + epilogue done with V
+    uint64_t* tfull = bars + 2 * NST;       // [2] accumulator ready
+    uint64_t* tempty = bars + 2 * NST + 2;  // [2] accumulator drained
+    uint64_t* afull = bars + 2 * NST + 4;
+    uint64_t* done = bars + 2 * NST + 5;
+    uint64_t* never = bars + 2 * NST + 6;   // test hook: no thread ever arrives here
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 7);
+    float* comb = reinterpret_cast<float*>(sStage);    // reused after the loop: [CB][TM]
+    float2* comb2 = reinterpret_cast<float2*>(sStage);  // EXACT: [CB][TM] pairs
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -284,7 +447,7 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
     const int ntiles = (int)max((int64_t)0, jt1 - jt0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1 + NEPI);
         }
@@ -294,6 +457,7 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
         }
         mbar_init(afull, 1);
         mbar_init(done, 1);
+        mbar_init(never, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -308,11 +472,11 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint64_t deadline = gtimer() + kWaitNs;
+    const uint64_t deadline = gtimer() + wait_ns;
     int fail = 0;
-    float acc[CB];
+    float acc[CB], cmp[CB];  // row sums; EXACT: their compensation terms
 #pragma unroll
-    for (int k = 0; k < CB; ++k) acc[k] = 0.f;
+    for (int k = 0; k < CB; ++k) acc[k] = cmp[k] = 0.f;
     const int quarter = warp & 3;         // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;     // epilogue: column half of a tile
     const int row = quarter * 32 + lane;  // epilogue: row of the tile
@@ -322,9 +486,10 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
             // A tile once, then B + V tiles through the ring
             mbar_expect_tx(afull, S::kA);
             bulk_g2s(sA, Aop + (size_t)rt * KCH * SUB, S::kA, afull);
-            for (int t = 0; t < ntiles; ++t) {
-                const int s = t % NSTAGE;
-                if (!mbar_wait(&empty[s], ((uint32_t)(t / NSTAGE) & 1u) ^ 1u, deadline)) {
+            int t = 0;
+            for (; t < ntiles; ++t) {
+                const int s = t % NST;
+                if (!mbar_wait(&empty[s], ((uint32_t)(t / NST) & 1u) ^ 1u, deadline)) {
                     fail = 1;
                     break;
                 }
@@ -336,15 +501,23 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                     bulk_g2s(st + S::kBst + (size_t)k * TN * 4, Vs + (size_t)k * n_pad + jt * TN,
                              TN * 4, &full[s]);
             }
+            // let the copies this thread issued land before the CTA exits (on
+            // the failure path some may still be in flight); own, fresh limit
+            const uint64_t dl2 = gtimer() + 200000000ull;
+            for (int q = (t > NST ? t - NST : 0); q < t; ++q)
+                (void)mbar_wait(&full[q % NST], (uint32_t)(q / NST) & 1u, dl2);
+            (void)mbar_wait(afull, 0, dl2);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            if (!mbar_wait(afull, 0, deadline)) fail = 1;
+            // test hook: a wait on a barrier nothing arrives at runs out
+            if (stall && !mbar_wait(never, 0, deadline)) fail = 1;
+            if (!fail && !mbar_wait(afull, 0, deadline)) fail = 1;
             fence_after();
             const uint32_t a0 = su32(sA);
             for (int t = 0; t < ntiles && !fail; ++t) {
-                const int s = t % NSTAGE, b = t & 1;
-                if (!mbar_wait(&full[s], (uint32_t)(t / NSTAGE) & 1u, deadline) ||
+                const int s = t % NST, b = t & 1;
+                if (!mbar_wait(&full[s], (uint32_t)(t / NST) & 1u, deadline) ||
                     !mbar_wait(&tempty[b], ((uint32_t)(t >> 1) & 1u) ^ 1u, deadline)) {
                     fail = 1;
                     break;
@@ -356,6 +529,8 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                 for (int kc = 0; kc < KCH; ++kc)
 #pragma unroll
                     for (int kk = 0; kk < KC / 16; ++kk) {
+                        // the exact operands stop at nmma chunks of K = 16
+                        if (EXACT && kc * (KC / 16) + kk >= nmma) continue;
                         const uint32_t off = (uint32_t)kc * S::kSub + (uint32_t)kk * 32;
                         mma_bf16(dt, sdesc(a0 + off), sdesc(b0 + off), (kc | kk) ? 1u : 0u);
                     }
@@ -368,7 +543,7 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
         }
     } else {
         for (int t = 0; t < ntiles; ++t) {
-            const int s = t % NSTAGE, b = t & 1;
+            const int s = t % NST, b = t & 1;
             // warp-uniform decision: the TMEM loads below are .sync.aligned
             const bool ok = __all_sync(0xffffffffu,
                                        mbar_wait(&tfull[b], (uint32_t)(t >> 1) & 1u, deadline));
@@ -379,35 +554,80 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
             fence_after();
             const float* vst =
                 reinterpret_cast<const float*>(sStage + (size_t)s * S::kStage + S::kBst);
-#pragma unroll 1
-            for (int ch = 0; ch < 4; ++ch) {
-                const int col0 = half * 64 + ch * 16;
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + col0), r);
-                float ev[16];
+            // this thread's 64 columns in NP passes of W (one TMEM wait per
+            // pass; NP = 2 where two CTAs share an SM and registers are short);
+            // the accumulator goes back to the MMA thread after the last load
+            constexpr int NP = (!EXACT && (CB >= 8 || (KCH == 1 && CB >= 2))) ? 2 : 1;
+            constexpr int W = 64 / NP;
+            // CH independent accumulation chains per column (latency, not
+            // throughput, bounds a single chain at 2 epilogue warps per scheduler)
+            constexpr int CH = (CB >= 4) ? 2 : 4;
+            const uint32_t taddr =
+                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + half * 64);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) ev[j] = ex2(__uint_as_float(r[j]));
+            for (int ps = 0; ps < NP; ++ps) {
+                uint32_t r[W];
+#pragma unroll
+                for (int w = 0; w < W; w += 32) tmem_ld32_nw(taddr + ps * W + w, r + w);
+                tmem_wait_ld();
+                if (ps == NP - 1) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    r[j] = __float_as_uint(
+                        ex2(EXACT ? __uint_as_float(r[j]) * escale : __uint_as_float(r[j])));
 #pragma unroll
                 for (int k = 0; k < CB; ++k) {
-                    const float4* vp = reinterpret_cast<const float4*>(vst + k * TN + col0);
-                    float a = acc[k];
+                    const float4* vp =
+                        reinterpret_cast<const float4*>(vst + k * TN + half * 64 + ps * W);
+                    float a[CH], cc[CH];
 #pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4) {
+                    for (int u = 0; u < CH; ++u) a[u] = cc[u] = 0.f;
+#pragma unroll
+                    for (int j4 = 0; j4 < W / 4; ++j4) {
                         const float4 v = vp[j4];
-                        a = fmaf(ev[4 * j4 + 0], v.x, a);
-                        a = fmaf(ev[4 * j4 + 1], v.y, a);
-                        a = fmaf(ev[4 * j4 + 2], v.z, a);
-                        a = fmaf(ev[4 * j4 + 3], v.w, a);
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = u % CH;
+                            const float e = __uint_as_float(r[4 * j4 + u]);
+                            if (EXACT) {  // TwoSum of every product into (a, cc)
+                                const float pv = e * vv[u];
+                                const float sum = a[q] + pv;
+                                const float bp = sum - a[q];
+                                cc[q] += (a[q] - (sum - bp)) + (pv - bp);
+                                a[q] = sum;
+                            } else {
+                                a[q] = fmaf(e, vv[u], a[q]);
+                            }
+                        }
                     }
-                    acc[k] = a;
+                    if (EXACT) {
+                        // fold the chains into (acc, cmp) with TwoSum, then Fast2Sum
+#pragma unroll
+                        for (int u = 0; u < CH; ++u) {
+                            const float sum = acc[k] + a[u];
+                            const float bp = sum - acc[k];
+                            cmp[k] += ((acc[k] - (sum - bp)) + (a[u] - bp)) + cc[u];
+                            acc[k] = sum;
+                        }
+                        const float sum = acc[k] + cmp[k];
+                        cmp[k] = cmp[k] - (sum - acc[k]);
+                        acc[k] = sum;
+                    } else {
+                        float t = a[0];
+#pragma unroll
+                        for (int u = 1; u < CH; ++u) t += a[u];
+                        acc[k] += t;
+                    }
                 }
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tempty[b]);
-                mbar_arrive(&empty[s]);
-            }
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
     // every role ends here
@@ -418,14 +638,25 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
     // add the two column halves of each row (ring memory is free now)
     if (warp >= 2 && half == 1)
 #pragma unroll
-        for (int k = 0; k < CB; ++k) comb[k * TM + row] = acc[k];
+        for (int k = 0; k < CB; ++k) {
+            if (EXACT)
+                comb2[k * TM + row] = make_float2(acc[k], cmp[k]);
+            else
+                comb[k * TM + row] = acc[k];
+        }
     __syncthreads();
     if (warp >= 2 && half == 0) {
         const int64_t i = rt * TM + row;
 #pragma unroll
         for (int k = 0; k < CB; ++k) {
-            const float v = acc[k] + comb[k * TM + row];
-            if (k < ncols && i < n) part[((size_t)blockIdx.y * CB + k) * n_pad + i] = v;
+            if (k >= ncols || i >= n) continue;
+            if (EXACT) {
+                const float2 o = comb2[k * TM + row];
+                part64[((size_t)blockIdx.y * CB + k) * n_pad + i] =
+                    ((double)acc[k] + (double)cmp[k]) + ((double)o.x + (double)o.y);
+            } else {
+                part[((size_t)blockIdx.y * CB + k) * n_pad + i] = acc[k] + comb[k * TM + row];
+            }
         }
     }
     if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
@@ -448,21 +679,36 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int64_t n_pad, 
 }
 
 
-template <int KCH, int CB>
+template <int KCH, int CB, int EXACT = 0>
 void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* Vs,
                int64_t n_pad, int ncols, float* part, int nsplit, int tps, int* err,
-               cudaStream_t st) {
+               cudaStream_t st, int nmma = 0, float escale = 1.f, double* part64 = nullptr) {
+    const uint64_t wait_ns =
+        h.opt.wait_limit_ns > 0 ? (uint64_t)h.opt.wait_limit_ns : kWaitNs;
     using S = TcSmem<KCH, CB>;
     static bool attr = false;
     if (!attr) {
-        KPCG_CUDA(cudaFuncSetAttribute(kv_tc_kernel<KCH, CB>,
+        KPCG_CUDA(cudaFuncSetAttribute(kv_tc_kernel<KCH, CB, EXACT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal));
         attr = true;
     }
     dim3 grid((unsigned)(n_pad / TM), (unsigned)nsplit);
-    kv_tc_kernel<KCH, CB><<<grid, NWARPS * 32, S::kTotal, st>>>(A, B, Vs, h.n, n_pad, ncols, tps,
-                                                                part, err);
-    KPCG_LAUNCHED("kv_tc_kernel");
+    kv_tc_kernel<KCH, CB, EXACT><<<grid, NWARPS * 32, S::kTotal, st>>>(
+        A, B, Vs, h.n, n_pad, ncols, tps, part, err, nmma, escale, part64, wait_ns,
+        h.opt.wait_stall ? 1 : 0);
+    KPCG_LAUNCHED(EXACT ? "kv_tcx_kernel" : "kv_tc_kernel");
+}
+
+// O = noise V + the FP64 partial sums of the exact kernel, rounded to FP32.
+__global__ void tcx_reduce_kernel(const double* __restrict__ part, int64_t n_pad, int nsplit,
+                                  int cb, int ncols, const float* __restrict__ V, int64_t ldv,
+                                  float noise, float* __restrict__ O, int64_t ldo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n || k >= ncols) return;
+    double s = (double)noise * (double)V[i + (int64_t)k * ldv];
+    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * cb + k) * n_pad + i];
+    O[i + (int64_t)k * ldo] = (float)s;
 }
 
 }  // namespace
@@ -541,6 +787,92 @@ void kv_tc_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t l
             part, n_pad, nsplit, cb, ncols, V + (int64_t)k0 * ldv, ldv, noise,
             O + (int64_t)k0 * ldo, ldo, n);
         KPCG_LAUNCHED("tc_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
+bool kv_tcx_supported(int d) { return d >= 1 && d <= 10; }
+
+static void tcx_prepare(Ctx& h) {
+    if (h.tcx_version == h.theta_version) return;
+    if (!kv_tcx_supported(h.d)) fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int64_t n_pad = ((n + TM - 1) / TM) * TM;
+    const TcxLayout L = tcx_layout(h.d);
+    const int kch = (L.off[TCX_L] + KC - 1) / KC;
+    double* mx = h.tcx_max.need(1);
+    tcx_absmax_kernel<<<1, 1024, 0, st>>>(h.xs64.p, n * h.dp, mx);
+    KPCG_LAUNCHED("tcx_absmax_kernel");
+    double hmax = 0.0;
+    KPCG_CUDA(cudaMemcpyAsync(&hmax, mx, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KPCG_CUDA(cudaStreamSynchronize(st));
+    const double scale = std::sqrt(kLog2e);
+    const double xmax = hmax * scale;
+    double S = 1.0;
+    while (S < xmax) S *= 2.0;
+    while (S > 2.0 * xmax && S > 1.0 / 1024.0 && xmax > 0.0) S *= 0.5;
+    h.tcxA.need((size_t)n_pad * kch * KC);
+    h.tcxB.need((size_t)n_pad * kch * KC);
+    tcx_prep_kernel<<<(unsigned)((n_pad + 127) / 128), 128, 0, st>>>(
+        h.xs64.p, n, n_pad, h.dp, kch, scale, std::log2(h.s2), 1.0 / S, 16384.0 / (S * S), L,
+        reinterpret_cast<__nv_bfloat16*>(h.tcxA.p), reinterpret_cast<__nv_bfloat16*>(h.tcxB.p));
+    KPCG_LAUNCHED("tcx_prep_kernel");
+    h.tcx_kch = kch;
+    h.tcx_nmma = L.off[TCX_L] / 16;
+    h.tcx_escale = (float)(S * S / 16384.0);
+    h.tcx_version = h.theta_version;
+    if (!h.tc_err.p) {
+        int* e = h.tc_err.need(1);
+        KPCG_CUDA(cudaMemsetAsync(e, 0, sizeof(int), st));
+    }
+}
+
+void kv_tcx_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                  float noise) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    if (n <= 0 || c <= 0) return;
+    const int64_t n_pad = ((n + TM - 1) / TM) * TM;
+    tcx_prepare(h);
+    const int kch = h.tcx_kch;
+    if (kch != 2 && kch != 3) fail(KPCG_ERR_ARG, "internal: exact operand layout");
+    const int n_ct = (int)(n_pad / TN);
+    const int n_rt = (int)(n_pad / TM);
+    // one CTA per SM (about 200 KB of shared memory each): about four waves
+    int nsplit = std::max(1, std::min(n_ct, (sm_count_tc() * 4 + n_rt - 1) / n_rt));
+    const int tps = (n_ct + nsplit - 1) / nsplit;
+    nsplit = (n_ct + tps - 1) / tps;
+    const int max_cb = 8;
+    float* Vs = h.tcV.need((size_t)n_pad * max_cb);
+    double* part = h.tcxPart.need((size_t)nsplit * max_cb * n_pad);
+    const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(h.tcxA.p);
+    const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(h.tcxB.p);
+    for (int k0 = 0; k0 < c;) {
+        const int rem = c - k0;
+        const int cb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int ncols = std::min(cb, rem);
+        tc_stage_v_kernel<<<dim3((unsigned)std::min<int64_t>((n_pad + 255) / 256, 2048),
+                                 (unsigned)ncols),
+                            256, 0, st>>>(V + (int64_t)k0 * ldv, ldv, n, n_pad, Vs);
+        KPCG_LAUNCHED("tc_stage_v_kernel");
+#define KPCG_TCX_CASE(KCHV, CBV)                                                             \
+    if (kch == KCHV && cb == CBV)                                                            \
+        launch_tc<KCHV, CBV, 1>(h, A, B, Vs, n_pad, ncols, nullptr, nsplit, tps, h.tc_err.p, st, \
+                                h.tcx_nmma, h.tcx_escale, part);
+        KPCG_TCX_CASE(2, 1)
+        KPCG_TCX_CASE(2, 2)
+        KPCG_TCX_CASE(2, 4)
+        KPCG_TCX_CASE(2, 8)
+        KPCG_TCX_CASE(3, 1)
+        KPCG_TCX_CASE(3, 2)
+        KPCG_TCX_CASE(3, 4)
+        KPCG_TCX_CASE(3, 8)
+#undef KPCG_TCX_CASE
+        tcx_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)ncols), 256, 0, st>>>(
+            part, n_pad, nsplit, cb, ncols, V + (int64_t)k0 * ldv, ldv, noise,
+            O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("tcx_reduce_kernel");
         k0 += ncols;
     }
 }
