@@ -50,9 +50,10 @@ WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum 
 # profiles/precision_n65536.md.
 HEADLINE_PREC = "tc_ir"
 MODE_OPTS = {
-    "tc_ir": dict(inner_shift=4.0, inner_tol=0.1),
+    "tc_ir": dict(inner_shift=2.0, inner_tol=0.1),
     "fp32_ir": dict(inner_shift=4.0, inner_tol=0.1),
     "xf_ir": dict(inner_shift=0.25, inner_tol=0.3),
+    "tcx_ir": dict(inner_shift=0.1, inner_tol=0.5),
     "df64": {},
     "fp64": {},
 }
@@ -60,7 +61,7 @@ MODE_OPTS = {
 
 def mode_id(kpcg, name):
     return {"tc_ir": kpcg.KPCG_TC_IR, "fp32_ir": kpcg.KPCG_FP32_IR, "xf_ir": kpcg.KPCG_FP32X_IR,
-            "df64": kpcg.KPCG_DF64, "fp64": kpcg.KPCG_FP64}[name]
+            "tcx_ir": kpcg.KPCG_TCX_IR, "df64": kpcg.KPCG_DF64, "fp64": kpcg.KPCG_FP64}[name]
 
 
 def kv_algorithmic(n, d, c):
@@ -923,8 +924,10 @@ def solve_once(kpcg, X, y, p, idx, opt, stream, kind="nystrom", size=M_INDUCING,
 DTYPES = {"tc_ir": "bf16x3 exponent, f32 inner, f64 outer (double-float directions, fp64 "
                    "certified residual)",
           "fp32_ir": "f32 inner, f64 outer", "xf_ir": "f32 inner (exact differences), f64 outer",
+          "tcx_ir": "sliced bf16 exponent, f32 inner, f64 outer",
           "df64": "double-float iterations, fp64 certified residual", "fp64": "f64"}
 KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
+            "tcx_ir": "kv_tcx_kernel (tcgen05 sliced exponent, compensated contraction)",
             "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
             "df64": "kv_df_sym_kernel (double-float)", "fp64": "kv_f64_sym_kernel (FP64)"}
 # DRAM bytes per launch from ncu captures (profiles/), by kernel name; a
@@ -1136,11 +1139,17 @@ def comparisons(kpcg, X, y, p, idx, stream, mode, extra_opts, args):
                                "rel_res_fp64": info.max_rel_res,
                                "note": f"same solver, block-Jacobi blocks of 512, at most "
                                        f"{args.bj_max_iter} iterations"}
-    if mode != "df64":
-        od = solve_options(kpcg, "df64", profile=0)
+    # the other solvers of the library on the same system, from scratch
+    others = {"df64": "double-float PCG, FP64-certified", "xf_ir": "exact-difference FP32 inner",
+              "tcx_ir": "sliced tensor-core inner"}
+    for m, what in others.items():
+        if m == mode:
+            continue
+        od = solve_options(kpcg, m, profile=0)
         info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, idx, od, stream)
-        out["df64"] = {"status": st, "time_s": tot_ms / 1e3, "iters": info.iters_total,
-                       "rel_res_fp64": info.max_rel_res}
+        out[m] = {"what": what, "status": st, "time_s": tot_ms / 1e3, "iters": info.iters_total,
+                  "outer_steps": info.outer_steps, "rel_res_fp64": info.max_rel_res,
+                  "inner_shift": od.inner_shift, "inner_tol": od.inner_tol}
     return out
 
 
@@ -1202,7 +1211,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kpcg", choices=["kpcg", "reference"])
     ap.add_argument("--precision", default="auto",
-                    choices=["auto", "tc_ir", "fp32_ir", "xf_ir", "df64", "fp64"])
+                    choices=["auto", "tc_ir", "fp32_ir", "xf_ir", "tcx_ir", "df64", "fp64"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--fp32-max-iter", type=int, default=3000)

@@ -125,6 +125,11 @@ typedef struct {
                              (ns); 0 = the default, 2 s; a wait that expires
                              records an error, lets the kernel's own bulk copies
                              land, frees its tensor memory and returns          */
+    int32_t inner_f64;    /* KPCG_TCX_IR: 1 runs the inner PCG on FP64 vectors
+                             (the sliced tensor-core product takes them as FP32
+                             pairs and returns FP64), so the inner solve is
+                             limited by the operator, not by FP32 vectors;
+                             default 0                                          */
 } kpcg_options;
 
 typedef struct {
@@ -225,7 +230,9 @@ kpcg_status kpcg_precond_pitc(kpcg_t h, int64_t m, const int64_t* idx, int64_t b
 /* O = (K + sigma^2 I) V for c columns (device float64, column-major), the
  * matrix-free product of Sec. 2.1.  impl 0: entries and sums in native FP64;
  * impl 1: the double-float kernel of KPCG_DF64 (FP32-pair arithmetic, about
- * 44 bits per entry, sums carried as FP32 pairs and added in FP64). */
+ * 44 bits per entry, sums carried as FP32 pairs and added in FP64);
+ * impl 2: the sliced tensor-core kernel of KPCG_TCX_IR with V as FP32 pairs
+ * (entries to FP32 accuracy, compensated sums, FP64 out; d <= 10). */
 kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
                             int64_t ldo, int32_t impl);
 
@@ -261,9 +268,11 @@ kpcg_status kpcg_solve(kpcg_t h, const double* B, int64_t ldb, int32_t c, double
                        kpcg_info* info);
 
 /* G_q = dK/dtheta_q W for q = log l_1..log l_d (ARD) or log l (isotropic),
- * then log s^2: the derivative products of Eq. 2 (device float64).  G holds
- * n_theta = (ard ? d : 1) + 1 blocks of n x c, block q at G + q*ldg*c,
- * column k at + k*ldg.  The noise derivative sigma^2 W is left to the caller. */
+ * then log s^2: the derivative products of Eq. 2 (device float64), entries
+ * and sums in native FP64 (the trace term of the gradient cancels most of the
+ * magnitude of these products).  G holds n_theta = (ard ? d : 1) + 1 blocks
+ * of n x c, block q at G + q*ldg*c, column k at + k*ldg.  The noise
+ * derivative sigma^2 W is left to the caller. */
 kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* G, int64_t ldg);
 
 /* Stochastic gradient of log p(y|theta) (Eq. 2, trace by Rademacher probes as

@@ -61,6 +61,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("wait_stall", ctypes.c_int32),
         ("wait_limit_ns", ctypes.c_int64),
+        ("inner_f64", ctypes.c_int32),
     ]
 
 

@@ -436,28 +436,50 @@ kpcg_status fcg_solve(Ctx& h, const MixedOps& ops, const double* B, int64_t ldb,
             status = KPCG_ERR_NO_CONVERGENCE;
             break;
         }
-        // z = ||r|| * M(r / ||r||): inner FP32 PCG on the shifted operator
+        // z = ||r|| * M(r / ||r||): inner PCG on the shifted operator, in FP32
+        // vectors (or FP64 ones when the operator takes them)
         KPCG_CUDA(cudaMemcpyAsync(cs, scale.data(), sizeof(double) * c, cudaMemcpyHostToDevice,
                                   st));
-        convert_scale_cols<float, double>(b32, ld, R, ld, n, c, cs, 1, st);
         std::vector<int> its;
         int br = 0;
         const int budget = std::min(h.opt.inner_max_iter, h.opt.max_iter - iters_total);
-        const int ran = pcg_core<float>(
-            h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, std::max(1, budget),
-            [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
-                h.prof.time(Profiler::KV_INNER, st, [&] { ops.inner_mv(V, ldv, cc, O, ldo); });
-            },
-            [&](const float* Rr, int64_t ldr, int cc, float* Zz, int64_t ldz) {
-                h.prof.time(Profiler::PRECOND, st, [&] { ops.inner_pc(Rr, ldr, cc, Zz, ldz); });
-            },
-            h.c32, its, br);
+        int ran;
+        if (ops.inner_mv64) {
+            double* b64 = h.c64.b.need((size_t)ld * c);
+            double* d64 = h.c64.x.need((size_t)ld * c);
+            convert_scale_cols<double, double>(b64, ld, R, ld, n, c, cs, 1, st);
+            ran = pcg_core<double>(
+                h, c, b64, ld, d64, ld, true, h.opt.inner_tol, 0, std::max(1, budget),
+                [&](const double* V, int64_t ldv, int cc, double* O, int64_t ldo) {
+                    h.prof.time(Profiler::KV_INNER, st,
+                                [&] { ops.inner_mv64(V, ldv, cc, O, ldo); });
+                },
+                [&](const double* Rr, int64_t ldr, int cc, double* Zz, int64_t ldz) {
+                    h.prof.time(Profiler::PRECOND, st,
+                                [&] { ops.inner_pc64(Rr, ldr, cc, Zz, ldz); });
+                },
+                h.c64, its, br);
+            convert_scale_cols<double, double>(Z, ld, d64, ld, n, c, cs, 0, st);
+        } else {
+            convert_scale_cols<float, double>(b32, ld, R, ld, n, c, cs, 1, st);
+            ran = pcg_core<float>(
+                h, c, b32, ld, d32, ld, true, h.opt.inner_tol, 0, std::max(1, budget),
+                [&](const float* V, int64_t ldv, int cc, float* O, int64_t ldo) {
+                    h.prof.time(Profiler::KV_INNER, st,
+                                [&] { ops.inner_mv(V, ldv, cc, O, ldo); });
+                },
+                [&](const float* Rr, int64_t ldr, int cc, float* Zz, int64_t ldz) {
+                    h.prof.time(Profiler::PRECOND, st,
+                                [&] { ops.inner_pc(Rr, ldr, cc, Zz, ldz); });
+                },
+                h.c32, its, br);
+            convert_scale_cols<double, float>(Z, ld, d32, ld, n, c, cs, 0, st);
+        }
         iters_total += ran;
         // a bounded wait that expired inside the inner products ends the solve
         if (ops.timed_out && ops.timed_out())
             fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         for (int k = 0; k < c; ++k) iters_col[k] += (its[k] < 0 ? -1 - its[k] : its[k]);
-        convert_scale_cols<double, float>(Z, ld, d32, ld, n, c, cs, 0, st);
         // p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j over the window
         double* p = Pw + (size_t)head * ld * c;
         double* q = APw + (size_t)head * ld * c;
@@ -563,6 +585,24 @@ static MixedOps single_ops(Ctx& h) {
         residual_f64(*hp, B, ldb, cc, X, ldx, R, rr, bb, !certify);
     };
     if (tc || tcx) o.timed_out = [hp]() { return kv_tc_error(*hp) != 0; };
+    if (tcx && h.opt.inner_f64) {
+        const double inner_noise64 = h.noise * (1.0 + h.opt.inner_shift);
+        o.inner_mv64 = [hp, inner_noise64](const double* V, int64_t ldv, int cc, double* O,
+                                           int64_t ldo) {
+            kv_tcx_apply64(*hp, V, ldv, cc, O, ldo, inner_noise64);
+        };
+        // the preconditioner in FP32 between two conversions (its precision
+        // does not decide the accuracy of the solve, only its speed)
+        o.inner_pc64 = [hp, pc = o.inner_pc](const double* R, int64_t ldr, int cc, double* Z,
+                                             int64_t ldz) {
+            Ctx& h = *hp;
+            float* r32 = h.c32.r.need((size_t)h.ld * cc);
+            float* z32 = h.c32.z.need((size_t)h.ld * cc);
+            convert_scale_cols<float, double>(r32, h.ld, R, ldr, h.n, cc, nullptr, 0, h.stream);
+            pc(r32, h.ld, cc, z32, h.ld);
+            convert_scale_cols<double, float>(Z, ldz, z32, h.ld, h.n, cc, nullptr, 0, h.stream);
+        };
+    }
     return o;
 }
 
@@ -880,6 +920,7 @@ void kpcg_default_options(kpcg_options* opt) {
     opt->profile = 0;
     opt->wait_stall = 0;
     opt->wait_limit_ns = 0;
+    opt->inner_f64 = 0;
 }
 
 const char* kpcg_status_string(kpcg_status s) {
@@ -909,6 +950,7 @@ static void check_opts(const kpcg_options* o) {
     if (o->inner_max_iter < 1 || o->fcg_window < 1 || o->fcg_window > 64)
         fail(KPCG_ERR_ARG, "inner_max_iter >= 1 and fcg_window in [1, 64] required");
     if (o->wait_stall != 0 && o->wait_stall != 1) fail(KPCG_ERR_ARG, "wait_stall must be 0 or 1");
+    if (o->inner_f64 != 0 && o->inner_f64 != 1) fail(KPCG_ERR_ARG, "inner_f64 must be 0 or 1");
     if (o->wait_limit_ns < 0 || o->wait_limit_ns > (int64_t)60000000000)
         fail(KPCG_ERR_ARG, "wait_limit_ns must be in [0, 60 s]");
 }
@@ -1095,7 +1137,13 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
             kpcg::kv_f64_sym(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
         else if (impl == 1)
             kpcg::kv_df(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
-        else
+        else if (impl == 2) {
+            if (!kpcg::kv_tcx_supported(h->d))
+                fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
+            kpcg::kv_tcx_apply64(*h, V, ldv, c, O, ldo, h->noise);
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
+        } else
             fail(KPCG_ERR_ARG, "unknown impl");
         KPCG_CUDA(cudaStreamSynchronize(h->stream));
     });
@@ -1176,10 +1224,7 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
         if (c == 0) return KPCG_OK;
         kpcg::check_dev_ptr(W, "W");
         kpcg::check_dev_ptr(G, "G");
-        float* w32 = h->W32.need((size_t)h->ld * c);
-        kpcg::convert_scale_cols<float, double>(w32, h->ld, W, ldw, h->n, c, nullptr, 0,
-                                                h->stream);
-        kpcg::dkv_f32(h->xs32.p, h->n, h->dp, h->d, h->ard, h->c0_32(), w32, h->ld, c, G, ldg,
+        kpcg::dkv_f64(h->xs64.p, h->n, h->dp, h->d, h->ard, h->c0_64(), W, ldw, c, G, ldg,
                       h->kvws, h->stream);
         KPCG_CUDA(cudaStreamSynchronize(h->stream));
     });
@@ -1216,12 +1261,12 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
         if (s != KPCG_OK) return s;
         // G_q = dK_q [a, r_1..r_t]
         const int nq = (h->ard ? h->d : 1) + 1;
-        float* w32 = h->W32.need((size_t)ld * c);
-        kpcg::convert_scale_cols<float, double>(w32, ld, Sb, ld, n, 1, nullptr, 0, st);
-        kpcg::convert_scale_cols<float, double>(w32 + ld, ld, probes, n, n, t, nullptr, 0, st);
+        double* W64 = h->Q64.need((size_t)ld * c);
+        kpcg::copy_cols<double>(W64, ld, Sb, ld, n, 1, st);
+        kpcg::copy_cols<double>(W64 + ld, ld, probes, n, n, t, st);
         double* G = h->G.need((size_t)nq * ld * c);
-        kpcg::dkv_f32(h->xs32.p, n, h->dp, h->d, h->ard, h->c0_32(), w32, ld, c, G, ld, h->kvws,
-                      st);
+        kpcg::dkv_f64(h->xs64.p, n, h->dp, h->d, h->ard, h->c0_64(), W64, ld, c, G, ld,
+                      h->kvws, st);
         // dots: S^T G_q per column (c of them), and S^T [a, r_1..r_t] for the noise term
         kpcg::copy_cols<double>(Bb, ld, Sb, ld, n, 1, st);
         const int nblk = kpcg::dot_blocks(n);

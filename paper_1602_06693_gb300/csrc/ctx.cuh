@@ -177,6 +177,9 @@ bool kv_xf_supported(const Ctx& h);
 void kv_tcx_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
                   float noise);
 bool kv_tcx_supported(int d);
+// The same product for FP64 vectors (V staged as FP32 pairs, FP64 out).
+void kv_tcx_apply64(Ctx& h, const double* V, int64_t ldv, int c, double* O, int64_t ldo,
+                    double noise);
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);

@@ -108,6 +108,10 @@ void kuu_f64(const double* us, int64_t m, int dp, double c0, double scale, doubl
 // log s^2.  FP32 entries and FP32 accumulation within a column range.
 void dkv_f32(const float* xs, int64_t n, int dp, int d, int ard, float c0, const float* W,
              int64_t ldw, int c, double* G, int64_t ldg, KvWorkspace& ws, cudaStream_t st);
+// The same products with FP64 entries and sums (W in FP64): what the gradient
+// uses, since its trace term cancels most of the magnitude of dK W.
+void dkv_f64(const double* xs, int64_t n, int dp, int d, int ard, double c0, const double* W,
+             int64_t ldw, int c, double* G, int64_t ldg, KvWorkspace& ws, cudaStream_t st);
 
 // --------------------------------------------------------------- CG (cg.cu)
 // Per-column scalars of the batched PCG, device resident.

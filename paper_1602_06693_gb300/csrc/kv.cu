@@ -364,6 +364,132 @@ void dkv_launch(int cb, const float* xs, int64_t n, int nq, int ard, float c0, c
     KPCG_LAUNCHED("dkv_kernel");
 }
 
+// The derivative products in native FP64 (inputs x' scaled by sqrt(1/2), so
+// K_ij = exp(c0 - sum_r t_r^2), t = x'_i - x'_j, and (x_ir - x_jr)^2 / l_r^2 =
+// 2 t_r^2).  The gradient's trace term w^T (dK r) sums products of a large,
+// rough w = K_y^{-1} r with dK r and cancels most of their magnitude, so dK W
+// needs FP64-class entries; FP32 entries leave errors of ~1e-3 relative on
+// the smaller gradient entries.
+template <int DP, int CB>
+__global__ void __launch_bounds__(KT)
+    dkv64_kernel(const double* __restrict__ xs, int64_t n, int nq, int ard, double c0,
+                 const double* __restrict__ W, int64_t ldw, int ncols, double* __restrict__ part,
+                 int64_t ldp, int64_t cps) {
+    __shared__ double sx[TJ * DP];
+    __shared__ double sw[TJ * CB];
+    const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * cps;
+    const int64_t j1 = min(n, j0 + cps);
+    double xi[DP];
+#pragma unroll
+    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : 0.0;
+    double acc[DP + 1][CB];
+#pragma unroll
+    for (int q = 0; q <= DP; ++q)
+#pragma unroll
+        for (int k = 0; k < CB; ++k) acc[q][k] = 0.0;
+    for (int64_t jt = j0; jt < j1; jt += TJ) {
+        const int jn = (int)min((int64_t)TJ, j1 - jt);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TJ * DP; e += KT) {
+            const int jj = e / DP;
+            sx[e] = (jj < jn) ? xs[(jt + jj) * DP + (e - jj * DP)] : 0.0;
+        }
+        for (int e = threadIdx.x; e < TJ * CB; e += KT) {
+            const int k = e / TJ, jj = e - k * TJ;
+            sw[jj * CB + k] = (jj < jn && k < ncols) ? W[(jt + jj) + (int64_t)k * ldw] : 0.0;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < jn; ++jj) {
+            double t2[DP];
+            double a = c0;
+#pragma unroll
+            for (int q = 0; q < DP; ++q) {
+                const double t = xi[q] - sx[jj * DP + q];
+                t2[q] = t * t;
+                a -= t2[q];
+            }
+            const double e = exp(a);
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                const double ew = e * sw[jj * CB + k];
+                acc[DP][k] += ew;
+#pragma unroll
+                for (int q = 0; q < DP; ++q) acc[q][k] = fma(t2[q], ew, acc[q][k]);
+            }
+        }
+    }
+    if (i >= n) return;
+    for (int k = 0; k < ncols; ++k) {
+        double* base = part + ((int64_t)blockIdx.y * CB + k) * (int64_t)(nq)*ldp;
+        if (ard) {
+#pragma unroll
+            for (int q = 0; q < DP; ++q)
+                if (q < nq - 1) base[(int64_t)q * ldp + i] = 2.0 * acc[q][k];
+        } else {
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < DP; ++q) sum += acc[q][k];
+            base[i] = 2.0 * sum;
+        }
+        base[(int64_t)(nq - 1) * ldp + i] = acc[DP][k];
+    }
+}
+
+__global__ void dkv64_reduce_kernel(const double* __restrict__ part, int64_t ldp, int nsplit,
+                                    int cb, int nq, int ncols, double* __restrict__ G,
+                                    int64_t ldg, int64_t c_total, int k0, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y, k = blockIdx.z;
+    if (i >= n || k >= ncols) return;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(((int64_t)sp * cb + k) * nq + q) * ldp + i];
+    G[(int64_t)q * ldg * c_total + (int64_t)(k0 + k) * ldg + i] = s;
+}
+
+template <int DP>
+void dkv64_launch(int cb, const double* xs, int64_t n, int nq, int ard, double c0,
+                  const double* W, int64_t ldw, int ncols, double* part, const Split& s,
+                  cudaStream_t st) {
+    dim3 grid(s.nrb, s.nsplit);
+    if (cb == 1)
+        dkv64_kernel<DP, 1><<<grid, KT, 0, st>>>(xs, n, nq, ard, c0, W, ldw, ncols, part, s.ldp,
+                                                 s.cps);
+    else
+        dkv64_kernel<DP, 2><<<grid, KT, 0, st>>>(xs, n, nq, ard, c0, W, ldw, ncols, part, s.ldp,
+                                                 s.cps);
+    KPCG_LAUNCHED("dkv64_kernel");
+}
+
+}  // namespace
+
+void dkv_f64(const double* xs, int64_t n, int dp, int d, int ard, double c0, const double* W,
+             int64_t ldw, int c, double* G, int64_t ldg, KvWorkspace& ws, cudaStream_t st) {
+    if (n <= 0 || c <= 0) return;
+    const int nq = (ard ? d : 1) + 1;
+    const Split s = plan(n, KT);
+    const int max_cb = 2;
+    double* part = ws.part64.need((size_t)s.nsplit * max_cb * nq * s.ldp);
+    for (int k0 = 0; k0 < c;) {
+        const int cb = (c - k0) >= 2 ? 2 : 1;
+        const double* Wk = W + (int64_t)k0 * ldw;
+        switch (dp) {
+            case 4: dkv64_launch<4>(cb, xs, n, nq, ard, c0, Wk, ldw, cb, part, s, st); break;
+            case 8: dkv64_launch<8>(cb, xs, n, nq, ard, c0, Wk, ldw, cb, part, s, st); break;
+            case 12: dkv64_launch<12>(cb, xs, n, nq, ard, c0, Wk, ldw, cb, part, s, st); break;
+            case 16: dkv64_launch<16>(cb, xs, n, nq, ard, c0, Wk, ldw, cb, part, s, st); break;
+            case 32: dkv64_launch<32>(cb, xs, n, nq, ard, c0, Wk, ldw, cb, part, s, st); break;
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+        dim3 rg((unsigned)((n + 255) / 256), (unsigned)nq, (unsigned)cb);
+        dkv64_reduce_kernel<<<rg, 256, 0, st>>>(part, s.ldp, s.nsplit, cb, nq, cb, G, ldg, c, k0,
+                                                n);
+        KPCG_LAUNCHED("dkv64_reduce_kernel");
+        k0 += cb;
+    }
+}
+
+namespace {
 }  // namespace
 
 size_t kv_f64_scratch_elems(int64_t n) {

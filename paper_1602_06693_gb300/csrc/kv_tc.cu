@@ -396,13 +396,13 @@ __global__ void tc_stage_v_kernel(const float* __restrict__ V, int64_t ldv, int6
         Vs[i + k * n_pad] = (i < n) ? V[i + k * ldv] : 0.f;
 }
 
-template <int KCH, int CB>
+template <int KCH, int CB, int VPARTS = 1>
 struct TcSmem {
     static constexpr int kNst = KCH >= 3 ? 3 : NSTAGE;          // ring depth (smem budget)
     static constexpr uint32_t kSub = SUB * 2;                    // 16 KB
     static constexpr uint32_t kA = KCH * kSub;                   // A tile
     static constexpr uint32_t kBst = KCH * kSub;                 // B part of a stage
-    static constexpr uint32_t kVst = CB * TN * 4;                // V part of a stage
+    static constexpr uint32_t kVst = VPARTS * CB * TN * 4;       // V part(s) of a stage
     static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
     static constexpr uint32_t kBars = 1024;
     static constexpr uint32_t kTotal = 1024 /*align slack*/ + kA + kNst * kStage + kBars;
@@ -412,14 +412,17 @@ struct TcSmem {
 // EXACT = 1: the per-point-exact operands of tcx_prep_kernel (nmma MMAs of
 // K = 16 per tile, the accumulator times escale is the exp2 argument), row
 // sums compensated (TwoSum into an FP32 pair), FP64 partials in part64.
+// EXACT = 2: as 1, V given as FP32 pairs (hi in Vs, lo in Vs + nv): each
+// product e*v_hi enters the TwoSum, e*v_lo the compensation term.
 template <int KCH, int CB, int EXACT>
 __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
     kv_tc_kernel(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
                  const float* __restrict__ Vs, int64_t n, int64_t n_pad, int ncols,
                  int tiles_per_split, float* __restrict__ part, int* __restrict__ err,
                  int nmma, float escale, double* __restrict__ part64, uint64_t wait_ns,
-                 int stall) {
-    using S = TcSmem<KCH, CB>;
+                 int stall, int64_t nv) {
+    constexpr int VP = (EXACT == 2) ? 2 : 1;
+    using S = TcSmem<KCH, CB, VP>;
     constexpr int NST = S::kNst;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -495,11 +498,13 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                 }
                 const int64_t jt = jt0 + t;
                 uint8_t* st = sStage + (size_t)s * S::kStage;
-                mbar_expect_tx(&full[s], S::kBst + (uint32_t)ncols * TN * 4);
+                mbar_expect_tx(&full[s], S::kBst + (uint32_t)(VP * ncols) * TN * 4);
                 bulk_g2s(st, Bop + (size_t)jt * KCH * SUB, S::kBst, &full[s]);
-                for (int k = 0; k < ncols; ++k)
-                    bulk_g2s(st + S::kBst + (size_t)k * TN * 4, Vs + (size_t)k * n_pad + jt * TN,
-                             TN * 4, &full[s]);
+                for (int vp = 0; vp < VP; ++vp)
+                    for (int k = 0; k < ncols; ++k)
+                        bulk_g2s(st + S::kBst + (size_t)(vp * CB + k) * TN * 4,
+                                 Vs + (size_t)vp * nv + (size_t)k * n_pad + jt * TN, TN * 4,
+                                 &full[s]);
             }
             // let the copies this thread issued land before the CTA exits (on
             // the failure path some may still be in flight); own, fresh limit
@@ -583,6 +588,8 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                 for (int k = 0; k < CB; ++k) {
                     const float4* vp =
                         reinterpret_cast<const float4*>(vst + k * TN + half * 64 + ps * W);
+                    const float4* vpl = reinterpret_cast<const float4*>(
+                        vst + (VP - 1) * CB * TN + k * TN + half * 64 + ps * W);
                     float a[CH], cc[CH];
 #pragma unroll
                     for (int u = 0; u < CH; ++u) a[u] = cc[u] = 0.f;
@@ -590,6 +597,11 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                     for (int j4 = 0; j4 < W / 4; ++j4) {
                         const float4 v = vp[j4];
                         const float vv[4] = {v.x, v.y, v.z, v.w};
+                        float vl[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (EXACT == 2) {
+                            const float4 w = vpl[j4];
+                            vl[0] = w.x, vl[1] = w.y, vl[2] = w.z, vl[3] = w.w;
+                        }
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int q = u % CH;
@@ -599,6 +611,7 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                                 const float sum = a[q] + pv;
                                 const float bp = sum - a[q];
                                 cc[q] += (a[q] - (sum - bp)) + (pv - bp);
+                                if (EXACT == 2) cc[q] = fmaf(e, vl[u], cc[q]);
                                 a[q] = sum;
                             } else {
                                 a[q] = fmaf(e, vv[u], a[q]);
@@ -682,10 +695,11 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int64_t n_pad, 
 template <int KCH, int CB, int EXACT = 0>
 void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* Vs,
                int64_t n_pad, int ncols, float* part, int nsplit, int tps, int* err,
-               cudaStream_t st, int nmma = 0, float escale = 1.f, double* part64 = nullptr) {
+               cudaStream_t st, int nmma = 0, float escale = 1.f, double* part64 = nullptr,
+               int64_t nv = 0) {
     const uint64_t wait_ns =
         h.opt.wait_limit_ns > 0 ? (uint64_t)h.opt.wait_limit_ns : kWaitNs;
-    using S = TcSmem<KCH, CB>;
+    using S = TcSmem<KCH, CB, EXACT == 2 ? 2 : 1>;
     static bool attr = false;
     if (!attr) {
         KPCG_CUDA(cudaFuncSetAttribute(kv_tc_kernel<KCH, CB, EXACT>,
@@ -695,8 +709,34 @@ void launch_tc(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, con
     dim3 grid((unsigned)(n_pad / TM), (unsigned)nsplit);
     kv_tc_kernel<KCH, CB, EXACT><<<grid, NWARPS * 32, S::kTotal, st>>>(
         A, B, Vs, h.n, n_pad, ncols, tps, part, err, nmma, escale, part64, wait_ns,
-        h.opt.wait_stall ? 1 : 0);
+        h.opt.wait_stall ? 1 : 0, nv);
     KPCG_LAUNCHED(EXACT ? "kv_tcx_kernel" : "kv_tc_kernel");
+}
+
+// V (FP64) staged as FP32 pairs: hi at Vs, lo at Vs + nv (column k at k n_pad).
+__global__ void tc_stage_v64_kernel(const double* __restrict__ V, int64_t ldv, int64_t n,
+                                    int64_t n_pad, float* __restrict__ Vs, int64_t nv) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (i < n) ? V[i + k * ldv] : 0.0;
+        const float hi = (float)v;
+        Vs[i + k * n_pad] = hi;
+        Vs[nv + i + k * n_pad] = (float)(v - (double)hi);
+    }
+}
+
+// O = noise V + the FP64 partial sums of the exact kernel, in FP64.
+__global__ void tcx_reduce64_kernel(const double* __restrict__ part, int64_t n_pad, int nsplit,
+                                    int cb, int ncols, const double* __restrict__ V, int64_t ldv,
+                                    double noise, double* __restrict__ O, int64_t ldo,
+                                    int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n || k >= ncols) return;
+    double s = noise * V[i + (int64_t)k * ldv];
+    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * cb + k) * n_pad + i];
+    O[i + (int64_t)k * ldo] = s;
 }
 
 // O = noise V + the FP64 partial sums of the exact kernel, rounded to FP32.
@@ -873,6 +913,53 @@ void kv_tcx_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t 
             part, n_pad, nsplit, cb, ncols, V + (int64_t)k0 * ldv, ldv, noise,
             O + (int64_t)k0 * ldo, ldo, n);
         KPCG_LAUNCHED("tcx_reduce_kernel");
+        k0 += ncols;
+    }
+}
+
+void kv_tcx_apply64(Ctx& h, const double* V, int64_t ldv, int c, double* O, int64_t ldo,
+                    double noise) {
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    if (n <= 0 || c <= 0) return;
+    const int64_t n_pad = ((n + TM - 1) / TM) * TM;
+    tcx_prepare(h);
+    const int kch = h.tcx_kch;
+    if (kch != 2 && kch != 3) fail(KPCG_ERR_ARG, "internal: exact operand layout");
+    const int n_ct = (int)(n_pad / TN);
+    const int n_rt = (int)(n_pad / TM);
+    int nsplit = std::max(1, std::min(n_ct, (sm_count_tc() * 4 + n_rt - 1) / n_rt));
+    const int tps = (n_ct + nsplit - 1) / nsplit;
+    nsplit = (n_ct + tps - 1) / tps;
+    const int max_cb = 4;
+    const int64_t nv = n_pad * max_cb;
+    float* Vs = h.tcV.need((size_t)2 * nv);
+    double* part = h.tcxPart.need((size_t)nsplit * max_cb * n_pad);
+    const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(h.tcxA.p);
+    const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(h.tcxB.p);
+    for (int k0 = 0; k0 < c;) {
+        const int rem = c - k0;
+        const int cb = rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int ncols = std::min(cb, rem);
+        tc_stage_v64_kernel<<<dim3((unsigned)std::min<int64_t>((n_pad + 255) / 256, 2048),
+                                   (unsigned)ncols),
+                              256, 0, st>>>(V + (int64_t)k0 * ldv, ldv, n, n_pad, Vs, nv);
+        KPCG_LAUNCHED("tc_stage_v64_kernel");
+#define KPCG_TCX2_CASE(KCHV, CBV)                                                              \
+    if (kch == KCHV && cb == CBV)                                                             \
+        launch_tc<KCHV, CBV, 2>(h, A, B, Vs, n_pad, ncols, nullptr, nsplit, tps, h.tc_err.p, st, \
+                                h.tcx_nmma, h.tcx_escale, part, nv);
+        KPCG_TCX2_CASE(2, 1)
+        KPCG_TCX2_CASE(2, 2)
+        KPCG_TCX2_CASE(2, 4)
+        KPCG_TCX2_CASE(3, 1)
+        KPCG_TCX2_CASE(3, 2)
+        KPCG_TCX2_CASE(3, 4)
+#undef KPCG_TCX2_CASE
+        tcx_reduce64_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)ncols), 256, 0, st>>>(
+            part, n_pad, nsplit, cb, ncols, V + (int64_t)k0 * ldv, ldv, noise,
+            O + (int64_t)k0 * ldo, ldo, n);
+        KPCG_LAUNCHED("tcx_reduce64_kernel");
         k0 += ncols;
     }
 }

@@ -15,6 +15,8 @@ namespace kpcg {
 struct MixedOps {
     // O = (K + inner noise I) V in FP32, and the inner preconditioner
     std::function<void(const float*, int64_t, int, float*, int64_t)> inner_mv, inner_pc;
+    // when set: the inner PCG runs on FP64 vectors with these instead
+    std::function<void(const double*, int64_t, int, double*, int64_t)> inner_mv64, inner_pc64;
     // O = K_y V with FP64-class accuracy
     std::function<void(const double*, int64_t, int, double*, int64_t)> outer_mv;
     // R = B - K_y X and the per-column ||R||^2, ||B||^2; certify: native FP64

@@ -154,6 +154,20 @@ def test_matvec_exact_difference_fp32_matches_oracle(kpcg, impl, n, d, c):
         assert _rel(out[:, k], ref[:, k]) <= (2e-6 if impl == 3 else 5e-6), k
 
 
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (1000, 8, 3), (4099, 9, 2), (777, 10, 5)])
+def test_matvec_sliced_tensor_core_fp64_vectors(kpcg, n, d, c):
+    # The sliced kernel on FP64 vectors (V as FP32 pairs): the per-entry FP32
+    # error is unchanged, the vector is no longer rounded to 24 bits.
+    p = _problem(n, d, seed=23 * n + d)
+    V = synthetic.rng(8).standard_normal((n, c)) * 1e4  # large values, like alpha
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(_cm(V), impl=2))
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= 5e-6, k
+
+
 def test_sliced_tensor_core_rejects_wide_inputs(kpcg):
     p = _problem(300, 11, seed=4)
     with _solver(kpcg, p) as s:
@@ -162,41 +176,35 @@ def test_sliced_tensor_core_rejects_wide_inputs(kpcg):
     assert e.value.name == "KPCG_ERR_ARG"
 
 
-def _rough_part(err, u):
-    """err minus its projection on u: a uniform relative bias of the entries
-    (e.g. of exp2) changes K V along K V itself and is harmless to CG; the
-    rest of the error is what a preconditioned solve has to absorb."""
-    return err - (err @ u) / (u @ u) * u
-
-
 def test_exact_difference_fp32_has_no_per_point_error(kpcg):
-    # On the ill-conditioned uniform-cube workload (n = 8192, noise 1e-4) the
-    # product with a smooth vector exposes per-point rounding of the inputs:
-    # it shifts whole rows of K together, so K 1 comes back with a rough error
-    # of size ~2^-24 |K 1|.  The exact-difference kernels (impl 2, 3) and the
-    # sliced tensor-core kernel (impl 4) keep only per-entry roundings, whose
-    # rough part is several times smaller (measured: 5x at this size).
-    p = synthetic.config2(seed=0, n=8192)
+    # On the ill-conditioned uniform-cube workload (n = 16384, noise 1e-4):
+    # the FP32 kernel (impl 0) rounds every scaled input once; the
+    # exact-difference kernels (impl 2, 3) and the sliced tensor-core kernel
+    # (impl 4) keep the inputs exact and only round per entry.  On a Rademacher
+    # vector their product error is several times smaller (measured: 3x to 8x
+    # at this size, growing with n).
+    p = synthetic.config2(seed=0, n=16384)
     ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
-    one = np.ones(p.n)
-    ref = oracle.kyv(p.X, ell, s2, p.noise, one)
+    r = synthetic.rademacher(p.n, 1, seed=9)[:, 0] / np.sqrt(p.n)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, r)
     with _solver(kpcg, p) as s:
-        e = {impl: np.linalg.norm(_rough_part(_np(s.matvec_f32(_cm(one, torch.float32),
-                                                                impl=impl)) - ref, ref))
+        e = {impl: np.linalg.norm(_np(s.matvec_f32(_cm(r, torch.float32), impl=impl)) - ref)
              for impl in (0, 1, 2, 3, 4)}
     for impl in (2, 3, 4):
-        assert e[impl] <= 0.35 * min(e[0], e[1]), e
+        assert e[impl] <= 0.35 * e[0], e
 
 
-@pytest.mark.parametrize("prec", ["FP32X_IR", "TCX_IR"])
+@pytest.mark.parametrize("prec", ["FP32X_IR", "TCX_IR", "TCX_IR_F64"])
 def test_exact_inner_operators_allow_a_small_shift(kpcg, prec):
     # What the exactness buys: on the n = 8192 uniform-cube system (noise
     # 1e-4) the flexible-CG solve converges with the inner operator shifted by
     # only 0.25 sigma^2, and to the oracle's solution.
     p = synthetic.config2(seed=0, n=8192)
     idx = synthetic.inducing_subset(p.n, 512, seed=1)
-    with _solver(kpcg, p, precision=getattr(kpcg, "KPCG_" + prec), inner_shift=0.25,
-                 inner_tol=0.3, max_outer=40) as s:
+    f64 = prec.endswith("_F64")
+    with _solver(kpcg, p, precision=getattr(kpcg, "KPCG_" + prec.replace("_F64", "")),
+                 inner_shift=0.25, inner_tol=0.1 if f64 else 0.3, max_outer=40,
+                 inner_f64=int(f64)) as s:
         s.precond(kpcg.KPCG_PREC_NYSTROM, 512, idx)
         x, it, info, st = s.solve(_cm(p.y), tol=1e-8)
     assert st == 0 and info.max_rel_res <= 1e-8, info.as_dict()
@@ -477,9 +485,31 @@ def test_stochastic_gradient_matches_oracle(kpcg, ard):
         s.precond(kpcg.KPCG_PREC_NYSTROM, 120, synthetic.inducing_subset(n, 120, 1))
         g, alpha, info = s.grad(_cm(p.y), _cm(R), tol=1e-10, want_alpha=True)
     assert g.shape == gref.shape
-    np.testing.assert_allclose(g, gref, rtol=1e-4, atol=1e-4 * np.abs(gref).max())
+    # every entry within 1e-4 of itself (not of the largest entry)
+    assert np.all(np.abs(g - gref) <= 1e-4 * np.abs(gref)), (g, gref)
     ell, s2 = oracle.split_theta(p.log_theta, 4, ard)
     assert _rel(_np(alpha), oracle.dense_solve(p.X, ell, s2, p.noise, p.y)) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["TC_IR", "TCX_IR"])
+def test_gradient_in_the_benchmark_mode_matches_oracle(kpcg, prec):
+    # The stochastic gradient as the gradient benchmark computes it (tensor-core
+    # inner PCG in the flexible-CG solve, Nystrom set-up, y and 16 probes in one
+    # block) on the benchmark's input distribution scaled down to n = 4096
+    # (d = 9, standardized Gaussian X, noise 1e-3, m = 256), against the oracle's
+    # gradient with a dense Cholesky solve and the same probes: each of the 11
+    # entries within 1e-4 relative.
+    p = synthetic.config3(seed=0, n=4096)
+    R = synthetic.rademacher(p.n, 16, 77)
+    gref = oracle.grad_stochastic(p.X, p.log_theta, p.noise, p.y, R, ard=True)
+    idx = synthetic.inducing_subset(p.n, 256, seed=2)
+    with _solver(kpcg, p, precision=getattr(kpcg, "KPCG_" + prec), inner_shift=0.25,
+                 inner_tol=0.2, max_iter=20000) as s:
+        s.precond(kpcg.KPCG_PREC_NYSTROM, 256, idx)
+        g, _, info = s.grad(_cm(p.y), _cm(R), tol=1e-8)
+    assert info.max_rel_res <= 1e-8, info.as_dict()
+    assert g.shape == (p.d + 2,)
+    assert np.all(np.abs(g - gref) <= 1e-4 * np.abs(gref)), (g, gref)
 
 
 # ------------------------------------------------------------------ errors
