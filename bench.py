@@ -50,7 +50,7 @@ WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum 
 # profiles/precision_n65536.md.
 HEADLINE_PREC = "tc_ir"
 MODE_OPTS = {
-    "tc_ir": dict(inner_shift=2.0, inner_tol=0.1),
+    "tc_ir": dict(inner_shift=1.0, inner_tol=0.1),
     "fp32_ir": dict(inner_shift=4.0, inner_tol=0.1),
     "xf_ir": dict(inner_shift=0.25, inner_tol=0.3),
     "tcx_ir": dict(inner_shift=0.1, inner_tol=0.5),
@@ -930,9 +930,22 @@ KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
             "tcx_ir": "kv_tcx_kernel (tcgen05 sliced exponent, compensated contraction)",
             "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
             "df64": "kv_df_sym_kernel (double-float)", "fp64": "kv_f64_sym_kernel (FP64)"}
-# DRAM bytes per launch from ncu captures (profiles/), by kernel name; a
-# kernel changed since its capture has no entry.
-KNOWN_TRAFFIC = {}
+# DRAM bytes per launch from ncu captures at n = 16384 (profiles/), by kernel
+# name, as a function of n: each kernel reads only its inputs from DRAM (the
+# n x n work stays on chip), so the traffic grows like n.  A kernel changed
+# since its capture has no entry.
+KNOWN_TRAFFIC = {
+    "kv_df_sym_kernel": lambda n: 2291712.0 * n / 16384,
+    "kv_f64_sym_kernel": lambda n: 1287552.0 * n / 16384,
+    "kv_tc_kernel": lambda n: 4278272.0 * n / 16384,
+}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at n = 16384, "
+                  "scaled by n (inputs only)")
+
+
+def known_traffic(kernel, n):
+    f = KNOWN_TRAFFIC.get(kernel.split(" ")[0])
+    return f(n) if f else None
 
 
 def run_solve(args):
@@ -1035,7 +1048,8 @@ def run_solve(args):
                                "MEASURED_PEAKS.json hbm_gbs (of measured)")
         roof["timing"] = ("average launch of this class from CUDA events on the handle's stream "
                           "in a profiled run of the same step right after the timed region")
-        roof["traffic"] = KNOWN_TRAFFIC.get(roof["kernel"].split(" ")[0])
+        roof["traffic"] = known_traffic(roof["kernel"], p.n)
+        roof["traffic_source"] = TRAFFIC_SOURCE if roof["traffic"] else None
 
     # end to end through the C ABI from host buffers
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -1191,7 +1205,7 @@ def run_kv(args):
     rates = probed_rates(kpcg)
     rates["bf16_tflops"] = float(measured_peaks().get("bf16_tflops", 1934.6))
     roof = alu_roofline(kname, p.n, p.d, c, ms, rates, fp64=(args.kv_impl == "f64"))
-    roof.update({"peak_source": PEAK_SOURCE, "traffic": KNOWN_TRAFFIC.get(kname.split(" ")[0]),
+    roof.update({"peak_source": PEAK_SOURCE, "traffic": known_traffic(kname, p.n),
                  "timing": f"{args.steps} back-to-back products, CUDA events on the stream"})
     if args.kv_impl == "df":
         roof["issue_efficiency"] = df_issue_efficiency(p.n, p.d, c, ms, rates)
@@ -1202,6 +1216,75 @@ def run_kv(args):
                       "config": {"workload": f"K.V of the n={p.n} uniform-cube ARD system"},
                       "roofline": roof, "peaks": rates, "clocks": clocks}))
     s.close()
+
+
+PRECISION_SWEEP = (("fp32_ir", 0.25, 0.1), ("fp32_ir", 1.0, 0.1), ("fp32_ir", 4.0, 0.1),
+                   ("tc_ir", 0.25, 0.1), ("tc_ir", 1.0, 0.1), ("tc_ir", 2.0, 0.1),
+                   ("tc_ir", 4.0, 0.1), ("xf_ir", 0.25, 0.3), ("tcx_ir", 0.1, 0.5),
+                   ("tcx_ir", 0.25, 0.3))
+
+
+def run_precision(args):
+    """The record behind the choice of solver for the headline system: for
+    each reduced-precision product, the norm of its error operator
+    ||K_op - K||_2 (power iteration against the native-FP64 product) and its
+    error on a smooth (constant) and a rough (Rademacher) unit vector, at
+    n = 4096, 16384 and --n; then the flexible-CG solve of the n = --n system
+    for each (mode, inner shift, inner tolerance) of the sweep, with the worst
+    relative residual after every outer step (KPCG_TRACE lines on stderr)."""
+    import torch
+    import paper_1602_06693_gb300 as kpcg
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    ops = {"fp32": ("f32", 0), "tc": ("f32", 1), "xf_ex2": ("f32", 2), "xf_poly": ("f32", 3),
+           "tcx": ("f32", 4), "df": ("f64", 1)}
+    sizes = sorted({4096, 16384, args.n})
+    recs = []
+    for n in sizes:
+        p = synthetic.config2(seed=0, n=n)
+        s = kpcg.Solver(torch.from_numpy(p.X).to(dev), p.log_theta, p.noise, ard=True)
+
+        def apply(name, v):
+            kind, impl = ops[name]
+            return (s.matvec_f64(v, impl=impl) if kind == "f64" else
+                    s.matvec_f32(v.float(), impl=impl).double())
+
+        ones = torch.ones(n, dtype=torch.float64, device=dev) / math.sqrt(n)
+        rad = torch.from_numpy(synthetic.rademacher(n, 1, seed=9)[:, 0].copy()).to(dev)
+        rad /= math.sqrt(n)
+        ref1, ref2 = s.matvec_f64(ones, impl=0), s.matvec_f64(rad, impl=0)
+        g = torch.Generator().manual_seed(5)
+        for name in ops:
+            v = torch.randn(n, generator=g, dtype=torch.float64).to(dev)
+            v /= v.norm()
+            est = 0.0
+            for _ in range(12):
+                w = apply(name, v) - s.matvec_f64(v, impl=0)
+                est = float(w.norm())
+                v = w / est
+            recs.append({"n": n, "op": name, "opnorm": est, "opnorm_over_noise": est / p.noise,
+                         "err_smooth": float((apply(name, ones) - ref1).norm()),
+                         "err_rough": float((apply(name, rad) - ref2).norm())})
+        s.close()
+    p = synthetic.config2(seed=0, n=args.n)
+    idx = synthetic.inducing_subset(p.n, M_INDUCING, seed=1)
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    solves = []
+    for mode, shift, itol in PRECISION_SWEEP:
+        opt = kpcg.default_options(precision=mode_id(kpcg, mode), inner_shift=shift,
+                                   inner_tol=itol, max_outer=40, inner_max_iter=300)
+        sys.stderr.write(f"=== {mode} inner_shift={shift} inner_tol={itol}\n")
+        sys.stderr.flush()
+        info, st, set_ms, tot_ms = solve_once(kpcg, X, y, p, idx, opt,
+                                              torch.cuda.current_stream(dev))
+        solves.append({"mode": mode, "inner_shift": shift, "inner_tol": itol, "status": st,
+                       "time_s": tot_ms / 1e3, "outer_steps": info.outer_steps,
+                       "inner_iters": info.iters_total, "rel_res_fp64": info.max_rel_res})
+    print(json.dumps({"metric": "operator error and mixed-precision convergence", "value": None,
+                      "unit": None, "config": {"workload": WORKLOAD},
+                      "operators": recs, "solves": solves}))
 
 
 def main():
@@ -1222,7 +1305,7 @@ def main():
     ap.add_argument("--kv-cols", type=int, default=1, help="kv: columns of V")
     ap.add_argument("--workload", default="solve65k",
                     choices=["solve65k", "batch64", "grad45k", "warm131k", "predict4k", "fig1",
-                             "laplace15k", "kv"],
+                             "laplace15k", "kv", "precision"],
                     help="solve65k: the headline single solve; batch64: 64 uneven problems")
     ap.add_argument("--batch-max-iter", type=int, default=20000,
                     help="batch64: cap on inner iterations (short runs for profiling)")
@@ -1259,6 +1342,8 @@ def main():
         return run_laplace(args)
     if args.workload == "kv":
         return run_kv(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_solve(args)
 
 

@@ -283,7 +283,10 @@ kpcg_status kpcg_dkv(kpcg_t h, const double* W, int64_t ldw, int32_t c, double* 
  * y (device, n doubles), probes (device, n x t column-major, ld = n, entries
  * +-1, t >= 1).  grad (host) receives n_theta + 1 values:
  * d/dlog l_r (or d/dlog l), d/dlog s^2, d/dlog sigma^2.  alpha (device,
- * nullable) receives a = K_y^{-1} y. */
+ * nullable) receives a = K_y^{-1} y.  The derivative products run in
+ * double-float arithmetic (FP32 pairs, about 44 bits; native FP64 for d > 16):
+ * the trace term cancels all but ~1e-5 of the magnitude of dK W, so FP32
+ * entries would leave errors of ~3e-4 on the smaller gradient entries. */
 kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t, double tol,
                       const double* alpha0, double* grad, double* alpha, kpcg_info* info);
 

@@ -1265,8 +1265,13 @@ kpcg_status kpcg_grad(kpcg_t h, const double* y, const double* probes, int32_t t
         kpcg::copy_cols<double>(W64, ld, Sb, ld, n, 1, st);
         kpcg::copy_cols<double>(W64 + ld, ld, probes, n, n, t, st);
         double* G = h->G.need((size_t)nq * ld * c);
-        kpcg::dkv_f64(h->xs64.p, n, h->dp, h->d, h->ard, h->c0_64(), W64, ld, c, G, ld,
-                      h->kvws, st);
+        // double-float entries and sums (the trace term cancels all but ~1e-5
+        // of the magnitude of dK W); native FP64 above d = 16
+        if (h->dp <= 16)
+            kpcg::dkv_df(*h, W64, ld, c, G, ld);
+        else
+            kpcg::dkv_f64(h->xs64.p, n, h->dp, h->d, h->ard, h->c0_64(), W64, ld, c, G, ld,
+                          h->kvws, st);
         // dots: S^T G_q per column (c of them), and S^T [a, r_1..r_t] for the noise term
         kpcg::copy_cols<double>(Bb, ld, Sb, ld, n, 1, st);
         const int nblk = kpcg::dot_blocks(n);

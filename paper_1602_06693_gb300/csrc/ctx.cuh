@@ -171,6 +171,9 @@ void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, in
 void kv_xf(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, float noise,
            int expp);
 bool kv_xf_supported(const Ctx& h);
+// dK/dtheta_q W (FP64 in and out) in double-float arithmetic (kv_df.cu;
+// d <= 16); layout of kpcg_dkv.
+void dkv_df(Ctx& h, const double* W, int64_t ldw, int c, double* G, int64_t ldg);
 // Tensor-core K.V on per-point-exact sliced operands (kv_tc.cu; d <= 10):
 // FP32 in and out, FP32 exponent rounding relative to the exponent itself,
 // compensated row sums.

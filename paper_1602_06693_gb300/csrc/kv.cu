@@ -420,7 +420,9 @@ __global__ void __launch_bounds__(KT)
         }
     }
     if (i >= n) return;
-    for (int k = 0; k < ncols; ++k) {
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        if (k >= ncols) break;
         double* base = part + ((int64_t)blockIdx.y * CB + k) * (int64_t)(nq)*ldp;
         if (ard) {
 #pragma unroll

@@ -556,6 +556,132 @@ __global__ void kv_xf_sym_reduce_kernel(const double* __restrict__ prow,
     O[i + (int64_t)k * ldo] = (float)s;
 }
 
+// ---------------------------------------------------------------------------
+// Derivative products dK/dtheta_q W in double-float arithmetic.  The
+// gradient's trace term sums w^T (dK r) over a large, rough w = K_y^{-1} r and
+// cancels all but ~1e-5 of its magnitude, so the entries K_ij t_ijq^2 need
+// about 28 bits even when every rounding is independent per entry (FP32
+// entries leave errors of 3e-4 relative on the smaller gradient entries).
+// Every quantity is an FP32 pair here: the squared differences from the split
+// inputs (exact hi difference, TwoProduct), the exponent summed with TwoSum,
+// exp2 of the pair (the table-driven method of kv_df_kernel), the products
+// K t^2 and (K t^2) w with TwoProduct, the sums with TwoSum.  Slots as
+// dkv_kernel: ARD per dimension then log s^2; isotropic the sum over
+// dimensions then log s^2; (x_r - x'_r)^2 / l_r^2 = 2 ln 2 t_r^2 in the exp2
+// scaling of x'.
+template <int DP, int CB>
+__global__ void __launch_bounds__(KT)
+    dkv_df_kernel(const float4* __restrict__ xs, int64_t n, int nq, int ard, float c0h,
+                  float c0l, const double* __restrict__ W, int64_t ldw, int ncols,
+                  const float2* __restrict__ gtab, double* __restrict__ part, int64_t ldp,
+                  int64_t cps) {
+    __shared__ float2 tab[NTAB];
+    __shared__ float4 sx[TJ * DP];
+    __shared__ float2 sw[TJ * CB];
+    for (int e = threadIdx.x; e < NTAB; e += KT) tab[e] = gtab[e];
+    const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * cps;
+    const int64_t j1 = min(n, j0 + cps);
+    float4 xi[DP];
+#pragma unroll
+    for (int q = 0; q < DP; ++q) xi[q] = (i < n) ? xs[i * DP + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float S[DP + 1][CB], C[DP + 1][CB];
+#pragma unroll
+    for (int q = 0; q <= DP; ++q)
+#pragma unroll
+        for (int k = 0; k < CB; ++k) S[q][k] = C[q][k] = 0.f;
+    for (int64_t jt = j0; jt < j1; jt += TJ) {
+        const int jn = (int)min((int64_t)TJ, j1 - jt);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TJ * DP; e += KT) {
+            const int jj = e / DP;
+            sx[e] = (jj < jn) ? xs[(jt + jj) * DP + (e - jj * DP)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = threadIdx.x; e < TJ * CB; e += KT) {
+            const int k = e / TJ, jj = e - k * TJ;
+            const double w = (jj < jn && k < ncols) ? W[(jt + jj) + (int64_t)k * ldw] : 0.0;
+            const float wh = (float)w;
+            sw[jj * CB + k] = make_float2(wh, (float)(w - (double)wh));
+        }
+        __syncthreads();
+        for (int jj = 0; jj < jn; ++jj) {
+            float Ph[DP], Pl[DP];  // t_q^2 as pairs
+            float ah = c0h, al = c0l;
+#pragma unroll
+            for (int q = 0; q < DP; ++q) {
+                const float4 xj = sx[jj * DP + q];
+                const float D = xi[q].x - xj.x;  // exact
+                const float E = (xi[q].y - xj.y) + (xi[q].z - xj.z);
+                const float P = D * D;
+                float Pe = fmaf(D, D, -P);
+                Pe = fmaf(D, E + E, Pe);
+                Pe = fmaf(E, E, Pe);
+                Ph[q] = P;
+                Pl[q] = Pe;
+                df_sub(ah, al, P, Pe);
+            }
+            const DF e = df_exp2(ah, al, tab);
+#pragma unroll
+            for (int q = 0; q <= DP; ++q) {
+                float uh, ul;  // e * t_q^2 (or e itself for log s^2)
+                if (q < DP) {
+                    uh = e.h * Ph[q];
+                    ul = fmaf(e.h, Ph[q], -uh);
+                    ul = fmaf(e.h, Pl[q], ul);
+                    ul = fmaf(e.l, Ph[q], ul);
+                } else {
+                    uh = e.h;
+                    ul = e.l;
+                }
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    const float2 w = sw[jj * CB + k];
+                    const float ph = uh * w.x;
+                    float pl = fmaf(uh, w.x, -ph);
+                    pl = fmaf(uh, w.y, pl);
+                    pl = fmaf(ul, w.x, pl);
+                    df_acc(S[q][k], C[q][k], ph, pl);
+                }
+            }
+            if ((jj & 31) == 31)
+#pragma unroll
+                for (int q = 0; q <= DP; ++q)
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) df_renorm(S[q][k], C[q][k]);
+        }
+    }
+    if (i >= n) return;
+    constexpr double kScale = 1.3862943611198906;  // 2 ln 2
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        if (k >= ncols) break;
+        double* base = part + ((int64_t)blockIdx.y * CB + k) * (int64_t)nq * ldp;
+        if (ard) {
+#pragma unroll
+            for (int q = 0; q < DP; ++q)
+                if (q < nq - 1)
+                    base[(int64_t)q * ldp + i] = kScale * ((double)S[q][k] + (double)C[q][k]);
+        } else {
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < DP; ++q) sum += (double)S[q][k] + (double)C[q][k];
+            base[i] = kScale * sum;
+        }
+        base[(int64_t)(nq - 1) * ldp + i] = (double)S[DP][k] + (double)C[DP][k];
+    }
+}
+
+__global__ void dkv_df_reduce_kernel(const double* __restrict__ part, int64_t ldp, int nsplit,
+                                     int cb, int nq, int ncols, double* __restrict__ G,
+                                     int64_t ldg, int64_t c_total, int k0, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y, k = blockIdx.z;
+    if (i >= n || k >= ncols) return;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(((int64_t)sp * cb + k) * nq + q) * ldp + i];
+    G[(int64_t)q * ldg * c_total + (int64_t)(k0 + k) * ldg + i] = s;
+}
+
 __global__ void kv_df_sym_reduce_kernel(const double* __restrict__ prow,
                                         const double* __restrict__ pcol, int nt, int G,
                                         int nchunk, int cb, int ncols,
@@ -1004,6 +1130,55 @@ void kv_xf(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo, fl
         kv_xf_sym_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)cb), 256, 0, st>>>(
             prow, pcol, nt, G, nchunk, cb, cb, Vk, ldv, noise, O + (int64_t)k0 * ldo, ldo, n);
         KPCG_LAUNCHED("kv_xf_sym_reduce_kernel");
+        k0 += cb;
+    }
+}
+
+template <int DP, int CB>
+static void dkv_df_launch1(const float4* xs, int64_t n, int nq, int ard, float c0h, float c0l,
+                           const double* W, int64_t ldw, int ncols, const float2* tab,
+                           double* part, const DfSplit& s, cudaStream_t st) {
+    dkv_df_kernel<DP, CB><<<dim3(s.nrb, s.nsplit), KT, 0, st>>>(xs, n, nq, ard, c0h, c0l, W, ldw,
+                                                               ncols, tab, part, s.ldp, s.cps);
+    KPCG_LAUNCHED("dkv_df_kernel");
+}
+
+void dkv_df(Ctx& h, const double* W, int64_t ldw, int c, double* G, int64_t ldg) {
+    if (h.n <= 0 || c <= 0) return;
+    if (h.dp > 16) fail(KPCG_ERR_ARG, "double-float derivative products need d <= 16");
+    df_prepare(h);
+    cudaStream_t st = h.stream;
+    const int64_t n = h.n;
+    const int nq = (h.ard ? h.d : 1) + 1;
+    const DfSplit s = df_plan(n);
+    const int max_cb = h.dp <= 8 ? 2 : 1;
+    double* part = h.kvws.part64.need((size_t)s.nsplit * max_cb * nq * s.ldp);
+    const float4* xs = reinterpret_cast<const float4*>(h.xdf.p);
+    const float2* tab = reinterpret_cast<const float2*>(h.df_tab.p);
+    for (int k0 = 0; k0 < c;) {
+        const int cb = std::min(max_cb, c - k0);
+        const double* Wk = W + (int64_t)k0 * ldw;
+#define KPCG_DKVDF(DPV)                                                                        \
+    case DPV:                                                                                  \
+        if (cb == 1)                                                                           \
+            dkv_df_launch1<DPV, 1>(xs, n, nq, h.ard, h.df_c0h, h.df_c0l, Wk, ldw, cb, tab, part, \
+                                   s, st);                                                     \
+        else if constexpr (DPV <= 8)                                                           \
+            dkv_df_launch1<DPV, 2>(xs, n, nq, h.ard, h.df_c0h, h.df_c0l, Wk, ldw, cb, tab, part, \
+                                   s, st);                                                     \
+        break;
+        switch (h.dp) {
+            KPCG_DKVDF(4)
+            KPCG_DKVDF(8)
+            KPCG_DKVDF(12)
+            KPCG_DKVDF(16)
+            default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
+        }
+#undef KPCG_DKVDF
+        dim3 rg((unsigned)((n + 255) / 256), (unsigned)nq, (unsigned)cb);
+        dkv_df_reduce_kernel<<<rg, 256, 0, st>>>(part, s.ldp, s.nsplit, cb, nq, cb, G, ldg, c, k0,
+                                                 n);
+        KPCG_LAUNCHED("dkv_df_reduce_kernel");
         k0 += cb;
     }
 }
