@@ -427,7 +427,9 @@ def run_warm(args):
         "vs_baseline": None, "dtype": "bf16x3+f32+f64 (network: fp32 train, bf16 infer)",
         "data": "synthetic",
         "config": {"workload": WARM_WORKLOAD, "trajectory_steps": n_steps, "n_train": n_train,
-                   "note": "shortened trajectory: the specified one has 200 steps, 50 for training"},
+                   "note": ("the specified trajectory" if (n_steps, n_train) == (200, 50) else
+                            "shortened trajectory: the specified one has 200 steps, 50 for "
+                            "training")},
         "warm": {"iters": wi, "solve_ms": wt, "mean_ms": statistics.mean(wt)},
         "cold": {"iters": ci, "solve_ms": ct, "mean_ms": statistics.mean(ct)},
         "iteration_ratio": sum(wi) / max(1, sum(ci)),
@@ -1320,8 +1322,8 @@ def main():
                     help="laplace15k: inducing points of the preconditioner of B (0: none)")
     ap.add_argument("--no-predict", action="store_true",
                     help="laplace15k: skip the predictions (a short target for profilers)")
-    ap.add_argument("--traj-steps", type=int, default=24, help="warm131k: trajectory length")
-    ap.add_argument("--traj-train", type=int, default=12, help="warm131k: training steps")
+    ap.add_argument("--traj-steps", type=int, default=200, help="warm131k: trajectory length")
+    ap.add_argument("--traj-train", type=int, default=50, help="warm131k: training steps")
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
                     help="batch64: only time full batched products (kv) or preconditioner "
                          "applies (precond) and exit; a small target for profilers")
