@@ -46,8 +46,8 @@ WORKLOAD = ("ARD-RBF n=65536 d=8 X~U[0,1]^8 l~LogU(0.3,3) s=1 noise=1e-4, y=sum 
 # The headline solver: flexible CG in FP64 (double-float outer directions,
 # native-FP64 certified residuals) around an inner FP32 PCG whose K.V runs on
 # the tensor cores, on the operator shifted by inner_shift * sigma^2.  The
-# shift and inner tolerance were picked by the sweep recorded in
-# profiles/precision_n65536.md.
+# shift and inner tolerance were picked by the sweep that
+# `--workload precision` runs.
 HEADLINE_PREC = "tc_ir"
 MODE_OPTS = {
     "tc_ir": dict(inner_shift=1.0, inner_tol=0.1),
@@ -407,30 +407,44 @@ def run_warm(args):
     pidx = synthetic.inducing_subset(p.n, 512, seed=3 + rank)
     probes = lambda k: torch.from_numpy(synthetic.rademacher(p.n, 4, 5000 + k)).to(dev)
     params = synthetic.mlp_init(11, p.d + 2, 256, 256, 4)
+    # the cold solve at the same theta (the comparison) on every k-th warm step
+    cmp_every = args.traj_compare_every
     tr = Trajectory(s, y, pidx, probes, basis="snapshots", q=4, lr=0.05, n_train=n_train,
-                    mlp_params=params, epochs=2000, mlp_lr=1e-3, tol=TOL, compare=True)
+                    mlp_params=params, epochs=2000, mlp_lr=1e-3, tol=TOL, compare=True,
+                    compare_every=cmp_every)
     z0 = np.concatenate([p.log_theta, [math.log(p.noise)]])
     stop_clock = sm_clock_probe()
     t0 = time.perf_counter()
     recs = tr.run(z0, n_steps)
     wall = time.perf_counter() - t0
     clocks = stop_clock()
-    warm = [r for r in recs if r.warm]
+    warm_all = [r for r in recs if r.warm]
+    if not warm_all:
+        raise SystemExit("the trajectory has no warm-started step: it needs more steps than "
+                         "--traj-train and more training steps than the 4 snapshots")
+    # ratios over the steps that ran both solves at the same theta
+    warm = [r for r in warm_all if r.cold_iters is not None]
     wi = [r.iters for r in warm]
     ci = [r.cold_iters for r in warm]
     wt = [r.solve_ms for r in warm]
     ct = [r.cold_ms for r in warm]
     line = {
         "metric": "per-solve time along the trajectory, learned warm start vs cold start",
-        "value": statistics.mean(wt) / 1e3, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "value": statistics.mean(r.solve_ms for r in warm_all) / 1e3, "unit": "s", "n_gpus": 1,
+        "steps": 1, "warmup": 0,
         "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f32+f64 (network: fp32 train, bf16 infer)",
         "data": "synthetic",
         "config": {"workload": WARM_WORKLOAD, "trajectory_steps": n_steps, "n_train": n_train,
+                   "cold_comparison_every": cmp_every,
                    "note": ("the specified trajectory" if (n_steps, n_train) == (200, 50) else
                             "shortened trajectory: the specified one has 200 steps, 50 for "
                             "training")},
-        "warm": {"iters": wi, "solve_ms": wt, "mean_ms": statistics.mean(wt)},
+        "warm": {"iters": wi, "solve_ms": wt, "mean_ms": statistics.mean(wt),
+                 "all_steps_mean_ms": statistics.mean(r.solve_ms for r in warm_all),
+                 "all_steps_iters": [r.iters for r in warm_all]},
+        "training_steps": {"iters": [r.iters for r in recs if not r.warm],
+                           "solve_ms": [r.solve_ms for r in recs if not r.warm]},
         "cold": {"iters": ci, "solve_ms": ct, "mean_ms": statistics.mean(ct)},
         "iteration_ratio": sum(wi) / max(1, sum(ci)),
         "time_ratio": sum(wt) / max(1e-9, sum(ct)),
@@ -932,7 +946,7 @@ KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
             "tcx_ir": "kv_tcx_kernel (tcgen05 sliced exponent, compensated contraction)",
             "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
             "df64": "kv_df_sym_kernel (double-float)", "fp64": "kv_f64_sym_kernel (FP64)"}
-# DRAM bytes per launch from ncu captures at n = 16384 (profiles/), by kernel
+# DRAM bytes per launch from ncu captures at n = 16384, by kernel
 # name, as a function of n: each kernel reads only its inputs from DRAM (the
 # n x n work stays on chip), so the traffic grows like n.  A kernel changed
 # since its capture has no entry.
@@ -1324,6 +1338,8 @@ def main():
                     help="laplace15k: skip the predictions (a short target for profilers)")
     ap.add_argument("--traj-steps", type=int, default=200, help="warm131k: trajectory length")
     ap.add_argument("--traj-train", type=int, default=50, help="warm131k: training steps")
+    ap.add_argument("--traj-compare-every", type=int, default=10,
+                    help="warm131k: a cold solve at the same theta on every k-th warm step")
     ap.add_argument("--probe", default="none", choices=["none", "kv", "precond"],
                     help="batch64: only time full batched products (kv) or preconditioner "
                          "applies (precond) and exit; a small target for profilers")

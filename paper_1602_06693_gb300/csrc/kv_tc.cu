@@ -128,6 +128,14 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy ones.  A consumer that read a ring stage with ordinary loads
+// issues it before releasing the stage: the mbarrier release alone does not
+// keep the next bulk copy into the stage (async proxy) from landing before
+// those loads were performed, and then they return the next tile's data.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -152,7 +160,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// 32 columns without the wait (tmem_wait_ld() completes them).
+// 32 columns without the wait (tmem_wait_ld_bind() completes them).
 __device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -166,8 +174,22 @@ __device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t* r) {
           "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// The registers of tcgen05.ld are undefined until tcgen05.wait::ld.  The load
+// asm declares them as outputs, so without a tie the compiler may schedule
+// their uses between the load and the wait; these two bind 32 registers at a
+// time to the wait (the first executes it, the second is an empty statement
+// that volatile ordering keeps after it), so every use follows the wait.
+__device__ __forceinline__ void tmem_wait_ld_bind(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_bind32(uint32_t* r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 __device__ __forceinline__ float ex2(float a) {
     float y;
@@ -574,7 +596,9 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                 uint32_t r[W];
 #pragma unroll
                 for (int w = 0; w < W; w += 32) tmem_ld32_nw(taddr + ps * W + w, r + w);
-                tmem_wait_ld();
+                tmem_wait_ld_bind(r);
+#pragma unroll
+                for (int w = 32; w < W; w += 32) tmem_bind32(r + w);
                 if (ps == NP - 1) {
                     fence_before();
                     __syncwarp();
@@ -638,6 +662,7 @@ __global__ void __launch_bounds__(NWARPS * 32, KCH == 1 ? 2 : 1)
                     }
                 }
             }
+            fence_proxy_async();
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -1217,6 +1242,7 @@ __global__ void __launch_bounds__(NWARPS * 32, 1)
                         }
                     }
                 }
+                fence_proxy_async();
                 fence_before();
                 __syncwarp();
                 if (lane == 0) {

@@ -52,7 +52,7 @@ class StepRecord:
 class Trajectory:
     def __init__(self, solver: "_b.Solver", y, precond_idx, probes_fn, *, basis="snapshots",
                  q=4, basis_idx=None, lr=0.05, n_train=50, mlp_params=None, epochs=2000,
-                 mlp_lr=1e-3, tol=1e-8, ridge=None, compare=False):
+                 mlp_lr=1e-3, tol=1e-8, ridge=None, compare=False, compare_every=1):
         import torch
 
         self.torch = torch
@@ -66,6 +66,7 @@ class Trajectory:
         self.mlp_lr = mlp_lr
         self.tol = tol
         self.compare = compare
+        self.compare_every = max(1, int(compare_every))
         self.basis = basis
         self.q = q
         if basis == "snapshots":
@@ -124,7 +125,7 @@ class Trajectory:
         s.precond(_b.KPCG_PREC_NYSTROM, len(self.precond_idx), self.precond_idx)
         warm = self.mlp is not None
         cold_it = cold_ms = None
-        if warm and self.compare:
+        if warm and self.compare and (k - self.n_train) % self.compare_every == 0:
             _, cold_it, cold_ms, _ = self._timed_solve(None)
         x0 = self.predict_x0(z) if warm else None
         alpha, it, ms, rel = self._timed_solve(x0)
@@ -144,7 +145,8 @@ class Trajectory:
         self.m1 = np.zeros_like(z)
         self.m2 = np.zeros_like(z)
         for k in range(steps):
-            if k == self.n_train and self.mlp is None and self.mlp_params is not None:
+            if (k == self.n_train and self.mlp is None and self.mlp_params is not None
+                    and self.inputs):
                 self.train()
             g = self.step(k, z)
             # Adam ascent on log p
