@@ -1188,7 +1188,8 @@ KV_IMPLS = {"f64": ("f64", 0, "kv_f64_sym_kernel (native FP64)"),
             "f32": ("f32", 0, "kv_simt_kernel<float>"),
             "tc": ("f32", 1, "kv_tc_kernel (tcgen05, BF16x3 exponent)"),
             "xf": ("f32", 3, "kv_xf_sym_kernel (exact differences)"),
-            "tcx": ("f32", 4, "kv_tcx_kernel (tcgen05, sliced per-point-exact exponent)")}
+            "tcx": ("f32", 4, "kv_tcx_kernel (tcgen05, sliced per-point-exact exponent)"),
+            "tcv": ("f32", 5, "kv_tcv_kernel (tcgen05 exponent and tcgen05 contraction)")}
 
 
 def run_kv(args):

@@ -248,7 +248,12 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
  *         solver uses); impl 2 and 3 need d <= 16;
  * impl 4: the KPCG_TCX_IR inner kernel (tcgen05 on sliced per-point-exact
  *         operands, compensated row sums); d <= 10, a bounded wait that
- *         expires returns KPCG_ERR_TIMEOUT. */
+ *         expires returns KPCG_ERR_TIMEOUT.
+ * impl 5: tcgen05 for both contractions: the exponent as impl 1, then the
+ *         exponentiated tile as FP16 (hi, lo) pairs in tensor memory against
+ *         V as FP16 pairs scaled per column (~2^-21 relative per product);
+ *         the KPCG_TC_IR inner product for blocks of 4 or more columns; d <= 20,
+ *         KPCG_ERR_TIMEOUT as impl 1. */
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 
@@ -511,12 +516,21 @@ kpcg_status kpcg_batch_matvec_f32(kpcg_batch_t b, const float* V, int64_t ld, in
 kpcg_status kpcg_batch_precond_apply_f32(kpcg_batch_t b, const float* R, int64_t ld, int32_t c,
                                          float* Z);
 /* Autotuner of the batched product for c columns per problem: times each
- * candidate length of the work-list items (1 .. 64 column tiles of 128) on one
- * persistent CTA per SM with CUDA events and keeps the fastest.  Runs by itself
- * before the first product unless kpcg_batch_set_tiling fixed the tiling.
+ * candidate length of the work-list items (1 .. 64 column tiles of 128) with
+ * each contraction path (see kpcg_batch_set_contraction) on one persistent
+ * CTA per SM with CUDA events and keeps the fastest.  Runs by itself before
+ * the first product unless kpcg_batch_set_tiling fixed the tiling.
  * Outputs (host, nullable): the chosen length, CTAs, and its time in ms. */
 kpcg_status kpcg_batch_tune(kpcg_batch_t b, int32_t c, int32_t* tiles_per_item, int32_t* ctas,
                             float* best_ms);
+/* The second contraction of the batched product (the exponentiated tile
+ * times V): 0 FP32 FMAs in the epilogue, pairs of row tiles sharing each
+ * shared-memory read of V; 1 the tile as FP16 (hi, lo) pairs in tensor memory
+ * against V as FP16 pairs scaled per problem and column, on the tensor cores
+ * (d <= 20; ~2^-21 relative per product); -1 (default) the autotuner's
+ * choice, or with a fixed tiling the tensor cores from 4 columns per problem.
+ * KPCG_ERR_ARG for another mode or mode 1 with a problem of d > 20. */
+kpcg_status kpcg_batch_set_contraction(kpcg_batch_t b, int32_t mode);
 /* Replace the options of the batch and of its problems (precision must stay
  * KPCG_TC_IR).  With opt->profile == 0 the inner CG replays chunks of
  * check_every iterations from a captured CUDA graph; with profiling on it

@@ -39,7 +39,7 @@ SYMBOLS = (
     "kpcg_batch_tune", "kpcg_batch_set_tiling", "kpcg_batch_set_options", "kpcg_batch_max_n",
     "kpcg_batch_destroy",
     "kpcg_batch_last_error", "kpcg_precond_spectral", "kpcg_laplace", "kpcg_laplace_predict",
-    "kpcg_precond_pitc", "kpcg_probe_rates",
+    "kpcg_precond_pitc", "kpcg_probe_rates", "kpcg_batch_set_contraction",
 )
 
 _NO_STATUS = ("kpcg_destroy", "kpcg_last_error", "kpcg_mlp_destroy", "kpcg_mlp_last_error",
@@ -186,6 +186,7 @@ def lib():
         L.kpcg_batch_tune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), pflt]
         L.kpcg_batch_set_tiling.argtypes = [vp, i32, i32]
+        L.kpcg_batch_set_contraction.argtypes = [vp, i32]
         L.kpcg_batch_set_options.argtypes = [vp, ctypes.POINTER(Options)]
         L.kpcg_batch_max_n.argtypes = [vp]
         L.kpcg_batch_max_n.restype = ctypes.c_int64
@@ -738,6 +739,10 @@ class Batch:
 
     def set_tiling(self, tiles_per_item, ctas=0):
         self._check(lib().kpcg_batch_set_tiling(self._h, int(tiles_per_item), int(ctas)))
+
+    def set_contraction(self, mode):
+        """-1 autotuner's choice, 0 FP32 FMAs, 1 tensor cores (kpcg_batch_set_contraction)."""
+        self._check(lib().kpcg_batch_set_contraction(self._h, int(mode)))
 
     def close(self):
         if getattr(self, "_h", None):

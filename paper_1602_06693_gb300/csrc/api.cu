@@ -553,7 +553,7 @@ static MixedOps single_ops(Ctx& h) {
         if (tcx)
             kv_tcx_apply(h, V, ldv, cc, O, ldo, inner_noise);
         else if (tc)
-            kv_tc_apply(h, V, ldv, cc, O, ldo, inner_noise);
+            kv_tc_inner(h, V, ldv, cc, O, ldo, inner_noise);
         else if (xf)
             kv_xf(h, V, ldv, cc, O, ldo, inner_noise, 1);
         else
@@ -1175,6 +1175,12 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             if (!kpcg::kv_tcx_supported(h->d))
                 fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
             kpcg::kv_tcx_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
+        } else if (impl == 5) {
+            if (!kpcg::kv_tcv_supported(h->d))
+                fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
+            kpcg::kv_tcv_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
             if (kpcg::kv_tc_error(*h))
                 fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         } else {

@@ -47,6 +47,8 @@ struct kpcg_batch {
     kpcg::DevBuf<int64_t> nrow;  // n_p per problem (device)
     kpcg::TcBatch tc;
     int tc_G = 0, tc_grid = 0;   // 0: autotune at the first product
+    int tc_tcv = -1;             // contraction on the tensor cores (-1: not chosen yet)
+    int tcv_mode = -1;           // the caller's choice of it (-1: autotuner / column count)
     float tuned_ms = 0.f;
     kpcg::NysBatch nys;
     kpcg::DevBuf<double> Bp, Xp;
@@ -66,8 +68,9 @@ std::vector<Ctx*> subs_of(const kpcg_batch& b) {
 }
 
 // Time the batched product for each candidate run length (tiles per work
-// item) and keep the fastest; the grid is one persistent CTA per SM (the
-// kernel's shared memory admits one).
+// item) and each contraction path (FP32 FMAs on pairs of row tiles, or the
+// tensor cores) and keep the fastest; the grid is one persistent CTA per SM
+// (the kernels' shared memory admits one).
 void autotune(kpcg_batch& b, int c) {
     cudaStream_t st = b.M.stream;
     const int64_t ld = b.M.ld;
@@ -80,10 +83,16 @@ void autotune(kpcg_batch& b, int c) {
     cudaEvent_t e0, e1;
     KPCG_CUDA(cudaEventCreate(&e0));
     KPCG_CUDA(cudaEventCreate(&e1));
-    int bestG = 8;
+    int bestG = 8, bestV = 0;
+    b.tc_tcv = -1;
     float best = INFINITY;
+    bool tcv_ok = true;
+    for (auto* h : b.sub) tcv_ok = tcv_ok && kv_tcv_supported(h->d);
+    const int tcv_lo = b.tcv_mode >= 0 ? b.tcv_mode : 0;
+    const int tcv_hi = b.tcv_mode >= 0 ? b.tcv_mode : (tcv_ok ? 1 : 0);
+    for (int tcv = tcv_lo; tcv <= tcv_hi; ++tcv)
     for (int G : {1, 2, 4, 8, 16, 32, 64}) {
-        tc_batch_plan(b.tc, subs, noise, G, 0, st);
+        tc_batch_plan(b.tc, subs, noise, G, 0, st, tcv);
         kv_tc_batch(b.tc, V, ld, c, O, ld, b.M.n, nullptr, st);  // warm-up
         KPCG_CUDA(cudaEventRecord(e0, st));
         for (int r = 0; r < 3; ++r) kv_tc_batch(b.tc, V, ld, c, O, ld, b.M.n, nullptr, st);
@@ -95,6 +104,7 @@ void autotune(kpcg_batch& b, int c) {
         if (ms < best) {
             best = ms;
             bestG = G;
+            bestV = tcv;
         }
     }
     cudaEventDestroy(e0);
@@ -102,12 +112,19 @@ void autotune(kpcg_batch& b, int c) {
     if (kv_tc_batch_error(b.tc, st)) fail(KPCG_ERR_TIMEOUT, "a bounded wait in the batched K.V expired");
     b.tc_G = bestG;
     b.tc_grid = sm_count_tc();
+    b.tc_tcv = bestV;
     b.tuned_ms = best;
 }
 
 void ensure_tc(kpcg_batch& b, int c) {
     if (b.tc_G == 0) autotune(b, c);
-    tc_batch_plan(b.tc, subs_of(b), inner_noise(b), b.tc_G, b.tc_grid, b.M.stream);
+    if (b.tcv_mode >= 0) b.tc_tcv = b.tcv_mode;
+    if (b.tc_tcv < 0) {  // a tiling fixed by the caller: the path by the column count
+        bool ok = true;
+        for (auto* h : b.sub) ok = ok && kv_tcv_supported(h->d);
+        b.tc_tcv = (ok && c >= 4) ? 1 : 0;
+    }
+    tc_batch_plan(b.tc, subs_of(b), inner_noise(b), b.tc_G, b.tc_grid, b.M.stream, b.tc_tcv);
 }
 
 void ensure_nys(kpcg_batch& b, int c) {
@@ -224,6 +241,20 @@ kpcg_status kpcg_batch_set_tiling(kpcg_batch_t b, int32_t tiles_per_item, int32_
         if (tiles_per_item < 1 || ctas < 0) fail(KPCG_ERR_ARG, "bad tiling");
         b->tc_G = tiles_per_item;
         b->tc_grid = ctas;
+    });
+    return KPCG_OK;
+}
+
+kpcg_status kpcg_batch_set_contraction(kpcg_batch_t b, int32_t mode) {
+    if (!b) return KPCG_ERR_ARG;
+    BATCH_GUARD(b, {
+        if (mode < -1 || mode > 1) fail(KPCG_ERR_ARG, "mode must be -1, 0 or 1");
+        if (mode == 1)
+            for (auto* h : b->sub)
+                if (!kpcg::kv_tcv_supported(h->d))
+                    fail(KPCG_ERR_ARG, "the tensor-core contraction supports d <= 20");
+        b->tcv_mode = mode;
+        b->tc_tcv = mode;
     });
     return KPCG_OK;
 }

@@ -132,6 +132,13 @@ struct Ctx {
     DevBuf<uint16_t> tcA, tcB;
     DevBuf<float> tcV, tcPart;
     DevBuf<int> tc_err;
+    // tensor-core K.V with the contraction on the tensor cores (kv_tcv_apply):
+    // exponent operands of 2^14 K / s^2, V staged as FP16 pairs, partials,
+    // per-column max and exponent of V
+    int tcv_version = -1, tcv_kch = 0;
+    DevBuf<uint16_t> tcvA, tcvB, tcvV;
+    DevBuf<float> tcvPart;
+    DevBuf<int> tcvAux;
     // per-point-exact tensor-core operands (kv_tcx_apply), rebuilt when theta changes
     int tcx_version = -1, tcx_kch = 0, tcx_nmma = 0;
     float tcx_escale = 1.f;
@@ -186,6 +193,28 @@ void kv_tcx_apply64(Ctx& h, const double* V, int64_t ldv, int c, double* O, int6
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);
+// The BF16x3 augmented exponent operands of kv_tc.cu for the handle's inputs
+// with log2(s^2) replaced by c0 (K-dim kch x 64), written to A and B.
+void tc_prep_operands(const Ctx& h, int kch, double c0, uint16_t* A, uint16_t* B);
+int sm_count_tc();
+// Tensor-core K.V with the second contraction on the tensor cores as well
+// (kv_tcv.cu; d <= 20): FP32 in and out, the exponentiated tile as FP16
+// pairs in tensor memory against V as FP16 pairs.
+void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                  float noise);
+bool kv_tcv_supported(int d);
+// Column count from which the inner products of the mixed solvers use
+// kv_tcv_apply: below it the FP32-FMA contraction of kv_tc_apply costs less
+// issue per entry than the FP16 split of the tile, above it more.
+constexpr int kTcvMinCols = 4;
+// The tensor-core inner product of the mixed solvers for c columns.
+inline void kv_tc_inner(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                        float noise) {
+    if (c >= kTcvMinCols && kv_tcv_supported(h.d))
+        kv_tcv_apply(h, V, ldv, c, O, ldo, noise);
+    else
+        kv_tc_apply(h, V, ldv, c, O, ldo, noise);
+}
 
 }  // namespace kpcg
 

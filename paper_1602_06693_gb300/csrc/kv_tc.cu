@@ -37,171 +37,14 @@
 
 #include "batch.cuh"
 #include "ctx.cuh"
+#include "tcgen05.cuh"
 
 namespace kpcg {
 namespace {
 
-constexpr int TM = 128;          // rows per tile (MMA M)
-constexpr int TN = 128;          // columns per tile (MMA N)
-constexpr int KC = 64;           // bf16 per 128-byte swizzle row
-constexpr int SUB = TM * KC;     // elements per 16 KB sub-tile
 constexpr int NSTAGE = 4;
 constexpr int NWARPS = 10;
 constexpr int NEPI = 8;          // epilogue warps
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b))
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-            su32(b)),
-        "r"(bytes)
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 "
-        "%0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait on the phase of the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t deadline) {
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try(b, parity)) return true;
-        if ((it & 255u) == 0 && gtimer() > deadline) return false;
-    }
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(su32(dst)),
-        "l"(src), "r"(bytes), "r"(su32(bar))
-        : "memory");
-}
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused: swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-    return d;
-}
-// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, K-major A and B.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], "
-        "%1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* b) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            su32(b))
-        : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Orders this thread's generic-proxy shared-memory accesses before later
-// async-proxy ones.  A consumer that read a ring stage with ordinary loads
-// issues it before releasing the stage: the mbarrier release alone does not
-// keep the next bulk copy into the stage (async proxy) from landing before
-// those loads were performed, and then they return the next tile's data.
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-// 32 columns without the wait (tmem_wait_ld_bind() completes them).
-__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-}
-// The registers of tcgen05.ld are undefined until tcgen05.wait::ld.  The load
-// asm declares them as outputs, so without a tie the compiler may schedule
-// their uses between the load and the wait; these two bind 32 registers at a
-// time to the wait (the first executes it, the second is an empty statement
-// that volatile ordering keeps after it), so every use follows the wait.
-__device__ __forceinline__ void tmem_wait_ld_bind(uint32_t* r) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_bind32(uint32_t* r) {
-    asm volatile(""
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-__device__ __forceinline__ float ex2(float a) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
-    return y;
-}
-
-// Byte offset of element (r, k) inside a 128-row x 64-col swizzled sub-tile.
-__device__ __forceinline__ uint32_t swz_off(int r, int k) {
-    const int chunk = (k >> 3) ^ (r & 7);
-    return (uint32_t)(r * 128 + chunk * 16 + (k & 7) * 2);
-}
 
 __device__ __forceinline__ void split3(double v, __nv_bfloat16& h, __nv_bfloat16& m,
                                        __nv_bfloat16& l) {
@@ -791,6 +634,14 @@ int sm_count_tc() {
 
 bool kv_tc_supported(int dp) { return dp <= 16; }
 
+void tc_prep_operands(const Ctx& h, int kch, double c0, uint16_t* A, uint16_t* B) {
+    const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
+    tc_prep_kernel<<<(unsigned)((n_pad + 127) / 128), 128, 0, h.stream>>>(
+        h.xs64.p, h.n, n_pad, h.d, h.dp, kch, std::sqrt(kLog2e), c0,
+        reinterpret_cast<__nv_bfloat16*>(A), reinterpret_cast<__nv_bfloat16*>(B));
+    KPCG_LAUNCHED("tc_prep_kernel");
+}
+
 void tc_prepare(Ctx& h) {
     cudaStream_t st = h.stream;
     const int64_t n = h.n;
@@ -1339,10 +1190,11 @@ void launch_tc_batch(TcBatch& b, int ncols, const int* active, int cpp, cudaStre
 }  // namespace
 
 void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<float>& noise,
-                   int G, int grid, cudaStream_t st) {
+                   int G, int grid, cudaStream_t st, int tcv) {
     if (G < 1) fail(KPCG_ERR_ARG, "tiles per item must be >= 1");
     b.P = (int)subs.size();
     b.G = G;
+    b.tcv = tcv ? 1 : 0;
     b.grid = grid > 0 ? grid : sm_count_tc();
     b.hprobs.assign((size_t)b.P, TcBatchProb{});
     std::vector<TcBatchItem> items;
@@ -1351,20 +1203,27 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
     int32_t rt_base = 0;
     for (int p = 0; p < b.P; ++p) {
         Ctx& h = *subs[(size_t)p];
-        tc_prepare(h);
+        if (b.tcv)
+            tcv_prepare(h);
+        else
+            tc_prepare(h);
         const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
         const int n_t = (int)(n_pad / TM);
         TcBatchProb& pb = b.hprobs[(size_t)p];
-        pb.A = h.tcA.p;
-        pb.B = h.tcB.p;
+        pb.A = b.tcv ? h.tcvA.p : h.tcA.p;
+        pb.B = b.tcv ? h.tcvB.p : h.tcB.p;
         pb.voff = voff;
         pb.n = (int32_t)h.n;
         pb.n_pad = (int32_t)n_pad;
-        pb.kch = h.tc_kch;
+        pb.kch = b.tcv ? h.tcv_kch : h.tc_kch;
         pb.rt_base = rt_base;
         pb.noise = noise[(size_t)p];
-        for (int rt = 0; rt < n_t; rt += 2) {
-            const int two = (rt + 1 < n_t) ? 1 : 0;
+        pb.s2 = (float)h.s2;
+        // pairs of row tiles share the V reads of the FP32 contraction; the
+        // tensor-core contraction takes one row tile per item
+        const int step = b.tcv ? 1 : 2;
+        for (int rt = 0; rt < n_t; rt += step) {
+            const int two = (!b.tcv && rt + 1 < n_t) ? 1 : 0;
             first.push_back((int32_t)items.size());
             int cnt = 0;
             for (int jt0 = 0; jt0 < n_t; jt0 += G, ++cnt)
@@ -1372,7 +1231,7 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
             count.push_back(cnt);
         }
         voff += n_pad;
-        rt_base += (n_t + 1) / 2;
+        rt_base += (n_t + step - 1) / step;
     }
     b.nv = voff;
     b.nitems = (int)items.size();
@@ -1388,8 +1247,14 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
                               cudaMemcpyHostToDevice, st));
     KPCG_CUDA(cudaMemcpyAsync(b.rt_count.p, count.data(), sizeof(int32_t) * count.size(),
                               cudaMemcpyHostToDevice, st));
-    b.Vs.need((size_t)b.nv * 16);
-    b.part.need((size_t)b.nitems * 2 * 2 * 16 * TM);
+    if (b.tcv) {
+        b.Vh.need((size_t)b.nv * 64);
+        b.part.need((size_t)b.nitems * 32 * TM);
+        b.aux.need((size_t)b.P * 64);
+    } else {
+        b.Vs.need((size_t)b.nv * 16);
+        b.part.need((size_t)b.nitems * 2 * 2 * 16 * TM);
+    }
     if (!b.err.p) {
         b.err.need(1);
         KPCG_CUDA(cudaMemsetAsync(b.err.p, 0, sizeof(int), st));
@@ -1401,6 +1266,10 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
 void kv_tc_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
                  int64_t nrows, const int* active, cudaStream_t st) {
     if (b.P == 0) return;
+    if (b.tcv) {
+        kv_tcv_batch(b, V, ldv, c, O, ldo, nrows, active, st);
+        return;
+    }
     int64_t nmax_pad = 0;
     for (const auto& pb : b.hprobs) nmax_pad = std::max<int64_t>(nmax_pad, pb.n_pad);
     for (int k0 = 0; k0 < c;) {

@@ -257,7 +257,7 @@ MixedOps lap_mixed_ops(Ctx* hp, const VecOp& mvB, const LapMixed& m, bool tc, bo
         lap_scale_kernel<float><<<gg, 256, 0, H.stream>>>(m.w32, H.ld, V, ldv, m.sW32, H.n);
         KPCG_LAUNCHED("lap_scale_kernel");
         if (tc)
-            kv_tc_apply(H, m.w32, H.ld, cc, m.u32, H.ld, 0.f);
+            kv_tc_inner(H, m.w32, H.ld, cc, m.u32, H.ld, 0.f);
         else
             kv_f32(H.xs32.p, H.n, H.dp, H.c0_32(), 0.f, m.w32, H.ld, cc, m.u32, H.ld, H.kvws,
                    H.stream);

@@ -1159,6 +1159,7 @@ void precond_apply_f32(const PrecondState& P, const float* R, int64_t ldr, int c
 namespace {
 
 constexpr int kSplitRows = 512;
+constexpr int kRb = 8;  // rows (projection) or row chunks (back product) loaded per batch
 
 __device__ __forceinline__ bool nb_live(const int* __restrict__ active, int p, int c) {
     if (!active) return true;
@@ -1197,16 +1198,31 @@ __global__ void __launch_bounds__(256)
         const int rn = (int)min((int64_t)128, r1 - rs);
         if (a < m) {
             const float2* Kp = pb.KXU + rs * m + a;
-#pragma unroll 2
-            for (int r = 0; r < rn; ++r) {
+            // batches of kRb rows: their loads are issued before any is used, so
+            // each thread keeps kRb * 8 bytes of K_XU in flight (the pass is
+            // bound by HBM latency times the bytes in flight, not by the Dot2)
+            int r = 0;
+            for (; r + kRb <= rn; r += kRb) {
+                float2 kv[kRb];
+#pragma unroll
+                for (int u = 0; u < kRb; ++u) kv[u] = __ldg(Kp + (int64_t)(r + u) * m);
+#pragma unroll
+                for (int u = 0; u < kRb; ++u)
+#pragma unroll
+                    for (int k = 0; k < NC; ++k)
+                        if (k < ncols) {
+                            dot2_add(acc[k], kv[u].x, sr[r + u][k]);
+                            acc[k].c = fmaf(kv[u].y, sr[r + u][k], acc[k].c);
+                        }
+            }
+            for (; r < rn; ++r) {
                 const float2 kv = __ldg(Kp + (int64_t)r * m);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
+                for (int k = 0; k < NC; ++k)
                     if (k < ncols) {
                         dot2_add(acc[k], kv.x, sr[r][k]);
                         acc[k].c = fmaf(kv.y, sr[r][k], acc[k].c);
                     }
-                }
             }
         }
     }
@@ -1219,17 +1235,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// w = sum of the split partials: a warp per entry (lanes stride over the
+// splits, then a fixed-order warp sum), so the dependent FP64 adds of one
+// entry are ~nsplit / 32 instead of nsplit.
 __global__ void nys_batch_sum_kernel(const NysBatchProb* __restrict__ probs, int c,
                                      const int* __restrict__ active,
                                      const double* __restrict__ part, double* __restrict__ w) {
     const int p = blockIdx.y;
     const NysBatchProb pb = probs[p];
     const int64_t len = (int64_t)c * pb.m;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (e >= len || !nb_live(active, p, c)) return;
     double s = 0.0;
-    for (int sp = 0; sp < pb.nsplit; ++sp) s += part[pb.pbase + (int64_t)sp * len + e];
-    w[pb.wbase + e] = s;
+    for (int sp = lane; sp < pb.nsplit; sp += 32) s += part[pb.pbase + (int64_t)sp * len + e];
+    s = warp_sum(s);
+    if (lane == 0) w[pb.wbase + e] = s;
 }
 
 // y = L^{-1} w per problem and column (same scheme as tri_lower_apply_kernel).
@@ -1335,18 +1356,27 @@ __global__ void __launch_bounds__(256)
         Acc2 acc[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) acc[k] = {0.f, 0.f};
-        // unrolled for several loads of K_XU in flight per warp (occupancy is
-        // limited by the staged coefficients)
-#pragma unroll 4
-        for (int64_t a = lane; a < pb.m; a += 32) {
-            const float2 kv = __ldg(Ki + a);
+        // the row in batches of kRb chunks of 32 entries, all loads of a batch
+        // issued before any is used (bytes in flight, as in the projection)
+        for (int64_t a0 = lane; a0 < pb.m; a0 += 32 * kRb) {
+            float2 kv[kRb];
 #pragma unroll
-            for (int k = 0; k < NC; ++k)
-                if (k < ncols) {
-                    const float2 uv = up[(int64_t)k * pb.m + a];
-                    dot2_add(acc[k], kv.x, uv.x);
-                    acc[k].c = fmaf(kv.x, uv.y, fmaf(kv.y, uv.x, acc[k].c));
-                }
+            for (int u = 0; u < kRb; ++u) {
+                const int64_t a = a0 + 32 * u;
+                kv[u] = (a < pb.m) ? __ldg(Ki + a) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kRb; ++u) {
+                const int64_t a = a0 + 32 * u;
+                if (a >= pb.m) break;
+#pragma unroll
+                for (int k = 0; k < NC; ++k)
+                    if (k < ncols) {
+                        const float2 uv = up[(int64_t)k * pb.m + a];
+                        dot2_add(acc[k], kv[u].x, uv.x);
+                        acc[k].c = fmaf(kv[u].x, uv.y, fmaf(kv[u].y, uv.x, acc[k].c));
+                    }
+            }
         }
         // warp sum of the pairs with TwoSum on every step (FP64 adds would
         // hold the FP64 pipe, ~1/64 rate, longer than the whole sweep above)
@@ -1460,7 +1490,7 @@ void nys_batch_apply(NysBatch& nb, const float* R, int64_t ldr, float* Z, int64_
                                                             nb.part.p);
             KPCG_LAUNCHED("nys_batch_proj_kernel");
         }
-        nys_batch_sum_kernel<<<dim3((unsigned)((c * nb.mmax + 255) / 256), (unsigned)nb.P), 256, 0,
+        nys_batch_sum_kernel<<<dim3((unsigned)((c * nb.mmax + 7) / 8), (unsigned)nb.P), 256, 0,
                                st>>>(nb.probs.p, c, active, nb.part.p, nb.w.p);
         KPCG_LAUNCHED("nys_batch_sum_kernel");
         nys_batch_lower_kernel<<<(unsigned)std::max(1, std::min(nb.nL, 2 * 152)), 1024, 0,

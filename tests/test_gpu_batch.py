@@ -55,11 +55,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_batched_product_matches_oracle(kpcg):
+@pytest.mark.parametrize("contraction,c", [(0, 3), (1, 3), (1, 9), (0, 9)])
+def test_batched_product_matches_oracle(kpcg, contraction, c):
+    # contraction 0: FP32 FMAs on pairs of row tiles; 1: the exponentiated tile
+    # as FP16 pairs in tensor memory against V on the tensor cores
     probs = _problems(SIZES)
-    c, shift = 3, 0.5
+    shift = 0.5
     V = [synthetic.rng(50 + k).standard_normal((p.n, c)) for k, (p, _) in enumerate(probs)]
     with _batch(kpcg, probs, inner_shift=shift) as b:
+        b.set_contraction(contraction)
         Vb = b.block(V, torch.float32)
         O = b.matvec_f32(Vb, c)
         again = b.matvec_f32(Vb, c)

@@ -148,6 +148,33 @@ def test_matvec_tensor_core_many_tiles_per_cta(kpcg, n, d, c):
         assert _rel(out[rows, k], ref[:, k]) <= 2e-5, k
 
 
+@pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 2), (1000, 8, 3), (4099, 16, 9),
+                                   (300, 9, 17), (129, 5, 8), (2000, 20, 24), (1500, 6, 40),
+                                   (16384, 10, 4), (14979, 14, 17)])
+def test_matvec_tensor_core_contraction_matches_oracle(kpcg, n, d, c):
+    # Both contractions on tcgen05: the exponent as impl 1, the exponentiated
+    # tile as FP16 (hi, lo) pairs in tensor memory against V as FP16 pairs
+    # scaled per column.  Each product carries ~2^-21 relative error,
+    # independent per entry, on top of impl 1's: well inside 2e-5 of the norm.
+    # The larger cases walk many column tiles per CTA; c = 40 takes two blocks.
+    p = _problem(n, d, seed=13 * n + d, ard=True, ell=1.0 if n > 5000 else None)
+    V = synthetic.rng(17).standard_normal((n, c))
+    V[:, 0] *= 1e-3  # columns of different scales
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    if n <= 5000:
+        rows = np.arange(n)
+        ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    else:
+        rows = np.sort(synthetic.rng(19).choice(n, 64, replace=False))
+        ref = oracle.gram(p.X[rows], p.X, ell, s2) @ V + p.noise * V[rows]
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=5))
+        again = _np(s.matvec_f32(_cm(V, torch.float32), impl=5))
+    np.testing.assert_array_equal(out, again)
+    for k in range(c):
+        assert _rel(out[rows, k], ref[:, k]) <= 2e-5, k
+
+
 @pytest.mark.parametrize("impl", [2, 3, 4])
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 2),
                                    (513, 12, 5), (6000, 8, 1), (129, 4, 2), (2000, 10, 9),
