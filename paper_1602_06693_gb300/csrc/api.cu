@@ -1137,7 +1137,18 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
             kpcg::kv_f64_sym(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
         else if (impl == 1)
             kpcg::kv_df(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
-        else if (impl == 2) {
+        else if (impl == 3) {
+            // the double-float kernel on the FP32 pipe alone (no tensor-core distances)
+            const bool saved = h->df_tensor;
+            h->df_tensor = false;
+            try {
+                kpcg::kv_df(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
+            } catch (...) {
+                h->df_tensor = saved;
+                throw;
+            }
+            h->df_tensor = saved;
+        } else if (impl == 2) {
             if (!kpcg::kv_tcx_supported(h->d))
                 fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");
             kpcg::kv_tcx_apply64(*h, V, ldv, c, O, ldo, h->noise);

@@ -139,6 +139,12 @@ struct Ctx {
     DevBuf<uint16_t> tcvA, tcvB, tcvV;
     DevBuf<float> tcvPart;
     DevBuf<int> tcvAux;
+    // double-float product with sliced tensor-core distances (kv_tcd.cu)
+    int tcd_version = -1;
+    DevBuf<uint16_t> tcdA, tcdB;
+    DevBuf<float2> tcdV;
+    DevBuf<double> tcdPart, tcd_max;
+    bool df_tensor = true;  // kv_df uses kv_tcd where supported (cleared by tests of the other)
     // per-point-exact tensor-core operands (kv_tcx_apply), rebuilt when theta changes
     int tcx_version = -1, tcx_kch = 0, tcx_nmma = 0;
     float tcx_escale = 1.f;
@@ -203,6 +209,14 @@ int sm_count_tc();
 void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
                   float noise);
 bool kv_tcv_supported(int d);
+// Double-float K.V (FP64 in and out, arguments of kv_df) with the squared
+// distances from exact integer level sums on the tensor cores (kv_tcd.cu;
+// d <= 10); the exp2 and the contraction in double-float on the FP32 pipe.
+void kv_tcd(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb, double* O,
+            int64_t ldo, double noise);
+bool kv_tcd_supported(const Ctx& h);
+// Double-float inputs of the handle (exp2 table, log2(s^2) pair), kv_df.cu.
+void df_prepare(Ctx& h);
 // Column count from which the inner products of the mixed solvers use
 // kv_tcv_apply: below it the FP32-FMA contraction of kv_tc_apply costs less
 // issue per entry than the FP16 split of the tile, above it more.

@@ -35,15 +35,13 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "df_arith.cuh"
 
 namespace kpcg {
 namespace {
 
 constexpr int KT = 256;
 constexpr int TJ = 64;
-constexpr int NTAB = 257;  // 2^(j/256), j = -128..128
-constexpr float kLn2Hi = 0.6931471824645996f;     // fl(ln 2)
-constexpr float kLn2Lo = -1.9046542121259336e-09f;  // fl(ln 2 - kLn2Hi)
 
 int sm_count_df() {
     static int cached = 0;
@@ -54,75 +52,6 @@ int sm_count_df() {
         if (cached <= 0) cached = 148;
     }
     return cached;
-}
-
-struct DF {
-    float h, l;
-};
-
-// a := a - (P + Pe) with TwoSum on the high parts.
-__device__ __forceinline__ void df_sub(float& ah, float& al, float P, float Pe) {
-    const float s = ah - P;
-    const float bb = s - ah;
-    const float err = (ah - (s - bb)) + (-P - bb);
-    ah = s;
-    al += err - Pe;
-}
-// (S, C) += (P, Pe) with TwoSum on the high parts.
-__device__ __forceinline__ void df_acc(float& S, float& C, float P, float Pe) {
-    const float s = S + P;
-    const float bb = s - S;
-    const float err = (S - (s - bb)) + (P - bb);
-    S = s;
-    C += err + Pe;
-}
-
-// Fold the compensation into the sum (Fast2Sum), keeping C small so its own
-// FP32 roundings stay below 2^-48 of the sum over long accumulations.
-__device__ __forceinline__ void df_renorm(float& S, float& C) {
-    const float s = S + C;
-    C = C - (s - S);
-    S = s;
-}
-
-// 2^(ah + al) as a double-float; zero below 2^-126.
-__device__ __forceinline__ DF df_exp2(float ah, float al, const float2* __restrict__ tab) {
-    // renormalise
-    const float s = ah + al;
-    al = al - (s - ah);
-    ah = s;
-    const float k = rintf(ah);
-    const float fh = ah - k;               // exact, |fh| <= 1/2
-    const float jf = rintf(fh * 256.f);
-    const float rh = fmaf(jf, -0.00390625f, fh);  // exact, |rh| <= 1/512
-    // t = (rh + al) ln 2 as th + tl (TwoProduct on rh * ln2_hi)
-    const float th = rh * kLn2Hi;
-    float tl = fmaf(rh, kLn2Hi, -th);
-    tl = fmaf(rh, kLn2Lo, tl);
-    tl = fmaf(al, kLn2Hi, tl);
-    // e^t - 1 - t = t^2 (1/2 + t (1/6 + t / 24)), t^2 split exactly
-    const float w = fmaf(th, fmaf(th, 0.041666666666666664f, 0.16666666666666666f), 0.5f);
-    const float p2 = th * th;
-    const float p2e = fmaf(th, th, -p2);
-    const float q = fmaf(p2, w, 0.5f * p2e);
-    tl = fmaf(th, tl, tl + q);
-    const float uh = 1.f + th;
-    const float ul = ((1.f - uh) + th) + tl;
-    const float2 T = tab[(int)jf + 128];
-    const float ph = T.x * uh;
-    float pl = fmaf(T.x, uh, -ph);
-    pl = fmaf(T.x, ul, pl);
-    pl = fmaf(T.y, uh, pl);
-    DF r;
-    if (k < -125.f) {
-        r.h = 0.f;
-        r.l = 0.f;
-    } else {
-        const float sc = __int_as_float(((int)k + 127) << 23);
-        r.h = ph * sc;
-        r.l = pl * sc;
-    }
-    return r;
 }
 
 template <int DP, int CB>
@@ -826,7 +755,7 @@ static bool df_prefer_plain(int64_t n, int dp, int c) {
 }  // namespace
 
 // Refresh the double-float inputs of the handle after theta changed.
-static void df_prepare(Ctx& h) {
+void df_prepare(Ctx& h) {
     if (h.df_version == h.theta_version) return;
     cudaStream_t st = h.stream;
     const int64_t n = h.n;
@@ -1030,6 +959,11 @@ void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, in
 void kv_df(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb, double* O,
            int64_t ldo, double noise) {
     if (h.n <= 0 || c <= 0) return;
+    // the squared distances on the tensor cores where the sliced layout fits
+    if (h.df_tensor && kv_tcd_supported(h)) {
+        kv_tcd(h, V, ldv, c, B, ldb, O, ldo, noise);
+        return;
+    }
     df_prepare(h);
     // The symmetric kernel pays off once there are several tile pairs per SM,
     // and while few columns are in the product.

@@ -81,21 +81,40 @@ def test_matvec_f64_matches_oracle(kpcg, n, d, c):
     assert _rel(out, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("impl", [1, 3])
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 6),
                                    (700, 32, 2), (513, 12, 5), (6000, 8, 1), (2000, 10, 9),
-                                   (3000, 5, 17)])
-def test_matvec_double_float_matches_oracle(kpcg, n, d, c):
-    # FP32-pair entries: exact grid differences, TwoSum accumulation and a
-    # table-driven exp2 keep each entry within about 2^-40 of FP64, so the
-    # products agree with the oracle far below FP32 rounding.
+                                   (3000, 5, 17), (200, 2, 4), (2500, 9, 2)])
+def test_matvec_double_float_matches_oracle(kpcg, impl, n, d, c):
+    # FP32-pair entries keep each entry within about 2^-40 of FP64, so the
+    # products agree with the oracle far below FP32 rounding.  impl 1: for
+    # d <= 10 the squared distances are exact integer level sums of 8-bit
+    # slices on the tensor cores (dropped levels ~2^-45 of the exponent);
+    # impl 3: exact grid differences on the FP32 pipe at every d.
     p = _problem(n, d, seed=13 * n + d)
     V = synthetic.rng(9).standard_normal((n, c))
     ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
     ref = oracle.kyv(p.X, ell, s2, p.noise, V)
     with _solver(kpcg, p) as s:
-        out = _np(s.matvec_f64(_cm(V), impl=1))
+        out = _np(s.matvec_f64(_cm(V), impl=impl))
+        again = _np(s.matvec_f64(_cm(V), impl=impl))
+    np.testing.assert_array_equal(out, again)
     for k in range(c):
         assert _rel(out[:, k], ref[:, k]) <= 1e-11, k
+
+
+def test_matvec_double_float_many_tiles_sampled_rows(kpcg):
+    # n = 40000, d = 8: each CTA of the tensor-core double-float product walks
+    # hundreds of column tiles; 64 rows recomputed by the oracle in FP64.
+    p = _problem(40000, 8, seed=77, dist="uniform", ell="loguniform", noise=1e-4)
+    V = synthetic.rng(10).standard_normal((p.n, 2))
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    rows = np.sort(synthetic.rng(11).choice(p.n, 64, replace=False))
+    ref = oracle.gram(p.X[rows], p.X, ell, s2) @ V + p.noise * V[rows]
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(_cm(V), impl=1))
+    for k in range(2):
+        assert _rel(out[rows, k], ref[:, k]) <= 1e-11, k
 
 
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (255, 2, 1), (1000, 8, 3), (4099, 16, 17),
