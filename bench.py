@@ -135,6 +135,23 @@ def df_issue_efficiency(n, d, c, ms, rates):
     return ops / (ms / 1e3) / rates["fp32_fma_per_s"]
 
 
+def df_kernel_name(d):
+    """The double-float product's kernel at dimension d (the tensor-core
+    distances of kv_tcd_kernel up to d = 10, the FP32-pipe kernel above)."""
+    return ("kv_tcd_kernel (double-float, tensor-core distances)" if d <= 10 else
+            "kv_df_sym_kernel (double-float)")
+
+
+def df_issue_eff(n, d, c, ms, rates):
+    """Issue efficiency of whichever double-float kernel runs at d: the
+    tensor-core-distance kernel's model is 67 + 11 c FP32-pipe instructions
+    per evaluated entry (n^2: double-float sum of the five level accumulators
+    and log2 s^2, Tang's exp2, TwoProduct/TwoSum per column)."""
+    if d > 10:
+        return df_issue_efficiency(n, d, c, ms, rates)
+    return n * float(n) * (67 + 11 * c) / (ms / 1e3) / rates["fp32_fma_per_s"]
+
+
 def nystrom_roofline(n, m, c, ms, hbm_gbs):
     """The Nystrom apply streams K_XU (n x m FP32 pairs) twice and reads and
     writes the n x c block: HBM-bound."""
@@ -674,11 +691,10 @@ def run_laplace(args):
     torch.cuda.synchronize(dev)
     kv_ms = e0.elapsed_time(e1) / reps
     rates = probed_rates(kpcg)
-    roof = alu_roofline("kv_df_sym_kernel (double-float K.V, 1 column)", p.n, p.d, 1, kv_ms,
-                        rates)
+    roof = alu_roofline(df_kernel_name(p.d) + ", 1 column", p.n, p.d, 1, kv_ms, rates)
     roof.update({"traffic": None, "peak_source": PEAK_SOURCE,
                  "timing": f"{reps} back-to-back products, CUDA events on the launching stream",
-                 "issue_efficiency": df_issue_efficiency(p.n, p.d, 1, kv_ms, rates)})
+                 "issue_efficiency": df_issue_eff(p.n, p.d, 1, kv_ms, rates)})
     # the inner product of the mixed B-solves: tensor-core K.V of one column
     roof_inner = None
     if prec == kpcg.KPCG_TC_IR:
@@ -945,7 +961,7 @@ DTYPES = {"tc_ir": "bf16x3 exponent, f32 inner, f64 outer (double-float directio
 KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
             "tcx_ir": "kv_tcx_kernel (tcgen05 sliced exponent, compensated contraction)",
             "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
-            "df64": "kv_df_sym_kernel (double-float)", "fp64": "kv_f64_sym_kernel (FP64)"}
+            "df64": df_kernel_name(D), "fp64": "kv_f64_sym_kernel (FP64)"}
 # DRAM bytes per launch from ncu captures at n = 16384, by kernel
 # name, as a function of n: each kernel reads only its inputs from DRAM (the
 # n x n work stays on chip), so the traffic grows like n.  A kernel changed
@@ -1041,13 +1057,13 @@ def run_solve(args):
                                         fp64=(mode == "fp64"))
         cats["kv_inner"].update(calls=pinfo.kv_inner_calls, total_ms=pinfo.kv_inner_ms)
         if mode == "df64":
-            cats["kv_inner"]["issue_efficiency"] = df_issue_efficiency(p.n, D, 1, ms, rates)
+            cats["kv_inner"]["issue_efficiency"] = df_issue_eff(p.n, D, 1, ms, rates)
     if pinfo.kv_outer_calls:
         ms = pinfo.kv_outer_ms / pinfo.kv_outer_calls
-        cats["kv_outer"] = alu_roofline("kv_df_sym_kernel (double-float outer directions)",
+        cats["kv_outer"] = alu_roofline(df_kernel_name(D) + " (outer directions)",
                                         p.n, D, 1, ms, rates)
         cats["kv_outer"].update(calls=pinfo.kv_outer_calls, total_ms=pinfo.kv_outer_ms,
-                                issue_efficiency=df_issue_efficiency(p.n, D, 1, ms, rates))
+                                issue_efficiency=df_issue_eff(p.n, D, 1, ms, rates))
     if pinfo.resid_calls:
         ms = pinfo.resid_ms / pinfo.resid_calls
         cats["resid"] = alu_roofline("kv_f64_sym_kernel (native FP64 certified residual)",
@@ -1184,7 +1200,8 @@ def comparisons(kpcg, X, y, p, idx, stream, mode, extra_opts, args):
 
 
 KV_IMPLS = {"f64": ("f64", 0, "kv_f64_sym_kernel (native FP64)"),
-            "df": ("f64", 1, "kv_df_sym_kernel (double-float)"),
+            "df": ("f64", 1, "kv_tcd_kernel (double-float, tensor-core distances)"),
+            "dfs": ("f64", 3, "kv_df_sym_kernel (double-float)"),
             "f32": ("f32", 0, "kv_simt_kernel<float>"),
             "tc": ("f32", 1, "kv_tc_kernel (tcgen05, BF16x3 exponent)"),
             "xf": ("f32", 3, "kv_xf_sym_kernel (exact differences)"),
@@ -1225,6 +1242,8 @@ def run_kv(args):
     roof.update({"peak_source": PEAK_SOURCE, "traffic": known_traffic(kname, p.n),
                  "timing": f"{args.steps} back-to-back products, CUDA events on the stream"})
     if args.kv_impl == "df":
+        roof["issue_efficiency"] = df_issue_eff(p.n, p.d, c, ms, rates)
+    elif args.kv_impl == "dfs":
         roof["issue_efficiency"] = df_issue_efficiency(p.n, p.d, c, ms, rates)
     print(json.dumps({"metric": f"time per K.V product ({args.kv_impl}, c={c})", "value": ms / 1e3,
                       "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

@@ -34,7 +34,7 @@ struct TcBatchItem {
 struct TcBatch {
     int P = 0, G = 0, grid = 0, nitems = 0;
     // tcv: the second contraction on the tensor cores too (kv_tcv.cu): one row
-    // tile per item, operands of 2^14 K / s^2, V staged as FP16 pairs in Vh,
+    // tile per item, V staged as FP16 pairs in Vh,
     // per (problem, column) max |V| and exponent in aux
     int tcv = 0;
     int64_t nv = 0;  // sum of the padded sizes
@@ -56,7 +56,8 @@ int sm_count_tc();
 // tcv: the kernel with the contraction on the tensor cores (single row tiles).
 void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<float>& noise,
                    int G, int grid, cudaStream_t st, int tcv = 0);
-// Operands of kv_tcv_apply for the handle's current theta (kv_tcv.cu).
+// Operands of kv_tcv_apply for the handle's current theta (kv_tcv.cu: those
+// of tc_prepare, after the dimension check of the tcv path).
 void tcv_prepare(Ctx& h);
 // The tcv batched product (kv_tcv.cu); called by kv_tc_batch when b.tcv is set.
 void kv_tcv_batch(TcBatch& b, const float* V, int64_t ldv, int c, float* O, int64_t ldo,

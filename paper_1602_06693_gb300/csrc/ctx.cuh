@@ -132,11 +132,10 @@ struct Ctx {
     DevBuf<uint16_t> tcA, tcB;
     DevBuf<float> tcV, tcPart;
     DevBuf<int> tc_err;
-    // tensor-core K.V with the contraction on the tensor cores (kv_tcv_apply):
-    // exponent operands of 2^14 K / s^2, V staged as FP16 pairs, partials,
+    // tensor-core K.V with the contraction on the tensor cores (kv_tcv_apply;
+    // the exponent operands tcA / tcB): V staged as FP16 pairs, partials,
     // per-column max and exponent of V
-    int tcv_version = -1, tcv_kch = 0;
-    DevBuf<uint16_t> tcvA, tcvB, tcvV;
+    DevBuf<uint16_t> tcvV;
     DevBuf<float> tcvPart;
     DevBuf<int> tcvAux;
     // double-float product with sliced tensor-core distances (kv_tcd.cu)
@@ -199,10 +198,9 @@ void kv_tcx_apply64(Ctx& h, const double* V, int64_t ldv, int c, double* O, int6
 // Nonzero if a bounded wait inside the tensor-core kernel expired since the
 // last call (the flag is cleared).
 int kv_tc_error(Ctx& h);
-// The BF16x3 augmented exponent operands of kv_tc.cu for the handle's inputs
-// with log2(s^2) replaced by c0 (K-dim kch x 64), written to A and B.
-void tc_prep_operands(const Ctx& h, int kch, double c0, uint16_t* A, uint16_t* B);
 int sm_count_tc();
+// Operands of the tensor-core products for the handle's current theta (kv_tc.cu).
+void tc_prepare(Ctx& h);
 // Tensor-core K.V with the second contraction on the tensor cores as well
 // (kv_tcv.cu; d <= 20): FP32 in and out, the exponentiated tile as FP16
 // pairs in tensor memory against V as FP16 pairs.

