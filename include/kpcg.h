@@ -77,7 +77,7 @@ typedef enum {
     KPCG_TC_IR = 3,    /* as KPCG_FP32_IR, the inner K.V on the tensor cores:
                           tcgen05 BF16 MMAs on a three-way split of the scaled
                           inputs form the exponent in FP32 (TMEM), exp2 on the
-                          MUFU; requires d <= 16                                 */
+                          MUFU; requires d <= 20                                 */
     KPCG_DF64 = 4,     /* FP64 vectors and scalars; iterations use the
                           double-float K.V (FP32-pair arithmetic on the FP32
                           pipe, about 44 bits); stop and restart decisions use
@@ -244,7 +244,7 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
  * impl 0: FP32 entries by direct differences on the CUDA cores;
  * impl 1: the tensor-core kernel KPCG_TC_IR iterates with (tcgen05 BF16x3
  *         split exponent, FP32 accumulate, exp2 and contraction in FP32);
- *         d <= 16, else KPCG_ERR_ARG.  A bounded wait that expires inside
+ *         d <= 20, else KPCG_ERR_ARG.  A bounded wait that expires inside
  *         the kernel returns KPCG_ERR_TIMEOUT;
  * impl 2: the KPCG_FP32X_IR inner kernel (exact differences of the split
  *         inputs, compensated sums) with exp2 on the MUFU (ex2.approx);

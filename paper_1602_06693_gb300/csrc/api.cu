@@ -616,8 +616,8 @@ kpcg_status solve_impl(Ctx& h, const double* B, int64_t ldb, int c, double tol,
     cudaStream_t st = h.stream;
     const int64_t n = h.n, ld = h.ld;
     const int prec = h.opt.precision;
-    if (prec == KPCG_TC_IR && !kv_tc_supported(h.dp))
-        fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+    if (prec == KPCG_TC_IR && !kv_tc_supported(h.d))
+        fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
     if (prec == KPCG_FP32X_IR && !kv_xf_supported(h))
         fail(KPCG_ERR_ARG, "exact-difference FP32 K.V needs d <= 16");
     if (prec == KPCG_TCX_IR && !kv_tcx_supported(h.d))
@@ -1173,8 +1173,8 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             kpcg::kv_f32(h->xs32.p, h->n, h->dp, h->c0_32(), (float)h->noise, V, ldv, c, O, ldo,
                          h->kvws, h->stream);
         } else if (impl == 1) {
-            if (!kpcg::kv_tc_supported(h->dp))
-                fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+            if (!kpcg::kv_tc_supported(h->d))
+                fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
             kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
             if (kpcg::kv_tc_error(*h))
                 fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");

@@ -90,8 +90,9 @@ void kv_f32(const float* xs, int64_t n, int dp, float c0, float noise, const flo
             int64_t ldv, int c, float* O, int64_t ldo, KvWorkspace& ws, cudaStream_t st);
 
 // Tensor-core variant (kv_tc.cu).  kv_tc_supported reports whether the
-// padded dimension has a tensor-core kernel; there is no fallback.
-bool kv_tc_supported(int dp);
+// input dimension fits the augmented K-dimension (6d + 6 <= 128, i.e.
+// d <= 20); there is no fallback.
+bool kv_tc_supported(int d);
 
 // Cross-kernel block K(X, U) (n x m row-major), FP32 entries from FP32-scaled inputs.
 void kxu_f32(const float* xs, int64_t n, const float* us, int64_t m, int dp, float c0,

@@ -632,7 +632,7 @@ int sm_count_tc() {
     return cached;
 }
 
-bool kv_tc_supported(int dp) { return dp <= 16; }
+bool kv_tc_supported(int d) { return d >= 1 && 6 * d + 6 <= 2 * KC; }
 
 
 void tc_prepare(Ctx& h) {

@@ -388,8 +388,8 @@ kpcg_status kpcg_laplace(kpcg_t h, const double* y, double newton_tol, int32_t m
         // mixed precision (KPCG_TC_IR / KPCG_FP32_IR): FP32 W^1/2 and scratch
         const bool tc = c.opt.precision == KPCG_TC_IR;
         const bool use_mixed = tc || c.opt.precision == KPCG_FP32_IR;
-        if (tc && !kv_tc_supported(c.dp))
-            fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+        if (tc && !kv_tc_supported(c.d))
+            fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
         float* f32 = c.lpw32.need((size_t)ld * 3);
         const LapMixed lm{f32, f32 + ld, f32 + 2 * ld};
         MixedOps mops;
@@ -537,8 +537,8 @@ kpcg_status kpcg_laplace_predict(kpcg_t h, const double* y, const double* f, con
             const VecOp pcB = make_bpc(&c, pre);
             const bool tc = c.opt.precision == KPCG_TC_IR;
             const bool use_mixed = tc || c.opt.precision == KPCG_FP32_IR;
-            if (tc && !kv_tc_supported(c.dp))
-                fail(KPCG_ERR_ARG, "tensor-core K.V does not support this dimension");
+            if (tc && !kv_tc_supported(c.d))
+                fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
             float* f32 = c.lpw32.need((size_t)ld * (1 + 2 * PB));
             const LapMixed lm{f32, f32 + ld, f32 + (1 + PB) * ld};
             MixedOps mops;
