@@ -137,19 +137,27 @@ def df_issue_efficiency(n, d, c, ms, rates):
 
 def df_kernel_name(d):
     """The double-float product's kernel at dimension d (the tensor-core
-    distances of kv_tcd_kernel up to d = 10, the FP32-pipe kernel above)."""
-    return ("kv_tcd_kernel (double-float, tensor-core distances)" if d <= 10 else
+    distances of kv_tcds_kernel, one evaluation per pair of points, up to
+    d = 10; the FP32-pipe kernel above)."""
+    return ("kv_tcds_kernel (double-float, tensor-core distances, symmetric)" if d <= 10 else
             "kv_df_sym_kernel (double-float)")
 
 
-def df_issue_eff(n, d, c, ms, rates):
-    """Issue efficiency of whichever double-float kernel runs at d: the
-    tensor-core-distance kernel's model is 67 + 11 c FP32-pipe instructions
-    per evaluated entry (n^2: double-float sum of the five level accumulators
-    and log2 s^2, Tang's exp2, TwoProduct/TwoSum per column)."""
+def df_issue_eff(n, d, c, ms, rates, symmetric=True):
+    """Issue efficiency of whichever double-float kernel runs at d.  The
+    tensor-core-distance kernels' model: 67 FP32-pipe instructions per
+    evaluated entry (double-float sum of the five level accumulators and
+    log2 s^2, Tang's exp2) + 11 per column (TwoProduct/TwoSum row sum); the
+    symmetric kernel evaluates n^2/2 + 64 n entries and adds 14 per column
+    for the mirrored column sum (its product and its share of the shuffle
+    butterfly), the one-sided kernel evaluates n^2."""
     if d > 10:
         return df_issue_efficiency(n, d, c, ms, rates)
-    return n * float(n) * (67 + 11 * c) / (ms / 1e3) / rates["fp32_fma_per_s"]
+    if symmetric:
+        instr = (n * float(n) / 2 + 64.0 * n) * (67 + 25 * c)
+    else:
+        instr = n * float(n) * (67 + 11 * c)
+    return instr / (ms / 1e3) / rates["fp32_fma_per_s"]
 
 
 def nystrom_roofline(n, m, c, ms, hbm_gbs):
@@ -1200,7 +1208,8 @@ def comparisons(kpcg, X, y, p, idx, stream, mode, extra_opts, args):
 
 
 KV_IMPLS = {"f64": ("f64", 0, "kv_f64_sym_kernel (native FP64)"),
-            "df": ("f64", 1, "kv_tcd_kernel (double-float, tensor-core distances)"),
+            "df": ("f64", 1, "kv_tcds_kernel (double-float, tensor-core distances, symmetric)"),
+            "df1": ("f64", 4, "kv_tcd_kernel (double-float, tensor-core distances, every entry)"),
             "dfs": ("f64", 3, "kv_df_sym_kernel (double-float)"),
             "f32": ("f32", 0, "kv_simt_kernel<float>"),
             "tc": ("f32", 1, "kv_tc_kernel (tcgen05, BF16x3 exponent)"),
@@ -1241,8 +1250,9 @@ def run_kv(args):
     roof = alu_roofline(kname, p.n, p.d, c, ms, rates, fp64=(args.kv_impl == "f64"))
     roof.update({"peak_source": PEAK_SOURCE, "traffic": known_traffic(kname, p.n),
                  "timing": f"{args.steps} back-to-back products, CUDA events on the stream"})
-    if args.kv_impl == "df":
-        roof["issue_efficiency"] = df_issue_eff(p.n, p.d, c, ms, rates)
+    if args.kv_impl in ("df", "df1"):
+        roof["issue_efficiency"] = df_issue_eff(p.n, p.d, c, ms, rates,
+                                                symmetric=(args.kv_impl == "df"))
     elif args.kv_impl == "dfs":
         roof["issue_efficiency"] = df_issue_efficiency(p.n, p.d, c, ms, rates)
     print(json.dumps({"metric": f"time per K.V product ({args.kv_impl}, c={c})", "value": ms / 1e3,

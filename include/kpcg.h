@@ -232,11 +232,14 @@ kpcg_status kpcg_precond_pitc(kpcg_t h, int64_t m, const int64_t* idx, int64_t b
  * impl 1: the double-float product of KPCG_DF64 and of the outer loop of the
  * mixed modes (FP32-pair arithmetic, about 44 bits per entry, sums carried as
  * FP32 pairs and added in FP64); for d <= 10 its squared distances come from
- * exact integer level sums of 8-bit slices of x' on the tensor cores, for
+ * exact integer level sums of 8-bit slices of x' on the tensor cores, each
+ * pair of points evaluated once for both triangles of K (n > 128), for
  * larger d from exact grid differences on the FP32 pipe;
  * impl 2: the sliced tensor-core kernel of KPCG_TCX_IR with V as FP32 pairs
  * (entries to FP32 accuracy, compensated sums, FP64 out; d <= 10);
- * impl 3: impl 1 with the FP32-pipe distances at every d. */
+ * impl 3: impl 1 with the FP32-pipe distances at every d;
+ * impl 4: impl 1 evaluating every entry of K (no use of its symmetry;
+ * d <= 10). */
 kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, double* O,
                             int64_t ldo, int32_t impl);
 

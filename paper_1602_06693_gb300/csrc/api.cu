@@ -1135,9 +1135,11 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
         kpcg::check_dev_ptr(O, "O");
         if (impl == 0)
             kpcg::kv_f64_sym(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
-        else if (impl == 1)
+        else if (impl == 1) {
             kpcg::kv_df(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
-        else if (impl == 3) {
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
+        } else if (impl == 3) {
             // the double-float kernel on the FP32 pipe alone (no tensor-core distances)
             const bool saved = h->df_tensor;
             h->df_tensor = false;
@@ -1148,6 +1150,21 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
                 throw;
             }
             h->df_tensor = saved;
+        } else if (impl == 4) {
+            // the tensor-core double-float product evaluating every entry
+            if (!kpcg::kv_tcd_supported(*h))
+                fail(KPCG_ERR_ARG, "the double-float tensor-core K.V needs d <= 10");
+            const bool saved = h->tcd_symmetric;
+            h->tcd_symmetric = false;
+            try {
+                kpcg::kv_tcd(*h, V, ldv, c, nullptr, 0, O, ldo, h->noise);
+            } catch (...) {
+                h->tcd_symmetric = saved;
+                throw;
+            }
+            h->tcd_symmetric = saved;
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         } else if (impl == 2) {
             if (!kpcg::kv_tcx_supported(h->d))
                 fail(KPCG_ERR_ARG, "exact tensor-core K.V supports d <= 10");

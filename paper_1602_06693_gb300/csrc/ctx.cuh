@@ -144,6 +144,14 @@ struct Ctx {
     DevBuf<float2> tcdV;
     DevBuf<double> tcdPart, tcd_max;
     bool df_tensor = true;  // kv_df uses kv_tcd where supported (cleared by tests of the other)
+    // its symmetric form (one evaluation per pair of points): B in 32-row
+    // tiles, the work list, row and column partials
+    bool tcd_symmetric = true;  // cleared by the tests of the one-sided kernel
+    int tcds_version = -1, tcds_nitems = 0;
+    int64_t tcds_n = -1;
+    DevBuf<uint16_t> tcdBs;
+    DevBuf<int> tcds_work, tcds_rows;
+    DevBuf<double> tcdsRow, tcdsCol;
     // per-point-exact tensor-core operands (kv_tcx_apply), rebuilt when theta changes
     int tcx_version = -1, tcx_kch = 0, tcx_nmma = 0;
     float tcx_escale = 1.f;

@@ -103,6 +103,30 @@ def test_matvec_double_float_matches_oracle(kpcg, impl, n, d, c):
         assert _rel(out[:, k], ref[:, k]) <= 1e-11, k
 
 
+@pytest.mark.parametrize("n,d,c", [(129, 3, 1), (300, 2, 4), (1000, 8, 3), (2000, 10, 9),
+                                   (4097, 9, 2), (5000, 8, 5)])
+def test_symmetric_double_float_product_matches_one_sided(kpcg, n, d, c):
+    # impl 1 evaluates each pair of points once: row sums, and from the same
+    # entries the mirrored column sums, reduced over the rows of a warp by a
+    # shuffle butterfly and added per row tile in FP64.  impl 4 evaluates
+    # every entry.  Both carry ~2^-45 per entry: each within 1e-11 of the
+    # oracle, within 1e-12 of each other, and each bit-identical when repeated.
+    p = _problem(n, d, seed=7 * n + d)
+    V = synthetic.rng(21).standard_normal((n, c))
+    V[:, 0] *= 1e3  # columns of different scales
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        sym = _np(s.matvec_f64(_cm(V), impl=1))
+        one = _np(s.matvec_f64(_cm(V), impl=4))
+        np.testing.assert_array_equal(sym, _np(s.matvec_f64(_cm(V), impl=1)))
+        np.testing.assert_array_equal(one, _np(s.matvec_f64(_cm(V), impl=4)))
+    for k in range(c):
+        assert _rel(sym[:, k], ref[:, k]) <= 1e-11, k
+        assert _rel(one[:, k], ref[:, k]) <= 1e-11, k
+        assert _rel(sym[:, k], one[:, k]) <= 1e-12, k
+
+
 def test_matvec_double_float_many_tiles_sampled_rows(kpcg):
     # n = 40000, d = 8: each CTA of the tensor-core double-float product walks
     # hundreds of column tiles; 64 rows recomputed by the oracle in FP64.
@@ -680,7 +704,11 @@ def test_fitc_apply_and_solve_match_oracle(kpcg, precision):
     ref_tol = 1e-10 if precision == "fp64" else 0.5e-10
     xref, it_ref = oracle.pcg_dense(Ky, p.y, F.apply, tol=ref_tol)
     assert _rel(_np(x), oracle.dense_solve(p.X, ell, s2, p.noise, p.y[:, None])[:, 0]) <= 1e-7
-    assert abs(int(it[0]) - it_ref) <= max(2, 0.05 * it_ref), (int(it[0]), it_ref)
+    # CG in finite precision lags exact CG by an amount that grows with the
+    # error of its products: the double-float products (~1e-13 relative here,
+    # against FP64's ~1e-15) may take a few percent more iterations to 5e-11
+    slack = 0.05 if precision == "fp64" else 0.08
+    assert abs(int(it[0]) - it_ref) <= max(2, slack * it_ref), (int(it[0]), it_ref)
 
 
 def test_fitc_in_the_mixed_solver(kpcg):
