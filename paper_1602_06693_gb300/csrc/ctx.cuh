@@ -162,7 +162,7 @@ struct Ctx {
     float df_c0h = 0.f, df_c0l = 0.f;
     DevBuf<float> xdf;
     DevBuf<float> xf2;  // (hi, lo) pairs of x' for the exact-difference FP32 kernel
-    DevBuf<float2> df_tab;
+    DevBuf<float2> df_tab, df_tab1k;
     DevBuf<double> df_grid;
     bool df_symmetric = true;  // symmetric tile-pair kernel (cleared by tests of the other)
     int64_t df_sym_n = -1;

@@ -1,8 +1,9 @@
 // Double-float arithmetic on the FP32 pipe (unevaluated sums hi + lo of two
 // FP32 numbers, ~44 bits): Knuth's TwoSum accumulation and the table-driven
 // exp2 of P. T. P. Tang ("Table-driven implementation of the exponential
-// function", 1989) with a 257-entry double-float table of 2^(j/256) built on
-// the host in FP64.  Shared by the double-float kernels (kv_df.cu, kv_tcd.cu).
+// function", 1989) with a 257-entry double-float table of 2^(j/256) (and a
+// 1024-entry one of 2^(j/1024)) built on the host in FP64.  Shared by the
+// double-float kernels (kv_df.cu, kv_tcd.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -80,6 +81,48 @@ __device__ __forceinline__ DF df_exp2(float ah, float al, const float2* __restri
         r.h = ph * sc;
         r.l = pl * sc;
     }
+    return r;
+}
+
+constexpr int NTAB1K = 1024;  // 2^(j/1024), j = 0..1023
+
+// 2^(ah + al) as a double-float, the same method with a finer table (for
+// the symmetric tensor-core kernel).  (ah, al) need not be normalised.
+// Arguments below -125 are clamped there
+// (the result is then 2^-125 instead of zero: far below any entry that
+// matters against s^2).  a = m/1024 + r with m = rint(1024 a), read off the
+// mantissa of 1024 a + 1.5 * 2^23 (no float-to-int conversion), |r| <=
+// 2^-11 exactly; 2^a = 2^(m >> 10) * 2^((m & 1023)/1024) * e^t with t = (r +
+// al) ln 2 as th + tl and e^t = 1 + t + t^2 (1/2 + t/6) (the next term is
+// below 2^-52; th^2 rounds at 2^-47).
+__device__ __forceinline__ DF df_exp2_1k(float ah, float al, const float2* __restrict__ tab) {
+    // renormalise: the low part of a sum of level accumulators can exceed
+    // half an ulp of the high part, and t below must stay within 2^-11
+    const float s = ah + al;
+    al = al - (s - ah);
+    ah = fmaxf(s, -125.f);
+    const float t = fmaf(ah, 1024.f, 12582912.f);     // 1.5 * 2^23 + m
+    const int mi = __float_as_int(t) - 0x4B400000;    // m
+    const float mf = t - 12582912.f;                   // m, exact
+    const float rh = fmaf(mf, -0.0009765625f, ah);     // exact, |rh| <= 2^-11
+    const float th = rh * kLn2Hi;
+    float tl = fmaf(rh, kLn2Hi, -th);
+    tl = fmaf(rh, kLn2Lo, tl);
+    tl = fmaf(al, kLn2Hi, tl);
+    const float w = fmaf(th, 0.16666666666666666f, 0.5f);
+    float q = fmaf(th * th, w, tl);
+    q = fmaf(th, tl, q);
+    const float uh = 1.f + th;
+    const float ul = ((1.f - uh) + th) + q;
+    const float2 T = tab[mi & (NTAB1K - 1)];
+    const float sc = __int_as_float(((mi >> 10) + 127) << 23);
+    const float ph = T.x * uh;
+    float pl = fmaf(T.x, uh, -ph);
+    pl = fmaf(T.x, ul, pl);
+    pl = fmaf(T.y, uh, pl);
+    DF r;
+    r.h = ph * sc;
+    r.l = pl * sc;
     return r;
 }
 

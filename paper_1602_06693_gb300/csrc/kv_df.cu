@@ -769,6 +769,16 @@ void df_prepare(Ctx& h) {
         h.df_tab.need(NTAB);
         KPCG_CUDA(cudaMemcpyAsync(h.df_tab.p, t.data(), sizeof(float2) * NTAB,
                                   cudaMemcpyHostToDevice, st));
+        std::vector<float2> t1(NTAB1K);
+        for (int j = 0; j < NTAB1K; ++j) {
+            const double v = std::exp2((double)j / NTAB1K);
+            const float hi = (float)v;
+            t1[j] = make_float2(hi, (float)(v - (double)hi));
+        }
+        h.df_tab1k.need(NTAB1K);
+        KPCG_CUDA(cudaMemcpyAsync(h.df_tab1k.p, t1.data(), sizeof(float2) * NTAB1K,
+                                  cudaMemcpyHostToDevice, st));
+        KPCG_CUDA(cudaStreamSynchronize(st));  // the host tables leave scope
     }
     // x' in the exp2 scaling: xs64 * sqrt(log2 e)
     const double scale = std::sqrt(kLog2e);

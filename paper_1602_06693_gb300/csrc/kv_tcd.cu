@@ -483,12 +483,15 @@ __global__ void tcd_absmax_kernel(const double* __restrict__ xs64, int64_t cnt,
 // only; tiles right of it (J >= 4I + 4) give the row sums K_IJ V_J and, from
 // the same entries, the column sums K_IJ^T V_I.  Every pair of points in
 // different row blocks is thus evaluated once, by the lower block's items.
-// A column sum is reduced over the 32 rows of a warp by a butterfly that
-// halves the columns a lane holds at each step (18 shuffles for 8 columns),
-// then over the four row quarters through shared memory, and leaves as one
-// FP64 partial per (column tile, row tile); a second kernel adds, for every
-// row, its row partials and the column partials of all row tiles below it,
-// in a fixed order.
+// Sixteen epilogue warps (four row quarters, the TMEM lanes each may read,
+// times four groups of 8 columns) keep four warps per scheduler to hide the
+// latency of the double-float chains.  A column sum is reduced over the 32
+// rows of a warp by a butterfly that halves the columns a lane holds at each
+// step (18 shuffles for 8 columns), then over the four row quarters through
+// shared memory behind a bounded mbarrier wait, and leaves as one FP64
+// partial per (column tile, row tile); a second kernel adds, for every row,
+// its row partials and the column partials of all row tiles below it, in a
+// fixed order.
 constexpr int STN = 32;   // columns per tile of the symmetric kernel (MMA N)
 constexpr int SNST = 3;   // ring depth
 
@@ -498,14 +501,18 @@ struct TcdsSmem {
     static constexpr uint32_t kBst = KCH * STN * 128;
     static constexpr uint32_t kVst = CB * STN * 8;
     static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
-    static constexpr uint32_t kTab = ((NTAB * 8 + 1023) / 1024) * 1024;
-    static constexpr uint32_t kCol = 2 * 2 * 4 * CB * 16 * 8;  // [buf][half][quarter][k][16] float2
+    static constexpr uint32_t kTab = NTAB1K * 8;
+    // [set][buf][half][quarter][k][16] float2
+    static constexpr uint32_t kCol = 2 * 2 * 2 * 4 * CB * 16 * 8;
     static constexpr uint32_t kBars = 1024;
     static constexpr uint32_t kTotal = 1024 + kA + SNST * kStage + kTab + kCol + kBars;
 };
 
 constexpr uint32_t kIdescS =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(STN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr int SEPI = 16;          // epilogue warps: two sets of 4 row quarters x 2 column halves
+constexpr int SSET = 8;           // warps per set; set s takes the tiles t = s mod 2
+constexpr int SWARPS = 2 + SEPI;  // + the producer and the MMA issuer
 
 // (h, l) += (bh, bl) for double-float values: TwoSum on the high parts.
 __device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
@@ -517,44 +524,30 @@ __device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
 }
 
 // Sums eight double-float values per lane (columns 0..7, one row per lane)
-// over the 32 lanes.  Each of the first three steps sends half of the
-// columns a lane holds to its partner and adds the other half; on return
-// lane l holds the sum of column 4 b4 + 2 b3 + b2 (b_k = bit k of l) over all
-// 32 rows, in (oh, ol).
+// over the 32 lanes.  While a lane holds w > 1 columns, it sends half of
+// them to its partner across the next lane bit (16, 8, 4) and adds the
+// other half to the partner's copy; the remaining bits (2, 1) are plain
+// reductions.  On return lane l holds the sum over all 32 rows of column
+// 4 b4 + 2 b3 + b2 (b_k = bit k of l), in (oh, ol).
 __device__ __forceinline__ void df_colsum8(float (&ph)[8], float (&pl)[8], int lane, float& oh,
                                            float& ol) {
-    const bool u4 = (lane & 16) != 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float sh = u4 ? ph[q] : ph[q + 4], sl = u4 ? pl[q] : pl[q + 4];
-        float kh = u4 ? ph[q + 4] : ph[q], kl = u4 ? pl[q + 4] : pl[q];
-        const float rh = __shfl_xor_sync(0xffffffffu, sh, 16);
-        const float rl = __shfl_xor_sync(0xffffffffu, sl, 16);
-        df_add(kh, kl, rh, rl);
-        ph[q] = kh;
-        pl[q] = kl;
-    }
-    const bool u3 = (lane & 8) != 0;
+    for (int w = 8, m = 16; w > 1; w >>= 1, m >>= 1) {
+        const bool u = (lane & m) != 0;
+        const int hw = w >> 1;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const float sh = u3 ? ph[q] : ph[q + 2], sl = u3 ? pl[q] : pl[q + 2];
-        float kh = u3 ? ph[q + 2] : ph[q], kl = u3 ? pl[q + 2] : pl[q];
-        const float rh = __shfl_xor_sync(0xffffffffu, sh, 8);
-        const float rl = __shfl_xor_sync(0xffffffffu, sl, 8);
-        df_add(kh, kl, rh, rl);
-        ph[q] = kh;
-        pl[q] = kl;
+        for (int q = 0; q < hw; ++q) {
+            const float sh = u ? ph[q] : ph[q + hw], sl = u ? pl[q] : pl[q + hw];
+            float kh = u ? ph[q + hw] : ph[q], kl = u ? pl[q + hw] : pl[q];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, m);
+            const float rl = __shfl_xor_sync(0xffffffffu, sl, m);
+            df_add(kh, kl, rh, rl);
+            ph[q] = kh;
+            pl[q] = kl;
+        }
     }
-    const bool u2 = (lane & 4) != 0;
-    {
-        const float sh = u2 ? ph[0] : ph[1], sl = u2 ? pl[0] : pl[1];
-        float kh = u2 ? ph[1] : ph[0], kl = u2 ? pl[1] : pl[0];
-        const float rh = __shfl_xor_sync(0xffffffffu, sh, 4);
-        const float rl = __shfl_xor_sync(0xffffffffu, sl, 4);
-        df_add(kh, kl, rh, rl);
-        oh = kh;
-        ol = kl;
-    }
+    oh = ph[0];
+    ol = pl[0];
 #pragma unroll
     for (int m = 2; m >= 1; m >>= 1) {
         const float rh = __shfl_xor_sync(0xffffffffu, oh, m);
@@ -571,7 +564,7 @@ __host__ __device__ __forceinline__ int64_t tcds_pair(int64_t J, int64_t I) {
 }
 
 template <int KCH, int CB>
-__global__ void __launch_bounds__(DWARPS * 32, 1)
+__global__ void __launch_bounds__(SWARPS * 32, 1)
     kv_tcds_kernel(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
                    const float2* __restrict__ Vs, int64_t n_pad, int ncols,
                    const int4* __restrict__ work, TcdLayout L, float c0h, float c0l,
@@ -590,11 +583,11 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
     uint64_t* empty = bars + SNST;       // [SNST] MMAs done + epilogue done with V
     uint64_t* tfull = bars + 2 * SNST;   // [2]
     uint64_t* tempty = tfull + 2;        // [2]
-    uint64_t* cfull = tempty + 2;        // [2 buffers][2 halves] column partials written
-    uint64_t* afull = cfull + 4;
+    uint64_t* cfull = tempty + 2;        // [set][buf][half] column partials written
+    uint64_t* afull = cfull + 8;
     uint64_t* done = afull + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-    float2* comb = reinterpret_cast<float2*>(sStage);  // after the loop: [CB][128]
+    float2* comb = reinterpret_cast<float2*>(sStage);  // after the loop: [CB][4][128]
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -603,17 +596,17 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
     const int64_t J0 = wk.y;
     const int ntiles = wk.z - wk.y;
 
-    for (int e = threadIdx.x; e < NTAB; e += blockDim.x) tab[e] = gtab[e];
+    for (int e = threadIdx.x; e < NTAB1K; e += blockDim.x) tab[e] = gtab[e];
     if (threadIdx.x == 0) {
         for (int s = 0; s < SNST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1 + DEPI);
+            mbar_init(&empty[s], 1 + SSET);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], DEPI);
+            mbar_init(&tempty[b], SSET);
         }
-        for (int b = 0; b < 4; ++b) mbar_init(&cfull[b], 128);
+        for (int b = 0; b < 8; ++b) mbar_init(&cfull[b], 128);
         mbar_init(afull, 1);
         mbar_init(done, 1);
         s_fail = 0;
@@ -632,8 +625,9 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
     const uint32_t tmem = *tmem_slot;
     const uint64_t deadline = gtimer() + wait_ns;
     int fail = 0;
-    const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int quarter = warp & 3;             // TMEM lanes (rows) 32 quarter .. +31
+    const int eset = (warp - 2) >> 3;         // tiles t with t mod 2 == eset, TMEM buffer eset
+    const int half = ((warp - 2) >> 2) & 1;   // columns 16 half .. +15 of each tile
     const int row = quarter * 32 + lane;
     float Sk[CB], Ck[CB];  // row sums (double-float)
 #pragma unroll
@@ -702,8 +696,8 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
 #pragma unroll
         for (int k = 0; k < CB; ++k)
             vi[k] = (k < ncols) ? Vs[(size_t)k * n_pad + (size_t)I * 128 + row] : make_float2(0.f, 0.f);
-        int mt = 0;  // mirrored tiles so far: picks the column-partial buffer and its phase
-        for (int t = 0; t < ntiles; ++t) {
+        int mt = 0;  // this set's mirrored tiles so far: the column-partial buffer and its phase
+        for (int t = eset; t < ntiles; t += 2) {
             const int s = t % SNST, b = t & 1;
             const int64_t jt = J0 + t;
             const bool mirror = jt >= 4 * I + 4;
@@ -717,7 +711,7 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
             const float2* vst =
                 reinterpret_cast<const float2*>(sStage + (size_t)s * S::kStage + S::kBst);
             const int cbuf = mt & 1;
-            float2* mine = colbuf + (size_t)((cbuf * 2 + half) * 4 + quarter) * CB * 16;
+            float2* mine = colbuf + (size_t)(((eset * 2 + cbuf) * 2 + half) * 4 + quarter) * CB * 16;
 #pragma unroll 1
             for (int ch = 0; ch < 2; ++ch) {
                 const int col0 = half * (STN / 2) + ch * 8;
@@ -758,7 +752,7 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
                     float ah, al;
                     two_sum(c0h, s1, ah, al);
                     al += e1 + c0l;
-                    const DF e = df_exp2(ah, al, tab);
+                    const DF e = df_exp2_1k(ah, al, tab);
                     eh[q] = e.h;
                     el[q] = e.l;
                 }
@@ -804,13 +798,14 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
             if (mirror) {
                 // the four row quarters of this half: their column partials are
                 // in shared memory once all 128 threads arrived
-                uint64_t* cb = &cfull[cbuf * 2 + half];
+                uint64_t* cb = &cfull[(eset * 2 + cbuf) * 2 + half];
                 mbar_arrive(cb);
                 if (!__all_sync(0xffffffffu, mbar_wait(cb, (uint32_t)(mt >> 1) & 1u, deadline))) {
                     fail = 1;
                     break;
                 }
-                const float2* base = colbuf + (size_t)(cbuf * 2 + half) * 4 * CB * 16;
+                const float2* base =
+                    colbuf + (size_t)((eset * 2 + cbuf) * 2 + half) * 4 * CB * 16;
                 const int64_t pair = tcds_pair(jt, I);
                 for (int idx = quarter * 32 + lane; idx < CB * 16; idx += 128) {
                     const int k = idx >> 4, col = idx & 15;
@@ -832,18 +827,24 @@ __global__ void __launch_bounds__(DWARPS * 32, 1)
     fence_before();
     __syncthreads();
     fence_after();
-    // the two column halves of each row (ring memory is free now)
-    if (warp >= 2 && half == 1)
+    // the four partial row sums of each row (two sets x two column halves;
+    // ring memory is free now), added in a fixed order
+    const int part = eset * 2 + half;
+    if (warp >= 2 && part > 0)
 #pragma unroll
-        for (int k = 0; k < CB; ++k) comb[k * 128 + row] = make_float2(Sk[k], Ck[k]);
+        for (int k = 0; k < CB; ++k) comb[(k * 4 + part) * 128 + row] = make_float2(Sk[k], Ck[k]);
     __syncthreads();
-    if (warp >= 2 && half == 0) {
+    if (warp >= 2 && part == 0) {
 #pragma unroll
         for (int k = 0; k < CB; ++k) {
             if (k >= ncols) continue;
-            const float2 o = comb[k * 128 + row];
-            prow[((size_t)blockIdx.x * CB + k) * 128 + row] =
-                ((double)Sk[k] + (double)Ck[k]) + ((double)o.x + (double)o.y);
+            double acc = (double)Sk[k] + (double)Ck[k];
+#pragma unroll
+            for (int g = 1; g < 4; ++g) {
+                const float2 o = comb[(k * 4 + g) * 128 + row];
+                acc += (double)o.x + (double)o.y;
+            }
+            prow[((size_t)blockIdx.x * CB + k) * 128 + row] = acc;
         }
     }
     if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
@@ -922,11 +923,11 @@ void launch_tcds(const Ctx& h, const TcdLayout& L, const float2* Vs, int64_t n_p
         attr = true;
     }
     const uint64_t wait_ns = h.opt.wait_limit_ns > 0 ? (uint64_t)h.opt.wait_limit_ns : kWaitNs;
-    kv_tcds_kernel<KCH, CB><<<(unsigned)h.tcds_nitems, DWARPS * 32, S::kTotal, st>>>(
+    kv_tcds_kernel<KCH, CB><<<(unsigned)h.tcds_nitems, SWARPS * 32, S::kTotal, st>>>(
         reinterpret_cast<const __nv_bfloat16*>(h.tcdA.p),
         reinterpret_cast<const __nv_bfloat16*>(h.tcdBs.p), Vs, n_pad, ncols,
         reinterpret_cast<const int4*>(h.tcds_work.p), L, h.df_c0h, h.df_c0l,
-        reinterpret_cast<const float2*>(h.df_tab.p), prow, pcol, h.tc_err.p, wait_ns);
+        reinterpret_cast<const float2*>(h.df_tab1k.p), prow, pcol, h.tc_err.p, wait_ns);
     KPCG_LAUNCHED("kv_tcds_kernel");
 }
 
