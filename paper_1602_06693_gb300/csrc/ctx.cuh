@@ -163,6 +163,7 @@ struct Ctx {
     DevBuf<float> xdf;
     DevBuf<float> xf2;  // (hi, lo) pairs of x' for the exact-difference FP32 kernel
     DevBuf<float2> df_tab, df_tab1k;
+    DevBuf<double> f64_tab;  // 2^(j/256) for the table-driven FP64 exp of kv_f64_sym
     DevBuf<double> df_grid;
     bool df_symmetric = true;  // symmetric tile-pair kernel (cleared by tests of the other)
     int64_t df_sym_n = -1;

@@ -249,19 +249,50 @@ __global__ void __launch_bounds__(ST)
 }
 
 
+constexpr int NTAB64 = 256;  // 2^(j/256), j = 0..255, FP64
+
+// e^a in FP64 by the table-driven method of P. T. P. Tang ("Table-driven
+// implementation of the exponential function", 1989): a = m ln2/256 + r with
+// m = rint(256 a / ln 2), read off the low word of 256 a / ln2 + 1.5 * 2^52;
+// r = a - m ln2/256 with ln2/256 split so that the first product is exact,
+// |r| <= ln2/512; e^a = 2^(m >> 8) * 2^((m & 255)/256) * e^r with e^r - 1 as
+// its Taylor polynomial to r^5 (the next term is below 2^-66 relative), and
+// the power of two added to the exponent field.  Arguments below -708 are
+// clamped there (e^-708 ~ 3e-308 instead of a smaller number).  About 1 ulp;
+// ten FP64 operations and one table read.
+__device__ __forceinline__ double exp_tab64(double a, const double* __restrict__ tab) {
+    a = fmax(a, -708.0);
+    const double t = fma(a, 0x1.71547652b82fep+8, 6755399441055744.0);
+    const int mi = __double2loint(t);
+    const double mf = t - 6755399441055744.0;
+    double r = fma(-mf, 0x1.62e42ff000000p-9, a);  // exact
+    r = fma(-mf, -0x1.718432a1b0e26p-43, r);
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    q = fma(r, q, 1.0);
+    const double T = tab[mi & (NTAB64 - 1)];
+    const double e = fma(T, r * q, T);
+    return __hiloint2double(__double2hiint(e) + ((mi >> 8) << 20), __double2loint(e));
+}
+
 // Native-FP64 symmetric variant (used for the FP64 residuals): the same tile
-// pairs, transpose and reduction, entries exp(c0 - |x'_i - x'_j|^2) in FP64.
+// pairs, transpose and reduction, entries exp(c0 - |x'_i - x'_j|^2) in FP64
+// (the exp by exp_tab64).
 template <int DP, int CB>
 __global__ void __launch_bounds__(ST)
     kv_f64_sym_kernel(const double* __restrict__ xs, int64_t n, int nt, double c0,
                       const double* __restrict__ V, int64_t ldv, int ncols,
                       const int4* __restrict__ work, int G, int nchunk,
-                      double* __restrict__ prow, double* __restrict__ pcol) {
+                      double* __restrict__ prow, double* __restrict__ pcol,
+                      const double* __restrict__ gtab64) {
     extern __shared__ double dsm64[];
     double* sx = dsm64;                 // ST * DP
     double* sv = sx + ST * DP;          // ST * CB
     double (*W)[ST][SCW + 1] = reinterpret_cast<double (*)[ST][SCW + 1]>(sv + ST * CB);
     double (*red)[4][SCW] = reinterpret_cast<double (*)[4][SCW]>(&W[CB][0][0]);
+    double* tab = &red[CB][0][0];       // NTAB64
+    for (int e = threadIdx.x; e < NTAB64; e += blockDim.x) tab[e] = gtab64[e];
     const int4 wk = work[blockIdx.x];
     const int I = wk.x;
     const int t = threadIdx.x;
@@ -299,7 +330,7 @@ __global__ void __launch_bounds__(ST)
                     const double dlt = xi[q] - sx[jc * DP + q];
                     a = fma(-dlt, dlt, a);
                 }
-                const double e = exp(a);
+                const double e = exp_tab64(a, tab);
 #pragma unroll
                 for (int k = 0; k < CB; ++k) {
                     S[k] = fma(e, sv[jc * CB + k], S[k]);
@@ -908,8 +939,9 @@ static void kv_df_sym(Ctx& h, const double* V, int64_t ldv, int c, const double*
 template <int DP, int CB>
 static void f64_sym_launch1(const double* xs, int64_t n, int nt, double c0, const double* V,
                             int64_t ldv, int ncols, const int4* work, int nwork, int G, int nchunk,
-                            double* prow, double* pcol, cudaStream_t st) {
-    const size_t smem = sizeof(double) * (ST * DP + ST * CB + CB * ST * (SCW + 1) + CB * 4 * SCW);
+                            double* prow, double* pcol, const double* tab64, cudaStream_t st) {
+    const size_t smem =
+        sizeof(double) * (ST * DP + ST * CB + CB * ST * (SCW + 1) + CB * 4 * SCW + NTAB64);
     static bool attr = false;
     if (!attr) {
         KPCG_CUDA(cudaFuncSetAttribute(kv_f64_sym_kernel<DP, CB>,
@@ -917,18 +949,18 @@ static void f64_sym_launch1(const double* xs, int64_t n, int nt, double c0, cons
         attr = true;
     }
     kv_f64_sym_kernel<DP, CB><<<nwork, ST, smem, st>>>(xs, n, nt, c0, V, ldv, ncols, work, G,
-                                                       nchunk, prow, pcol);
+                                                       nchunk, prow, pcol, tab64);
     KPCG_LAUNCHED("kv_f64_sym_kernel");
 }
 
 template <int DP>
 static void f64_sym_launch(int cb, const double* xs, int64_t n, int nt, double c0, const double* V,
                            int64_t ldv, int ncols, const int4* work, int nwork, int G, int nchunk,
-                           double* prow, double* pcol, cudaStream_t st) {
+                           double* prow, double* pcol, const double* tab64, cudaStream_t st) {
     if (cb == 1)
-        f64_sym_launch1<DP, 1>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+        f64_sym_launch1<DP, 1>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, tab64, st);
     else
-        f64_sym_launch1<DP, 2>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, st);
+        f64_sym_launch1<DP, 2>(xs, n, nt, c0, V, ldv, ncols, work, nwork, G, nchunk, prow, pcol, tab64, st);
 }
 
 void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_t ldb,
@@ -948,14 +980,23 @@ void kv_f64_sym(Ctx& h, const double* V, int64_t ldv, int c, const double* B, in
     double* pcol = h.df_pcol.need((size_t)nt * nt * max_cb * ST);
     const int4* work = reinterpret_cast<const int4*>(h.df_work.p);
     const double c0 = h.c0_64();
+    if (!h.f64_tab.p) {
+        std::vector<double> t(NTAB64);
+        for (int j = 0; j < NTAB64; ++j) t[j] = std::exp2((double)j / NTAB64);
+        h.f64_tab.need(NTAB64);
+        KPCG_CUDA(cudaMemcpyAsync(h.f64_tab.p, t.data(), sizeof(double) * NTAB64,
+                                  cudaMemcpyHostToDevice, st));
+        KPCG_CUDA(cudaStreamSynchronize(st));
+    }
+    const double* tab64 = h.f64_tab.p;
     for (int k0 = 0; k0 < c;) {
         const int cb = (c - k0 >= 2) ? 2 : 1;
         const double* Vk = V + (int64_t)k0 * ldv;
         switch (h.dp) {
-            case 4: f64_sym_launch<4>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
-            case 8: f64_sym_launch<8>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
-            case 12: f64_sym_launch<12>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
-            case 16: f64_sym_launch<16>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, st); break;
+            case 4: f64_sym_launch<4>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, tab64, st); break;
+            case 8: f64_sym_launch<8>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, tab64, st); break;
+            case 12: f64_sym_launch<12>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, tab64, st); break;
+            case 16: f64_sym_launch<16>(cb, h.xs64.p, n, nt, c0, Vk, ldv, cb, work, h.df_nwork, G, nchunk, prow, pcol, tab64, st); break;
             default: fail(KPCG_ERR_ARG, "unsupported padded dimension");
         }
         kv_df_sym_reduce_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)cb), 256, 0, st>>>(

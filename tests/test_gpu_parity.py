@@ -81,6 +81,22 @@ def test_matvec_f64_matches_oracle(kpcg, n, d, c):
     assert _rel(out, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("n,d,c,dist", [(1000, 8, 3, "uniform"), (4099, 9, 2, "normal"),
+                                        (600, 4, 1, "normal"), (2048, 16, 2, "uniform")])
+def test_fp64_residual_product_is_fp64_accurate(kpcg, n, d, c, dist):
+    # The product that certifies residuals (impl 0: FP64 differences, sums and
+    # a table-driven FP64 exp within about 1 ulp) agrees with the oracle to
+    # FP64 accuracy, not just the 1e-12 of the double-float products.
+    p = _problem(n, d, seed=5 * n + d, dist=dist)
+    V = synthetic.rng(13).standard_normal((n, c))
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f64(_cm(V)))
+    for k in range(c):
+        assert _rel(out[:, k], ref[:, k]) <= 2e-14, k
+
+
 @pytest.mark.parametrize("impl", [1, 3])
 @pytest.mark.parametrize("n,d,c", [(1, 1, 1), (127, 3, 1), (1000, 8, 3), (4099, 16, 6),
                                    (700, 32, 2), (513, 12, 5), (6000, 8, 1), (2000, 10, 9),
