@@ -966,7 +966,7 @@ DTYPES = {"tc_ir": "bf16x3 exponent, f32 inner, f64 outer (double-float directio
           "fp32_ir": "f32 inner, f64 outer", "xf_ir": "f32 inner (exact differences), f64 outer",
           "tcx_ir": "sliced bf16 exponent, f32 inner, f64 outer",
           "df64": "double-float iterations, fp64 certified residual", "fp64": "f64"}
-KV_NAMES = {"tc_ir": "kv_tc_kernel (tcgen05 exponent, FP32 contraction)",
+KV_NAMES = {"tc_ir": "kv_tcs_kernel (tcgen05 exponent, symmetric tile pairs)",
             "tcx_ir": "kv_tcx_kernel (tcgen05 sliced exponent, compensated contraction)",
             "fp32_ir": "kv_simt_kernel<float>", "xf_ir": "kv_xf_sym_kernel (exact differences)",
             "df64": df_kernel_name(D), "fp64": "kv_f64_sym_kernel (FP64)"}
@@ -1215,7 +1215,8 @@ KV_IMPLS = {"f64": ("f64", 0, "kv_f64_sym_kernel (native FP64)"),
             "tc": ("f32", 1, "kv_tc_kernel (tcgen05, BF16x3 exponent)"),
             "xf": ("f32", 3, "kv_xf_sym_kernel (exact differences)"),
             "tcx": ("f32", 4, "kv_tcx_kernel (tcgen05, sliced per-point-exact exponent)"),
-            "tcv": ("f32", 5, "kv_tcv_kernel (tcgen05 exponent and tcgen05 contraction)")}
+            "tcv": ("f32", 5, "kv_tcv_kernel (tcgen05 exponent and tcgen05 contraction)"),
+            "tcs": ("f32", 6, "kv_tcs_kernel (tcgen05 exponent, symmetric tile pairs)")}
 
 
 def run_kv(args):

@@ -260,7 +260,12 @@ kpcg_status kpcg_matvec_f64(kpcg_t h, const double* V, int64_t ldv, int32_t c, d
  *         exponentiated tile as FP16 (hi, lo) pairs in tensor memory against
  *         V as FP16 pairs scaled per column (~2^-21 relative per product);
  *         the KPCG_TC_IR inner product for blocks of 4 or more columns; d <= 20,
- *         KPCG_ERR_TIMEOUT as impl 1. */
+ *         KPCG_ERR_TIMEOUT as impl 1.
+ * impl 6: the entries of impl 1 on symmetric tile pairs, one column at a
+ *         time: each pair of 128-point tiles evaluated once for its row and
+ *         its mirrored column sums (FP32, partials added in FP64); the
+ *         KPCG_TC_IR inner product for blocks of up to 3 columns (n > 128;
+ *         a single tile uses impl 1); d <= 20, KPCG_ERR_TIMEOUT as impl 1. */
 kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, float* O,
                             int64_t ldo, int32_t impl);
 

@@ -1211,6 +1211,15 @@ kpcg_status kpcg_matvec_f32(kpcg_t h, const float* V, int64_t ldv, int32_t c, fl
             kpcg::kv_tcv_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
             if (kpcg::kv_tc_error(*h))
                 fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
+        } else if (impl == 6) {
+            if (!kpcg::kv_tc_supported(h->d))
+                fail(KPCG_ERR_ARG, "tensor-core K.V supports d <= 20");
+            if (kpcg::kv_tcs_usable(*h))
+                kpcg::kv_tcs_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
+            else  // a single tile has no symmetric pairs
+                kpcg::kv_tc_apply(*h, V, ldv, c, O, ldo, (float)h->noise);
+            if (kpcg::kv_tc_error(*h))
+                fail(KPCG_ERR_TIMEOUT, "a bounded wait in the tensor-core K.V expired");
         } else {
             fail(KPCG_ERR_ARG, "unknown impl");
         }

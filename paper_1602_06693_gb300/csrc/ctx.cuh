@@ -138,6 +138,12 @@ struct Ctx {
     DevBuf<uint16_t> tcvV;
     DevBuf<float> tcvPart;
     DevBuf<int> tcvAux;
+    // the same product on symmetric tile pairs (kv_tcs.cu): work list, CSR of
+    // the items per column tile, staged V, row and column partials
+    int tcs_nitems = 0;
+    int64_t tcs_n = -1;
+    DevBuf<int> tcs_work, tcs_cols;
+    DevBuf<float> tcsV, tcsRow, tcsCol;
     // double-float product with sliced tensor-core distances (kv_tcd.cu)
     int tcd_version = -1;
     DevBuf<uint16_t> tcdA, tcdB;
@@ -228,11 +234,18 @@ void df_prepare(Ctx& h);
 // kv_tcv_apply: below it the FP32-FMA contraction of kv_tc_apply costs less
 // issue per entry than the FP16 split of the tile, above it more.
 constexpr int kTcvMinCols = 4;
+// Tensor-core K.V (the entries of kv_tc_apply) on symmetric tile pairs, one
+// column at a time (kv_tcs.cu); usable for n > 128 and d <= 20.
+void kv_tcs_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
+                  float noise);
+bool kv_tcs_usable(const Ctx& h);
 // The tensor-core inner product of the mixed solvers for c columns.
 inline void kv_tc_inner(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
                         float noise) {
     if (c >= kTcvMinCols && kv_tcv_supported(h.d))
         kv_tcv_apply(h, V, ldv, c, O, ldo, noise);
+    else if (kv_tcs_usable(h))
+        kv_tcs_apply(h, V, ldv, c, O, ldo, noise);
     else
         kv_tc_apply(h, V, ldv, c, O, ldo, noise);
 }

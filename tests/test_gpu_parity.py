@@ -187,6 +187,50 @@ def test_matvec_tensor_core_matches_oracle(kpcg, n, d, c):
         assert _rel(out[:, k], ref[:, k]) <= 2e-5, k
 
 
+@pytest.mark.parametrize("n,d,c,dist", [(129, 3, 1, "normal"), (1000, 8, 3, "normal"),
+                                        (4099, 16, 2, "normal"), (300, 9, 1, "normal"),
+                                        (2000, 20, 1, "normal"), (6000, 8, 1, "uniform"),
+                                        (5000, 10, 2, "normal")])
+def test_matvec_symmetric_tensor_core_matches_oracle(kpcg, n, d, c, dist):
+    # impl 6: the entries of impl 1, each pair of 128-point tiles evaluated
+    # once (row sums, and from the same entries the mirrored column sums,
+    # held in registers over the row tiles of a work item), partials added in
+    # FP64: within 2e-5 of the oracle like impl 1, within 2e-5 of impl 1
+    # itself, and bit-identical when repeated.
+    p = _problem(n, d, seed=17 * n + d, dist=dist)
+    V = synthetic.rng(12).standard_normal((n, c))
+    V[:, 0] *= 1e-3  # columns of different scales
+    ell, s2 = oracle.split_theta(p.log_theta, d, p.ard)
+    ref = oracle.kyv(p.X, ell, s2, p.noise, V)
+    with _solver(kpcg, p) as s:
+        sym = _np(s.matvec_f32(_cm(V, torch.float32), impl=6))
+        again = _np(s.matvec_f32(_cm(V, torch.float32), impl=6))
+        one = _np(s.matvec_f32(_cm(V, torch.float32), impl=1))
+    np.testing.assert_array_equal(sym, again)
+    for k in range(c):
+        if d <= 16:
+            assert _rel(sym[:, k], ref[:, k]) <= 2e-5, k
+        else:
+            # above d = 16 the BF16x3 exponent's own error (shared with impl 1)
+            # nears 2e-5: the symmetric evaluation may add at most half of it
+            e1 = _rel(one[:, k], ref[:, k])
+            assert _rel(sym[:, k], ref[:, k]) <= 1.5 * e1 + 2e-6, (k, e1)
+        assert _rel(sym[:, k], one[:, k]) <= 2e-5, k
+
+
+def test_matvec_symmetric_tensor_core_many_tiles_sampled_rows(kpcg):
+    # n = 65536 (the benchmark's system): work items of up to 128 row tiles
+    # per resident column tile; 64 rows recomputed by the oracle in FP64.
+    p = synthetic.config2(seed=0)
+    V = synthetic.rng(14).standard_normal((p.n, 1))
+    ell, s2 = oracle.split_theta(p.log_theta, p.d, p.ard)
+    rows = np.sort(synthetic.rng(15).choice(p.n, 64, replace=False))
+    ref = oracle.gram(p.X[rows], p.X, ell, s2) @ V + p.noise * V[rows]
+    with _solver(kpcg, p) as s:
+        out = _np(s.matvec_f32(_cm(V, torch.float32), impl=6))
+    assert _rel(out[rows, 0], ref[:, 0]) <= 2e-5
+
+
 @pytest.mark.parametrize("n,d,c", [(16384, 8, 2), (16384, 10, 1), (16384, 10, 2),
                                    (14979, 14, 1), (20000, 12, 4)])
 def test_matvec_tensor_core_many_tiles_per_cta(kpcg, n, d, c):

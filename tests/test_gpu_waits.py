@@ -32,7 +32,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("impl", [1, 4, 5])
+@pytest.mark.parametrize("impl", [1, 4, 5, 6])
 def test_expired_wait_reports_timeout_and_the_handle_recovers(kpcg, impl):
     p = synthetic.make_problem(3000, 8, 5, dist="normal", ell="loguniform", noise=1e-2)
     V = synthetic.rng(3).standard_normal(p.n)
