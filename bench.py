@@ -976,8 +976,8 @@ KV_NAMES = {"tc_ir": "kv_tcs_kernel (tcgen05 exponent, symmetric tile pairs)",
 # since its capture has no entry.
 KNOWN_TRAFFIC = {
     "kv_df_sym_kernel": lambda n: 2291712.0 * n / 16384,
-    "kv_f64_sym_kernel": lambda n: 1287552.0 * n / 16384,
-    "kv_tc_kernel": lambda n: 4278272.0 * n / 16384,
+    "kv_tc_kernel": lambda n: 4284000.0 * n / 16384,
+    "kv_tcds_kernel": lambda n: 21168128.0 * n / 16384,
 }
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at n = 16384, "
                   "scaled by n (inputs only)")
