@@ -1058,8 +1058,14 @@ void kv_tcd(Ctx& h, const double* V, int64_t ldv, int c, const double* B, int64_
     const TcdLayout L = tcd_layout(h.d);
     const int kch = (L.off[DNG] + 63) / 64;
     if (kch < 2 || kch > 6) fail(KPCG_ERR_ARG, "internal: sliced operand layout");
-    // one evaluation per pair of points once there is more than one row tile
-    if (h.tcd_symmetric && n > 128) {
+    // one evaluation per pair of points once there is more than one row tile,
+    // while its column partials (2 n_t (n_t - 1) tile pairs x up to 4 columns
+    // x 32 FP64 values) stay within 4 GiB; beyond that (n above ~185 000 for
+    // four columns, ~370 000 for one) the one-sided kernel evaluates every entry
+    const int64_t n_rt_sym = (n + 127) / 128;
+    const double sym_bytes = 2.0 * (double)n_rt_sym * (double)(n_rt_sym - 1) *
+                             (double)(c >= 4 ? 4 : c >= 2 ? 2 : 1) * STN * 8.0;
+    if (h.tcd_symmetric && n > 128 && sym_bytes <= 4.0 * 1024 * 1024 * 1024) {
         kv_tcd_sym(h, L, kch, V, ldv, c, B, ldb, O, ldo, noise);
         return;
     }

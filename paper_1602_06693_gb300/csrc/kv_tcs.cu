@@ -370,7 +370,14 @@ void tcs_plan(Ctx& h, int64_t n_t) {
 
 }  // namespace
 
-bool kv_tcs_usable(const Ctx& h) { return h.n > TM && kv_tc_supported(h.d); }
+// Usable while its row partials (n_t (n_t + 1) / 2 tile pairs x 2 halves x 128
+// FP32 values) stay within 4 GiB, i.e. up to n ~ 370 000; beyond that the
+// one-sided kernel evaluates every entry.
+bool kv_tcs_usable(const Ctx& h) {
+    const double n_t = (double)((h.n + TM - 1) / TM);
+    const double bytes = n_t * (n_t + 1.0) / 2.0 * 2.0 * TM * 4.0;
+    return h.n > TM && kv_tc_supported(h.d) && bytes <= 4.0 * 1024 * 1024 * 1024;
+}
 
 void kv_tcs_apply(Ctx& h, const float* V, int64_t ldv, int c, float* O, int64_t ldo,
                   float noise) {
