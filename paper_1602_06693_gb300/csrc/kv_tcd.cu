@@ -195,7 +195,6 @@ struct TcdSmem {
     static constexpr uint32_t kVst = CB * DTN * 8;        // V: CB columns of DTN FP32 pairs
     static constexpr uint32_t kStage = ((kBst + kVst + 1023) / 1024) * 1024;
     static constexpr uint32_t kTab = ((NTAB * 8 + 1023) / 1024) * 1024;
-    static constexpr uint32_t kComb = CB * 128 * 8;       // half-sum exchange (FP32 pairs)
     static constexpr uint32_t kBars = 1024;
     static constexpr uint32_t kTotal = 1024 + kA + DNST * kStage + kTab + kBars;
 };
